@@ -1,0 +1,275 @@
+/*
+ * ds.h -- C ABI of the GB300 direct-search library (libds.so).
+ *
+ * Interval lookup by "direct search" (F. Cannizzo, "A Fast and Vectorizable
+ * Alternative to Binary Search in O(1) with Wide Applicability to Arrays of
+ * Floating Point Numbers", arXiv 1506.08620).
+ *
+ * Problem (Section 2, "Formal Problem Statement"): given strictly increasing
+ * knots X_0 < X_1 < ... < X_N and queries z, return for each z the index i
+ * with X_i <= z < X_{i+1}, i.e. the index of the largest knot <= z.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named *_dev are CUDA device pointers (or managed memory); the
+ *    caller owns them and keeps them alive until the stream work that uses
+ *    them has finished.  Pointers named *_host are host pointers (pinned for
+ *    asynchronous copies).  `stream` is a cudaStream_t (NULL = legacy default
+ *    stream).
+ *  - Knots and queries are float32 (DS_F32) or float64 (DS_F64); results are
+ *    int32.  Vector loads are used when Z and I are 16-byte aligned; other
+ *    alignments take a scalar path with the same results.
+ *  - Result domain: for every non-NaN query the result equals the definition
+ *    above extended to the whole line: -1 for z < X_0, N for z >= X_N
+ *    (Section 2 restricts z to [X_0, X_N); the table answers the same way
+ *    outside it).  A NaN query gives -1 with DS_CHECKED and an unspecified
+ *    value in [-1, N] without it.  Every memory access stays in bounds for
+ *    every input.
+ *  - Builds are synchronous (the table size R must be known on the host) and
+ *    return only after the handle is usable; searches are asynchronous,
+ *    stream-ordered and allocate nothing.
+ *  - Errors are returned as ds_status; nothing is thrown across the ABI.
+ *    ds_last_error() gives a message for the calling thread's last failure.
+ *  - A handle may be searched from one stream at a time: entry points that
+ *    use the handle's scratch words (batched and learned searches) race if
+ *    two calls with the same handle overlap on the GPU.
+ */
+#ifndef DS_H
+#define DS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DS_API __attribute__((visibility("default")))
+#else
+#define DS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ds_status {
+    DS_OK = 0,
+    DS_E_ARG = 1,               /* bad argument: null pointer, size < 2, bad dtype/flag */
+    DS_E_NOT_INCREASING = 2,    /* X not strictly increasing or not finite (Section 2) */
+    DS_E_INDISTINGUISHABLE = 3, /* m(X_i - X_0) == m(X_{i-1} - X_0): Eq. distinguishable-exact */
+    DS_E_OVERFLOW = 4,          /* m(H D_N) >= 2^32: Eq. overflowexact with Q = 32 */
+    DS_E_TABLE_TOO_LARGE = 5,   /* (R+1) table entries exceed the byte budget */
+    DS_E_NOMEM = 6,             /* device allocation failed */
+    DS_E_CUDA = 7,              /* a CUDA runtime call failed (see ds_last_error) */
+    DS_E_TIMEOUT = 8,           /* a bounded device wait gave up */
+    DS_E_UNIMPLEMENTED = 9,
+    DS_E_NO_CONVERGENCE = 10,   /* ComputeHR growth did not settle in 64 passes */
+    DS_E_DEVICE = 11            /* a device-side check recorded an error */
+} ds_status;
+
+typedef enum ds_dtype { DS_F32 = 0, DS_F64 = 1 } ds_dtype;
+
+/* build flags */
+enum {
+    DS_FMA = 1u,          /* f(z) = trunc(H z - W), W = H X_0: Section 4.9 "Fused Multiply Add", Eq. fma */
+    DS_CACHE_LAYOUT = 2u, /* table of (K_j, X_{K_j}) pairs: Section 4.8, Algorithm directcache */
+    DS_CHECKED = 4u,      /* NaN queries return -1 */
+    DS_NO_SMEM = 8u,      /* never stage the table in shared memory (keep it L2/HBM resident) */
+    DS_STRICT = 16u       /* batched builds: an infeasible array is an error instead of a fallback */
+};
+
+typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
+typedef struct ds_batch ds_batch;     /* many independent knot arrays (CSR) */
+typedef struct ds_learned ds_learned; /* learned-index form (one or many arrays) */
+
+/* Summary of a handle.  Fields that do not apply are 0. */
+typedef struct ds_info_t {
+    int32_t kind;           /* 1 = ds_index, 2 = ds_batch, 3 = ds_learned */
+    int32_t dtype;          /* ds_dtype */
+    uint32_t flags;
+    int32_t n_arrays;
+    int64_t n_knots;        /* total knots over all arrays */
+    double H;               /* single array: grid density H (Section 4.2) */
+    double W;               /* single array, DS_FMA: W = m(H X_0) (Eq. fma) */
+    double X0, XN;          /* single array: first and last knot */
+    uint64_t R;             /* single array: largest cell index; sum of R+1 over arrays otherwise */
+    int64_t table_bytes;    /* device bytes of tables, knots copies and models */
+    int64_t h_updates;      /* ComputeHR growth steps (all arrays) */
+    int64_t hr_passes;      /* ComputeHR passes (single array) */
+    double build_ms;        /* wall time of the build call */
+    int32_t smem_resident;  /* single array: 1 if searches stage the table in shared memory */
+    int32_t n_direct;       /* arrays served by direct search */
+    int32_t n_learned;      /* arrays served by the learned predictor */
+    int32_t n_fallback;     /* arrays served by the fixed-depth bisection (Algorithm binaryopt) */
+    int64_t max_window;     /* learned: largest bounded window (e_lo + e_hi + 3) over arrays */
+    int64_t train_steps;    /* learned: Adam steps run per model */
+    double train_ms;        /* learned: time spent training */
+    double final_loss;      /* learned: mean final training loss */
+    uint64_t fallback_queries; /* learned: queries whose window certificate failed (since the build) */
+    int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error */
+    int32_t reserved_;
+} ds_info_t;
+
+/* ------------------------------------------------------------------------
+ * Single array.
+ * ------------------------------------------------------------------------ */
+
+/* Build the direct-search table of one knot array (Section 4): validate X,
+ * compute H and R with ComputeHR (Section 4.4, algorithm "Computation of H and
+ * R"), fill K by Eq. indexdef, optionally pack (K_j, X_{K_j}) pairs
+ * (Section 4.8).
+ *   X_dev    n_knots = N+1 strictly increasing finite values of `dtype`; read
+ *            once and copied (the handle does not keep the pointer).
+ *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM.
+ *   out      receives the handle (NULL on failure); release with ds_free.
+ * Errors: DS_E_ARG, DS_E_NOT_INCREASING, DS_E_INDISTINGUISHABLE (Section 4.4
+ * first counter-example), DS_E_OVERFLOW (second counter-example, Eq.
+ * overflowexact), DS_E_NO_CONVERGENCE, DS_E_TABLE_TOO_LARGE (budget: half of
+ * the free device memory, or the DS_TABLE_BUDGET_BYTES environment variable),
+ * DS_E_NOMEM, DS_E_CUDA.  Synchronous: returns after the table is built. */
+DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, void *stream,
+                   ds_index **out);
+
+/* Search m queries (Algorithm direct, Section 4.3): j = min(f(z), R),
+ * t = K_j, I = t - [z < X_t].
+ *   Z_dev  m queries of the index's dtype; I_dev  m int32 results.
+ * m == 0 is a no-op.  Asynchronous on `stream`; allocates nothing; safe to
+ * capture in a CUDA graph. */
+DS_API ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, int32_t *I_dev, void *stream);
+
+/* The same search with HOST buffers: copies queries in and results out in
+ * pipelined chunks (host->device, search, device->host on separate streams).
+ * Z_host / I_host should be pinned; the call returns when the last result has
+ * been written to I_host.  Allocates its device staging buffers on the first
+ * call and keeps them in the handle. */
+DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *I_host, void *stream);
+
+/* Read-only device views of the index's tables (for inspection and tests):
+ * K (R+1 int32, Eq. indexdef), the library's copy of X (N+1 values), and,
+ * with DS_CACHE_LAYOUT, the (R+1) pairs (8 bytes for float32: int32 K_j then
+ * float X_{K_j}; 16 bytes for float64: int32 K_j, 4 bytes of padding, double
+ * X_{K_j}).  Any output pointer may be NULL. */
+DS_API ds_status ds_index_tables(const ds_index *idx, const int32_t **K_dev, const void **X_dev,
+                          const void **pairs_dev);
+
+/* Copy the same tables into caller-owned device buffers (each may be NULL):
+ * K_out (R+1 int32), X_out (N+1 values), pairs_out ((R+1) pairs, only with
+ * DS_CACHE_LAYOUT).  Asynchronous on `stream`. */
+DS_API ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, void *X_out_dev, void *pairs_out_dev,
+                                 void *stream);
+
+/* ------------------------------------------------------------------------
+ * Many independent arrays ("vectorial problem" of Section 2, batched).
+ * ------------------------------------------------------------------------ */
+
+/* Build one direct-search table per array.  Array a owns the knots
+ * Xcat_dev[x_off[a] .. x_off[a+1]-1] (device CSR offsets, n_arrays+1 int64,
+ * x_off[0] = 0, at least 2 knots per array).  Each array is validated and
+ * gets its own H, R and K exactly as ds_build would compute them.  An array
+ * on which direct search is infeasible is served by the fixed-depth bisection
+ * of Algorithm binaryopt (the log-time fall-back the Conclusion names) unless
+ * DS_STRICT is set, in which case the build fails with that array's status.
+ * Synchronous. */
+DS_API ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, ds_dtype dtype,
+                         uint32_t flags, void *stream, ds_batch **out);
+
+/* Search every array's queries in one persistent launch: queries of array a
+ * are Zcat_dev[z_off[a] .. z_off[a+1]-1] (device CSR, n_arrays+1 int64), their
+ * results (local indices into array a) go to the same positions of Icat_dev.
+ * Asynchronous, allocation-free and capturable; uses the handle's scratch. */
+DS_API ds_status ds_batch_search(const ds_batch *b, const void *Zcat_dev, const int64_t *z_off_dev, int32_t *Icat_dev,
+                          void *stream);
+
+/* Launch parameters of the batched search. */
+typedef struct ds_tune_t {
+    int32_t block;       /* threads per block (multiple of 32) */
+    int32_t items;       /* queries per thread per tile */
+    int32_t smem_limit;  /* largest per-array table (bytes) staged in shared memory; 0 = never */
+    int32_t blocks_per_sm;
+    float ms;            /* measured time of the chosen configuration (autotune output) */
+} ds_tune_t;
+
+/* Time a fixed set of launch configurations on the given queries (each run
+ * several times with CUDA events on `stream`), keep the fastest in the handle
+ * and return it in *best.  The outputs are overwritten with valid results.
+ * Synchronous. */
+DS_API ds_status ds_batch_autotune(ds_batch *b, const void *Zcat_dev, const int64_t *z_off_dev, int32_t *Icat_dev,
+                            void *stream, ds_tune_t *best);
+DS_API ds_status ds_batch_set_tune(ds_batch *b, const ds_tune_t *cfg);
+DS_API ds_status ds_batch_get_tune(const ds_batch *b, ds_tune_t *cfg);
+
+/* Per-array parameters (host copies) for inspection: H, W (as double), R and
+ * the mode (0 = direct, 2 = bisection fall-back) of array a. */
+DS_API ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double *W, uint64_t *R, int32_t *mode);
+
+/* ------------------------------------------------------------------------
+ * Learned index (not in the paper): a 1 -> 32 -> 32 -> 1 ReLU network
+ * predicting the index from u = (z - X_0) / (X_N - X_0), trained on the GPU by
+ * this library's own forward/backward/Adam kernels on the pairs (X_i, i) and
+ * on exact answers of sampled queries; the largest prediction error over all
+ * knots is recorded at build time and each query is answered exactly by a
+ * fixed-depth bisection (Algorithm binaryopt) inside the bounded window around
+ * the prediction, certified by X_lo <= z < X_{hi+1}; a failed certificate
+ * falls back to the array's exact full search.  Arrays on which direct search
+ * is feasible use it instead (unless DS_LEARNED_FORCE).
+ * ------------------------------------------------------------------------ */
+enum {
+    DS_LEARNED_FORCE = 1u,    /* use the learned predictor even where direct search is feasible */
+    DS_LEARNED_LINEAR = 2u    /* no network: predict N u (the model "without it", for comparison) */
+};
+
+typedef struct ds_learned_cfg {
+    int32_t steps;       /* Adam steps per model (0 = untrained initial network) */
+    int32_t batch;       /* samples per step */
+    int32_t n_queries;   /* exact-answer query samples per model, in addition to the knots */
+    float lr;            /* Adam step size */
+    uint64_t seed;       /* Philox-4x32-10 key for initialisation and sampling */
+    uint32_t flags;      /* DS_LEARNED_* */
+    int32_t reserved[5];
+} ds_learned_cfg;
+
+DS_API void ds_learned_cfg_default(ds_learned_cfg *cfg);
+
+/* Build the learned form.  Single array: x_off_dev = NULL, n_arrays = 1 and
+ * n_knots_if_single = N+1.  Batched: device CSR offsets as in ds_batch_build.
+ * Synchronous. */
+DS_API ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays,
+                           int64_t n_knots_if_single, ds_dtype dtype, const ds_learned_cfg *cfg, void *stream,
+                           ds_learned **out);
+
+/* Search: single array: z_off_dev = NULL and m queries; batched: device CSR
+ * z_off_dev (m ignored).  With Ycat_dev and y_out_dev both non-NULL the
+ * linear interpolant y = Y_i + (Y_{i+1} - Y_i) (z - X_i) / (X_{i+1} - X_i) of
+ * knot values Y (same dtype and CSR layout as X) is written for every query
+ * whose index lies in [0, N-1] (the use case of the Introduction); other
+ * queries get NaN.  Asynchronous, allocation-free. */
+DS_API ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
+                            const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream);
+
+/* Host copy of array a's network parameters (1153 floats: W1[32] b1[32]
+ * W2[32][32] b2[32] w3[32] b3) and its recorded error bounds: every knot i
+ * satisfies floor(p(X_i)) - e_lo <= i <= floor(p(X_i)) + e_hi.  mode: 0 direct,
+ * 1 learned, 2 bisection. */
+DS_API ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, int32_t *e_lo, int32_t *e_hi,
+                           int32_t *mode);
+
+/* The training kernels on explicit inputs (used to check gradients):
+ * forward output of the network for n inputs u; mean squared error over n
+ * samples against targets y and its gradient (1153 floats); one Adam step
+ * (t is 1-based) on 1153 parameters in place. */
+DS_API ds_status ds_mlp_forward(const float *theta_dev, const float *u_dev, int64_t n, float *out_dev, void *stream);
+DS_API ds_status ds_mlp_loss_grad(const float *theta_dev, const float *u_dev, const float *y_dev, int64_t n,
+                           float *grad_dev, float *loss_dev, void *stream);
+DS_API ds_status ds_adam_step(float *theta_dev, float *m_dev, float *v_dev, const float *grad_dev, int32_t t, float lr,
+                       void *stream);
+
+/* ------------------------------------------------------------------------
+ * Handles and diagnostics.
+ * ------------------------------------------------------------------------ */
+DS_API ds_status ds_info(const void *handle, ds_info_t *out); /* any handle */
+DS_API void ds_free(void *handle);                            /* any handle; NULL is a no-op */
+DS_API const char *ds_status_str(ds_status s);
+DS_API const char *ds_last_error(void);
+DS_API int32_t ds_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DS_H */

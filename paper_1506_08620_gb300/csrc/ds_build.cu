@@ -1,0 +1,284 @@
+// ds_build.cu -- single-array build (Section 4: ComputeHR, Eq. indexdef,
+// Section 4.8 pairs) and the single-array search entry.
+#include <cstdlib>
+#include <cstring>
+
+#include "ds_index.cuh"
+
+namespace ds {
+
+__global__ void k_hr_state_init(HRState *st, int count)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= count) return;
+    HRState s;
+    memset(&s, 0, sizeof(s));
+    s.first_violation = NONE64;
+    s.bad_nonfinite = NONE64;
+    s.bad_order = NONE64;
+    s.bad_indist = NONE64;
+    s.min_gap_bits = NONE64;
+    st[a] = s;
+}
+
+static int grid_for(const DeviceProps &p, long long work, int block)
+{
+    long long want = (work + block - 1) / block;
+    long long cap = (long long)p.num_sms * 8;
+    if (want > cap) want = cap;
+    return want < 1 ? 1 : (int)want;
+}
+
+static uint32_t smem_limit_bytes(const DeviceProps &p)
+{
+    long long lim = 96 * 1024;
+    if (const char *e = getenv("DS_SMEM_LIMIT")) lim = atoll(e);
+    long long cap = (long long)p.max_smem_optin - 1024;  // room for the static barrier
+    if (lim > cap) lim = cap;
+    return lim < 0 ? 0u : (uint32_t)lim;
+}
+
+static bool f64_intops_default()
+{
+    if (const char *e = getenv("DS_F64_INTOPS")) return atoi(e) != 0;
+    return true;
+}
+
+// ComputeHR on the device, driven from the host: validation, start, then
+// rounds of (pair scan, growth step) until done.  Writes the final state to
+// *host_st.  `st` is device scratch for one HRState.
+template <typename T, bool FMA>
+static ds_status run_compute_hr(const T *X, long long n_knots, HRState *st, HRState *host_st, cudaStream_t s,
+                                const DeviceProps &props)
+{
+    const int block = 256;
+    const int grid = grid_for(props, n_knots, block);
+    k_hr_state_init<<<1, 1, 0, s>>>(st, 1);
+    k_validate<T><<<grid, block, 0, s>>>(X, n_knots, st);
+    k_hr_init<T, FMA><<<1, 1, 0, s>>>(X, n_knots, st);
+    DS_TRY_CUDA(cudaGetLastError());
+    for (long long round = 0;; ++round) {
+        for (int k = 0; k < 3; ++k) {
+            k_hr_check<T, FMA><<<grid, block, 0, s>>>(X, n_knots, st);
+            k_hr_grow<T, FMA><<<1, 1, 0, s>>>(X, n_knots, st);
+        }
+        DS_TRY_CUDA(cudaGetLastError());
+        DS_TRY_CUDA(cudaMemcpyAsync(host_st, st, sizeof(HRState), cudaMemcpyDeviceToHost, s));
+        DS_TRY_CUDA(cudaStreamSynchronize(s));
+        if (host_st->done) break;
+        if (round > 1000000) {
+            set_error("ComputeHR did not finish");
+            return DS_E_NO_CONVERGENCE;
+        }
+    }
+    return DS_OK;
+}
+
+static const char *hr_message(int status)
+{
+    switch (status) {
+    case DS_E_NOT_INCREASING: return "knots are not strictly increasing finite values";
+    case DS_E_INDISTINGUISHABLE: return "m(X_i - X_0) == m(X_{i-1} - X_0): direct search infeasible";
+    case DS_E_OVERFLOW: return "m(H (X_N - X_0)) >= 2^32: direct search infeasible (Q = 32)";
+    case DS_E_NO_CONVERGENCE: return "growth of H did not settle";
+    default: return "";
+    }
+}
+
+template <typename T, bool FMA>
+static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, cudaStream_t s, ds_index *idx)
+{
+    const DeviceProps &props = idx->props;
+    HRState *st = nullptr;
+    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
+    HRState hs;
+    ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props);
+    cudaFree(st);
+    if (rc != DS_OK) return rc;
+    idx->updates = hs.updates;
+    idx->passes = hs.passes;
+    idx->H = hs.H;
+    idx->W = hs.W;
+    if (hs.status != DS_OK) {
+        set_error("ds_build: %s (knot %lld)", hr_message(hs.status),
+                  (long long)(hs.status == DS_E_NOT_INCREASING
+                                  ? (hs.bad_nonfinite != NONE64 ? hs.bad_nonfinite : hs.bad_order)
+                                  : hs.bad_indist));
+        return (ds_status)hs.status;
+    }
+    const unsigned long long R = hs.R;
+    idx->R = R;
+    idx->k_bytes = round_up((size_t)(R + 1) * sizeof(int32_t), 16);
+    idx->x_bytes = round_up((size_t)n_knots * sizeof(T), 16);
+    const bool cache = (flags & DS_CACHE_LAYOUT) != 0;
+    idx->pair_bytes = cache ? round_up((size_t)(R + 1) * sizeof(Pair<T>), 16) : 0;
+    idx->table_bytes = idx->k_bytes + idx->x_bytes + idx->pair_bytes;
+    const size_t budget = table_budget_bytes();
+    if (idx->table_bytes > budget) {
+        set_error("ds_build: table needs %zu bytes, budget is %zu (R = %llu)", idx->table_bytes, budget, R);
+        return DS_E_TABLE_TOO_LARGE;
+    }
+    DS_TRY_CUDA(cudaMalloc(&idx->tab, idx->k_bytes + idx->x_bytes));
+    DS_TRY_CUDA(cudaMemsetAsync(idx->tab, 0, idx->k_bytes + idx->x_bytes, s));
+    T *Xc = reinterpret_cast<T *>(idx->tab + idx->k_bytes);
+    int32_t *K = reinterpret_cast<int32_t *>(idx->tab);
+    DS_TRY_CUDA(cudaMemcpyAsync(Xc, X_user, (size_t)n_knots * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (cache) DS_TRY_CUDA(cudaMalloc(&idx->pairs, idx->pair_bytes));
+    uint32_t *F = nullptr;
+    DS_TRY_CUDA(cudaMalloc(&F, (size_t)n_knots * sizeof(uint32_t)));
+    const int block = 256;
+    k_fill_F<T, FMA><<<grid_for(props, n_knots, block), block, 0, s>>>(Xc, n_knots, (T)hs.H, (T)hs.W, F);
+    long long warps_work = (n_knots + 31) / 32 * 32;
+    k_fill_K<T><<<grid_for(props, warps_work, block), block, 0, s>>>(
+        F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t se = cudaStreamSynchronize(s);
+    cudaFree(F);
+    if (le != cudaSuccess || se != cudaSuccess) {
+        set_error("ds_build: table fill failed: %s", cudaGetErrorString(le != cudaSuccess ? le : se));
+        return DS_E_CUDA;
+    }
+    // search plan
+    SearchPlan &plan = idx->plan;
+    plan.fma = FMA;
+    plan.cache = cache;
+    plan.intops = sizeof(T) == 8 && f64_intops_default();
+    plan.block = SEARCH_BLOCK;
+    plan.vpt = SEARCH_VPT;
+    const size_t image = cache ? idx->pair_bytes : idx->k_bytes + idx->x_bytes;
+    plan.smem = !(flags & DS_NO_SMEM) && image <= smem_limit_bytes(props);
+    idx->smem_bytes = plan.smem ? (uint32_t)image : 0;
+    DS_TRY(prepare_search<T>(&plan, idx->smem_bytes, props.num_sms));
+    return DS_OK;
+}
+
+ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, cudaStream_t s,
+                       ds_index **out)
+{
+    const double t0 = now_ms();
+    ds_index *idx = new ds_index;
+    memset(idx, 0, sizeof(*idx));
+    idx->hdr.kind = KIND_INDEX;
+    idx->hdr.magic = HANDLE_MAGIC;
+    idx->dtype = dtype;
+    idx->flags = flags;
+    idx->n_knots = n_knots;
+    ds_status rc = device_props(&idx->props);
+    if (rc == DS_OK) {
+        cudaError_t e = cudaMalloc(&idx->dev_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(idx->dev_err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            set_error("ds_build: %s", cudaGetErrorString(e));
+            rc = DS_E_CUDA;
+        }
+    }
+    if (rc == DS_OK) {
+        const bool fma = (flags & DS_FMA) != 0;
+        if (dtype == DS_F32) {
+            rc = fma ? build_typed<float, true>((const float *)X_dev, n_knots, flags, s, idx)
+                     : build_typed<float, false>((const float *)X_dev, n_knots, flags, s, idx);
+        } else {
+            rc = fma ? build_typed<double, true>((const double *)X_dev, n_knots, flags, s, idx)
+                     : build_typed<double, false>((const double *)X_dev, n_knots, flags, s, idx);
+        }
+    }
+    if (rc != DS_OK) {
+        free_index(idx);
+        return rc;
+    }
+    // first and last knot on the host
+    if (dtype == DS_F32) {
+        float e2[2];
+        cudaMemcpy(&e2[0], idx->tab + idx->k_bytes, sizeof(float), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&e2[1], idx->tab + idx->k_bytes + (n_knots - 1) * sizeof(float), sizeof(float),
+                   cudaMemcpyDeviceToHost);
+        idx->X0 = e2[0];
+        idx->XN = e2[1];
+    } else {
+        double e2[2];
+        cudaMemcpy(&e2[0], idx->tab + idx->k_bytes, sizeof(double), cudaMemcpyDeviceToHost);
+        cudaMemcpy(&e2[1], idx->tab + idx->k_bytes + (n_knots - 1) * sizeof(double), sizeof(double),
+                   cudaMemcpyDeviceToHost);
+        idx->X0 = e2[0];
+        idx->XN = e2[1];
+    }
+    idx->x0zero = idx->X0 == 0.0;
+    idx->build_ms = now_ms() - t0;
+    *out = idx;
+    return DS_OK;
+}
+
+template <typename T>
+static ds_status search_typed(const ds_index *idx, const void *Z, long long m, int32_t *I, cudaStream_t s)
+{
+    SearchArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.K = reinterpret_cast<const int32_t *>(idx->tab);
+    a.X = reinterpret_cast<const T *>(idx->tab + idx->k_bytes);
+    a.P = reinterpret_cast<const Pair<T> *>(idx->pairs);
+    a.smem_src = idx->plan.cache ? idx->pairs : (const void *)idx->tab;
+    a.smem_bytes = idx->smem_bytes;
+    a.x_smem_off = (uint32_t)idx->k_bytes;
+    a.H = (T)idx->H;
+    a.W = (T)idx->W;
+    a.X0 = (T)idx->X0;
+    a.R = (uint32_t)idx->R;
+    a.x0zero = idx->x0zero;
+    a.checked = (idx->flags & DS_CHECKED) != 0;
+    a.Z = reinterpret_cast<const T *>(Z);
+    a.I = I;
+    a.m = m;
+    a.err = idx->dev_err;
+    return launch_search<T>(a, idx->plan, s);
+}
+
+ds_status search_index(const ds_index *idx, const void *Z, long long m, int32_t *I, cudaStream_t s)
+{
+    if (m == 0) return DS_OK;
+    if (!Z || !I || m < 0) {
+        set_error("ds_search: null pointer or negative size");
+        return DS_E_ARG;
+    }
+    return idx->dtype == DS_F32 ? search_typed<float>(idx, Z, m, I, s) : search_typed<double>(idx, Z, m, I, s);
+}
+
+}  // namespace ds
+
+extern "C" ds_status ds_index_tables(const ds_index *idx, const int32_t **K_dev, const void **X_dev,
+                                     const void **pairs_dev)
+{
+    if (!idx || idx->hdr.kind != ds::KIND_INDEX) {
+        ds::set_error("ds_index_tables: not an index handle");
+        return DS_E_ARG;
+    }
+    if (K_dev) *K_dev = reinterpret_cast<const int32_t *>(idx->tab);
+    if (X_dev) *X_dev = idx->tab + idx->k_bytes;
+    if (pairs_dev) *pairs_dev = idx->pairs;
+    return DS_OK;
+}
+
+extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, void *X_out_dev, void *pairs_out_dev,
+                                     void *stream)
+{
+    if (!idx || idx->hdr.kind != ds::KIND_INDEX || idx->hdr.magic != ds::HANDLE_MAGIC) {
+        ds::set_error("ds_index_export: not an index handle");
+        return DS_E_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t esz = idx->dtype == DS_F32 ? 4 : 8;
+    if (K_out_dev)
+        DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)(idx->R + 1) * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s));
+    if (X_out_dev)
+        DS_TRY_CUDA(cudaMemcpyAsync(X_out_dev, idx->tab + idx->k_bytes, (size_t)idx->n_knots * esz,
+                                    cudaMemcpyDeviceToDevice, s));
+    if (pairs_out_dev) {
+        if (!idx->pairs) {
+            ds::set_error("ds_index_export: the index has no pair table (built without DS_CACHE_LAYOUT)");
+            return DS_E_ARG;
+        }
+        DS_TRY_CUDA(cudaMemcpyAsync(pairs_out_dev, idx->pairs, (size_t)(idx->R + 1) * (esz == 4 ? 8 : 16),
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    return DS_OK;
+}

@@ -1,0 +1,226 @@
+// ds_common.cuh -- internal definitions shared by the libds translation units.
+//
+// Floating-point discipline: every step of the map f (Eq. function, Eq. fma)
+// is written with explicit round-to-nearest intrinsics (__fmul_rn, __fsub_rn,
+// __fmaf_rn, __dmul_rn, ...), which the compiler never contracts or
+// reassociates, so the table built on the device and the lookups that read it
+// evaluate exactly the same rounded expression (Section 4.4: "all phases of the
+// algorithm ... consistently use the function").
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "ds.h"
+
+namespace ds {
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define DS_TRY_CUDA(call)                                                                       \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            ::ds::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,   \
+                            __LINE__);                                                          \
+            return e_ == cudaErrorMemoryAllocation ? DS_E_NOMEM : DS_E_CUDA;                    \
+        }                                                                                       \
+    } while (0)
+
+#define DS_TRY(expr)                          \
+    do {                                      \
+        ds_status s_ = (expr);                \
+        if (s_ != DS_OK) return s_;           \
+    } while (0)
+
+// ------------------------------------------------------------------ handles
+enum Kind : int32_t { KIND_INDEX = 1, KIND_BATCH = 2, KIND_LEARNED = 3 };
+constexpr int32_t HANDLE_MAGIC = 0x0D5E5C;
+
+struct HandleHeader {
+    int32_t kind;
+    int32_t magic;
+};
+
+// Status words written by device code (bounded waits, bounds checks).
+enum DeviceErr : int32_t { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
+
+// Device-resident state of ComputeHR (one per array).  H, W, P are kept in
+// the array's precision; they are stored in double slots, which hold float
+// values exactly.
+struct HRState {
+    double H, W, P;
+    unsigned long long R;
+    long long updates, passes, cursor;
+    int status, done, grew, pad_;
+    unsigned long long first_violation;  // atomicMin target of the pair scan
+    unsigned long long bad_nonfinite;    // first knot that is NaN/Inf
+    unsigned long long bad_order;        // first i with !(X_{i-1} < X_i)
+    unsigned long long bad_indist;       // first i with D_{i-1} == D_i
+    unsigned long long min_gap_bits;     // min m(D_i - D_{i-1}) as bits (positive floats order like uints)
+};
+constexpr unsigned long long NONE64 = ~0ull;
+constexpr int MAX_HR_PASSES = 64;
+
+// ------------------------------------------------------------------ arithmetic
+template <typename T> struct Arith;
+
+template <> struct Arith<float> {
+    using Bits = uint32_t;
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    // cvt.rzi.u32.f32: toward zero, negatives and NaN -> 0, saturates at 2^32-1
+    static __device__ __forceinline__ uint32_t trunc_u32(float v) { return __float2uint_rz(v); }
+    static __device__ __forceinline__ Bits bits(float v) { return __float_as_uint(v); }
+    static __device__ __forceinline__ float from_bits(Bits b) { return __uint_as_float(b); }
+};
+
+template <> struct Arith<double> {
+    using Bits = unsigned long long;
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+    static __device__ __forceinline__ uint32_t trunc_u32(double v) { return __double2uint_rz(v); }
+    static __device__ __forceinline__ Bits bits(double v) { return (Bits)__double_as_longlong(v); }
+    static __device__ __forceinline__ double from_bits(Bits b) { return __longlong_as_double((long long)b); }
+};
+
+// phi(x) of Section 4.4: the smallest float greater than x, for x >= 0
+// (positive finite floats are ordered like their bit patterns; +inf stays).
+template <typename T> __device__ __forceinline__ T next_up(T x)
+{
+    using A = Arith<T>;
+    if (!(x < T(INFINITY))) return x;
+    return A::from_bits(A::bits(x) + 1);
+}
+
+// trunc to 32 bits from the IEEE-754 bit pattern of a double, with the
+// semantics of cvt.rzi.u32.f64 (toward zero; negative, zero and NaN -> 0;
+// >= 2^32 -> 2^32-1), using integer instructions only.
+__device__ __forceinline__ uint32_t trunc_u32_bits(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if ((long long)b < 0 || e < 0) return 0u;
+    if (e >= 32) return (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull ? 0u : 0xFFFFFFFFu;
+    const unsigned long long mant = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    return (uint32_t)(mant >> (52 - e));
+}
+
+// Signed integer key ordering doubles like their values (+0 and -0 equal);
+// for non-NaN a, b:  a < b  <=>  okey(a) < okey(b).
+__device__ __forceinline__ long long okey(double v)
+{
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll);
+}
+
+// The map f: plain form trunc(m(H m(z - X0))) (Eq. function) or FMA form
+// trunc(m(H z - W)) (Eq. fma).  Returns the value before truncation.
+template <typename T, bool FMA>
+__device__ __forceinline__ T fval(T H, T W, T X0, T z)
+{
+    using A = Arith<T>;
+    if constexpr (FMA) return A::fma(H, z, -W);
+    else return A::mul(H, A::sub(z, X0));
+}
+
+template <typename T> struct Pair;
+template <> struct __align__(8) Pair<float> { int32_t k; float x; };
+template <> struct __align__(16) Pair<double> { int32_t k; int32_t pad; double x; };
+
+// ------------------------------------------------------------------ async copies
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy completed on an mbarrier (TMA, non-tensor form).
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after `limit` polls (each poll may suspend the
+// thread for a hardware-defined time), returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;
+constexpr uint32_t BULK_CHUNK = 32768;  // bytes per cp.async.bulk
+
+// Stage `bytes` (multiple of 16) from global to shared memory with bulk
+// copies issued by one thread; every thread of the block waits.  Returns false
+// (and records DEVERR_TIMEOUT in *err) if the copy did not complete in time.
+__device__ __forceinline__ bool stage_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                              int *err)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += BULK_CHUNK) {
+            const uint32_t n = bytes - off < BULK_CHUNK ? bytes - off : BULK_CHUNK;
+            bulk_g2s((char *)dst + off, (const char *)src + off, n, bar);
+        }
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLL_LIMIT);
+    if (!ok && err) atomicExch(err, (int)DEVERR_TIMEOUT);
+    return __syncthreads_and(ok) != 0;
+}
+
+// ------------------------------------------------------------------ host helpers
+struct DeviceProps {
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    int l2_bytes = 0;
+};
+ds_status device_props(DeviceProps *p);
+double now_ms();
+size_t table_budget_bytes();
+size_t round_up(size_t v, size_t a);
+
+}  // namespace ds

@@ -1,0 +1,209 @@
+// ds_search.cuh -- the direct-search lookup kernels (Algorithm direct,
+// Algorithm directcache, Eq. fma).
+//
+// One thread answers VPT vectors of queries per tile (4 floats or 2 doubles
+// per vector); queries are streamed with evict-first vector loads, results
+// with evict-first vector stores.  The table (K and X, or the (K_j, X_{K_j})
+// pairs) is either read through the read-only path from global memory, where
+// it stays L2-resident, or staged once per block into shared memory with a
+// bulk asynchronous copy when it fits.  Blocks are persistent: the grid is one
+// wave of resident blocks and each block walks tiles with a grid stride.
+#pragma once
+
+#include "ds_common.cuh"
+
+namespace ds {
+
+template <typename T> struct SearchArgs {
+    const int32_t *K;     // R+1 cells (Eq. indexdef)
+    const T *X;           // N+1 knots
+    const Pair<T> *P;     // R+1 (K_j, X_{K_j}) pairs (cache layout)
+    const void *smem_src; // contiguous image staged to shared memory
+    uint32_t smem_bytes;  // bytes of the image (multiple of 16)
+    uint32_t x_smem_off;  // byte offset of X inside the image
+    T H, W, X0;
+    uint32_t R;
+    int x0zero;           // X_0 == 0: z - X_0 == z exactly, the subtraction is skipped
+    int checked;          // NaN -> -1
+    const T *Z;
+    int32_t *I;
+    long long m;
+    int *err;
+};
+
+template <typename T> struct VecOf;
+template <> struct VecOf<float> { using V = float4; using IV = int4; static constexpr int L = 4; };
+template <> struct VecOf<double> { using V = double2; using IV = int2; static constexpr int L = 2; };
+
+// Cell of a query: j = min(f(z), R) (Eq. function / Eq. fma).
+template <typename T, bool FMA, bool INTOPS>
+__device__ __forceinline__ uint32_t cell_of(T z, const SearchArgs<T> &a)
+{
+    using A = Arith<T>;
+    T v;
+    if constexpr (FMA) {
+        v = A::fma(a.H, z, -a.W);
+    } else {
+        v = A::mul(a.H, a.x0zero ? z : A::sub(z, a.X0));
+    }
+    uint32_t j;
+    if constexpr (INTOPS && sizeof(T) == 8) j = trunc_u32_bits((double)v);
+    else j = A::trunc_u32(v);
+    return min(j, a.R);
+}
+
+// Gather of the table entry of cell j: t = K_j and x = X_t (two dependent
+// reads), or the pair (K_j, X_{K_j}) in one read (cache layout).
+template <typename T, bool CACHE, bool SMEM>
+__device__ __forceinline__ int32_t gather_k(uint32_t j, const int32_t *K, const Pair<T> *P, T *x_out)
+{
+    if constexpr (CACHE) {
+        if constexpr (SMEM) {
+            const Pair<T> p = P[j];
+            *x_out = p.x;
+            return p.k;
+        } else if constexpr (sizeof(T) == 4) {
+            const int2 p = __ldg(reinterpret_cast<const int2 *>(P) + j);
+            *x_out = __int_as_float(p.y);
+            return p.x;
+        } else {
+            const longlong2 p = __ldg(reinterpret_cast<const longlong2 *>(P) + j);
+            *x_out = __longlong_as_double(p.y);
+            return (int32_t)(p.x & 0xFFFFFFFFll);
+        }
+    } else {
+        if constexpr (SMEM) return K[j];
+        else return __ldg(K + j);
+    }
+}
+
+template <typename T, bool SMEM>
+__device__ __forceinline__ T gather_x(int32_t t, const T *X)
+{
+    if constexpr (SMEM) return X[t];
+    else return __ldg(X + t);
+}
+
+// Correction step: i = t - [z < X_t]; NaN -> -1 when checked.
+template <typename T, bool INTOPS>
+__device__ __forceinline__ int32_t correct(T z, int32_t t, T x, int checked)
+{
+    bool lt;
+    if constexpr (INTOPS && sizeof(T) == 8) lt = okey((double)z) < okey((double)x);
+    else lt = z < x;
+    int32_t i = t - (int32_t)lt;
+    if (checked && !(z == z)) i = -1;
+    return i;
+}
+
+template <typename T, bool FMA, bool CACHE, bool SMEM, bool INTOPS>
+__device__ __forceinline__ int32_t lookup(T z, const int32_t *K, const T *X, const Pair<T> *P,
+                                          const SearchArgs<T> &a)
+{
+    const uint32_t j = cell_of<T, FMA, INTOPS>(z, a);
+    T x;
+    const int32_t t = gather_k<T, CACHE, SMEM>(j, K, P, &x);
+    if constexpr (!CACHE) x = gather_x<T, SMEM>(t, X);
+    return correct<T, INTOPS>(z, t, x, a.checked);
+}
+
+template <typename T, bool FMA, bool CACHE, bool SMEM, bool INTOPS, int VPT>
+__global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long nvec, long long ntiles)
+{
+    using V = typename VecOf<T>::V;
+    using IV = typename VecOf<T>::IV;
+    constexpr int L = VecOf<T>::L;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+
+    const int32_t *K;
+    const T *X;
+    const Pair<T> *P;
+    if constexpr (SMEM) {
+        if (!stage_to_smem(smem, a.smem_src, a.smem_bytes, &bar, a.err)) return;
+        K = reinterpret_cast<const int32_t *>(smem);
+        X = reinterpret_cast<const T *>(smem + a.x_smem_off);
+        P = reinterpret_cast<const Pair<T> *>(smem);
+    } else {
+        K = a.K;
+        X = a.X;
+        P = a.P;
+    }
+    const V *__restrict__ Zv = reinterpret_cast<const V *>(a.Z);
+    IV *__restrict__ Iv = reinterpret_cast<IV *>(a.I);
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long b = tile * (long long)VPT * blockDim.x + threadIdx.x;
+        V zv[VPT];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const long long idx = b + (long long)v * blockDim.x;
+            if (idx < nvec) zv[v] = __ldcs(Zv + idx);
+        }
+        // phase 1: cells; phase 2: all K gathers; phase 3: all X gathers;
+        // phase 4: corrections -- every gather of the thread is in flight at once
+        constexpr int NQ = VPT * L;
+        const T *zs = reinterpret_cast<const T *>(zv);
+        uint32_t j[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) j[q] = cell_of<T, FMA, INTOPS>(zs[q], a);
+        int32_t t[NQ];
+        T x[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) t[q] = gather_k<T, CACHE, SMEM>(j[q], K, P, &x[q]);
+        if constexpr (!CACHE) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) x[q] = gather_x<T, SMEM>(t[q], X);
+        }
+        int32_t r[VPT][L];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v)
+#pragma unroll
+            for (int l = 0; l < L; ++l) r[v][l] = correct<T, INTOPS>(zs[v * L + l], t[v * L + l], x[v * L + l], a.checked);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const long long idx = b + (long long)v * blockDim.x;
+            if (idx < nvec) {
+                IV o;
+                if constexpr (L == 4) o = make_int4(r[v][0], r[v][1], r[v][2], r[v][3]);
+                else o = make_int2(r[v][0], r[v][1]);
+                __stcs(Iv + idx, o);
+            }
+        }
+    }
+    // the last m mod L queries
+    if (blockIdx.x == 0) {
+        const long long q = nvec * L + threadIdx.x;
+        if (q < a.m) a.I[q] = lookup<T, FMA, CACHE, SMEM, INTOPS>(a.Z[q], K, X, P, a);
+    }
+}
+
+// Scalar path for queries or results that are not aligned for vector access.
+template <typename T, bool FMA, bool CACHE, bool INTOPS>
+__global__ void __launch_bounds__(256) k_search_scalar(SearchArgs<T> a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride)
+        a.I[q] = lookup<T, FMA, CACHE, false, INTOPS>(a.Z[q], a.K, a.X, a.P, a);
+}
+
+struct SearchPlan {
+    bool fma, cache, smem, intops;
+    int block;     // threads per block
+    int vpt;       // vectors per thread per tile
+    int grid_cap;  // resident blocks (one wave)
+};
+
+constexpr int SEARCH_BLOCK = 256;
+constexpr int SEARCH_VPT = 4;
+
+// Launch one search (defined in ds_search_f32.cu / ds_search_f64.cu).
+template <typename T>
+ds_status launch_search(const SearchArgs<T> &a, const SearchPlan &plan, cudaStream_t stream);
+
+// Resident blocks per SM of the vector kernel chosen by `plan` with the given
+// dynamic shared memory, and the opt-in of large shared memory.
+template <typename T>
+ds_status prepare_search(SearchPlan *plan, uint32_t smem_bytes, int num_sms);
+
+}  // namespace ds

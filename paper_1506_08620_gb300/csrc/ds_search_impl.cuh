@@ -1,0 +1,98 @@
+// ds_search_impl.cuh -- kernel selection and launch for one element type.
+// Included by exactly one translation unit per type (ds_search_f32.cu,
+// ds_search_f64.cu) so the two sets of instantiations compile in parallel.
+#pragma once
+
+#include "ds_search.cuh"
+
+namespace ds {
+
+template <typename T, bool FMA, bool CACHE, bool SMEM>
+static const void *pick_vec4(bool intops)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (intops) return (const void *)k_search_vec<T, FMA, CACHE, SMEM, true, SEARCH_VPT>;
+    }
+    (void)intops;
+    return (const void *)k_search_vec<T, FMA, CACHE, SMEM, false, SEARCH_VPT>;
+}
+template <typename T, bool FMA, bool CACHE>
+static const void *pick_vec3(bool smem, bool intops)
+{
+    return smem ? pick_vec4<T, FMA, CACHE, true>(intops) : pick_vec4<T, FMA, CACHE, false>(intops);
+}
+template <typename T, bool FMA>
+static const void *pick_vec2(bool cache, bool smem, bool intops)
+{
+    return cache ? pick_vec3<T, FMA, true>(smem, intops) : pick_vec3<T, FMA, false>(smem, intops);
+}
+template <typename T>
+static const void *pick_vec(const SearchPlan &p)
+{
+    return p.fma ? pick_vec2<T, true>(p.cache, p.smem, p.intops) : pick_vec2<T, false>(p.cache, p.smem, p.intops);
+}
+
+template <typename T, bool FMA, bool CACHE>
+static const void *pick_scalar3(bool intops)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (intops) return (const void *)k_search_scalar<T, FMA, CACHE, true>;
+    }
+    (void)intops;
+    return (const void *)k_search_scalar<T, FMA, CACHE, false>;
+}
+template <typename T>
+static const void *pick_scalar(const SearchPlan &p)
+{
+    if (p.fma) return p.cache ? pick_scalar3<T, true, true>(p.intops) : pick_scalar3<T, true, false>(p.intops);
+    return p.cache ? pick_scalar3<T, false, true>(p.intops) : pick_scalar3<T, false, false>(p.intops);
+}
+
+template <typename T>
+ds_status prepare_search(SearchPlan *plan, uint32_t smem_bytes, int num_sms)
+{
+    const void *fn = pick_vec<T>(*plan);
+    if (plan->smem) {
+        DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
+    }
+    int occ = 0;
+    DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, plan->block, plan->smem ? smem_bytes : 0));
+    if (occ < 1) {
+        set_error("search kernel cannot be resident with %u bytes of shared memory", smem_bytes);
+        return DS_E_ARG;
+    }
+    plan->grid_cap = occ * num_sms;
+    return DS_OK;
+}
+
+template <typename T>
+ds_status launch_search(const SearchArgs<T> &a, const SearchPlan &plan, cudaStream_t stream)
+{
+    if (a.m <= 0) return DS_OK;
+    constexpr int L = VecOf<T>::L;
+    const bool aligned = (((uintptr_t)a.Z) % 16 == 0) && (((uintptr_t)a.I) % (L * sizeof(int32_t)) == 0);
+    if (!aligned) {
+        SearchPlan p = plan;
+        p.smem = false;
+        const void *fn = pick_scalar<T>(p);
+        long long blocks = (a.m + plan.block - 1) / plan.block;
+        if (blocks > (long long)plan.grid_cap * 4) blocks = (long long)plan.grid_cap * 4;
+        SearchArgs<T> args = a;
+        void *kargs[] = {&args};
+        DS_TRY_CUDA(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(plan.block), kargs, 0, stream));
+        return DS_OK;
+    }
+    const void *fn = pick_vec<T>(plan);
+    long long nvec = a.m / L;
+    long long per_tile = (long long)plan.vpt * plan.block;
+    long long ntiles = (nvec + per_tile - 1) / per_tile;
+    long long blocks = ntiles < plan.grid_cap ? ntiles : plan.grid_cap;
+    if (blocks < 1) blocks = 1;  // the tail (m < L) still needs one block
+    SearchArgs<T> args = a;
+    void *kargs[] = {&args, &nvec, &ntiles};
+    DS_TRY_CUDA(cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(plan.block), kargs,
+                                 plan.smem ? a.smem_bytes : 0, stream));
+    return DS_OK;
+}
+
+}  // namespace ds
