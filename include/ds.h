@@ -126,7 +126,7 @@ typedef struct ds_info_t {
 DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, void *stream,
                    ds_index **out);
 
-/* Search m queries (Algorithm direct, Section 4.3): j = min(f(z), R),
+/* Search m queries (Algorithm direct, Section 4.2): j = min(f(z), R),
  * t = K_j, I = t - [z < X_t].
  *   Z_dev  m queries of the index's dtype; I_dev  m int32 results.
  * m == 0 is a no-op.  Asynchronous on `stream`; allocates nothing; safe to

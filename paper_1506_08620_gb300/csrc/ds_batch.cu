@@ -1,44 +1,688 @@
-// ds_batch.cu -- many independent knot arrays (CSR): segmented build and the
-// persistent ragged search.
+// ds_batch.cu -- many independent knot arrays (CSR): segmented build of one
+// direct-search table per array and the persistent ragged search, with its
+// CUDA-graph launch and autotuner.
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
+#include <vector>
 
-#include "ds_index.cuh"
+#include "ds_engine.cuh"
 
+namespace ds {
+
+// ---------------------------------------------------------------- kernels
+__global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
+                              long long *chunk_off, unsigned long long *counter)
+{
+    __shared__ long long warp_sum[32];
+    const int per = (n_arrays + blockDim.x - 1) / blockDim.x;
+    const int a0 = threadIdx.x * per;
+    const int a1 = min(a0 + per, n_arrays);
+    long long local = 0;
+    for (int a = a0; a < a1; ++a) {
+        long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
+        q = q < 0 ? 0 : q;
+        local += (q + chunk - 1) / chunk;
+    }
+    // block-wide exclusive scan of `local`
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) / 32;
+        long long v = lane < nw ? warp_sum[lane] : 0;
+        long long inc2 = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc2, o);
+            if (lane >= o) inc2 += y;
+        }
+        if (lane < nw) warp_sum[lane] = inc2 - v;
+    }
+    __syncthreads();
+    long long prefix = warp_sum[wid] + incl - local;
+    for (int a = a0; a < a1; ++a) {
+        chunk_off[a] = prefix;
+        long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
+        q = q < 0 ? 0 : q;
+        prefix += (q + chunk - 1) / chunk;
+    }
+    if (a1 == n_arrays && a0 < a1) chunk_off[n_arrays] = prefix;
+    if (n_arrays <= 0 && threadIdx.x == 0) chunk_off[0] = 0;
+    if (threadIdx.x == 0) *counter = 0;
+}
+
+__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
+                             const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
+                             unsigned char *blob)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long total = kc_off[n_arrays];
+    for (long long c = warp; c < total; c += nwarps) {
+        int lo = 0, hi = n_arrays - 1;  // array owning chunk c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (kc_off[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const int arr = lo;
+        const ArrDesc d = desc[arr];
+        const long long lc = c - kc_off[arr];
+        const long long start = x_off[arr];
+        const long long N = d.n;
+        uint32_t *K = reinterpret_cast<uint32_t *>(blob + d.img);
+        const long long i = lc * 32 + lane;
+        const uint32_t Fi = F[start + (i <= N ? i : N)];
+        const long long prev = lc == 0 ? -1 : (long long)F[start + lc * 32 - 1];
+        const long long last = (long long)__shfl_sync(0xffffffffu, Fi, 31);
+        for (long long base = prev + 1; base <= last; base += 32) {
+            const long long j = base + lane;
+            int k = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const uint32_t Fc = __shfl_sync(0xffffffffu, Fi, k + s - 1);
+                if ((long long)Fc < j) k += s;
+            }
+            const uint32_t Fk = __shfl_sync(0xffffffffu, Fi, k);
+            if (j <= last) K[j] = (uint32_t)(lc * 32 + k) | ((long long)Fk == j ? KNOT_FLAG : 0u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- engine (host)
+void engine_free(Engine *e)
+{
+    if (e->gexec) cudaGraphExecDestroy(e->gexec);
+    if (e->gstream) cudaStreamDestroy(e->gstream);
+    if (e->desc_dev) cudaFree(e->desc_dev);
+    if (e->blob) cudaFree(e->blob);
+    if (e->chunk_off) cudaFree(e->chunk_off);
+    if (e->counter) cudaFree(e->counter);
+    if (e->dev_err) cudaFree(e->dev_err);
+    if (e->seg_x) cudaFree(e->seg_x);
+    if (e->seg_a) cudaFree(e->seg_a);
+    if (e->seg_b) cudaFree(e->seg_b);
+    *e = Engine();
+}
+
+static std::vector<Segment> make_segments(const std::vector<long long> &x_off)
+{
+    std::vector<Segment> segs;
+    const int A = (int)x_off.size() - 1;
+    for (int a = 0; a < A; ++a)
+        for (long long lo = x_off[a]; lo < x_off[a + 1]; lo += SEG_KNOTS) {
+            Segment s;
+            s.lo = lo;
+            s.hi = std::min(lo + SEG_KNOTS, x_off[a + 1]);
+            s.arr = a;
+            s.pad_ = 0;
+            segs.push_back(s);
+        }
+    return segs;
+}
+
+static int top_pow2(long long n)
+{
+    long long t = 1;
+    while (t * 2 <= n) t *= 2;
+    return (int)t;
+}
+
+template <typename T, bool FMA>
+static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const Segment *segs_dev, int n_segs,
+                                int A, cudaStream_t s, const DeviceProps &props, std::vector<HRState> &hs)
+{
+    HRState *st = nullptr;
+    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState) * (size_t)A));
+    const int sgrid = std::max(1, std::min(n_segs, props.num_sms * 8));
+    const int agrid = (A + 127) / 128;
+    k_hr_state_init<<<agrid, 128, 0, s>>>(st, A);
+    k_seg_validate<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, st);
+    k_seg_hr_init<T, FMA><<<agrid, 128, 0, s>>>(Xcat, x_off_dev, A, st);
+    hs.resize(A);
+    ds_status rc = DS_OK;
+    for (long long round = 0;; ++round) {
+        for (int k = 0; k < 3; ++k) {
+            k_seg_hr_check<T, FMA><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, st);
+            k_seg_hr_grow<T, FMA><<<agrid, 128, 0, s>>>(Xcat, x_off_dev, A, st);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), st, sizeof(HRState) * (size_t)A, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("batched ComputeHR: %s", cudaGetErrorString(e));
+            rc = DS_E_CUDA;
+            break;
+        }
+        bool all = true;
+        for (int a = 0; a < A && all; ++a) all = hs[a].done != 0;
+        if (all) break;
+        if (round > 1000000) {
+            set_error("batched ComputeHR did not finish");
+            rc = DS_E_NO_CONVERGENCE;
+            break;
+        }
+    }
+    cudaFree(st);
+    return rc;
+}
+
+// Validate, run ComputeHR per array, lay out the blob and fill every table.
+// `want_direct[a] == false` forces array a into `other_mode` (learned build).
+template <typename T, bool FMA>
+static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x_off_dev,
+                                    const std::vector<long long> &x_off, uint32_t flags, cudaStream_t s,
+                                    const std::vector<char> *force_other, int other_mode, std::vector<HRState> *hs_out)
+{
+    const int A = e->n_arrays;
+    std::vector<Segment> segs = make_segments(x_off);
+    const int n_segs = (int)segs.size();
+    Segment *segs_dev = nullptr;
+    DS_TRY_CUDA(cudaMalloc(&segs_dev, sizeof(Segment) * segs.size()));
+    ds_status rc = DS_OK;
+    std::vector<HRState> hs;
+    uint32_t *F = nullptr;
+    long long *kc_dev = nullptr;
+    do {
+        if (cudaMemcpyAsync(segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess) {
+            set_error("batched build: segment upload failed");
+            rc = DS_E_CUDA;
+            break;
+        }
+        rc = compute_hr_all<T, FMA>(Xcat, x_off_dev, segs_dev, n_segs, A, s, e->props, hs);
+        if (rc != DS_OK) break;
+        // modes and layout
+        e->desc_host.assign(A, ArrDesc());
+        size_t off = 0;
+        std::vector<long long> kc(A + 1, 0);
+        for (int a = 0; a < A; ++a) {
+            ArrDesc &d = e->desc_host[a];
+            memset(&d, 0, sizeof(d));
+            const long long nk = x_off[a + 1] - x_off[a];
+            d.n = (int32_t)(nk - 1);
+            d.yoff = x_off[a];
+            d.pbits = top_pow2(d.n);
+            e->h_updates += hs[a].updates;
+            const bool feasible = hs[a].status == DS_OK;
+            const bool forced = force_other && (*force_other)[a];
+            if (!feasible && (flags & DS_STRICT)) {
+                set_error("array %d: %s", a, ds_status_str((ds_status)hs[a].status));
+                rc = (ds_status)hs[a].status;
+                break;
+            }
+            if (hs[a].status == DS_E_NOT_INCREASING) {
+                set_error("array %d: knots are not strictly increasing finite values (knot %lld)", a,
+                          (long long)(hs[a].bad_nonfinite != NONE64 ? hs[a].bad_nonfinite : hs[a].bad_order));
+                rc = DS_E_NOT_INCREASING;
+                break;
+            }
+            d.img = (long long)off;
+            if (feasible && !forced) {
+                d.mode = MODE_DIRECT;
+                d.R = (uint32_t)hs[a].R;
+                d.H = hs[a].H;
+                d.W = hs[a].W;
+                const size_t kb = round_up(((size_t)hs[a].R + 1) * 4, 16);
+                d.x_in_img = (uint32_t)std::min<size_t>(kb, 0xFFFFFFFFu);
+                d.xg = (long long)(off + kb);
+                const size_t xb = round_up((size_t)nk * sizeof(T), 16);
+                const size_t ib = kb + xb;
+                d.img_bytes = ib <= 0xFFFFFFF0u ? (uint32_t)ib : 0u;
+                off += ib;
+                kc[a + 1] = (nk + 31) / 32;
+                e->n_direct += 1;
+                e->R_total += (unsigned long long)hs[a].R + 1;
+            } else {
+                d.mode = forced ? other_mode : (other_mode == MODE_LEARNED ? MODE_LEARNED : MODE_BISECT);
+                d.R = 0;
+                d.xg = (long long)off;
+                d.x_in_img = 0;
+                const size_t xb = round_up((size_t)nk * sizeof(T), 16);
+                d.img_bytes = d.mode == MODE_BISECT && xb <= 0xFFFFFFF0u ? (uint32_t)xb : 0u;
+                off += xb;
+                if (d.mode == MODE_BISECT) e->n_fallback += 1;
+                else e->n_learned += 1;
+            }
+            d.form = FMA ? F_FMA : F_PLAIN;
+            // X0 and XN are read back below
+        }
+        if (rc != DS_OK) break;
+        // knots X_0, X_N per array (for the descriptors)
+        {
+            std::vector<T> ends(2 * (size_t)A);
+            for (int a = 0; a < A; ++a) {
+                cudaMemcpyAsync(&ends[2 * a], Xcat + x_off[a], sizeof(T), cudaMemcpyDeviceToHost, s);
+                cudaMemcpyAsync(&ends[2 * a + 1], Xcat + x_off[a + 1] - 1, sizeof(T), cudaMemcpyDeviceToHost, s);
+            }
+            if (cudaStreamSynchronize(s) != cudaSuccess) {
+                set_error("batched build: cannot read knots");
+                rc = DS_E_CUDA;
+                break;
+            }
+            for (int a = 0; a < A; ++a) {
+                ArrDesc &d = e->desc_host[a];
+                d.X0 = (double)ends[2 * a];
+                d.XN = (double)ends[2 * a + 1];
+                if (!FMA && d.X0 == 0.0) d.form = F_PLAIN_X0ZERO;
+            }
+        }
+        for (int a = 0; a < A; ++a) kc[a + 1] += kc[a];
+        e->blob_bytes = off;
+        e->table_bytes = off;
+        const size_t budget = table_budget_bytes();
+        if (off > budget) {
+            set_error("batched build: tables need %zu bytes, budget is %zu", off, budget);
+            rc = DS_E_TABLE_TOO_LARGE;
+            break;
+        }
+        if (cudaMalloc(&e->blob, std::max<size_t>(off, 16)) != cudaSuccess ||
+            cudaMalloc(&e->desc_dev, sizeof(ArrDesc) * (size_t)A) != cudaSuccess ||
+            cudaMalloc(&F, sizeof(uint32_t) * std::max<long long>(x_off[A], 1)) != cudaSuccess ||
+            cudaMalloc(&kc_dev, sizeof(long long) * (size_t)(A + 1)) != cudaSuccess) {
+            set_error("batched build: device allocation failed");
+            rc = DS_E_NOMEM;
+            break;
+        }
+        cudaMemsetAsync(e->blob, 0, std::max<size_t>(off, 16), s);
+        cudaMemcpyAsync(e->desc_dev, e->desc_host.data(), sizeof(ArrDesc) * (size_t)A, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(kc_dev, kc.data(), sizeof(long long) * (size_t)(A + 1), cudaMemcpyHostToDevice, s);
+        const int sgrid = std::max(1, std::min(n_segs, e->props.num_sms * 8));
+        k_seg_copy_fill_F<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, e->desc_dev, e->blob, F);
+        const long long kchunks = kc[A];
+        if (kchunks > 0) {
+            const long long kgrid = std::min<long long>((kchunks * 32 + 255) / 256, (long long)e->props.num_sms * 16);
+            k_seg_fill_K<<<(int)kgrid, 256, 0, s>>>(F, x_off_dev, kc_dev, A, e->desc_dev, e->blob);
+        }
+        cudaError_t ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            set_error("batched build: table fill failed: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+            break;
+        }
+    } while (0);
+    cudaFree(segs_dev);
+    if (F) cudaFree(F);
+    if (kc_dev) cudaFree(kc_dev);
+    if (hs_out) *hs_out = hs;
+    return rc;
+}
+
+ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
+                       uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
+                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out)
+{
+    e->dtype = dtype;
+    e->flags = flags;
+    e->n_arrays = n_arrays;
+    DS_TRY(device_props(&e->props));
+    std::vector<long long> x_off(n_arrays + 1);
+    DS_TRY_CUDA(cudaMemcpy(x_off.data(), x_off_dev, sizeof(long long) * (size_t)(n_arrays + 1),
+                           cudaMemcpyDeviceToHost));
+    if (x_off[0] != 0) {
+        set_error("x_off[0] must be 0");
+        return DS_E_ARG;
+    }
+    for (int a = 0; a < n_arrays; ++a) {
+        if (x_off[a + 1] - x_off[a] < 2) {
+            set_error("array %d has %lld knots (at least 2 needed)", a, x_off[a + 1] - x_off[a]);
+            return DS_E_ARG;
+        }
+        if (x_off[a + 1] - x_off[a] > (1ll << 31) - 1) {
+            set_error("array %d: at most 2^31-1 knots (int32 results)", a);
+            return DS_E_ARG;
+        }
+    }
+    e->n_knots = x_off[n_arrays];
+    if (x_off_host) *x_off_host = x_off;
+    DS_TRY_CUDA(cudaMalloc(&e->chunk_off, sizeof(long long) * (size_t)(n_arrays + 1)));
+    DS_TRY_CUDA(cudaMalloc(&e->counter, 2 * sizeof(unsigned long long)));
+    DS_TRY_CUDA(cudaMemset(e->counter, 0, 2 * sizeof(unsigned long long)));
+    DS_TRY_CUDA(cudaMalloc(&e->dev_err, sizeof(int)));
+    DS_TRY_CUDA(cudaMemset(e->dev_err, 0, sizeof(int)));
+    const bool fma = (flags & DS_FMA) != 0;
+    if (dtype == DS_F32)
+        return fma ? build_engine_typed<float, true>(e, (const float *)Xcat, x_off_dev, x_off, flags, s, force_other,
+                                                     other_mode, hs_out)
+                   : build_engine_typed<float, false>(e, (const float *)Xcat, x_off_dev, x_off, flags, s,
+                                                      force_other, other_mode, hs_out);
+    return fma ? build_engine_typed<double, true>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
+                                                  other_mode, hs_out)
+               : build_engine_typed<double, false>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
+                                                   other_mode, hs_out);
+}
+
+// ---------------------------------------------------------------- launch
+template <typename T, int VPT, bool INTERP>
+static const void *pick3(bool vec)
+{
+    return vec ? (const void *)k_batch_search<T, VPT, INTERP, true> : (const void *)k_batch_search<T, VPT, INTERP, false>;
+}
+template <typename T, int VPT>
+static const void *pick2(bool interp, bool vec)
+{
+    return interp ? pick3<T, VPT, true>(vec) : pick3<T, VPT, false>(vec);
+}
+template <typename T>
+static const void *pick1(int vpt, bool interp, bool vec)
+{
+    switch (vpt) {
+    case 1: return pick2<T, 1>(interp, vec);
+    case 2: return pick2<T, 2>(interp, vec);
+    default: return pick2<T, 4>(interp, vec);
+    }
+}
+static const void *pick_kernel(int dtype, int vpt, bool interp, bool vec)
+{
+    return dtype == DS_F32 ? pick1<float>(vpt, interp, vec) : pick1<double>(vpt, interp, vec);
+}
+
+static int clamp_block(int b) { return b == 128 || b == 512 ? b : 256; }
+static int clamp_vpt(int v) { return v == 1 || v == 2 ? v : 4; }
+
+// Resident blocks for a configuration (and the shared-memory opt-in).
+static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid)
+{
+    const void *fn = pick_kernel(e->dtype, clamp_vpt(t.items), interp, vec);
+    const int smem = std::max(0, t.smem_limit);
+    if (smem > 0) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int occ = 0;
+    DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, clamp_block(t.block), smem));
+    if (occ < 1) {
+        set_error("batched search: configuration cannot be resident (block %d, smem %d)", t.block, smem);
+        return DS_E_ARG;
+    }
+    if (t.blocks_per_sm > 0) occ = std::min(occ, t.blocks_per_sm);
+    *grid = occ * e->props.num_sms;
+    return DS_OK;
+}
+
+ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
+                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s)
+{
+    const bool interp = Y && y_out;
+    const int L = e->dtype == DS_F32 ? 4 : 2;
+    const size_t esz = e->dtype == DS_F32 ? 4 : 8;
+    const bool vec = ((uintptr_t)Z % 16 == 0) && ((uintptr_t)I % (L * 4) == 0) &&
+                     (!interp || (uintptr_t)y_out % esz == 0);
+    int grid = 0;
+    DS_TRY(occupancy(e, t, interp, vec, &grid));
+    const int block = clamp_block(t.block), vpt = clamp_vpt(t.items);
+    const long long chunk = (long long)block * vpt * L * CHUNK_TILES;
+    k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->chunk_off, e->counter);
+    DS_TRY_CUDA(cudaGetLastError());
+    const void *fn = pick_kernel(e->dtype, vpt, interp, vec);
+    if (e->dtype == DS_F32) {
+        BatchArgs<float> a;
+        memset(&a, 0, sizeof(a));
+        a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
+        a.Z = (const float *)Z; a.I = I; a.Y = (const float *)Y; a.y_out = (float *)y_out;
+        a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1; a.chunk = chunk;
+        a.smem_limit = (uint32_t)std::max(0, t.smem_limit); a.checked = (e->flags & DS_CHECKED) != 0;
+        a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
+        void *args[] = {&a};
+        DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
+    } else {
+        BatchArgs<double> a;
+        memset(&a, 0, sizeof(a));
+        a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
+        a.Z = (const double *)Z; a.I = I; a.Y = (const double *)Y; a.y_out = (double *)y_out;
+        a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1; a.chunk = chunk;
+        a.smem_limit = (uint32_t)std::max(0, t.smem_limit); a.checked = (e->flags & DS_CHECKED) != 0;
+        a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
+        void *args[] = {&a};
+        DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
+    }
+    return DS_OK;
+}
+
+// Launch through a CUDA graph holding (planner, search) for these pointers;
+// the graph is re-captured when the pointers or the tuning change.  When the
+// caller's stream is itself being captured the kernels are launched directly
+// (and become part of the caller's graph).
+ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
+                        void *y_out, int32_t *I, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    DS_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
+    static const bool no_graph = getenv("DS_NO_GRAPH") != nullptr;
+    if (cs != cudaStreamCaptureStatusNone || no_graph)
+        return engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, s);
+    const void *key[6] = {Z, z_off, (const void *)(uintptr_t)m_single, Y, y_out, I};
+    const bool same = e->gexec && !memcmp(key, e->gkey, sizeof(key)) && !memcmp(&e->tune, &e->gtune, sizeof(ds_tune_t));
+    if (!same) {
+        if (e->gexec) {
+            cudaGraphExecDestroy(e->gexec);
+            e->gexec = nullptr;
+        }
+        if (!e->gstream) DS_TRY_CUDA(cudaStreamCreateWithFlags(&e->gstream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        DS_TRY_CUDA(cudaStreamBeginCapture(e->gstream, cudaStreamCaptureModeThreadLocal));
+        ds_status rc = engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, e->gstream);
+        cudaError_t ce = cudaStreamEndCapture(e->gstream, &g);
+        if (rc != DS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ce != cudaSuccess) {
+            set_error("graph capture failed: %s", cudaGetErrorString(ce));
+            return DS_E_CUDA;
+        }
+        ce = cudaGraphInstantiate(&e->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+            e->gexec = nullptr;
+            return DS_E_CUDA;
+        }
+        memcpy(e->gkey, key, sizeof(key));
+        e->gtune = e->tune;
+    }
+    DS_TRY_CUDA(cudaGraphLaunch(e->gexec, s));
+    return DS_OK;
+}
+
+ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
+                          cudaStream_t s, ds_tune_t *best_out)
+{
+    const int blocks[] = {128, 256, 512};
+    const int items[] = {1, 2, 4};
+    const int smems[] = {0, 24 * 1024, 48 * 1024, 96 * 1024, 200 * 1024};
+    cudaEvent_t e0, e1;
+    DS_TRY_CUDA(cudaEventCreate(&e0));
+    DS_TRY_CUDA(cudaEventCreate(&e1));
+    ds_tune_t best;
+    memset(&best, 0, sizeof(best));
+    best.ms = 1e30f;
+    ds_status rc = DS_OK;
+    for (int b : blocks)
+        for (int it : items)
+            for (int sm : smems) {
+                if (sm > e->props.max_smem_optin - 2048) continue;
+                ds_tune_t t;
+                memset(&t, 0, sizeof(t));
+                t.block = b;
+                t.items = it;
+                t.smem_limit = sm;
+                int grid = 0;
+                if (occupancy(e, t, false, true, &grid) != DS_OK) continue;
+                rc = engine_launch_direct(e, t, Z, z_off, m_single, nullptr, nullptr, I, s);
+                if (rc != DS_OK) break;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 3; ++r) engine_launch_direct(e, t, Z, z_off, m_single, nullptr, nullptr, I, s);
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = DS_E_CUDA;
+                    set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                    break;
+                }
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= 3;
+                if (ms < best.ms) {
+                    best = t;
+                    best.ms = ms;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DS_OK) return rc;
+    e->tune = best;
+    if (best_out) *best_out = best;
+    return DS_OK;
+}
+
+ds_tune_t default_tune()
+{
+    ds_tune_t t;
+    memset(&t, 0, sizeof(t));
+    t.block = 256;
+    t.items = 4;
+    t.smem_limit = 48 * 1024;
+    t.blocks_per_sm = 0;
+    return t;
+}
+
+}  // namespace ds
+
+// ---------------------------------------------------------------- handle and API
 struct ds_batch {
     ds::HandleHeader hdr;
-    int32_t dtype;
-    uint32_t flags;
+    ds::Engine eng;
 };
 
 namespace ds {
-void free_batch(ds_batch *b) { delete b; }
+void free_batch(ds_batch *b)
+{
+    engine_free(&b->eng);
+    b->hdr.magic = 0;
+    delete b;
+}
 ds_status info_batch(const ds_batch *b, ds_info_t *o)
 {
+    const Engine &e = b->eng;
     o->kind = KIND_BATCH;
-    o->dtype = b->dtype;
+    o->dtype = e.dtype;
+    o->flags = e.flags;
+    o->n_arrays = e.n_arrays;
+    o->n_knots = e.n_knots;
+    o->R = e.R_total;
+    o->table_bytes = (int64_t)e.table_bytes;
+    o->h_updates = e.h_updates;
+    o->build_ms = e.build_ms;
+    o->n_direct = e.n_direct;
+    o->n_fallback = e.n_fallback;
+    o->n_learned = e.n_learned;
+    int err = 0;
+    if (e.dev_err && cudaMemcpy(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+        o->device_error = err;
     return DS_OK;
 }
 }  // namespace ds
 
+static bool batch_ok(const ds_batch *b)
+{
+    return b && b->hdr.magic == ds::HANDLE_MAGIC && b->hdr.kind == ds::KIND_BATCH;
+}
+
 extern "C" {
-ds_status ds_batch_build(const void *, const int64_t *, int32_t, ds_dtype, uint32_t, void *, ds_batch **out)
+
+ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, ds_dtype dtype,
+                         uint32_t flags, void *stream, ds_batch **out)
 {
-    if (out) *out = nullptr;
-    ds::set_error("ds_batch_build: not implemented yet");
-    return DS_E_UNIMPLEMENTED;
+    ds::clear_error();
+    if (!out) {
+        ds::set_error("ds_batch_build: out is NULL");
+        return DS_E_ARG;
+    }
+    *out = nullptr;
+    if (!Xcat_dev || !x_off_dev || n_arrays < 1 || (dtype != DS_F32 && dtype != DS_F64) ||
+        (flags & ~(uint32_t)(DS_FMA | DS_CHECKED | DS_STRICT | DS_NO_SMEM))) {
+        ds::set_error("ds_batch_build: bad argument");
+        return DS_E_ARG;
+    }
+    const double t0 = ds::now_ms();
+    ds_batch *b = new ds_batch;
+    b->hdr.kind = ds::KIND_BATCH;
+    b->hdr.magic = ds::HANDLE_MAGIC;
+    ds_status rc = ds::engine_build(&b->eng, Xcat_dev, (const long long *)x_off_dev, n_arrays, dtype, flags,
+                                    (cudaStream_t)stream, nullptr, ds::MODE_BISECT, nullptr, nullptr);
+    if (rc != DS_OK) {
+        ds::free_batch(b);
+        return rc;
+    }
+    b->eng.tune = ds::default_tune();
+    if (flags & DS_NO_SMEM) b->eng.tune.smem_limit = 0;
+    b->eng.build_ms = ds::now_ms() - t0;
+    *out = b;
+    return DS_OK;
 }
-ds_status ds_batch_search(const ds_batch *, const void *, const int64_t *, int32_t *, void *)
+
+ds_status ds_batch_search(const ds_batch *b, const void *Zcat_dev, const int64_t *z_off_dev, int32_t *Icat_dev,
+                          void *stream)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!batch_ok(b) || !Zcat_dev || !z_off_dev || !Icat_dev) {
+        ds::set_error("ds_batch_search: bad argument");
+        return DS_E_ARG;
+    }
+    return ds::engine_launch(const_cast<ds::Engine *>(&b->eng), Zcat_dev, (const long long *)z_off_dev, 0, nullptr,
+                             nullptr, Icat_dev, (cudaStream_t)stream);
 }
-ds_status ds_batch_autotune(ds_batch *, const void *, const int64_t *, int32_t *, void *, ds_tune_t *)
+
+ds_status ds_batch_autotune(ds_batch *b, const void *Zcat_dev, const int64_t *z_off_dev, int32_t *Icat_dev,
+                            void *stream, ds_tune_t *best)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!batch_ok(b) || !Zcat_dev || !z_off_dev || !Icat_dev) {
+        ds::set_error("ds_batch_autotune: bad argument");
+        return DS_E_ARG;
+    }
+    return ds::engine_autotune(&b->eng, Zcat_dev, (const long long *)z_off_dev, 0, Icat_dev, (cudaStream_t)stream,
+                               best);
 }
-ds_status ds_batch_set_tune(ds_batch *, const ds_tune_t *) { return DS_E_UNIMPLEMENTED; }
-ds_status ds_batch_get_tune(const ds_batch *, ds_tune_t *) { return DS_E_UNIMPLEMENTED; }
-ds_status ds_batch_array(const ds_batch *, int32_t, double *, double *, uint64_t *, int32_t *)
+
+ds_status ds_batch_set_tune(ds_batch *b, const ds_tune_t *cfg)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!batch_ok(b) || !cfg || cfg->smem_limit < 0 || cfg->smem_limit > b->eng.props.max_smem_optin - 2048) {
+        ds::set_error("ds_batch_set_tune: bad argument");
+        return DS_E_ARG;
+    }
+    ds_tune_t t = *cfg;
+    t.block = t.block == 128 || t.block == 512 ? t.block : 256;
+    t.items = t.items == 1 || t.items == 2 ? t.items : 4;
+    int grid = 0;
+    DS_TRY(ds::occupancy(&b->eng, t, false, true, &grid));
+    b->eng.tune = t;
+    return DS_OK;
 }
+
+ds_status ds_batch_get_tune(const ds_batch *b, ds_tune_t *cfg)
+{
+    if (!batch_ok(b) || !cfg) return DS_E_ARG;
+    *cfg = b->eng.tune;
+    return DS_OK;
 }
+
+ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double *W, uint64_t *R, int32_t *mode)
+{
+    if (!batch_ok(b) || a < 0 || a >= b->eng.n_arrays) {
+        ds::set_error("ds_batch_array: bad argument");
+        return DS_E_ARG;
+    }
+    const ds::ArrDesc &d = b->eng.desc_host[a];
+    if (H) *H = d.H;
+    if (W) *W = d.W;
+    if (R) *R = d.R;
+    if (mode) *mode = d.mode;
+    return DS_OK;
+}
+
+}  // extern "C"

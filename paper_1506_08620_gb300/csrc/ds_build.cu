@@ -21,6 +21,13 @@ __global__ void k_hr_state_init(HRState *st, int count)
     st[a] = s;
 }
 
+__global__ void k_clear_flags(uint32_t *p, long long count, int stride)
+{
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += step)
+        p[i * stride] &= ~KNOT_FLAG;
+}
+
 static int grid_for(const DeviceProps &p, long long work, int block)
 {
     long long want = (work + block - 1) / block;
@@ -86,7 +93,8 @@ static const char *hr_message(int status)
 }
 
 template <typename T, bool FMA>
-static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, cudaStream_t s, ds_index *idx)
+static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, cudaStream_t s, ds_index *idx,
+                             bool x0zero)
 {
     const DeviceProps &props = idx->props;
     HRState *st = nullptr;
@@ -121,7 +129,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     DS_TRY_CUDA(cudaMalloc(&idx->tab, idx->k_bytes + idx->x_bytes));
     DS_TRY_CUDA(cudaMemsetAsync(idx->tab, 0, idx->k_bytes + idx->x_bytes, s));
     T *Xc = reinterpret_cast<T *>(idx->tab + idx->k_bytes);
-    int32_t *K = reinterpret_cast<int32_t *>(idx->tab);
+    uint32_t *K = reinterpret_cast<uint32_t *>(idx->tab);
     DS_TRY_CUDA(cudaMemcpyAsync(Xc, X_user, (size_t)n_knots * sizeof(T), cudaMemcpyDeviceToDevice, s));
     if (cache) DS_TRY_CUDA(cudaMalloc(&idx->pairs, idx->pair_bytes));
     uint32_t *F = nullptr;
@@ -140,7 +148,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     }
     // search plan
     SearchPlan &plan = idx->plan;
-    plan.fma = FMA;
+    plan.form = FMA ? F_FMA : (x0zero ? F_PLAIN_X0ZERO : F_PLAIN);
     plan.cache = cache;
     plan.intops = sizeof(T) == 8 && f64_intops_default();
     plan.block = SEARCH_BLOCK;
@@ -172,37 +180,42 @@ ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uin
             rc = DS_E_CUDA;
         }
     }
+    // first and last knot on the host (X_0 == 0 selects the subtraction-free form)
+    if (rc == DS_OK) {
+        const size_t esz = dtype == DS_F32 ? sizeof(float) : sizeof(double);
+        unsigned char e2[16];
+        cudaError_t e = cudaMemcpy(e2, X_dev, esz, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(e2 + 8, (const unsigned char *)X_dev + (n_knots - 1) * esz, esz, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            set_error("ds_build: cannot read X: %s", cudaGetErrorString(e));
+            rc = DS_E_CUDA;
+        } else if (dtype == DS_F32) {
+            float a, b;
+            memcpy(&a, e2, 4);
+            memcpy(&b, e2 + 8, 4);
+            idx->X0 = a;
+            idx->XN = b;
+        } else {
+            memcpy(&idx->X0, e2, 8);
+            memcpy(&idx->XN, e2 + 8, 8);
+        }
+    }
     if (rc == DS_OK) {
         const bool fma = (flags & DS_FMA) != 0;
+        const bool x0zero = idx->X0 == 0.0;
         if (dtype == DS_F32) {
-            rc = fma ? build_typed<float, true>((const float *)X_dev, n_knots, flags, s, idx)
-                     : build_typed<float, false>((const float *)X_dev, n_knots, flags, s, idx);
+            rc = fma ? build_typed<float, true>((const float *)X_dev, n_knots, flags, s, idx, x0zero)
+                     : build_typed<float, false>((const float *)X_dev, n_knots, flags, s, idx, x0zero);
         } else {
-            rc = fma ? build_typed<double, true>((const double *)X_dev, n_knots, flags, s, idx)
-                     : build_typed<double, false>((const double *)X_dev, n_knots, flags, s, idx);
+            rc = fma ? build_typed<double, true>((const double *)X_dev, n_knots, flags, s, idx, x0zero)
+                     : build_typed<double, false>((const double *)X_dev, n_knots, flags, s, idx, x0zero);
         }
     }
     if (rc != DS_OK) {
         free_index(idx);
         return rc;
     }
-    // first and last knot on the host
-    if (dtype == DS_F32) {
-        float e2[2];
-        cudaMemcpy(&e2[0], idx->tab + idx->k_bytes, sizeof(float), cudaMemcpyDeviceToHost);
-        cudaMemcpy(&e2[1], idx->tab + idx->k_bytes + (n_knots - 1) * sizeof(float), sizeof(float),
-                   cudaMemcpyDeviceToHost);
-        idx->X0 = e2[0];
-        idx->XN = e2[1];
-    } else {
-        double e2[2];
-        cudaMemcpy(&e2[0], idx->tab + idx->k_bytes, sizeof(double), cudaMemcpyDeviceToHost);
-        cudaMemcpy(&e2[1], idx->tab + idx->k_bytes + (n_knots - 1) * sizeof(double), sizeof(double),
-                   cudaMemcpyDeviceToHost);
-        idx->X0 = e2[0];
-        idx->XN = e2[1];
-    }
-    idx->x0zero = idx->X0 == 0.0;
     idx->build_ms = now_ms() - t0;
     *out = idx;
     return DS_OK;
@@ -213,7 +226,7 @@ static ds_status search_typed(const ds_index *idx, const void *Z, long long m, i
 {
     SearchArgs<T> a;
     memset(&a, 0, sizeof(a));
-    a.K = reinterpret_cast<const int32_t *>(idx->tab);
+    a.K = reinterpret_cast<const uint32_t *>(idx->tab);
     a.X = reinterpret_cast<const T *>(idx->tab + idx->k_bytes);
     a.P = reinterpret_cast<const Pair<T> *>(idx->pairs);
     a.smem_src = idx->plan.cache ? idx->pairs : (const void *)idx->tab;
@@ -223,7 +236,6 @@ static ds_status search_typed(const ds_index *idx, const void *Z, long long m, i
     a.W = (T)idx->W;
     a.X0 = (T)idx->X0;
     a.R = (uint32_t)idx->R;
-    a.x0zero = idx->x0zero;
     a.checked = (idx->flags & DS_CHECKED) != 0;
     a.Z = reinterpret_cast<const T *>(Z);
     a.I = I;
@@ -266,9 +278,13 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
     }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t esz = idx->dtype == DS_F32 ? 4 : 8;
-    if (K_out_dev)
-        DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)(idx->R + 1) * sizeof(int32_t),
-                                    cudaMemcpyDeviceToDevice, s));
+    const long long cells = (long long)idx->R + 1;
+    const int grid = (int)((cells + 255) / 256 < idx->props.num_sms * 8 ? (cells + 255) / 256 : idx->props.num_sms * 8);
+    if (K_out_dev) {
+        DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(K_out_dev), cells, 1);
+        DS_TRY_CUDA(cudaGetLastError());
+    }
     if (X_out_dev)
         DS_TRY_CUDA(cudaMemcpyAsync(X_out_dev, idx->tab + idx->k_bytes, (size_t)idx->n_knots * esz,
                                     cudaMemcpyDeviceToDevice, s));
@@ -277,8 +293,10 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
             ds::set_error("ds_index_export: the index has no pair table (built without DS_CACHE_LAYOUT)");
             return DS_E_ARG;
         }
-        DS_TRY_CUDA(cudaMemcpyAsync(pairs_out_dev, idx->pairs, (size_t)(idx->R + 1) * (esz == 4 ? 8 : 16),
+        DS_TRY_CUDA(cudaMemcpyAsync(pairs_out_dev, idx->pairs, (size_t)cells * (esz == 4 ? 8 : 16),
                                     cudaMemcpyDeviceToDevice, s));
+        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(pairs_out_dev), cells, esz == 4 ? 2 : 4);
+        DS_TRY_CUDA(cudaGetLastError());
     }
     return DS_OK;
 }

@@ -75,6 +75,7 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
     static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
     static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
     // cvt.rzi.u32.f32: toward zero, negatives and NaN -> 0, saturates at 2^32-1
     static __device__ __forceinline__ uint32_t trunc_u32(float v) { return __float2uint_rz(v); }
     static __device__ __forceinline__ Bits bits(float v) { return __float_as_uint(v); }
@@ -88,6 +89,7 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
     static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
     static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
     static __device__ __forceinline__ uint32_t trunc_u32(double v) { return __double2uint_rz(v); }
     static __device__ __forceinline__ Bits bits(double v) { return (Bits)__double_as_longlong(v); }
     static __device__ __forceinline__ double from_bits(Bits b) { return __longlong_as_double((long long)b); }
@@ -188,7 +190,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
-constexpr uint32_t MBAR_POLL_LIMIT = 1u << 22;
+constexpr uint32_t MBAR_POLL_LIMIT = 1u << 20;
 constexpr uint32_t BULK_CHUNK = 32768;  // bytes per cp.async.bulk
 
 // Stage `bytes` (multiple of 16) from global to shared memory with bulk
@@ -207,6 +209,26 @@ __device__ __forceinline__ bool stage_to_smem(void *dst, const void *src, uint32
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(bar, 0, MBAR_POLL_LIMIT);
+    if (!ok && err) atomicExch(err, (int)DEVERR_TIMEOUT);
+    return __syncthreads_and(ok) != 0;
+}
+
+// Repeated staging through one mbarrier initialised once per block (thread 0
+// called mbar_init and the block synchronised).  The caller synchronises the
+// block before the call so that nobody still reads the previous image;
+// `parity` is the phase being completed (it flips after every staging).
+__device__ __forceinline__ bool stage_again(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                            uint32_t parity, int *err)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += BULK_CHUNK) {
+            const uint32_t n = bytes - off < BULK_CHUNK ? bytes - off : BULK_CHUNK;
+            bulk_g2s((char *)dst + off, (const char *)src + off, n, bar);
+        }
+    }
+    const bool ok = mbar_wait_bounded(bar, parity, MBAR_POLL_LIMIT);
     if (!ok && err) atomicExch(err, (int)DEVERR_TIMEOUT);
     return __syncthreads_and(ok) != 0;
 }

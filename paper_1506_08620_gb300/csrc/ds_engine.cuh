@@ -1,0 +1,57 @@
+// ds_engine.cuh -- host side of the multi-array engine shared by ds_batch and
+// ds_learned: per-array descriptors, one device blob holding every array's
+// image, the chunk planner's scratch, the tuned launch configuration and the
+// cached CUDA graph of a search.
+#pragma once
+
+#include <vector>
+
+#include "ds_multi_kernels.cuh"
+
+namespace ds {
+
+constexpr long long SEG_KNOTS = 1 << 16;  // knots per build segment
+constexpr int CHUNK_TILES = 8;            // tiles per search chunk
+
+struct Engine {
+    int dtype = 0;
+    uint32_t flags = 0;
+    int n_arrays = 0;
+    long long n_knots = 0;
+    DeviceProps props;
+    ArrDesc *desc_dev = nullptr;
+    std::vector<ArrDesc> desc_host;
+    unsigned char *blob = nullptr;
+    size_t blob_bytes = 0;
+    size_t table_bytes = 0;
+    long long *chunk_off = nullptr;
+    unsigned long long *counter = nullptr;  // [0] chunk counter, [1] certificate failures
+    int *dev_err = nullptr;
+    float *seg_x = nullptr, *seg_a = nullptr, *seg_b = nullptr;
+    ds_tune_t tune = {};
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    const void *gkey[6] = {};
+    ds_tune_t gtune = {};
+    long long h_updates = 0;
+    unsigned long long R_total = 0;
+    int n_direct = 0, n_learned = 0, n_fallback = 0;
+    double build_ms = 0;
+};
+
+// Validate, ComputeHR per array, lay out and fill all tables.  Arrays with
+// force_other[a] set (or infeasible for direct search) get mode other_mode
+// (MODE_LEARNED) or MODE_BISECT.
+ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
+                       uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
+                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out);
+ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
+                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s);
+ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
+                        void *y_out, int32_t *I, cudaStream_t s);
+ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
+                          cudaStream_t s, ds_tune_t *best_out);
+void engine_free(Engine *e);
+ds_tune_t default_tune();
+
+}  // namespace ds

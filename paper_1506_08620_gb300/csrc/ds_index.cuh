@@ -17,14 +17,13 @@ struct ds_index {
     unsigned long long R;
     long long updates, passes;
     double build_ms;
-    unsigned char *tab;   // [K: (R+1) int32, padded to 16 B][X copy: N+1 values, padded to 16 B]
+    unsigned char *tab;   // [K: (R+1) uint32 (bit 31: cell holds a knot), padded to 16 B][X copy: N+1 values, padded]
     size_t k_bytes, x_bytes;
     void *pairs;          // (R+1) Pair<T> when DS_CACHE_LAYOUT
     size_t pair_bytes;
     size_t table_bytes;
     ds::SearchPlan plan;
     uint32_t smem_bytes;
-    int x0zero;
     int *dev_err;
     ds::DeviceProps props;
     ds::HostPipe *pipe;
@@ -192,12 +191,13 @@ __global__ void k_fill_F(const T *__restrict__ X, long long n_knots, T H, T W, u
 }
 
 // K_j = min{ i : F_i >= j }, j = 0..R (Eq. indexdef: K_j = i for
-// F_{i-1} < j <= F_i, K_j = 0 for j <= F_0).  One warp per 32 consecutive
-// knots writes the concatenation of their cell runs with coalesced stores;
-// each lane finds the knot of its cell by a 5-step search over the 32 F
-// values held in the warp's registers.
+// F_{i-1} < j <= F_i, K_j = 0 for j <= F_0), stored with bit 31 set when the
+// cell holds knot K_j (F_{K_j} == j).  One warp per 32 consecutive knots
+// writes the concatenation of their cell runs with coalesced stores; each lane
+// finds the knot of its cell by a 5-step search over the 32 F values held in
+// the warp's registers.
 template <typename T>
-__global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, int32_t *__restrict__ K,
+__global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, uint32_t *__restrict__ K,
                          Pair<T> *__restrict__ pairs, const T *__restrict__ X)
 {
     const int lane = threadIdx.x & 31;
@@ -218,12 +218,14 @@ __global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, int3
                 const uint32_t Fc = __shfl_sync(0xffffffffu, Fi, k + s - 1);
                 if ((long long)Fc < j) k += s;
             }
+            const uint32_t Fk = __shfl_sync(0xffffffffu, Fi, k);
             if (j <= last) {
                 const int32_t kk = (int32_t)(c * 32 + k);
-                K[j] = kk;
+                const uint32_t entry = (uint32_t)kk | ((long long)Fk == j ? KNOT_FLAG : 0u);
+                K[j] = entry;
                 if (pairs) {
                     Pair<T> p;
-                    p.k = kk;
+                    p.k = (int32_t)entry;
                     if constexpr (sizeof(T) == 8) p.pad = 0;
                     p.x = X[kk];
                     pairs[j] = p;
@@ -232,6 +234,10 @@ __global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, int3
         }
     }
 }
+
+// Clear the knot flag (bit 31) of every stride-th 32-bit word: turns a copy of
+// the flagged table into the plain K of Eq. indexdef.
+__global__ void k_clear_flags(uint32_t *p, long long count, int stride);
 
 // host side, defined in ds_build.cu
 ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, cudaStream_t s,

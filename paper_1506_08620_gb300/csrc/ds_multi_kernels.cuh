@@ -1,0 +1,393 @@
+// ds_multi_kernels.cuh -- the persistent ragged search kernel and the
+// segmented build kernels shared by the batched and learned forms.
+#pragma once
+
+#include "ds_index.cuh"
+#include "ds_multi.cuh"
+
+namespace ds {
+
+// ------------------------------------------------------------------ learned predictor
+// Float32 image of a query for the predictor: z - X0 scaled to [0, 1].  For
+// float64 arrays the query is first narrowed to float32 by truncating its
+// significand (integer instructions only; any fixed narrowing is valid
+// because the error bound is recorded with this same function).
+template <typename T> __device__ __forceinline__ float narrow(T z);
+template <> __device__ __forceinline__ float narrow<float>(float z) { return z; }
+template <> __device__ __forceinline__ float narrow<double>(double z)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(z);
+    const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if (e == 1024) return __uint_as_float(s | 0x7F800000u | (unsigned)((b & 0x000FFFFFFFFFFFFFull) != 0));
+    if (e > 127) return __uint_as_float(s | 0x7F800000u);
+    if (e < -126) return __uint_as_float(s);
+    return __uint_as_float(s | ((unsigned)(e + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+template <typename T>
+__device__ __forceinline__ float pred_u(T z, const ArrDesc &d)
+{
+    return __fmul_rn(__fsub_rn(narrow<T>(z), narrow<T>((T)d.X0)), (float)d.uscale);
+}
+
+// Piecewise-linear served form of the network: segment k covers
+// [seg_x[k], seg_x[k+1]) (seg_x[0] = -inf), value seg_a[k] * u + seg_b[k].
+__device__ __forceinline__ float pred_eval(float u, const float *sx, const float *sa, const float *sb, int n,
+                                           int top)
+{
+    int k = 0;
+    for (int s = top; s > 0; s >>= 1) {
+        const int r = k + s;
+        if (r < n && sx[r] <= u) k = r;
+    }
+    return __fmaf_rn(sa[k], u, sb[k]);
+}
+
+__device__ __forceinline__ int32_t floor_clamped(float p, int32_t n)
+{
+    // floor, with NaN and out-of-range predictions pinned inside [-2^30, 2^30]
+    if (!(p > -1073741824.0f)) p = -1073741824.0f;
+    if (p > 1073741824.0f) p = 1073741824.0f;
+    return __float2int_rd(p);
+}
+
+// Window [lo, hi] around the prediction (both clamped into [0, N-1]).
+__device__ __forceinline__ void window_of(int32_t pf, const ArrDesc &d, int32_t *lo, int32_t *hi)
+{
+    long long l = (long long)pf - d.e_lo - 1, h = (long long)pf + d.e_hi + 1;
+    const long long nm1 = d.n - 1;
+    l = l < 0 ? 0 : (l > nm1 ? nm1 : l);
+    h = h < 0 ? 0 : (h > nm1 ? nm1 : h);
+    *lo = (int32_t)l;
+    *hi = (int32_t)h;
+}
+
+// ------------------------------------------------------------------ NQ queries of one array
+template <typename T, int NQ>
+__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
+                                             const T *z, int32_t *r)
+{
+    if (d.mode == MODE_DIRECT) {
+        uint32_t e[NQ];
+        T x[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) e[q] = K[cell_rt<T>(z[q], d)];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) x[q] = (e[q] & KNOT_FLAG) ? X[e[q] & ~KNOT_FLAG] : T(0);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) r[q] = correct<T, true>(z[q], e[q], x[q], a.checked);
+        return;
+    }
+    int32_t lo[NQ], n[NQ], top;
+    bool done[NQ];
+    if (d.mode == MODE_LEARNED) {
+        const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
+        int stop = 1;
+        while (stop * 2 <= d.seg_n) stop *= 2;
+        int32_t hi[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float p = pred_eval(pred_u<T>(z[q], d), sx, sa, sb, d.seg_n, stop);
+            window_of(floor_clamped(p, d.n), d, &lo[q], &hi[q]);
+        }
+        T xl[NQ], xh[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            xl[q] = X[lo[q]];
+            xh[q] = X[hi[q] + 1];
+        }
+        int nfail = 0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            // certificate X_lo <= z < X_{hi+1}; otherwise the exact full search
+            const bool ok = !lt_exact<T>(z[q], xl[q]) && lt_exact<T>(z[q], xh[q]);
+            if (ok) {
+                n[q] = hi[q] + 1 - lo[q];
+            } else {
+                lo[q] = 0;
+                n[q] = d.n;
+                ++nfail;
+            }
+            done[q] = false;
+        }
+        if (nfail) {
+            atomicAdd(a.fallbacks, (unsigned long long)nfail);
+            top = d.pbits;
+        } else {
+            top = d.wbits;
+        }
+        // the full search also needs the out-of-range answers
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (n[q] == d.n && lo[q] == 0) {
+                if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
+                else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            lo[q] = 0;
+            n[q] = d.n;
+            done[q] = false;
+            if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
+            else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
+        }
+        top = d.pbits;
+    }
+    // interleaved fixed-depth bisection (Algorithm binaryoptnopad)
+    int32_t i[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) i[q] = 0;
+    for (int32_t k = top; k > 0; k >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t rr = i[q] | k;
+            const int32_t w = rr < n[q] ? rr : n[q];
+            if (!lt_exact<T>(z[q], X[lo[q] + w])) i[q] = rr;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        if (!done[q]) r[q] = lo[q] + (i[q] < n[q] ? i[q] : n[q] - 1);
+        if (a.checked && is_nan<T>(z[q])) r[q] = -1;
+    }
+}
+
+template <typename T, int VPT, bool INTERP, bool VEC>
+__device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
+                                              long long zs, long long ze)
+{
+    constexpr int L = VecOf<T>::L;
+    long long va, vb;
+    if constexpr (VEC) {
+        va = (zs + L - 1) / L * L;
+        if (va > ze) va = ze;
+        vb = va + (ze - va) / L * L;
+    } else {
+        va = ze;
+        vb = ze;
+    }
+    // scalar head and tail
+    for (long long q = zs + threadIdx.x; q < va; q += blockDim.x) {
+        T z = a.Z[q];
+        int32_t r;
+        answer_block<T, 1>(a, d, K, X, &z, &r);
+        a.I[q] = r;
+        interp_store<T, INTERP>(a, d, X, q, z, r);
+    }
+    for (long long q = vb + threadIdx.x; q < ze; q += blockDim.x) {
+        T z = a.Z[q];
+        int32_t r;
+        answer_block<T, 1>(a, d, K, X, &z, &r);
+        a.I[q] = r;
+        interp_store<T, INTERP>(a, d, X, q, z, r);
+    }
+    if constexpr (VEC) {
+        using V = typename VecOf<T>::V;
+        using IV = typename VecOf<T>::IV;
+        constexpr int NQ = VPT * L;
+        const long long v0 = va / L, nv = (vb - va) / L;
+        const V *Zv = reinterpret_cast<const V *>(a.Z) + v0;
+        IV *Iv = reinterpret_cast<IV *>(a.I) + v0;
+        for (long long base = threadIdx.x; base < nv; base += (long long)VPT * blockDim.x) {
+            V zv[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const long long idx = base + (long long)v * blockDim.x;
+                zv[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
+            }
+            const T *zs4 = reinterpret_cast<const T *>(zv);
+            int32_t r[NQ];
+            answer_block<T, NQ>(a, d, K, X, zs4, r);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const long long idx = base + (long long)v * blockDim.x;
+                if (idx < nv) {
+                    IV o;
+                    if constexpr (L == 4) o = make_int4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+                    else o = make_int2(r[2 * v], r[2 * v + 1]);
+                    __stcs(Iv + idx, o);
+                    if constexpr (INTERP) {
+#pragma unroll
+                        for (int l = 0; l < L; ++l)
+                            interp_store<T, INTERP>(a, d, X, (v0 + idx) * L + l, zs4[v * L + l], r[v * L + l]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int VPT, bool INTERP, bool VEC>
+__global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ long long s_c;
+    __shared__ int s_a;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    int staged = -1;
+    const long long total = a.chunk_off[a.n_arrays];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const long long c = (long long)atomicAdd(a.counter, 1ull);
+            int arr = -1;
+            if (c < total) {
+                int lo = 0, hi = a.n_arrays - 1;  // largest array with chunk_off <= c
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.chunk_off[mid] <= c) lo = mid;
+                    else hi = mid - 1;
+                }
+                arr = lo;
+            }
+            s_c = c;
+            s_a = arr;
+        }
+        __syncthreads();
+        const long long c = s_c;
+        const int arr = s_a;
+        if (arr < 0) break;
+        const ArrDesc d = a.desc[arr];
+        const long long zb = q_begin(a.z_off, arr);
+        const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
+        const long long zs = zb + (c - a.chunk_off[arr]) * a.chunk;
+        const long long ze = zs + a.chunk < zend ? zs + a.chunk : zend;
+        const bool use_smem = d.img_bytes > 0 && d.img_bytes <= a.smem_limit;
+        if (use_smem && staged != arr) {
+            if (!stage_again(smem, a.blob + d.img, d.img_bytes, &bar, parity, a.err)) return;
+            parity ^= 1u;
+            staged = arr;
+        }
+        const uint32_t *K;
+        const T *X;
+        if (use_smem) {
+            K = reinterpret_cast<const uint32_t *>(smem);
+            X = reinterpret_cast<const T *>(smem + d.x_in_img);
+        } else {
+            K = reinterpret_cast<const uint32_t *>(a.blob + d.img);
+            X = reinterpret_cast<const T *>(a.blob + d.xg);
+        }
+        process_chunk<T, VPT, INTERP, VEC>(a, d, K, X, zs, ze);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ segmented build kernels
+// A segment is a range of at most SEG_KNOTS knots of one array; blocks walk
+// segments with a grid stride.
+struct Segment {
+    long long lo, hi;  // global knot range [lo, hi)
+    int32_t arr;
+    int32_t pad_;
+};
+
+template <typename T>
+__global__ void k_seg_validate(const T *__restrict__ Xcat, const long long *__restrict__ x_off,
+                               const Segment *__restrict__ segs, int n_segs, HRState *st)
+{
+    using A = Arith<T>;
+    for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
+        const Segment sg = segs[s];
+        const long long start = x_off[sg.arr];
+        const T X0 = Xcat[start];
+        HRState *S = st + sg.arr;
+        unsigned long long gmin = NONE64;
+        for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
+            const T xi = Xcat[i];
+            const long long li = i - start;
+            if (!isfinite(xi)) atomicMin(&S->bad_nonfinite, (unsigned long long)li);
+            if (li >= 1) {
+                const T xp = Xcat[i - 1];
+                if (!(xp < xi)) atomicMin(&S->bad_order, (unsigned long long)li);
+                const T dp = A::sub(xp, X0), di = A::sub(xi, X0);
+                if (dp == di) atomicMin(&S->bad_indist, (unsigned long long)li);
+                const T gap = A::sub(di, dp);
+                if (gap > T(0)) {
+                    const unsigned long long b = (unsigned long long)A::bits(gap);
+                    gmin = b < gmin ? b : gmin;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, gmin, o);
+            gmin = other < gmin ? other : gmin;
+        }
+        if ((threadIdx.x & 31) == 0 && gmin != NONE64) atomicMin(&S->min_gap_bits, gmin);
+    }
+}
+
+template <typename T, bool FMA>
+__global__ void k_seg_hr_init(const T *Xcat, const long long *x_off, int n_arrays, HRState *st)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_arrays) hr_init_one<T, FMA>(Xcat + x_off[a], x_off[a + 1] - x_off[a], st + a);
+}
+
+template <typename T, bool FMA>
+__global__ void k_seg_hr_check(const T *__restrict__ Xcat, const long long *__restrict__ x_off,
+                               const Segment *__restrict__ segs, int n_segs, HRState *st)
+{
+    using A = Arith<T>;
+    for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
+        const Segment sg = segs[s];
+        HRState *S = st + sg.arr;
+        if (S->done) continue;
+        const long long start = x_off[sg.arr];
+        const T H = (T)S->H, W = (T)S->W, X0 = Xcat[start];
+        long long first = start + S->cursor;
+        if (first < sg.lo) first = sg.lo;
+        for (long long i = first + threadIdx.x; i < sg.hi; i += blockDim.x) {
+            const uint32_t fa = A::trunc_u32(fval<T, FMA>(H, W, X0, Xcat[i - 1]));
+            const uint32_t fb = A::trunc_u32(fval<T, FMA>(H, W, X0, Xcat[i]));
+            if (fa == fb) atomicMin(&S->first_violation, (unsigned long long)(i - start));
+        }
+    }
+}
+
+template <typename T, bool FMA>
+__global__ void k_seg_hr_grow(const T *Xcat, const long long *x_off, int n_arrays, HRState *st)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < n_arrays) hr_grow_one<T, FMA>(Xcat + x_off[a], x_off[a + 1] - x_off[a], st + a);
+}
+
+// Copy every array's knots into its place in the blob; cells F_i of the
+// knots of direct arrays into F (packed like Xcat).
+template <typename T>
+__global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *__restrict__ x_off,
+                                  const Segment *__restrict__ segs, int n_segs, const ArrDesc *__restrict__ desc,
+                                  unsigned char *blob, uint32_t *__restrict__ F)
+{
+    using A = Arith<T>;
+    for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
+        const Segment sg = segs[s];
+        const ArrDesc d = desc[sg.arr];
+        const long long start = x_off[sg.arr];
+        T *Xd = reinterpret_cast<T *>(blob + d.xg);
+        const T H = (T)d.H, W = (T)d.W, X0 = (T)d.X0;
+        for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
+            const T x = Xcat[i];
+            Xd[i - start] = x;
+            if (d.mode == MODE_DIRECT) {
+                T v;
+                if (d.form == F_FMA) v = A::fma(H, x, -W);
+                else v = A::mul(H, A::sub(x, X0));
+                F[i] = A::trunc_u32(v);
+            }
+        }
+    }
+}
+
+// Flagged K of every direct array (as k_fill_K); warps walk 32-knot chunks of
+// all direct arrays, chunk -> array through the chunk offsets kc_off.
+__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
+                             const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
+                             unsigned char *blob);
+
+}  // namespace ds

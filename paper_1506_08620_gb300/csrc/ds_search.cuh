@@ -8,22 +8,32 @@
 // it stays L2-resident, or staged once per block into shared memory with a
 // bulk asynchronous copy when it fits.  Blocks are persistent: the grid is one
 // wave of resident blocks and each block walks tiles with a grid stride.
+//
+// Table entries carry a flag in bit 31: set when a knot lies in the cell
+// (F_t == j for t = K_j).  A query z in a cell without a knot satisfies
+// f(z) = j < F_t = f(X_t), so z < X_t by the monotonicity of f (property
+// monotonic of Eq. fprop) and the answer is t - 1 without reading X_t; only
+// queries in a cell that holds a knot need the correcting comparison.
 #pragma once
 
 #include "ds_common.cuh"
 
 namespace ds {
 
+// the three forms of f
+enum FForm : int { F_PLAIN = 0, F_FMA = 1, F_PLAIN_X0ZERO = 2 };
+
+constexpr uint32_t KNOT_FLAG = 0x80000000u;
+
 template <typename T> struct SearchArgs {
-    const int32_t *K;     // R+1 cells (Eq. indexdef)
+    const uint32_t *K;    // R+1 cells (Eq. indexdef), flag in bit 31
     const T *X;           // N+1 knots
-    const Pair<T> *P;     // R+1 (K_j, X_{K_j}) pairs (cache layout)
+    const Pair<T> *P;     // R+1 (K_j | flag, X_{K_j}) pairs (cache layout)
     const void *smem_src; // contiguous image staged to shared memory
     uint32_t smem_bytes;  // bytes of the image (multiple of 16)
     uint32_t x_smem_off;  // byte offset of X inside the image
     T H, W, X0;
     uint32_t R;
-    int x0zero;           // X_0 == 0: z - X_0 == z exactly, the subtraction is skipped
     int checked;          // NaN -> -1
     const T *Z;
     int32_t *I;
@@ -35,41 +45,43 @@ template <typename T> struct VecOf;
 template <> struct VecOf<float> { using V = float4; using IV = int4; static constexpr int L = 4; };
 template <> struct VecOf<double> { using V = double2; using IV = int2; static constexpr int L = 2; };
 
-// Cell of a query: j = min(f(z), R) (Eq. function / Eq. fma).
-template <typename T, bool FMA, bool INTOPS>
+// Cell of a query: j = min(f(z), R).  F_PLAIN: trunc(m(H m(z - X0)))
+// (Eq. function); F_PLAIN_X0ZERO: the same with X0 == 0, where m(z - 0) == z
+// exactly; F_FMA: trunc(m(H z - W)) (Eq. fma).  Exactly one floating-point
+// operation of the array's precision per query besides the conversion, and
+// for float64 with INTOPS the conversion is done on the bit pattern by
+// integer instructions (the FP64 pipe is the scarce one on GB300).
+template <typename T, int FM, bool INTOPS>
 __device__ __forceinline__ uint32_t cell_of(T z, const SearchArgs<T> &a)
 {
     using A = Arith<T>;
     T v;
-    if constexpr (FMA) {
-        v = A::fma(a.H, z, -a.W);
-    } else {
-        v = A::mul(a.H, a.x0zero ? z : A::sub(z, a.X0));
-    }
+    if constexpr (FM == F_FMA) v = A::fma(a.H, z, -a.W);
+    else if constexpr (FM == F_PLAIN_X0ZERO) v = A::mul(a.H, z);
+    else v = A::mul(a.H, A::sub(z, a.X0));
     uint32_t j;
     if constexpr (INTOPS && sizeof(T) == 8) j = trunc_u32_bits((double)v);
     else j = A::trunc_u32(v);
     return min(j, a.R);
 }
 
-// Gather of the table entry of cell j: t = K_j and x = X_t (two dependent
-// reads), or the pair (K_j, X_{K_j}) in one read (cache layout).
+// Table entry of cell j: flagged t = K_j, and for the cache layout X_{K_j}.
 template <typename T, bool CACHE, bool SMEM>
-__device__ __forceinline__ int32_t gather_k(uint32_t j, const int32_t *K, const Pair<T> *P, T *x_out)
+__device__ __forceinline__ uint32_t gather_k(uint32_t j, const uint32_t *K, const Pair<T> *P, T *x_out)
 {
     if constexpr (CACHE) {
         if constexpr (SMEM) {
             const Pair<T> p = P[j];
             *x_out = p.x;
-            return p.k;
+            return (uint32_t)p.k;
         } else if constexpr (sizeof(T) == 4) {
             const int2 p = __ldg(reinterpret_cast<const int2 *>(P) + j);
             *x_out = __int_as_float(p.y);
-            return p.x;
+            return (uint32_t)p.x;
         } else {
             const longlong2 p = __ldg(reinterpret_cast<const longlong2 *>(P) + j);
             *x_out = __longlong_as_double(p.y);
-            return (int32_t)(p.x & 0xFFFFFFFFll);
+            return (uint32_t)(p.x & 0xFFFFFFFFll);
         }
     } else {
         if constexpr (SMEM) return K[j];
@@ -84,30 +96,43 @@ __device__ __forceinline__ T gather_x(int32_t t, const T *X)
     else return __ldg(X + t);
 }
 
-// Correction step: i = t - [z < X_t]; NaN -> -1 when checked.
-template <typename T, bool INTOPS>
-__device__ __forceinline__ int32_t correct(T z, int32_t t, T x, int checked)
+template <typename T> __device__ __forceinline__ bool is_nan(T z);
+template <> __device__ __forceinline__ bool is_nan<float>(float z) { return !(z == z); }
+template <> __device__ __forceinline__ bool is_nan<double>(double z)
 {
-    bool lt;
-    if constexpr (INTOPS && sizeof(T) == 8) lt = okey((double)z) < okey((double)x);
-    else lt = z < x;
+    return ((unsigned long long)__double_as_longlong(z) & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+}
+
+// Correction step: i = t - [z < X_t] (the comparison only where the cell
+// holds a knot); NaN -> -1 when checked.
+template <typename T, bool INTOPS>
+__device__ __forceinline__ int32_t correct(T z, uint32_t e, T x, int checked)
+{
+    const int32_t t = (int32_t)(e & ~KNOT_FLAG);
+    bool lt = true;
+    if (e & KNOT_FLAG) {
+        if constexpr (INTOPS && sizeof(T) == 8) lt = okey((double)z) < okey((double)x);
+        else lt = z < x;
+    }
     int32_t i = t - (int32_t)lt;
-    if (checked && !(z == z)) i = -1;
+    if (checked && is_nan<T>(z)) i = -1;
     return i;
 }
 
-template <typename T, bool FMA, bool CACHE, bool SMEM, bool INTOPS>
-__device__ __forceinline__ int32_t lookup(T z, const int32_t *K, const T *X, const Pair<T> *P,
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS>
+__device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, const Pair<T> *P,
                                           const SearchArgs<T> &a)
 {
-    const uint32_t j = cell_of<T, FMA, INTOPS>(z, a);
-    T x;
-    const int32_t t = gather_k<T, CACHE, SMEM>(j, K, P, &x);
-    if constexpr (!CACHE) x = gather_x<T, SMEM>(t, X);
-    return correct<T, INTOPS>(z, t, x, a.checked);
+    const uint32_t j = cell_of<T, FM, INTOPS>(z, a);
+    T x = T(0);
+    const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x);
+    if constexpr (!CACHE) {
+        if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
+    }
+    return correct<T, INTOPS>(z, e, x, a.checked);
 }
 
-template <typename T, bool FMA, bool CACHE, bool SMEM, bool INTOPS, int VPT>
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, int VPT>
 __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long nvec, long long ntiles)
 {
     using V = typename VecOf<T>::V;
@@ -116,12 +141,12 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
 
-    const int32_t *K;
+    const uint32_t *K;
     const T *X;
     const Pair<T> *P;
     if constexpr (SMEM) {
         if (!stage_to_smem(smem, a.smem_src, a.smem_bytes, &bar, a.err)) return;
-        K = reinterpret_cast<const int32_t *>(smem);
+        K = reinterpret_cast<const uint32_t *>(smem);
         X = reinterpret_cast<const T *>(smem + a.x_smem_off);
         P = reinterpret_cast<const Pair<T> *>(smem);
     } else {
@@ -140,33 +165,35 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
             const long long idx = b + (long long)v * blockDim.x;
             if (idx < nvec) zv[v] = __ldcs(Zv + idx);
         }
-        // phase 1: cells; phase 2: all K gathers; phase 3: all X gathers;
-        // phase 4: corrections -- every gather of the thread is in flight at once
+        // phase 1: cells; phase 2: all table gathers; phase 3: the knot gathers
+        // of cells that hold a knot; phase 4: corrections.  Every gather of the
+        // thread is in flight at once.
         constexpr int NQ = VPT * L;
         const T *zs = reinterpret_cast<const T *>(zv);
-        uint32_t j[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) j[q] = cell_of<T, FMA, INTOPS>(zs[q], a);
-        int32_t t[NQ];
+        uint32_t e[NQ];
         T x[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) t[q] = gather_k<T, CACHE, SMEM>(j[q], K, P, &x[q]);
+        for (int q = 0; q < NQ; ++q) {
+            x[q] = T(0);
+            e[q] = cell_of<T, FM, INTOPS>(zs[q], a);
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q]);
         if constexpr (!CACHE) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) x[q] = gather_x<T, SMEM>(t[q], X);
+            for (int q = 0; q < NQ; ++q)
+                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & ~KNOT_FLAG), X);
         }
-        int32_t r[VPT][L];
+        int32_t r[NQ];
 #pragma unroll
-        for (int v = 0; v < VPT; ++v)
-#pragma unroll
-            for (int l = 0; l < L; ++l) r[v][l] = correct<T, INTOPS>(zs[v * L + l], t[v * L + l], x[v * L + l], a.checked);
+        for (int q = 0; q < NQ; ++q) r[q] = correct<T, INTOPS>(zs[q], e[q], x[q], a.checked);
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const long long idx = b + (long long)v * blockDim.x;
             if (idx < nvec) {
                 IV o;
-                if constexpr (L == 4) o = make_int4(r[v][0], r[v][1], r[v][2], r[v][3]);
-                else o = make_int2(r[v][0], r[v][1]);
+                if constexpr (L == 4) o = make_int4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+                else o = make_int2(r[2 * v], r[2 * v + 1]);
                 __stcs(Iv + idx, o);
             }
         }
@@ -174,21 +201,22 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
     // the last m mod L queries
     if (blockIdx.x == 0) {
         const long long q = nvec * L + threadIdx.x;
-        if (q < a.m) a.I[q] = lookup<T, FMA, CACHE, SMEM, INTOPS>(a.Z[q], K, X, P, a);
+        if (q < a.m) a.I[q] = lookup<T, FM, CACHE, SMEM, INTOPS>(a.Z[q], K, X, P, a);
     }
 }
 
 // Scalar path for queries or results that are not aligned for vector access.
-template <typename T, bool FMA, bool CACHE, bool INTOPS>
+template <typename T, int FM, bool CACHE, bool INTOPS>
 __global__ void __launch_bounds__(256) k_search_scalar(SearchArgs<T> a)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride)
-        a.I[q] = lookup<T, FMA, CACHE, false, INTOPS>(a.Z[q], a.K, a.X, a.P, a);
+        a.I[q] = lookup<T, FM, CACHE, false, INTOPS>(a.Z[q], a.K, a.X, a.P, a);
 }
 
 struct SearchPlan {
-    bool fma, cache, smem, intops;
+    int form;      // FForm
+    bool cache, smem, intops;
     int block;     // threads per block
     int vpt;       // vectors per thread per tile
     int grid_cap;  // resident blocks (one wave)

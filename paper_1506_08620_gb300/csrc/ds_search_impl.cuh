@@ -7,45 +7,57 @@
 
 namespace ds {
 
-template <typename T, bool FMA, bool CACHE, bool SMEM>
+template <typename T, int FM, bool CACHE, bool SMEM>
 static const void *pick_vec4(bool intops)
 {
     if constexpr (sizeof(T) == 8) {
-        if (intops) return (const void *)k_search_vec<T, FMA, CACHE, SMEM, true, SEARCH_VPT>;
+        if (intops) return (const void *)k_search_vec<T, FM, CACHE, SMEM, true, SEARCH_VPT>;
     }
     (void)intops;
-    return (const void *)k_search_vec<T, FMA, CACHE, SMEM, false, SEARCH_VPT>;
+    return (const void *)k_search_vec<T, FM, CACHE, SMEM, false, SEARCH_VPT>;
 }
-template <typename T, bool FMA, bool CACHE>
+template <typename T, int FM, bool CACHE>
 static const void *pick_vec3(bool smem, bool intops)
 {
-    return smem ? pick_vec4<T, FMA, CACHE, true>(intops) : pick_vec4<T, FMA, CACHE, false>(intops);
+    return smem ? pick_vec4<T, FM, CACHE, true>(intops) : pick_vec4<T, FM, CACHE, false>(intops);
 }
-template <typename T, bool FMA>
+template <typename T, int FM>
 static const void *pick_vec2(bool cache, bool smem, bool intops)
 {
-    return cache ? pick_vec3<T, FMA, true>(smem, intops) : pick_vec3<T, FMA, false>(smem, intops);
+    return cache ? pick_vec3<T, FM, true>(smem, intops) : pick_vec3<T, FM, false>(smem, intops);
 }
 template <typename T>
 static const void *pick_vec(const SearchPlan &p)
 {
-    return p.fma ? pick_vec2<T, true>(p.cache, p.smem, p.intops) : pick_vec2<T, false>(p.cache, p.smem, p.intops);
+    switch (p.form) {
+    case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops);
+    case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops);
+    default: return pick_vec2<T, F_PLAIN>(p.cache, p.smem, p.intops);
+    }
 }
 
-template <typename T, bool FMA, bool CACHE>
+template <typename T, int FM, bool CACHE>
 static const void *pick_scalar3(bool intops)
 {
     if constexpr (sizeof(T) == 8) {
-        if (intops) return (const void *)k_search_scalar<T, FMA, CACHE, true>;
+        if (intops) return (const void *)k_search_scalar<T, FM, CACHE, true>;
     }
     (void)intops;
-    return (const void *)k_search_scalar<T, FMA, CACHE, false>;
+    return (const void *)k_search_scalar<T, FM, CACHE, false>;
+}
+template <typename T, int FM>
+static const void *pick_scalar2(bool cache, bool intops)
+{
+    return cache ? pick_scalar3<T, FM, true>(intops) : pick_scalar3<T, FM, false>(intops);
 }
 template <typename T>
 static const void *pick_scalar(const SearchPlan &p)
 {
-    if (p.fma) return p.cache ? pick_scalar3<T, true, true>(p.intops) : pick_scalar3<T, true, false>(p.intops);
-    return p.cache ? pick_scalar3<T, false, true>(p.intops) : pick_scalar3<T, false, false>(p.intops);
+    switch (p.form) {
+    case F_FMA: return pick_scalar2<T, F_FMA>(p.cache, p.intops);
+    case F_PLAIN_X0ZERO: return pick_scalar2<T, F_PLAIN_X0ZERO>(p.cache, p.intops);
+    default: return pick_scalar2<T, F_PLAIN>(p.cache, p.intops);
+    }
 }
 
 template <typename T>

@@ -11,8 +11,8 @@ from tests import exact
 
 
 # ---------------------------------------------------------------- worked examples
-def test_section_4_2_example_h3_is_admissible():
-    # Section 4.2: X = {0, 0.5, 0.7, 1.1} admits H = 3 although Eq. minh gives ~6.36.
+def test_section_4_1_example_h3_is_admissible():
+    # Section 4.1: X = {0, 0.5, 0.7, 1.1} admits H = 3 although Eq. minh gives ~6.36.
     X = np.array([0.0, 0.5, 0.7, 1.1])
     R = exact.trunc_u32(exact.mul(3.0, 1.1, np.float64))
     assert R == 3
@@ -23,7 +23,7 @@ def test_section_4_2_example_h3_is_admissible():
     assert np.array_equal(oracle.direct(X, K, 3.0, 0.0, R, Z), oracle.upper_bound(X, Z))
 
 
-def test_section_4_2_example_compute_hr():
+def test_section_4_1_example_compute_hr():
     # min m(D_{i+1}-D_i) = m(0.7-0.5) = 0.19999999999999996; m(1/that) = 5.000000000000001;
     # H = phi(.) = 5.000000000000002; R = trunc(m(H*1.1)) = trunc(5.500000000000002) = 5.
     X = np.array([0.0, 0.5, 0.7, 1.1])
