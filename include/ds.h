@@ -260,6 +260,36 @@ DS_API ds_status ds_adam_step(float *theta_dev, float *m_dev, float *v_dev, cons
                        void *stream);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free table build.  The paper has no counterpart to this entry
+ * point; it exists for callers that may not allocate device memory when
+ * they build a table: code under a host framework that owns every device
+ * allocation (a fixed pool handed out at start-up), real-time loops where the
+ * implicit device synchronisation of cudaMalloc/cudaFree is not acceptable,
+ * and plug-ins that are forbidden to allocate after initialisation.
+ *
+ * It computes H, W and R exactly as ds_build does (ComputeHR, Section 4.4)
+ * and writes the K table of Eq. indexdef (R+1 int32) into the caller's
+ * buffer K_out_dev of K_capacity entries.  Its scratch is a fixed array inside
+ * the library's device image: DS_STATIC_MAX_KNOTS cells (4 bytes each) plus
+ * one 256-byte ComputeHR state, about 1 MiB, held by every GPU that loads the
+ * library until the process exits.  Arrays with more than DS_STATIC_MAX_KNOTS
+ * knots are rejected with DS_E_ARG; a K buffer smaller than R+1 entries is
+ * rejected with DS_E_ARG after *R_out has been set, so the caller can size a
+ * new buffer.  The call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine) and returns after the table is written.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  Every call uses the same scratch and re-initialises the parts
+ * that must start from a known value; calls whose GPU work overlaps (from two
+ * streams or two host threads) race on the scratch.  flags: 0 or DS_FMA.
+ * ------------------------------------------------------------------------ */
+#define DS_STATIC_MAX_KNOTS 262144
+DS_API ds_status ds_build_table_static(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags,
+                                       int32_t *K_out_dev, int64_t K_capacity, double *H_out, double *W_out,
+                                       uint64_t *R_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Handles and diagnostics.
  * ------------------------------------------------------------------------ */
 DS_API ds_status ds_info(const void *handle, ds_info_t *out); /* any handle */

@@ -34,6 +34,8 @@ DS_STRICT = 16
 DS_LEARNED_FORCE = 1
 DS_LEARNED_LINEAR = 2
 
+DS_STATIC_MAX_KNOTS = 262144
+
 P = ctypes.c_void_p
 I32 = ctypes.c_int32
 I64 = ctypes.c_int64
@@ -90,6 +92,8 @@ _SIGS = {
     "ds_mlp_forward": (ST, [P, P, I64, P, P]),
     "ds_mlp_loss_grad": (ST, [P, P, P, I64, P, P, P]),
     "ds_adam_step": (ST, [P, P, P, P, I32, F32, P]),
+    "ds_build_table_static": (ST, [P, I64, ST, U32, P, I64, ctypes.POINTER(F64), ctypes.POINTER(F64),
+                                   ctypes.POINTER(U64), P]),
     "ds_info": (ST, [P, ctypes.POINTER(ds_info_t)]),
     "ds_free": (None, [P]),
     "ds_status_str": (ctypes.c_char_p, [ST]),
