@@ -198,6 +198,9 @@ def workload_config(args):
                                           "2^27 sorted uniform queries", "knots": (1 << 20) + 1, "queries": 1 << 27},
         "direct_f32": {"workload": "direct search f32: 1025 knots, 1,002,048 queries tiled 512x into one stream",
                        "knots": 1025, "queries": 1002048 * 512},
+        "batched_f32": {"workload": "batched direct search f32: 4096 arrays of 16..65536 knots (log-uniform), "
+                                    "2^28 queries in proportion, CSR, one persistent launch", "arrays": 4096,
+                        "queries": 1 << 28},
     }.get(args.workload, {"workload": args.workload})
     base = dict(base)
     base["variant"] = args.variant
@@ -209,6 +212,135 @@ def workload_config(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+class Job:
+    """One timed workload: search() runs one step on device-resident inputs;
+    e2e() runs one step through the public API from pinned host memory."""
+    kernel_key = ""
+    dtype_name = ""
+    launches_per_step = 1
+    bytes_per_lookup = 0
+    m = 0
+    build_ms = 0.0
+    table = None
+    extras = None
+
+
+def setup_direct(args, ds, W, torch, dev, rank):
+    job = Job()
+    flags = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
+             "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT}[args.variant]
+    if args.workload in ("direct_f64", "direct_f64_sorted"):
+        w = W.workload2(seed=W.SEED_BASE + 2 + 1000 * rank if rank else None, m=args.queries or (1 << 27),
+                        sort=args.workload.endswith("sorted"))
+        X, Zh = w["X"], w["Z"]
+        job.bytes_per_lookup, job.dtype_name = 8 + 4, "f64"
+    else:
+        w = W.workload1()
+        X = w["X"]
+        Zh = np.tile(w["Z"], 512)
+        if args.queries:
+            Zh = Zh[: args.queries]
+        job.bytes_per_lookup, job.dtype_name = 4 + 4, "f32"
+    job.m = Zh.size
+    Xd = torch.from_numpy(X).to(dev)
+    Zd = torch.from_numpy(Zh).to(dev)
+    out = torch.empty(job.m, dtype=torch.int32, device=dev)
+    builds = []
+    for k in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        idx = ds.ds_build(Xd, flags)
+        torch.cuda.synchronize()
+        builds.append((time.perf_counter() - t0) * 1e3)
+        if k < 2:
+            idx.free()
+    job.build_ms = float(np.median(builds))
+    info = idx.info()
+    job.table = {"H": info["H"], "R": info["R"], "table_bytes": info["table_bytes"],
+                 "smem_resident": info["smem_resident"], "h_updates": info["h_updates"]}
+    job.kernel_key = "search_%s_%s" % (job.dtype_name, args.variant)
+    job.search = lambda: ds.ds_search(idx, Zd, out)
+    job.out = out
+    job.keep = (idx, Xd, Zd)
+    Zp = torch.from_numpy(Zh).pin_memory()
+    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
+
+    def e2e():
+        ds.ds_search_host(idx, Zp, Ip)
+        return Zp.numel() * Zp.element_size(), Ip.numel() * 4
+    job.e2e = e2e
+    job.e2e_out = Ip
+
+    def extras(stream):
+        res = {}
+        for name, fl in (("fma", ds.DS_FMA), ("cache", ds.DS_CACHE_LAYOUT),
+                         ("fma_cache", ds.DS_FMA | ds.DS_CACHE_LAYOUT), ("plain", 0)):
+            if name == args.variant:
+                continue
+            j = ds.ds_build(Xd, fl)
+            res[name] = job.m / time_calls(torch, stream, lambda: ds.ds_search(j, Zd, out), 5)
+            j.free()
+        if args.workload == "direct_f64":
+            Zs = torch.sort(Zd).values
+            res["sorted_queries_" + args.variant] = job.m / time_calls(torch, stream,
+                                                                       lambda: ds.ds_search(idx, Zs, out), 5)
+            del Zs
+        return res
+    job.extras = extras
+    return job
+
+
+def setup_batched(args, ds, W, torch, dev, rank):
+    job = Job()
+    w = W.workload3(seed=W.SEED_BASE + 3 + 1000 * rank if rank else None, total_queries=args.queries or (1 << 28))
+    job.dtype_name = "f32"
+    job.m = int(w["z_off"][-1])
+    Xd, xo = torch.from_numpy(w["Xcat"]).to(dev), torch.from_numpy(w["x_off"]).to(dev)
+    Zd, zo = torch.from_numpy(w["Zcat"]).to(dev), torch.from_numpy(w["z_off"]).to(dev)
+    out = torch.empty(job.m, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = ds.ds_batch_build(Xd, xo)
+    torch.cuda.synchronize()
+    job.build_ms = (time.perf_counter() - t0) * 1e3
+    info = b.info()
+    tune = ds.ds_batch_autotune(b, Zd, zo, out)
+    job.bytes_per_lookup = 8 + info["table_bytes"] / job.m
+    job.table = {"arrays": info["n_arrays"], "R_total": info["R"], "table_bytes": info["table_bytes"],
+                 "tune": tune}
+    job.kernel_key = "batch_search_f32"
+    job.launches_per_step = 2
+    job.search = lambda: ds.ds_batch_search(b, Zd, zo, out)
+    job.out = out
+    job.keep = (b, Xd, xo, Zd, zo)
+    Zp = torch.from_numpy(w["Zcat"]).pin_memory()
+    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
+    zbuf = torch.empty_like(Zd)
+    obuf = torch.empty_like(out)
+
+    def e2e():
+        zbuf.copy_(Zp, non_blocking=True)
+        ds.ds_batch_search(b, zbuf, zo, obuf)
+        Ip.copy_(obuf, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return Zp.numel() * 4, Ip.numel() * 4
+    job.e2e = e2e
+    job.e2e_out = Ip
+    return job
+
+
+def time_calls(torch, stream, fn, n):
+    for _ in range(2):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n * 1e-3
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -225,46 +357,17 @@ def main():
     import paper_1506_08620_gb300 as ds
     from paper_1506_08620_gb300 import workloads as W
 
-    flags = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
-             "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT}[args.variant]
-    if args.workload in ("direct_f64", "direct_f64_sorted"):
-        w = W.workload2(seed=W.SEED_BASE + 2 + 1000 * rank if rank else None, m=args.queries or (1 << 27),
-                        sort=args.workload.endswith("sorted"))
-        X, Z = w["X"], w["Z"]
-        Zh = Z
-        bytes_per_lookup = 8 + 4
-        dtype_name = "f64"
-    elif args.workload == "direct_f32":
-        w = W.workload1()
-        X = w["X"]
-        Zh = np.tile(w["Z"], 512)
-        if args.queries:
-            Zh = Zh[: args.queries]
-        bytes_per_lookup = 4 + 4
-        dtype_name = "f32"
+    if args.workload.startswith("direct"):
+        job = setup_direct(args, ds, W, torch, dev, rank)
+    elif args.workload == "batched_f32":
+        job = setup_batched(args, ds, W, torch, dev, rank)
     else:
         raise SystemExit("workload %s: not timed by this bench" % args.workload)
-    m = Zh.size
-    Xd = torch.from_numpy(X).to(dev)
-    Zd = torch.from_numpy(Zh).to(dev)
-    out = torch.empty(m, dtype=torch.int32, device=dev)
+    m = job.m
     stream = torch.cuda.current_stream()
 
-    # build (timed separately; the paper reports setup cost apart from throughput)
-    builds = []
-    for _ in range(3):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        idx = ds.ds_build(Xd, flags)
-        torch.cuda.synchronize()
-        builds.append((time.perf_counter() - t0) * 1e3)
-        info = idx.info()
-        if _ < 2:
-            idx.free()
-    build_ms = float(np.median(builds))
-
     for _ in range(max(args.warmup, 3)):
-        ds.ds_search(idx, Zd, out)
+        job.search()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -275,7 +378,7 @@ def main():
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev[0].record(stream)
     for k in range(args.steps):
-        ds.ds_search(idx, Zd, out)
+        job.search()
         ev[k + 1].record(stream)
     torch.cuda.synchronize()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
@@ -289,82 +392,60 @@ def main():
     ms_per_step = total_ms / args.steps
     value = world * m / (ms_per_step * 1e-3)
 
-    # dominant kernel: the search kernel, one launch per step
+    # dominant kernel: the search kernel (one launch per step, plus the chunk planner when batched)
     peak, peak_kind = peaks()
-    achieved = bytes_per_lookup * m / (float(np.mean(per)) * 1e-3) / 1e9
-    kernel_key = "search_%s_%s" % (dtype_name, args.variant)
-    traffic = traffic_for(kernel_key)
+    achieved = job.bytes_per_lookup * m / (float(np.mean(per)) * 1e-3) / 1e9
+    traffic = traffic_for(job.kernel_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": bytes_per_lookup * m, "kernel": kernel_key}
+                "algorithmic_bytes_per_launch": job.bytes_per_lookup * m, "kernel": job.kernel_key}
 
     line = {"metric": "lookups/s", "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": dtype_name, "data": "synthetic", "config": workload_config(args),
-            "roofline": roofline, "gpu_launches": args.steps, "clocks": clk, "build_ms": build_ms,
-            "lookups_per_s_with_build": world * m / ((ms_per_step + build_ms) * 1e-3),
-            "table": {"H": info["H"], "R": info["R"], "table_bytes": info["table_bytes"],
-                      "smem_resident": info["smem_resident"], "h_updates": info["h_updates"]}}
+            "vs_baseline": None, "dtype": job.dtype_name, "data": "synthetic", "config": workload_config(args),
+            "roofline": roofline, "gpu_launches": args.steps * job.launches_per_step, "clocks": clk,
+            "build_ms": job.build_ms, "lookups_per_s_with_build": world * m / ((ms_per_step + job.build_ms) * 1e-3),
+            "table": job.table}
 
-    # end to end through the public API with host buffers (pinned), copies inside the timed region
-    if rank == 0 or world > 1:
-        Zp = torch.from_numpy(Zh).pin_memory()
-        Ip = torch.empty(m, dtype=torch.int32).pin_memory()
-        ds.ds_search_host(idx, Zp, Ip)
-        torch.cuda.synchronize()
-        e2e_steps = max(3, min(args.steps, 10))
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            ds.ds_search_host(idx, Zp, Ip)
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        line["e2e"] = {"value": world * m / e2e_s, "unit": "lookups/s", "h2d_bytes_per_step": Zp.numel() * Zp.element_size(),
-                       "d2h_bytes_per_step": Ip.numel() * 4}
-        if rank == 0:
-            ok = bool(torch.equal(Ip.to(dev), out))
-            line["e2e"]["matches_device_path"] = ok
-        del Zp, Ip
-
-    if rank == 0 and not args.no_extras:
-        extras = {}
-        for name, fl in (("fma", ds.DS_FMA), ("cache", ds.DS_CACHE_LAYOUT), ("fma_cache", ds.DS_FMA | ds.DS_CACHE_LAYOUT),
-                         ("plain", 0)):
-            if name == args.variant:
-                continue
-            j = ds.ds_build(Xd, fl)
-            for _ in range(3):
-                ds.ds_search(j, Zd, out)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(5):
-                ds.ds_search(j, Zd, out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            extras[name] = m / (e0.elapsed_time(e1) / 5 * 1e-3)
-            j.free()
-        if args.workload == "direct_f64":
-            Zs = torch.sort(Zd).values
-            for _ in range(3):
-                ds.ds_search(idx, Zs, out)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(5):
-                ds.ds_search(idx, Zs, out)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            extras["sorted_queries_" + args.variant] = m / (e0.elapsed_time(e1) / 5 * 1e-3)
-            del Zs
-        line["variants_lookups_per_s"] = extras
+    # end to end through the public API from pinned host memory, copies inside the timed region
+    job.e2e()
+    torch.cuda.synchronize()
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        h2d, d2h = job.e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    line["e2e"] = {"value": world * m / e2e_s, "unit": "lookups/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h}
     if rank == 0:
-        line["cpu_baseline"] = cpu_baseline(X, Zh[: 1 << 26], args.cpu_seconds)
+        line["e2e"]["matches_device_path"] = bool(torch.equal(job.e2e_out.to(dev), job.out))
+
+    if rank == 0 and not args.no_extras and job.extras:
+        line["variants_lookups_per_s"] = job.extras(stream)
+    if rank == 0:
+        cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
+        line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds) if args.workload.startswith(
+            "direct") else cpu_baseline_batched(W, args.cpu_seconds)
         print(json.dumps(line), flush=True)
-    idx.free()
     if world > 1:
         dist.destroy_process_group()
+
+
+def cpu_baseline_batched(W, seconds):
+    import oracle
+    w = W.workload3(total_queries=1 << 22)
+    n_arr = len(w["x_off"]) - 1
+    t0 = time.perf_counter()
+    oracle.upper_bound_batch(w["Xcat"], w["x_off"], w["Zcat"], w["z_off"])
+    dt = time.perf_counter() - t0
+    return {"value": w["Zcat"].size / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+            "sample": "%d arrays of the batched workload with 2^22 queries in proportion, one pass, %.1f s"
+                      % (n_arr, dt)}
 
 
 if __name__ == "__main__":

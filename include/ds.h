@@ -211,7 +211,9 @@ DS_API ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double 
  * ------------------------------------------------------------------------ */
 enum {
     DS_LEARNED_FORCE = 1u,    /* use the learned predictor even where direct search is feasible */
-    DS_LEARNED_LINEAR = 2u    /* no network: predict N u (the model "without it", for comparison) */
+    DS_LEARNED_LINEAR = 2u,   /* no network: predict N u (the model "without it", for comparison) */
+    DS_LEARNED_ZERO_BOUND = 4u /* testing: record e_lo = e_hi = 0 instead of the measured bounds, so every
+                                  misprediction must be caught by the window certificate */
 };
 
 typedef struct ds_learned_cfg {

@@ -33,6 +33,7 @@ DS_STRICT = 16
 
 DS_LEARNED_FORCE = 1
 DS_LEARNED_LINEAR = 2
+DS_LEARNED_ZERO_BOUND = 4
 
 DS_STATIC_MAX_KNOTS = 262144
 

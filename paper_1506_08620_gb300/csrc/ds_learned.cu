@@ -1,56 +1,926 @@
-// ds_learned.cu -- learned-index form: MLP training kernels, error bound,
-// bounded-window search with certificate and fall-back, fused interpolation.
+// ds_learned.cu -- learned-index form (not in the paper): a 1 -> 32 -> 32 -> 1
+// ReLU network predicting i / N from u = (z - X_0) / (X_N - X_0), trained on
+// the GPU by the forward/backward/Adam kernels below; served as the network's
+// exact piecewise-linear form; error bound recorded at build time; exact
+// bounded window + certificate + fall-back in the shared ragged search kernel
+// (MODE_LEARNED in ds_multi_kernels.cuh).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <vector>
 
-#include "ds_index.cuh"
+#include "ds_engine.cuh"
 
+namespace ds {
+
+constexpr int HID = 32;
+constexpr int NP = HID + HID + HID * HID + HID + HID + 1;  // 1153
+constexpr int OW1 = 0, OB1 = 32, OW2 = 64, OB2 = 64 + 1024, OW3 = OB2 + 32, OB3 = OW3 + 32;
+constexpr int TB = 128;  // samples (threads) per training block
+constexpr size_t TH_BYTES = ((NP * sizeof(float) + 15) / 16) * 16;  // parameters at the head of shared memory
+constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
+
+// ------------------------------------------------------------------ Philox-4x32-10
+// Counter-based generator of Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64-bit
+// multiplications with the published multipliers and Weyl key increments.
+struct P4 {
+    uint32_t v[4];
+};
+__device__ __forceinline__ P4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    P4 o;
+    o.v[0] = c0;
+    o.v[1] = c1;
+    o.v[2] = c2;
+    o.v[3] = c3;
+    return o;
+}
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ uint32_t below(uint32_t x, uint32_t n) { return (uint32_t)(((uint64_t)x * n) >> 32); }
+
+// ------------------------------------------------------------------ network
+__device__ __forceinline__ float relu(float a) { return a > 0.f ? a : 0.f; }
+
+// Forward and backward of one sample; returns out and fills the per-sample
+// vectors the gradient needs.  dscale = 2 / (batch size).
+__device__ __forceinline__ float mlp_sample(const float *th, float u, float y, float dscale, float *h1, float *da1,
+                                            float *da2, float *h2, float *dout)
+{
+    float a1[HID], a2[HID];
+#pragma unroll
+    for (int m = 0; m < HID; ++m) {
+        a1[m] = __fmaf_rn(th[OW1 + m], u, th[OB1 + m]);
+        h1[m] = relu(a1[m]);
+    }
+#pragma unroll
+    for (int n = 0; n < HID; ++n) {
+        float acc = th[OB2 + n];
+#pragma unroll
+        for (int m = 0; m < HID; ++m) acc = __fmaf_rn(th[OW2 + n * HID + m], h1[m], acc);
+        a2[n] = acc;
+        h2[n] = relu(acc);
+    }
+    float out = th[OB3];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) out = __fmaf_rn(th[OW3 + n], h2[n], out);
+    const float d = dscale * (out - y);
+    *dout = d;
+#pragma unroll
+    for (int n = 0; n < HID; ++n) da2[n] = a2[n] > 0.f ? d * th[OW3 + n] : 0.f;
+#pragma unroll
+    for (int m = 0; m < HID; ++m) {
+        float acc = 0.f;
+#pragma unroll
+        for (int n = 0; n < HID; ++n) acc = __fmaf_rn(th[OW2 + n * HID + m], da2[n], acc);
+        da1[m] = a1[m] > 0.f ? acc : 0.f;
+    }
+    return out;
+}
+
+__device__ __forceinline__ float mlp_forward1(const float *th, float u)
+{
+    float h1[HID];
+#pragma unroll
+    for (int m = 0; m < HID; ++m) h1[m] = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
+    float out = th[OB3];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) {
+        float acc = th[OB2 + n];
+#pragma unroll
+        for (int m = 0; m < HID; ++m) acc = __fmaf_rn(th[OW2 + n * HID + m], h1[m], acc);
+        out = __fmaf_rn(th[OW3 + n], relu(acc), out);
+    }
+    return out;
+}
+
+// Shared-memory tile of one block's samples and the block's gradient sum.
+struct GradTile {
+    float U[TB], DOUT[TB], LOSS[TB];
+    float H1[TB][HID + 1], DA1[TB][HID + 1], DA2[TB][HID + 1], H2[TB][HID + 1];
+};
+
+__device__ __forceinline__ void tile_gradient(const GradTile &t, int count, float *gout)
+{
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        float acc = 0.f;
+        if (p < OB1) {
+            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DA1[s][p], t.U[s], acc);
+        } else if (p < OW2) {
+            for (int s = 0; s < count; ++s) acc += t.DA1[s][p - OB1];
+        } else if (p < OB2) {
+            const int n = (p - OW2) / HID, m = (p - OW2) % HID;
+            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DA2[s][n], t.H1[s][m], acc);
+        } else if (p < OW3) {
+            for (int s = 0; s < count; ++s) acc += t.DA2[s][p - OB2];
+        } else if (p < OB3) {
+            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DOUT[s], t.H2[s][p - OW3], acc);
+        } else {
+            for (int s = 0; s < count; ++s) acc += t.DOUT[s];
+        }
+        gout[p] = acc;
+    }
+}
+
+__device__ __forceinline__ float tile_loss(const GradTile &t, int count)
+{
+    float l = 0.f;
+    for (int s = 0; s < count; ++s) l += t.LOSS[s];
+    return l;
+}
+
+__device__ __forceinline__ void store_sample(GradTile &t, float u, float y, float out, float dout, const float *h1,
+                                             const float *da1, const float *da2, const float *h2)
+{
+    const int s = threadIdx.x;
+    t.U[s] = u;
+    t.DOUT[s] = dout;
+    const float r = out - y;
+    t.LOSS[s] = r * r;
+#pragma unroll
+    for (int m = 0; m < HID; ++m) {
+        t.H1[s][m] = h1[m];
+        t.DA1[s][m] = da1[m];
+        t.DA2[s][m] = da2[m];
+        t.H2[s][m] = h2[m];
+    }
+}
+
+// Gradient of the mean squared error over explicit samples: block b writes
+// the sum over its samples into partial[b][*] and partial_loss[b].
+__global__ void __launch_bounds__(TB) k_grad_explicit(const float *theta, const float *u, const float *y, long long n,
+                                                      float *partial, float *partial_loss)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float *th = reinterpret_cast<float *>(sm_raw);
+    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + TH_BYTES);
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    __syncthreads();
+    const long long i = (long long)blockIdx.x * TB + threadIdx.x;
+    const int count = (int)min((long long)TB, n - (long long)blockIdx.x * TB);
+    if (i < n) {
+        float h1[HID], da1[HID], da2[HID], h2[HID], dout;
+        const float out = mlp_sample(th, u[i], y[i], 2.0f / (float)n, h1, da1, da2, h2, &dout);
+        store_sample(t, u[i], y[i], out, dout, h1, da1, da2, h2);
+    }
+    __syncthreads();
+    tile_gradient(t, count, partial + (size_t)blockIdx.x * NP);
+    if (threadIdx.x == 0) partial_loss[blockIdx.x] = tile_loss(t, count);
+}
+
+__global__ void k_reduce_grad(const float *partial, const float *partial_loss, int nblocks, long long n, float *grad,
+                              float *loss)
+{
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        float acc = 0.f;
+        for (int b = 0; b < nblocks; ++b) acc += partial[(size_t)b * NP + p];
+        grad[p] = acc;
+    }
+    if (threadIdx.x == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nblocks; ++b) l += partial_loss[b];
+        *loss = l / (float)n;
+    }
+}
+
+__device__ __forceinline__ void adam_update(float *theta, float *m, float *v, int p, float g, int t, float lr)
+{
+    const float mm = ADAM_B1 * m[p] + (1.f - ADAM_B1) * g;
+    const float vv = ADAM_B2 * v[p] + (1.f - ADAM_B2) * g * g;
+    m[p] = mm;
+    v[p] = vv;
+    const float mhat = mm / (1.f - powf(ADAM_B1, (float)t));
+    const float vhat = vv / (1.f - powf(ADAM_B2, (float)t));
+    theta[p] -= lr * mhat / (sqrtf(vhat) + ADAM_EPS);
+}
+
+__global__ void k_adam_explicit(float *theta, float *m, float *v, const float *grad, int t, float lr)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NP; p += gridDim.x * blockDim.x)
+        adam_update(theta, m, v, p, grad[p], t, lr);
+}
+
+__global__ void k_forward(const float *theta, const float *u, long long n, float *out)
+{
+    __shared__ float th[NP];
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = mlp_forward1(th, u[i]);
+}
+
+// ------------------------------------------------------------------ training on an array
+struct TrainArgs {
+    const ArrDesc *desc;
+    const unsigned char *blob;
+    const int *model_arr;      // model -> array
+    const float2 *pool;        // (u, i/N) of exact-answer query samples
+    const long long *pool_off; // n_models+1
+    float *theta;              // n_models x NP
+    float *m, *v;              // Adam moments
+    float *partial;            // n_models x gb x NP
+    float *partial_loss;       // n_models x gb
+    float *loss;               // n_models
+    int *step;                 // n_models (1-based step of the next update = step + 1)
+    int gb;                    // blocks per model (batch = gb * TB)
+    int steps;                 // schedule length
+    float lr;
+    uint32_t seed_lo, seed_hi;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    float *th = reinterpret_cast<float *>(sm_raw);
+    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + TH_BYTES);
+    const int model = blockIdx.y;
+    const float *theta = a.theta + (size_t)model * NP;
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    const ArrDesc d = a.desc[a.model_arr[model]];
+    const T *X = reinterpret_cast<const T *>(a.blob + d.xg);
+    const int step = a.step[model];
+    __syncthreads();
+    const P4 r = philox((uint32_t)step, (uint32_t)model, blockIdx.x, threadIdx.x, a.seed_lo, a.seed_hi);
+    const long long p0 = a.pool_off[model], np = a.pool_off[model + 1] - p0;
+    float u, y;
+    if ((r.v[0] & 1u) && np > 0) {
+        const float2 s = a.pool[p0 + below(r.v[1], (uint32_t)np)];
+        u = s.x;
+        y = s.y;
+    } else {
+        const int32_t i = (int32_t)below(r.v[1], (uint32_t)d.n + 1u);
+        u = pred_u<T>(X[i], d);
+        y = (float)i / (float)d.n;
+    }
+    float h1[HID], da1[HID], da2[HID], h2[HID], dout;
+    const float out = mlp_sample(th, u, y, 2.0f / (float)(a.gb * TB), h1, da1, da2, h2, &dout);
+    store_sample(t, u, y, out, dout, h1, da1, da2, h2);
+    __syncthreads();
+    tile_gradient(t, TB, a.partial + ((size_t)model * a.gb + blockIdx.x) * NP);
+    if (threadIdx.x == 0) a.partial_loss[(size_t)model * a.gb + blockIdx.x] = tile_loss(t, TB);
+}
+
+// Adam on each model with a cosine-decayed step size; advances the model's
+// step counter (so a captured graph can be replayed).
+__global__ void k_train_adam(TrainArgs a)
+{
+    const int model = blockIdx.x;
+    const int t = a.step[model] + 1;
+    const float frac = fminf((float)t / (float)a.steps, 1.f);
+    const float lr = a.lr * (0.05f + 0.95f * 0.5f * (1.f + cospif(frac)));
+    float *theta = a.theta + (size_t)model * NP;
+    float *m = a.m + (size_t)model * NP;
+    float *v = a.v + (size_t)model * NP;
+    const float *part = a.partial + (size_t)model * a.gb * NP;
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        float g = 0.f;
+        for (int b = 0; b < a.gb; ++b) g += part[(size_t)b * NP + p];
+        adam_update(theta, m, v, p, g, t, lr);
+    }
+    if (threadIdx.x == 0) {
+        float l = 0.f;
+        for (int b = 0; b < a.gb; ++b) l += a.partial_loss[(size_t)model * a.gb + b];
+        a.loss[model] = l / (float)(a.gb * TB);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.step[model] = t;
+}
+
+// Initial network: hinge units W1 = +-1 with their kinks spread over [0, 1],
+// He-normal W2, small normal w3 (Box-Muller on Philox uniforms).
+__global__ void k_init_params(float *theta, int n_models, uint32_t seed_lo, uint32_t seed_hi)
+{
+    const int model = blockIdx.x;
+    float *th = theta + (size_t)model * NP;
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        const P4 r = philox(0xA5A5A5A5u, (uint32_t)model, (uint32_t)p, 0x5EEDu, seed_lo, seed_hi);
+        const float g = sqrtf(-2.f * logf(fmaxf(u01(r.v[0]), 1e-7f))) * cospif(2.f * u01(r.v[1]));
+        float val = 0.f;
+        if (p < OB1) val = (r.v[2] & 1u) ? 1.f : -1.f;          // W1: +-1
+        else if (p >= OW2 && p < OB2) val = g * sqrtf(2.f / HID);  // W2: He normal
+        else if (p >= OW3 && p < OB3) val = g * (1.f / sqrtf((float)HID));
+        th[p] = val;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < HID; m += blockDim.x) {
+        const P4 r = philox(0x0C0FFEEu, (uint32_t)model, (uint32_t)m, 7u, seed_lo, seed_hi);
+        const float kink = u01(r.v[0]);
+        th[OB1 + m] = -th[OW1 + m] * kink;  // unit m bends at u = kink
+    }
+}
+
+// Exact-answer query samples: z uniform over [X_0, X_N), answered by the
+// fixed-depth bisection over all knots, stored as (u(z), i / N).
+template <typename T>
+__global__ void k_pool_queries(const ArrDesc *desc, const unsigned char *blob, const int *model_arr,
+                               const long long *pool_off, float2 *pool, int n_models, uint32_t seed_lo,
+                               uint32_t seed_hi)
+{
+    const int model = blockIdx.y;
+    const ArrDesc d = desc[model_arr[model]];
+    const T *X = reinterpret_cast<const T *>(blob + d.xg);
+    const long long p0 = pool_off[model], np = pool_off[model + 1] - p0;
+    const T X0 = (T)d.X0, XN = (T)d.XN;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < np; k += (long long)gridDim.x * blockDim.x) {
+        const P4 r = philox((uint32_t)k, (uint32_t)(k >> 32), (uint32_t)model, 0xB0B0u, seed_lo, seed_hi);
+        const double f = ((double)r.v[0] * 4294967296.0 + (double)r.v[1]) * (1.0 / 18446744073709551616.0);
+        T z = (T)((double)X0 + f * ((double)XN - (double)X0));
+        if (!(z < XN)) z = X[d.n - 1];
+        if (z < X0) z = X0;
+        const int32_t i = bisect<T>(X, 0, d.n, d.pbits, z);
+        pool[p0 + k] = make_float2(pred_u<T>(z, d), (float)i / (float)d.n);
+    }
+}
+
+// Error bound of the served predictor: at every knot i (answer i) and at the
+// largest value of every interval, nextafter(X_{i+1}, -inf) (answer i).
+template <typename T> __device__ __forceinline__ T next_down(T x)
+{
+    using A = Arith<T>;
+    if constexpr (sizeof(T) == 8) {
+        const long long k = okey((double)x) - 1;
+        const long long b = k >= 0 ? k : ((-k) | (long long)0x8000000000000000ull);
+        return __longlong_as_double(b);
+    } else {
+        const int ib = __float_as_int(x);
+        const int k = (ib >= 0 ? ib : -(ib & 0x7FFFFFFF)) - 1;
+        const int b = k >= 0 ? k : ((-k) | (int)0x80000000u);
+        return __int_as_float(b);
+    }
+}
+
+template <typename T>
+__global__ void k_error_bound(const ArrDesc *desc, const unsigned char *blob, const int *model_arr,
+                              const float *seg_x, const float *seg_a, const float *seg_b, int *e_lo, int *e_hi)
+{
+    const int model = blockIdx.y;
+    const ArrDesc d = desc[model_arr[model]];
+    const T *X = reinterpret_cast<const T *>(blob + d.xg);
+    const float *sx = seg_x + d.seg_off, *sa = seg_a + d.seg_off, *sb = seg_b + d.seg_off;
+    int top = 1;
+    while (top * 2 <= d.seg_n) top *= 2;
+    int lo = 0, hi = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= d.n; i += (long long)gridDim.x * blockDim.x) {
+        const int32_t pf = floor_clamped(pred_eval(pred_u<T>(X[i], d), sx, sa, sb, d.seg_n, top), d.n);
+        lo = max(lo, (int)min((long long)pf - i, (long long)1 << 30));
+        hi = max(hi, (int)min(i - (long long)pf, (long long)1 << 30));
+        if (i < d.n) {
+            const T z = next_down<T>(X[i + 1]);
+            const int32_t pz = floor_clamped(pred_eval(pred_u<T>(z, d), sx, sa, sb, d.seg_n, top), d.n);
+            lo = max(lo, (int)min((long long)pz - i, (long long)1 << 30));
+            hi = max(hi, (int)min(i - (long long)pz, (long long)1 << 30));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = max(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(e_lo + model, lo);
+        atomicMax(e_hi + model, hi);
+    }
+}
+
+// ------------------------------------------------------------------ piecewise-linear form
+// The network restricted to a scalar input is piecewise linear: its kinks are
+// the zeros of the first layer's units and, between those, the zeros of the
+// second layer's (affine) pre-activations.  Computed in double from the
+// float32 parameters; the served form is whatever these rounded tables give,
+// and the error bound is measured on it.
+struct Segments {
+    std::vector<float> x, a, b;
+};
+
+static void pwl_of(const float *thf, double scale, Segments &out)
+{
+    double W1[HID], b1[HID], W2[HID][HID], b2[HID], w3[HID], b3;
+    for (int m = 0; m < HID; ++m) {
+        W1[m] = thf[OW1 + m];
+        b1[m] = thf[OB1 + m];
+        b2[m] = thf[OB2 + m];
+        w3[m] = thf[OW3 + m];
+        for (int k = 0; k < HID; ++k) W2[m][k] = thf[OW2 + m * HID + k];
+    }
+    b3 = thf[OB3];
+    std::vector<double> bp;
+    for (int m = 0; m < HID; ++m)
+        if (W1[m] != 0.0) {
+            const double t = -b1[m] / W1[m];
+            if (std::isfinite(t) && t > -4.0 && t < 5.0) bp.push_back(t);
+        }
+    std::sort(bp.begin(), bp.end());
+    bp.erase(std::unique(bp.begin(), bp.end()), bp.end());
+    std::vector<double> edges;
+    edges.push_back(-INFINITY);
+    for (double t : bp) edges.push_back(t);
+    edges.push_back(INFINITY);
+    std::vector<double> sx, sa, sb;
+    for (size_t k = 0; k + 1 < edges.size(); ++k) {
+        const double lo = edges[k], hi = edges[k + 1];
+        const double mid = std::isinf(lo) ? (std::isinf(hi) ? 0.5 : hi - 1.0) : (std::isinf(hi) ? lo + 1.0 : 0.5 * (lo + hi));
+        double al[HID], be[HID];
+        for (int m = 0; m < HID; ++m) {
+            const bool on = W1[m] * mid + b1[m] > 0.0;
+            al[m] = on ? W1[m] : 0.0;
+            be[m] = on ? b1[m] : 0.0;
+        }
+        double s[HID], c[HID];
+        for (int n = 0; n < HID; ++n) {
+            double ss = 0, cc = b2[n];
+            for (int m = 0; m < HID; ++m) {
+                ss += W2[n][m] * al[m];
+                cc += W2[n][m] * be[m];
+            }
+            s[n] = ss;
+            c[n] = cc;
+        }
+        std::vector<double> sub;
+        sub.push_back(lo);
+        for (int n = 0; n < HID; ++n)
+            if (s[n] != 0.0) {
+                const double t = -c[n] / s[n];
+                if (t > lo && t < hi && t > -4.0 && t < 5.0) sub.push_back(t);
+            }
+        std::sort(sub.begin() + 1, sub.end());
+        sub.push_back(hi);
+        for (size_t q = 0; q + 1 < sub.size(); ++q) {
+            const double l2 = sub[q], h2 = sub[q + 1];
+            if (!(h2 > l2)) continue;
+            const double m2 = std::isinf(l2) ? (std::isinf(h2) ? 0.5 : h2 - 1.0) : (std::isinf(h2) ? l2 + 1.0 : 0.5 * (l2 + h2));
+            double slope = 0, icpt = b3;
+            for (int n = 0; n < HID; ++n)
+                if (s[n] * m2 + c[n] > 0.0) {
+                    slope += w3[n] * s[n];
+                    icpt += w3[n] * c[n];
+                }
+            sx.push_back(l2);
+            sa.push_back(slope * scale);
+            sb.push_back(icpt * scale);
+        }
+    }
+    out.x.clear();
+    out.a.clear();
+    out.b.clear();
+    for (size_t k = 0; k < sx.size(); ++k) {
+        const float fx = k == 0 ? -INFINITY : (float)sx[k];
+        if (k > 0 && !(fx > out.x.back())) {  // kinks closer than a float apart: keep the later piece
+            out.a.back() = (float)sa[k];
+            out.b.back() = (float)sb[k];
+            continue;
+        }
+        out.x.push_back(fx);
+        out.a.push_back((float)sa[k]);
+        out.b.push_back((float)sb[k]);
+    }
+}
+
+}  // namespace ds
+
+// ------------------------------------------------------------------ handle
 struct ds_learned {
     ds::HandleHeader hdr;
-    int32_t dtype;
+    ds::Engine eng;
+    std::vector<int> model_arr;        // model -> array
+    std::vector<int> arr_model;        // array -> model or -1
+    std::vector<float> theta_host;     // n_models x NP
+    int steps = 0;
+    double train_ms = 0, final_loss = 0;
+    long long max_window = 0;
 };
 
 namespace ds {
-void free_learned(ds_learned *L) { delete L; }
+void free_learned(ds_learned *L)
+{
+    engine_free(&L->eng);
+    L->hdr.magic = 0;
+    delete L;
+}
 ds_status info_learned(const ds_learned *L, ds_info_t *o)
 {
+    const Engine &e = L->eng;
     o->kind = KIND_LEARNED;
-    o->dtype = L->dtype;
+    o->dtype = e.dtype;
+    o->flags = e.flags;
+    o->n_arrays = e.n_arrays;
+    o->n_knots = e.n_knots;
+    o->R = e.R_total;
+    o->table_bytes = (int64_t)e.table_bytes;
+    o->h_updates = e.h_updates;
+    o->build_ms = e.build_ms;
+    o->n_direct = e.n_direct;
+    o->n_learned = e.n_learned;
+    o->n_fallback = e.n_fallback;
+    o->max_window = L->max_window;
+    o->train_steps = L->steps;
+    o->train_ms = L->train_ms;
+    o->final_loss = L->final_loss;
+    if (e.n_arrays == 1) {
+        const ArrDesc &d = e.desc_host[0];
+        o->X0 = d.X0;
+        o->XN = d.XN;
+        o->H = d.H;
+        o->W = d.W;
+    }
+    unsigned long long fb = 0;
+    if (e.counter && cudaMemcpy(&fb, e.counter + 1, sizeof(fb), cudaMemcpyDeviceToHost) == cudaSuccess)
+        o->fallback_queries = fb;
+    int err = 0;
+    if (e.dev_err && cudaMemcpy(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
+        o->device_error = err;
     return DS_OK;
 }
+
+template <typename T>
+static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaStream_t s)
+{
+    Engine &e = L->eng;
+    const int nm = (int)L->model_arr.size();
+    if (nm == 0) return DS_OK;
+    const double t0 = now_ms();
+    const uint32_t slo = (uint32_t)cfg.seed, shi = (uint32_t)(cfg.seed >> 32);
+    const bool linear = (cfg.flags & DS_LEARNED_LINEAR) != 0;
+    std::vector<long long> pool_off(nm + 1, 0);
+    for (int k = 0; k < nm; ++k) {
+        const ArrDesc &d = e.desc_host[L->model_arr[k]];
+        long long nq = cfg.n_queries > 0 ? cfg.n_queries : 0;
+        if (linear || cfg.steps <= 0) nq = 0;
+        pool_off[k + 1] = pool_off[k] + std::min<long long>(nq, 4ll * (d.n + 1) + 4096);
+    }
+    const int gb = std::max(1, cfg.batch / TB);
+    int *model_arr = nullptr, *step = nullptr, *elo = nullptr, *ehi = nullptr;
+    long long *pool_off_d = nullptr;
+    float2 *pool = nullptr;
+    float *theta = nullptr, *mom = nullptr, *vel = nullptr, *part = nullptr, *plos = nullptr, *loss = nullptr;
+    ds_status rc = DS_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cs = nullptr;
+    do {
+        cudaError_t ce = cudaSuccess;
+        auto A = [&](void **p, size_t bytes) {
+            if (ce == cudaSuccess) ce = cudaMalloc(p, std::max<size_t>(bytes, 16));
+        };
+        A((void **)&model_arr, sizeof(int) * nm);
+        A((void **)&step, sizeof(int) * nm);
+        A((void **)&elo, sizeof(int) * nm);
+        A((void **)&ehi, sizeof(int) * nm);
+        A((void **)&pool_off_d, sizeof(long long) * (nm + 1));
+        A((void **)&pool, sizeof(float2) * (size_t)pool_off[nm]);
+        A((void **)&theta, sizeof(float) * (size_t)nm * NP);
+        A((void **)&mom, sizeof(float) * (size_t)nm * NP);
+        A((void **)&vel, sizeof(float) * (size_t)nm * NP);
+        A((void **)&part, sizeof(float) * (size_t)nm * gb * NP);
+        A((void **)&plos, sizeof(float) * (size_t)nm * gb);
+        A((void **)&loss, sizeof(float) * nm);
+        if (ce != cudaSuccess) {
+            set_error("learned build: allocation failed: %s", cudaGetErrorString(ce));
+            rc = DS_E_NOMEM;
+            break;
+        }
+        cudaMemcpyAsync(model_arr, L->model_arr.data(), sizeof(int) * nm, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(pool_off_d, pool_off.data(), sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(step, 0, sizeof(int) * nm, s);
+        cudaMemsetAsync(mom, 0, sizeof(float) * (size_t)nm * NP, s);
+        cudaMemsetAsync(vel, 0, sizeof(float) * (size_t)nm * NP, s);
+        cudaMemsetAsync(loss, 0, sizeof(float) * nm, s);
+        k_init_params<<<nm, 256, 0, s>>>(theta, nm, slo, shi);
+        if (pool_off[nm] > 0)
+            k_pool_queries<T><<<dim3(std::max(1, std::min(e.props.num_sms * 4 / std::max(1, nm), 1024)), nm), 256, 0, s>>>(
+                e.desc_dev, e.blob, model_arr, pool_off_d, pool, nm, slo, shi);
+        if (!linear && cfg.steps > 0) {
+            TrainArgs ta;
+            ta.desc = e.desc_dev; ta.blob = e.blob; ta.model_arr = model_arr; ta.pool = pool; ta.pool_off = pool_off_d;
+            ta.theta = theta; ta.m = mom; ta.v = vel; ta.partial = part; ta.partial_loss = plos; ta.loss = loss;
+            ta.step = step; ta.gb = gb; ta.steps = cfg.steps; ta.lr = cfg.lr; ta.seed_lo = slo; ta.seed_hi = shi;
+            const size_t smem = TH_BYTES + sizeof(GradTile);
+            ce = cudaFuncSetAttribute(k_train_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            // one graph of `per` steps, replayed
+            const int per = std::min(cfg.steps, 50);
+            if (ce == cudaSuccess) ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (ce == cudaSuccess) {
+                for (int k = 0; k < per; ++k) {
+                    k_train_grad<T><<<dim3(gb, nm), TB, smem, cs>>>(ta);
+                    k_train_adam<<<nm, 256, 0, cs>>>(ta);
+                }
+                ce = cudaStreamEndCapture(cs, &graph);
+            }
+            if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec, graph, 0);
+            int done = 0;
+            while (ce == cudaSuccess && done + per <= cfg.steps) {
+                ce = cudaGraphLaunch(gexec, cs);
+                done += per;
+            }
+            for (; ce == cudaSuccess && done < cfg.steps; ++done) {
+                k_train_grad<T><<<dim3(gb, nm), TB, smem, cs>>>(ta);
+                k_train_adam<<<nm, 256, 0, cs>>>(ta);
+                ce = cudaGetLastError();
+            }
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(cs);
+            if (ce != cudaSuccess) {
+                set_error("learned build: training failed: %s", cudaGetErrorString(ce));
+                rc = DS_E_CUDA;
+                break;
+            }
+            L->steps = cfg.steps;
+        }
+        // parameters to the host, piecewise-linear form, back to the device
+        L->theta_host.resize((size_t)nm * NP);
+        std::vector<float> lh(nm);
+        ce = cudaMemcpyAsync(L->theta_host.data(), theta, sizeof(float) * (size_t)nm * NP, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(lh.data(), loss, sizeof(float) * nm, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            set_error("learned build: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+            break;
+        }
+        double ls = 0;
+        for (float v : lh) ls += v;
+        L->final_loss = ls / nm;
+        Segments all, one;
+        for (int k = 0; k < nm; ++k) {
+            ArrDesc &d = e.desc_host[L->model_arr[k]];
+            if (linear) {
+                one.x.assign(1, -INFINITY);
+                one.a.assign(1, (float)d.n);
+                one.b.assign(1, 0.f);
+            } else {
+                pwl_of(&L->theta_host[(size_t)k * NP], (double)d.n, one);
+            }
+            d.seg_off = (int32_t)all.x.size();
+            d.seg_n = (int32_t)one.x.size();
+            all.x.insert(all.x.end(), one.x.begin(), one.x.end());
+            all.a.insert(all.a.end(), one.a.begin(), one.a.end());
+            all.b.insert(all.b.end(), one.b.begin(), one.b.end());
+        }
+        const size_t nseg = all.x.size();
+        A((void **)&e.seg_x, sizeof(float) * nseg);
+        A((void **)&e.seg_a, sizeof(float) * nseg);
+        A((void **)&e.seg_b, sizeof(float) * nseg);
+        if (ce != cudaSuccess) {
+            set_error("learned build: allocation failed");
+            rc = DS_E_NOMEM;
+            break;
+        }
+        e.table_bytes += 3 * sizeof(float) * nseg;
+        cudaMemcpyAsync(e.seg_x, all.x.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(e.seg_a, all.a.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(e.seg_b, all.b.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(elo, 0, sizeof(int) * nm, s);
+        cudaMemsetAsync(ehi, 0, sizeof(int) * nm, s);
+        k_error_bound<T><<<dim3(std::max(1, std::min(e.props.num_sms * 8 / std::max(1, nm), 2048)), nm), 256, 0, s>>>(
+            e.desc_dev, e.blob, model_arr, e.seg_x, e.seg_a, e.seg_b, elo, ehi);
+        std::vector<int> hlo(nm), hhi(nm);
+        ce = cudaGetLastError();
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hlo.data(), elo, sizeof(int) * nm, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(hhi.data(), ehi, sizeof(int) * nm, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            set_error("learned build: error bound failed: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+            break;
+        }
+        for (int k = 0; k < nm; ++k) {
+            ArrDesc &d = e.desc_host[L->model_arr[k]];
+            const bool zero = (cfg.flags & DS_LEARNED_ZERO_BOUND) != 0;
+            d.e_lo = zero ? 0 : hlo[k];
+            d.e_hi = zero ? 0 : hhi[k];
+            long long w = (long long)d.e_lo + d.e_hi + 3;
+            long long t = 1;
+            while (t * 2 <= w) t *= 2;
+            d.wbits = (int32_t)t;
+            L->max_window = std::max(L->max_window, w);
+        }
+        ce = cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+            set_error("learned build: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+        }
+    } while (0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) cudaStreamDestroy(cs);
+    for (void *p : {(void *)model_arr, (void *)step, (void *)elo, (void *)ehi, (void *)pool_off_d, (void *)pool,
+                    (void *)theta, (void *)mom, (void *)vel, (void *)part, (void *)plos, (void *)loss})
+        if (p) cudaFree(p);
+    L->train_ms = now_ms() - t0;
+    return rc;
+}
+
 }  // namespace ds
 
+static bool learned_ok(const ds_learned *L)
+{
+    return L && L->hdr.magic == ds::HANDLE_MAGIC && L->hdr.kind == ds::KIND_LEARNED;
+}
+
 extern "C" {
+
 void ds_learned_cfg_default(ds_learned_cfg *cfg)
 {
+    if (!cfg) return;
     memset(cfg, 0, sizeof(*cfg));
     cfg->steps = 2000;
     cfg->batch = 8192;
-    cfg->n_queries = 1 << 20;
-    cfg->lr = 1e-3f;
+    cfg->n_queries = 1 << 18;
+    cfg->lr = 3e-3f;
     cfg->seed = 1506086200ull;
+    cfg->flags = 0;
 }
-ds_status ds_learned_build(const void *, const int64_t *, int32_t, int64_t, ds_dtype, const ds_learned_cfg *,
-                           void *, ds_learned **out)
+
+ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, int64_t n_knots_if_single,
+                           ds_dtype dtype, const ds_learned_cfg *cfg_in, void *stream, ds_learned **out)
 {
-    if (out) *out = nullptr;
-    return DS_E_UNIMPLEMENTED;
+    ds::clear_error();
+    if (!out) {
+        ds::set_error("ds_learned_build: out is NULL");
+        return DS_E_ARG;
+    }
+    *out = nullptr;
+    ds_learned_cfg cfg;
+    if (cfg_in) cfg = *cfg_in;
+    else ds_learned_cfg_default(&cfg);
+    if (!Xcat_dev || n_arrays < 1 || (dtype != DS_F32 && dtype != DS_F64) || (!x_off_dev && n_arrays != 1) ||
+        (!x_off_dev && n_knots_if_single < 2) || cfg.batch < 1 || cfg.steps < 0 || !(cfg.lr > 0.f) ||
+        (cfg.flags & ~(uint32_t)(DS_LEARNED_FORCE | DS_LEARNED_LINEAR | DS_LEARNED_ZERO_BOUND))) {
+        ds::set_error("ds_learned_build: bad argument");
+        return DS_E_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const double t0 = ds::now_ms();
+    ds_learned *L = new ds_learned;
+    L->hdr.kind = ds::KIND_LEARNED;
+    L->hdr.magic = ds::HANDLE_MAGIC;
+    long long *single_off = nullptr;
+    const long long *xo = (const long long *)x_off_dev;
+    if (!x_off_dev) {
+        long long h[2] = {0, (long long)n_knots_if_single};
+        if (cudaMalloc(&single_off, sizeof(h)) != cudaSuccess ||
+            cudaMemcpy(single_off, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
+            ds::set_error("ds_learned_build: allocation failed");
+            delete L;
+            return DS_E_NOMEM;
+        }
+        xo = single_off;
+    }
+    std::vector<char> force;
+    std::vector<char> *fp = nullptr;
+    if (cfg.flags & DS_LEARNED_FORCE) {
+        force.assign(n_arrays, 1);
+        fp = &force;
+    }
+    ds_status rc = ds::engine_build(&L->eng, Xcat_dev, xo, n_arrays, dtype, 0, s, fp, ds::MODE_LEARNED, nullptr,
+                                    nullptr);
+    if (single_off) cudaFree(single_off);
+    if (rc == DS_OK) {
+        ds::Engine &e = L->eng;
+        L->arr_model.assign(n_arrays, -1);
+        for (int a = 0; a < n_arrays; ++a) {
+            ds::ArrDesc &d = e.desc_host[a];
+            if (d.mode != ds::MODE_LEARNED) continue;
+            L->arr_model[a] = (int)L->model_arr.size();
+            L->model_arr.push_back(a);
+            // predictor input u = (narrow(z) - narrow(X_0)) * uscale, in float32
+            const double span = d.XN - d.X0;
+            float x0f = (float)d.X0;
+            if (dtype == DS_F64) {  // truncating narrowing, as on the device
+                double x0 = d.X0;
+                unsigned long long b;
+                memcpy(&b, &x0, 8);
+                const int ex = (int)((b >> 52) & 0x7FF) - 1023;
+                if (ex < -126) x0f = 0.f * (float)((b >> 63) ? -1 : 1);
+                else {
+                    uint32_t fb = (uint32_t)((b >> 32) & 0x80000000u) | ((uint32_t)(ex + 127) << 23) |
+                                  (uint32_t)((b >> 29) & 0x7FFFFFu);
+                    memcpy(&x0f, &fb, 4);
+                }
+            }
+            d.x0f = x0f;
+            d.uscale = (float)(1.0 / span);
+        }
+        if (cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ds::ArrDesc) * e.desc_host.size(),
+                            cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            ds::set_error("ds_learned_build: descriptor upload failed");
+            rc = DS_E_CUDA;
+        }
+    }
+    if (rc == DS_OK) {
+        rc = dtype == DS_F32 ? ds::train_and_bound<float>(L, cfg, s) : ds::train_and_bound<double>(L, cfg, s);
+    }
+    if (rc != DS_OK) {
+        ds::free_learned(L);
+        return rc;
+    }
+    L->eng.tune = ds::default_tune();
+    L->eng.build_ms = ds::now_ms() - t0;
+    *out = L;
+    return DS_OK;
 }
-ds_status ds_learned_search(const ds_learned *, const void *, const int64_t *, int64_t, const void *, void *,
-                            int32_t *, void *)
+
+ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
+                            const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!learned_ok(L) || !Zcat_dev || !Icat_dev || (!z_off_dev && (m < 0 || L->eng.n_arrays != 1)) ||
+        ((Ycat_dev == nullptr) != (y_out_dev == nullptr))) {
+        ds::set_error("ds_learned_search: bad argument");
+        return DS_E_ARG;
+    }
+    if (!z_off_dev && m == 0) return DS_OK;
+    return ds::engine_launch(const_cast<ds::Engine *>(&L->eng), Zcat_dev, (const long long *)z_off_dev,
+                             z_off_dev ? 0 : m, Ycat_dev, y_out_dev, Icat_dev, (cudaStream_t)stream);
 }
-ds_status ds_learned_array(const ds_learned *, int32_t, float *, int32_t *, int32_t *, int32_t *)
+
+ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, int32_t *e_lo, int32_t *e_hi,
+                           int32_t *mode)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!learned_ok(L) || a < 0 || a >= L->eng.n_arrays) {
+        ds::set_error("ds_learned_array: bad argument");
+        return DS_E_ARG;
+    }
+    const ds::ArrDesc &d = L->eng.desc_host[a];
+    if (mode) *mode = d.mode;
+    if (e_lo) *e_lo = d.e_lo;
+    if (e_hi) *e_hi = d.e_hi;
+    if (theta_host) {
+        const int k = L->arr_model[a];
+        if (k >= 0 && !L->theta_host.empty()) memcpy(theta_host, &L->theta_host[(size_t)k * ds::NP], sizeof(float) * ds::NP);
+        else memset(theta_host, 0, sizeof(float) * ds::NP);
+    }
+    return DS_OK;
 }
-ds_status ds_mlp_forward(const float *, const float *, int64_t, float *, void *) { return DS_E_UNIMPLEMENTED; }
-ds_status ds_mlp_loss_grad(const float *, const float *, const float *, int64_t, float *, float *, void *)
+
+ds_status ds_mlp_forward(const float *theta_dev, const float *u_dev, int64_t n, float *out_dev, void *stream)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!theta_dev || (n > 0 && (!u_dev || !out_dev)) || n < 0) {
+        ds::set_error("ds_mlp_forward: bad argument");
+        return DS_E_ARG;
+    }
+    if (n == 0) return DS_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    ds::k_forward<<<(int)blocks, 256, 0, (cudaStream_t)stream>>>(theta_dev, u_dev, n, out_dev);
+    DS_TRY_CUDA(cudaGetLastError());
+    return DS_OK;
 }
-ds_status ds_adam_step(float *, float *, float *, const float *, int32_t, float, void *)
+
+ds_status ds_mlp_loss_grad(const float *theta_dev, const float *u_dev, const float *y_dev, int64_t n, float *grad_dev,
+                           float *loss_dev, void *stream)
 {
-    return DS_E_UNIMPLEMENTED;
+    if (!theta_dev || !u_dev || !y_dev || !grad_dev || !loss_dev || n < 1 || n > (1ll << 30)) {
+        ds::set_error("ds_mlp_loss_grad: bad argument");
+        return DS_E_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)((n + ds::TB - 1) / ds::TB);
+    float *part = nullptr, *plos = nullptr;
+    DS_TRY_CUDA(cudaMallocAsync(&part, sizeof(float) * (size_t)nb * ds::NP, s));
+    cudaError_t ce = cudaMallocAsync(&plos, sizeof(float) * (size_t)nb, s);
+    const size_t smem = ds::TH_BYTES + sizeof(ds::GradTile);
+    if (ce == cudaSuccess)
+        ce = cudaFuncSetAttribute(ds::k_grad_explicit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce == cudaSuccess) {
+        ds::k_grad_explicit<<<nb, ds::TB, smem, s>>>(theta_dev, u_dev, y_dev, n, part, plos);
+        ds::k_reduce_grad<<<1, 256, 0, s>>>(part, plos, nb, n, grad_dev, loss_dev);
+        ce = cudaGetLastError();
+    }
+    cudaFreeAsync(part, s);
+    if (plos) cudaFreeAsync(plos, s);
+    if (ce != cudaSuccess) {
+        ds::set_error("ds_mlp_loss_grad: %s", cudaGetErrorString(ce));
+        return DS_E_CUDA;
+    }
+    return DS_OK;
 }
+
+ds_status ds_adam_step(float *theta_dev, float *m_dev, float *v_dev, const float *grad_dev, int32_t t, float lr,
+                       void *stream)
+{
+    if (!theta_dev || !m_dev || !v_dev || !grad_dev || t < 1 || !(lr > 0.f)) {
+        ds::set_error("ds_adam_step: bad argument");
+        return DS_E_ARG;
+    }
+    ds::k_adam_explicit<<<5, 256, 0, (cudaStream_t)stream>>>(theta_dev, m_dev, v_dev, grad_dev, t, lr);
+    DS_TRY_CUDA(cudaGetLastError());
+    return DS_OK;
 }
+
+}  // extern "C"

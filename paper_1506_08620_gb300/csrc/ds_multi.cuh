@@ -41,7 +41,8 @@ struct __align__(16) ArrDesc {
     int32_t wbits;        // learned: 2^floor(log2(window width))
     double H, W, X0;      // direct: parameters in the array's precision (held exactly)
     double XN;            // last knot
-    double uscale;        // learned: u = (z - X0) * uscale
+    float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32)
+    float x0f;            // learned: narrow(X0)
     int32_t e_lo, e_hi;   // learned: recorded error bounds
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments

@@ -28,7 +28,7 @@ template <> __device__ __forceinline__ float narrow<double>(double z)
 template <typename T>
 __device__ __forceinline__ float pred_u(T z, const ArrDesc &d)
 {
-    return __fmul_rn(__fsub_rn(narrow<T>(z), narrow<T>((T)d.X0)), (float)d.uscale);
+    return __fmul_rn(__fsub_rn(narrow<T>(z), d.x0f), d.uscale);
 }
 
 // Piecewise-linear served form of the network: segment k covers
