@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     p.add_argument("--queries", type=int, default=0, help="override the query count (profiling runs)")
+    p.add_argument("--tune", default="auto", choices=["auto", "default"],
+                   help="batched/learned launch configuration: autotuned, or the library default")
     return p.parse_args()
 
 
@@ -201,6 +203,12 @@ def workload_config(args):
         "batched_f32": {"workload": "batched direct search f32: 4096 arrays of 16..65536 knots (log-uniform), "
                                     "2^28 queries in proportion, CSR, one persistent launch", "arrays": 4096,
                         "queries": 1 << 28},
+        "learned_f64": {"workload": "learned index f64: 2^24+1 knots, gaps U[1e-3,1e-2] or (1%) U[1e3,1e4], "
+                                    "2^27 uniform queries, 1-32-32-1 MLP + bounded window", "knots": (1 << 24) + 1,
+                        "queries": 1 << 27},
+        "learned_interp_f32": {"workload": "batched learned lookup + linear interpolation f32: 256 arrays of "
+                                           "2^10..2^22 knots, mixed gap laws, 2^28 queries", "arrays": 256,
+                               "queries": 1 << 28},
     }.get(args.workload, {"workload": args.workload})
     base = dict(base)
     base["variant"] = args.variant
@@ -304,7 +312,7 @@ def setup_batched(args, ds, W, torch, dev, rank):
     torch.cuda.synchronize()
     job.build_ms = (time.perf_counter() - t0) * 1e3
     info = b.info()
-    tune = ds.ds_batch_autotune(b, Zd, zo, out)
+    tune = ds.ds_batch_autotune(b, Zd, zo, out) if args.tune == "auto" else ds.ds_batch_get_tune(b)
     job.bytes_per_lookup = 8 + info["table_bytes"] / job.m
     job.table = {"arrays": info["n_arrays"], "R_total": info["R"], "table_bytes": info["table_bytes"],
                  "tune": tune}
@@ -326,6 +334,80 @@ def setup_batched(args, ds, W, torch, dev, rank):
         return Zp.numel() * 4, Ip.numel() * 4
     job.e2e = e2e
     job.e2e_out = Ip
+    return job
+
+
+def setup_learned(args, ds, W, torch, dev, rank):
+    """Workload 4 (one float64 array where direct search overflows) or
+    workload 5 (256 float32 arrays, per-array selector, fused interpolation)."""
+    job = Job()
+    five = args.workload == "learned_interp_f32"
+    if five:
+        w = W.workload5(seed=W.SEED_BASE + 5 + 1000 * rank if rank else None, total_queries=args.queries or (1 << 28))
+        Xd, xo = torch.from_numpy(w["Xcat"]).to(dev), torch.from_numpy(w["x_off"]).to(dev)
+        Yd = torch.from_numpy(w["Ycat"]).to(dev)
+        Zh, zo = w["Zcat"], torch.from_numpy(w["z_off"]).to(dev)
+        job.dtype_name = "f32"
+    else:
+        w = W.workload4(seed=W.SEED_BASE + 4 + 1000 * rank if rank else None, m=args.queries or (1 << 27))
+        Xd, xo, Yd, zo = torch.from_numpy(w["X"]).to(dev), None, None, None
+        Zh = w["Z"]
+        job.dtype_name = "f64"
+    job.m = Zh.size
+    Zd = torch.from_numpy(Zh).to(dev)
+    out = torch.empty(job.m, dtype=torch.int32, device=dev)
+    yout = torch.empty(job.m, dtype=Xd.dtype, device=dev) if five else None
+    cfg = ds.ds_learned_cfg_default(n_queries=1 << 20) if not five else ds.ds_learned_cfg_default()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = ds.ds_learned_build(Xd, xo, cfg=cfg)
+    torch.cuda.synchronize()
+    job.build_ms = (time.perf_counter() - t0) * 1e3
+    info = L.info()
+    esz = 4 if five else 8
+    job.bytes_per_lookup = (esz + 4 + (4 if five else 0))
+    job.table = {k: info[k] for k in ("n_arrays", "n_direct", "n_learned", "n_fallback", "max_window",
+                                      "train_steps", "train_ms", "final_loss", "table_bytes")}
+    job.kernel_key = "learned_search_%s" % job.dtype_name
+    job.launches_per_step = 2
+    if five:
+        job.search = lambda: ds.ds_learned_search(L, Zd, zo, Y=Yd, out=out, y_out=yout)
+    else:
+        job.search = lambda: ds.ds_learned_search(L, Zd, out=out)
+    job.out = out
+    job.keep = (L, Xd, Zd, Yd)
+    Zp = torch.from_numpy(Zh).pin_memory()
+    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
+    yp = torch.empty(job.m, dtype=Xd.dtype).pin_memory() if five else None
+    zbuf, obuf = torch.empty_like(Zd), torch.empty_like(out)
+    ybuf = torch.empty_like(yout) if five else None
+
+    def e2e():
+        zbuf.copy_(Zp, non_blocking=True)
+        if five:
+            ds.ds_learned_search(L, zbuf, zo, Y=Yd, out=obuf, y_out=ybuf)
+            yp.copy_(ybuf, non_blocking=True)
+        else:
+            ds.ds_learned_search(L, zbuf, out=obuf)
+        Ip.copy_(obuf, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return Zp.numel() * esz, Ip.numel() * 4 + (yp.numel() * esz if five else 0)
+    job.e2e = e2e
+    job.e2e_out = Ip
+
+    def extras(stream):
+        res = {"fallback_queries_per_step": None}
+        f0 = L.info()["fallback_queries"]
+        job.search()
+        torch.cuda.synchronize()
+        res["fallback_queries_per_step"] = L.info()["fallback_queries"] - f0
+        if not five:  # the model without the network, same search path
+            lin = ds.ds_learned_build(Xd, cfg=ds.ds_learned_cfg_default(flags=ds.DS_LEARNED_LINEAR))
+            res["linear_model"] = job.m / time_calls(torch, stream, lambda: ds.ds_learned_search(lin, Zd, out=out), 3)
+            res["linear_model_max_window"] = lin.info()["max_window"]
+            lin.free()
+        return res
+    job.extras = extras
     return job
 
 
@@ -361,6 +443,8 @@ def main():
         job = setup_direct(args, ds, W, torch, dev, rank)
     elif args.workload == "batched_f32":
         job = setup_batched(args, ds, W, torch, dev, rank)
+    elif args.workload in ("learned_f64", "learned_interp_f32"):
+        job = setup_learned(args, ds, W, torch, dev, rank)
     else:
         raise SystemExit("workload %s: not timed by this bench" % args.workload)
     m = job.m
@@ -429,8 +513,12 @@ def main():
         line["variants_lookups_per_s"] = job.extras(stream)
     if rank == 0:
         cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
-        line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds) if args.workload.startswith(
-            "direct") else cpu_baseline_batched(W, args.cpu_seconds)
+        if args.workload.startswith("direct") or args.workload == "learned_f64":
+            if args.workload == "learned_f64":
+                cw = W.workload4(m=1 << 22)
+            line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds)
+        else:
+            line["cpu_baseline"] = cpu_baseline_batched(W, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -207,7 +207,8 @@ DS_API ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double 
  * fixed-depth bisection (Algorithm binaryopt) inside the bounded window around
  * the prediction, certified by X_lo <= z < X_{hi+1}; a failed certificate
  * falls back to the array's exact full search.  Arrays on which direct search
- * is feasible use it instead (unless DS_LEARNED_FORCE).
+ * is feasible with at most max_cells_per_knot cells per knot use it instead
+ * (unless DS_LEARNED_FORCE).
  * ------------------------------------------------------------------------ */
 enum {
     DS_LEARNED_FORCE = 1u,    /* use the learned predictor even where direct search is feasible */
@@ -223,7 +224,9 @@ typedef struct ds_learned_cfg {
     float lr;            /* Adam step size */
     uint64_t seed;       /* Philox-4x32-10 key for initialisation and sampling */
     uint32_t flags;      /* DS_LEARNED_* */
-    int32_t reserved[5];
+    int32_t max_cells_per_knot; /* direct search only where (R+1) <= this x (N+1) (its table stays small);
+                                   other feasible arrays use the predictor; <= 0: no limit */
+    int32_t reserved[4];
 } ds_learned_cfg;
 
 DS_API void ds_learned_cfg_default(ds_learned_cfg *cfg);

@@ -70,7 +70,7 @@ class ds_tune_t(ctypes.Structure):
 
 class ds_learned_cfg(ctypes.Structure):
     _fields_ = [("steps", I32), ("batch", I32), ("n_queries", I32), ("lr", F32), ("seed", U64),
-                ("flags", U32), ("reserved", I32 * 5)]
+                ("flags", U32), ("max_cells_per_knot", I32), ("reserved", I32 * 4)]
 
 
 _SIGS = {

@@ -136,6 +136,11 @@ static int top_pow2(long long n)
     return (int)t;
 }
 
+static bool feasible_sparse(const HRState &h, long long nk, double max_cells)
+{
+    return h.status == DS_OK && max_cells > 0.0 && (double)h.R + 1.0 > max_cells * (double)nk;
+}
+
 template <typename T, bool FMA>
 static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const Segment *segs_dev, int n_segs,
                                 int A, cudaStream_t s, const DeviceProps &props, std::vector<HRState> &hs)
@@ -180,7 +185,8 @@ static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const
 template <typename T, bool FMA>
 static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x_off_dev,
                                     const std::vector<long long> &x_off, uint32_t flags, cudaStream_t s,
-                                    const std::vector<char> *force_other, int other_mode, std::vector<HRState> *hs_out)
+                                    const std::vector<char> *force_other, int other_mode, std::vector<HRState> *hs_out,
+                                    double max_cells)
 {
     const int A = e->n_arrays;
     std::vector<Segment> segs = make_segments(x_off);
@@ -213,7 +219,8 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
             d.pbits = top_pow2(d.n);
             e->h_updates += hs[a].updates;
             const bool feasible = hs[a].status == DS_OK;
-            const bool forced = force_other && (*force_other)[a];
+            const bool sparse = feasible_sparse(hs[a], nk, max_cells);
+            const bool forced = (force_other && (*force_other)[a]) || sparse;
             if (!feasible && (flags & DS_STRICT)) {
                 set_error("array %d: %s", a, ds_status_str((ds_status)hs[a].status));
                 rc = (ds_status)hs[a].status;
@@ -319,7 +326,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
 
 ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
                        uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
-                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out)
+                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out, double max_cells)
 {
     e->dtype = dtype;
     e->flags = flags;
@@ -352,38 +359,46 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
     const bool fma = (flags & DS_FMA) != 0;
     if (dtype == DS_F32)
         return fma ? build_engine_typed<float, true>(e, (const float *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                     other_mode, hs_out)
+                                                     other_mode, hs_out, max_cells)
                    : build_engine_typed<float, false>(e, (const float *)Xcat, x_off_dev, x_off, flags, s,
-                                                      force_other, other_mode, hs_out);
+                                                      force_other, other_mode, hs_out, max_cells);
     return fma ? build_engine_typed<double, true>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                  other_mode, hs_out)
+                                                  other_mode, hs_out, max_cells)
                : build_engine_typed<double, false>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                   other_mode, hs_out);
+                                                   other_mode, hs_out, max_cells);
 }
 
 // ---------------------------------------------------------------- launch
-template <typename T, int VPT, bool INTERP>
-static const void *pick3(bool vec)
+template <typename T, int VPT, bool INTERP, bool DO>
+static const void *pick4(bool vec)
 {
-    return vec ? (const void *)k_batch_search<T, VPT, INTERP, true> : (const void *)k_batch_search<T, VPT, INTERP, false>;
+    return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, DO>
+               : (const void *)k_batch_search<T, VPT, INTERP, false, DO>;
+}
+template <typename T, int VPT, bool INTERP>
+static const void *pick3(bool vec, bool direct_only)
+{
+    return direct_only ? pick4<T, VPT, INTERP, true>(vec) : pick4<T, VPT, INTERP, false>(vec);
 }
 template <typename T, int VPT>
-static const void *pick2(bool interp, bool vec)
+static const void *pick2(bool interp, bool vec, bool direct_only)
 {
-    return interp ? pick3<T, VPT, true>(vec) : pick3<T, VPT, false>(vec);
+    return interp ? pick3<T, VPT, true>(vec, direct_only) : pick3<T, VPT, false>(vec, direct_only);
 }
 template <typename T>
-static const void *pick1(int vpt, bool interp, bool vec)
+static const void *pick1(int vpt, bool interp, bool vec, bool direct_only)
 {
     switch (vpt) {
-    case 1: return pick2<T, 1>(interp, vec);
-    case 2: return pick2<T, 2>(interp, vec);
-    default: return pick2<T, 4>(interp, vec);
+    case 1: return pick2<T, 1>(interp, vec, direct_only);
+    case 2: return pick2<T, 2>(interp, vec, direct_only);
+    default: return pick2<T, 4>(interp, vec, direct_only);
     }
 }
-static const void *pick_kernel(int dtype, int vpt, bool interp, bool vec)
+static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec)
 {
-    return dtype == DS_F32 ? pick1<float>(vpt, interp, vec) : pick1<double>(vpt, interp, vec);
+    const bool direct_only = e->n_learned == 0 && e->n_fallback == 0;
+    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, direct_only)
+                              : pick1<double>(vpt, interp, vec, direct_only);
 }
 
 static int clamp_block(int b) { return b == 128 || b == 512 ? b : 256; }
@@ -392,7 +407,7 @@ static int clamp_vpt(int v) { return v == 1 || v == 2 ? v : 4; }
 // Resident blocks for a configuration (and the shared-memory opt-in).
 static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid)
 {
-    const void *fn = pick_kernel(e->dtype, clamp_vpt(t.items), interp, vec);
+    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec);
     const int smem = std::max(0, t.smem_limit);
     if (smem > 0) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
@@ -420,7 +435,7 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
     const long long chunk = (long long)block * vpt * L * CHUNK_TILES;
     k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->chunk_off, e->counter);
     DS_TRY_CUDA(cudaGetLastError());
-    const void *fn = pick_kernel(e->dtype, vpt, interp, vec);
+    const void *fn = pick_kernel(e, vpt, interp, vec);
     if (e->dtype == DS_F32) {
         BatchArgs<float> a;
         memset(&a, 0, sizeof(a));

@@ -153,6 +153,9 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     plan.intops = sizeof(T) == 8 && f64_intops_default();
     plan.block = SEARCH_BLOCK;
     plan.vpt = SEARCH_VPT;
+    if (sizeof(T) == 8 && plan.intops) {
+        if (const char *e = getenv("DS_F64_VPT")) plan.vpt = atoi(e) == 2 || atoi(e) == 8 ? atoi(e) : SEARCH_VPT;
+    }
     const size_t image = cache ? idx->pair_bytes : idx->k_bytes + idx->x_bytes;
     plan.smem = !(flags & DS_NO_SMEM) && image <= smem_limit_bytes(props);
     idx->smem_bytes = plan.smem ? (uint32_t)image : 0;

@@ -139,6 +139,51 @@ template <typename T> struct Pair;
 template <> struct __align__(8) Pair<float> { int32_t k; float x; };
 template <> struct __align__(16) Pair<double> { int32_t k; int32_t pad; double x; };
 
+// ------------------------------------------------------------------ table loads
+// Read-only table gathers marked evict-last in L2 (the query stream is
+// evict-first), not allocated in L1 (random cells have no L1 reuse).
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t *ptr, uint64_t pol)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ long long ld_keep(const long long *ptr, uint64_t pol)
+{
+    long long v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ longlong2 ld_keep(const longlong2 *ptr, uint64_t pol)
+{
+    longlong2 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b64 {%0, %1}, [%2], %3;"
+        : "=l"(v.x), "=l"(v.y)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// Read-only gathers that skip L1 allocation but keep the default L2 policy
+// (for tables larger than L2, where evict-last would crowd out the stream).
+__device__ __forceinline__ uint32_t ld_na(const uint32_t *ptr)
+{
+    uint32_t v;
+    asm("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(ptr));
+    return v;
+}
+__device__ __forceinline__ long long ld_na(const long long *ptr)
+{
+    long long v;
+    asm("ld.global.nc.L1::no_allocate.b64 %0, [%1];" : "=l"(v) : "l"(ptr));
+    return v;
+}
+
 // ------------------------------------------------------------------ async copies
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

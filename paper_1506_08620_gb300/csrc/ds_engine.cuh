@@ -42,9 +42,12 @@ struct Engine {
 // Validate, ComputeHR per array, lay out and fill all tables.  Arrays with
 // force_other[a] set (or infeasible for direct search) get mode other_mode
 // (MODE_LEARNED) or MODE_BISECT.
+// max_cells_per_knot > 0: a feasible array with (R+1) > max_cells_per_knot (N+1)
+// also gets other_mode.
 ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
                        uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
-                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out);
+                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out,
+                       double max_cells_per_knot = 0.0);
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
                                long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s);
 ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,

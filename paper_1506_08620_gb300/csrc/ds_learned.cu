@@ -1,5 +1,7 @@
 // ds_learned.cu -- learned-index form (not in the paper): a 1 -> 32 -> 32 -> 1
-// ReLU network predicting i / N from u = (z - X_0) / (X_N - X_0), trained on
+// ReLU network g predicting i / N = u + g(u) from u = (z - X_0) / (X_N - X_0)
+// (the network learns the deviation from the uniform-grid model N u, and its
+// output layer starts at zero, so the untrained model is that linear model), trained on
 // the GPU by the forward/backward/Adam kernels below; served as the network's
 // exact piecewise-linear form; error bound recorded at build time; exact
 // bounded window + certificate + fall-back in the shared ragged search kernel
@@ -268,8 +270,9 @@ __global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
         y = (float)i / (float)d.n;
     }
     float h1[HID], da1[HID], da2[HID], h2[HID], dout;
-    const float out = mlp_sample(th, u, y, 2.0f / (float)(a.gb * TB), h1, da1, da2, h2, &dout);
-    store_sample(t, u, y, out, dout, h1, da1, da2, h2);
+    const float res = y - u;  // the network's target: deviation from the linear model
+    const float out = mlp_sample(th, u, res, 2.0f / (float)(a.gb * TB), h1, da1, da2, h2, &dout);
+    store_sample(t, u, res, out, dout, h1, da1, da2, h2);
     __syncthreads();
     tile_gradient(t, TB, a.partial + ((size_t)model * a.gb + blockIdx.x) * NP);
     if (threadIdx.x == 0) a.partial_loss[(size_t)model * a.gb + blockIdx.x] = tile_loss(t, TB);
@@ -302,7 +305,8 @@ __global__ void k_train_adam(TrainArgs a)
 }
 
 // Initial network: hinge units W1 = +-1 with their kinks spread over [0, 1],
-// He-normal W2, small normal w3 (Box-Muller on Philox uniforms).
+// He-normal W2 (Box-Muller on Philox uniforms), output layer zero (the
+// starting model is the linear one).
 __global__ void k_init_params(float *theta, int n_models, uint32_t seed_lo, uint32_t seed_hi)
 {
     const int model = blockIdx.x;
@@ -313,7 +317,6 @@ __global__ void k_init_params(float *theta, int n_models, uint32_t seed_lo, uint
         float val = 0.f;
         if (p < OB1) val = (r.v[2] & 1u) ? 1.f : -1.f;          // W1: +-1
         else if (p >= OW2 && p < OB2) val = g * sqrtf(2.f / HID);  // W2: He normal
-        else if (p >= OW3 && p < OB3) val = g * (1.f / sqrtf((float)HID));
         th[p] = val;
     }
     __syncthreads();
@@ -470,7 +473,7 @@ static void pwl_of(const float *thf, double scale, Segments &out)
                     icpt += w3[n] * c[n];
                 }
             sx.push_back(l2);
-            sa.push_back(slope * scale);
+            sa.push_back((slope + 1.0) * scale);  // prediction N (u + g(u))
             sb.push_back(icpt * scale);
         }
     }
@@ -746,6 +749,7 @@ void ds_learned_cfg_default(ds_learned_cfg *cfg)
     cfg->lr = 3e-3f;
     cfg->seed = 1506086200ull;
     cfg->flags = 0;
+    cfg->max_cells_per_knot = 16;
 }
 
 ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, int64_t n_knots_if_single,
@@ -790,7 +794,7 @@ ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32
         fp = &force;
     }
     ds_status rc = ds::engine_build(&L->eng, Xcat_dev, xo, n_arrays, dtype, 0, s, fp, ds::MODE_LEARNED, nullptr,
-                                    nullptr);
+                                    nullptr, (double)cfg.max_cells_per_knot);
     if (single_off) cudaFree(single_off);
     if (rc == DS_OK) {
         ds::Engine &e = L->eng;

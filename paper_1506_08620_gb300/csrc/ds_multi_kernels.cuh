@@ -63,18 +63,37 @@ __device__ __forceinline__ void window_of(int32_t pf, const ArrDesc &d, int32_t 
     *hi = (int32_t)h;
 }
 
-// ------------------------------------------------------------------ NQ queries of one array
-template <typename T, int NQ>
-__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
-                                             const T *z, int32_t *r)
+// Table read: shared memory (staged image) or global memory (read-only,
+// not allocated in L1; all arrays' tables together exceed L2, so no L2
+// priority is requested).
+template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint32_t *p, uint64_t)
 {
-    if (d.mode == MODE_DIRECT) {
+    if constexpr (SM) return *p;
+    else return ld_na(p);
+}
+template <bool SM> __device__ __forceinline__ float tab_ld(const float *p, uint64_t)
+{
+    if constexpr (SM) return *p;
+    else return __uint_as_float(ld_na(reinterpret_cast<const uint32_t *>(p)));
+}
+template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uint64_t)
+{
+    if constexpr (SM) return *p;
+    else return __longlong_as_double(ld_na(reinterpret_cast<const long long *>(p)));
+}
+
+// ------------------------------------------------------------------ NQ queries of one array
+template <typename T, int NQ, bool DIRECT_ONLY, bool SM>
+__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
+                                             const T *z, int32_t *r, uint64_t pol)
+{
+    if (DIRECT_ONLY || d.mode == MODE_DIRECT) {
         uint32_t e[NQ];
         T x[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) e[q] = K[cell_rt<T>(z[q], d)];
+        for (int q = 0; q < NQ; ++q) e[q] = tab_ld<SM>(K + cell_rt<T>(z[q], d), pol);
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) x[q] = (e[q] & KNOT_FLAG) ? X[e[q] & ~KNOT_FLAG] : T(0);
+        for (int q = 0; q < NQ; ++q) x[q] = (e[q] & KNOT_FLAG) ? tab_ld<SM>(X + (e[q] & ~KNOT_FLAG), pol) : T(0);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) r[q] = correct<T, true>(z[q], e[q], x[q], a.checked);
         return;
@@ -94,8 +113,8 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         T xl[NQ], xh[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            xl[q] = X[lo[q]];
-            xh[q] = X[hi[q] + 1];
+            xl[q] = tab_ld<SM>(X + lo[q], pol);
+            xh[q] = tab_ld<SM>(X + hi[q] + 1, pol);
         }
         int nfail = 0;
 #pragma unroll
@@ -145,7 +164,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         for (int q = 0; q < NQ; ++q) {
             const int32_t rr = i[q] | k;
             const int32_t w = rr < n[q] ? rr : n[q];
-            if (!lt_exact<T>(z[q], X[lo[q] + w])) i[q] = rr;
+            if (!lt_exact<T>(z[q], tab_ld<SM>(X + lo[q] + w, pol))) i[q] = rr;
         }
     }
 #pragma unroll
@@ -155,9 +174,9 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
     }
 }
 
-template <typename T, int VPT, bool INTERP, bool VEC>
+template <typename T, int VPT, bool INTERP, bool VEC, bool DIRECT_ONLY, bool SM>
 __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
-                                              long long zs, long long ze)
+                                              long long zs, long long ze, uint64_t pol)
 {
     constexpr int L = VecOf<T>::L;
     long long va, vb;
@@ -173,14 +192,14 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     for (long long q = zs + threadIdx.x; q < va; q += blockDim.x) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1>(a, d, K, X, &z, &r);
+        answer_block<T, 1, DIRECT_ONLY, SM>(a, d, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
     for (long long q = vb + threadIdx.x; q < ze; q += blockDim.x) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1>(a, d, K, X, &z, &r);
+        answer_block<T, 1, DIRECT_ONLY, SM>(a, d, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
@@ -200,7 +219,7 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
             }
             const T *zs4 = reinterpret_cast<const T *>(zv);
             int32_t r[NQ];
-            answer_block<T, NQ>(a, d, K, X, zs4, r);
+            answer_block<T, NQ, DIRECT_ONLY, SM>(a, d, K, X, zs4, r, pol);
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = base + (long long)v * blockDim.x;
@@ -220,7 +239,9 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     }
 }
 
-template <typename T, int VPT, bool INTERP, bool VEC>
+// DIRECT_ONLY: every array of the handle is in direct mode (the learned and
+// bisection paths are compiled out, which keeps the register count low).
+template <typename T, int VPT, bool INTERP, bool VEC, bool DIRECT_ONLY>
 __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -231,6 +252,7 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
     __syncthreads();
     uint32_t parity = 0;
     int staged = -1;
+    const uint64_t pol = 0;
     const long long total = a.chunk_off[a.n_arrays];
     for (;;) {
         if (threadIdx.x == 0) {
@@ -272,7 +294,8 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
             K = reinterpret_cast<const uint32_t *>(a.blob + d.img);
             X = reinterpret_cast<const T *>(a.blob + d.xg);
         }
-        process_chunk<T, VPT, INTERP, VEC>(a, d, K, X, zs, ze);
+        if (use_smem) process_chunk<T, VPT, INTERP, VEC, DIRECT_ONLY, true>(a, d, K, X, zs, ze, pol);
+        else process_chunk<T, VPT, INTERP, VEC, DIRECT_ONLY, false>(a, d, K, X, zs, ze, pol);
         __syncthreads();
     }
 }

@@ -214,6 +214,122 @@ __global__ void __launch_bounds__(256) k_search_scalar(SearchArgs<T> a)
         a.I[q] = lookup<T, FM, CACHE, false, INTOPS>(a.Z[q], a.K, a.X, a.P, a);
 }
 
+// Float64 lookups with the data kept as IEEE bit patterns (long long)
+// throughout: the only double-precision instruction per query is the DMUL
+// (or DFMA, or DADD + DMUL for the plain form with X_0 != 0) of f.  The
+// truncation works on the product's bits, the comparison z < X_t on
+// order-preserving integer keys, and no double value is ever moved or
+// selected, so the compiler has no reason to emit further FP64-pipe
+// instructions (GB300's FP64 pipe is its scarce resource).
+__device__ __forceinline__ long long okey_bits(long long b) { return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll); }
+
+template <int FM>
+__device__ __forceinline__ uint32_t cell_bits(long long zb, double H, double NW, double X0, uint32_t R)
+{
+    const double z = __longlong_as_double(zb);
+    double v;
+    if constexpr (FM == F_FMA) v = __fma_rn(H, z, NW);
+    else if constexpr (FM == F_PLAIN_X0ZERO) v = __dmul_rn(H, z);
+    else v = __dmul_rn(H, __dsub_rn(z, X0));
+    const uint32_t j = trunc_u32_bits(v);
+    return j < R ? j : R;
+}
+
+__device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long long xb, int checked)
+{
+    const int32_t t = (int32_t)(e & ~KNOT_FLAG);
+    const bool lt = (e & KNOT_FLAG) ? okey_bits(zb) < okey_bits(xb) : true;
+    int32_t i = t - (int32_t)lt;
+    if (checked && ((unsigned long long)zb & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) i = -1;
+    return i;
+}
+
+template <int FM, bool CACHE, bool SMEM, int VPT>
+__global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, long long nvec, long long ntiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t *K;
+    const long long *Xb;
+    const longlong2 *P;
+    if constexpr (SMEM) {
+        if (!stage_to_smem(smem, a.smem_src, a.smem_bytes, &bar, a.err)) return;
+        K = reinterpret_cast<const uint32_t *>(smem);
+        Xb = reinterpret_cast<const long long *>(smem + a.x_smem_off);
+        P = reinterpret_cast<const longlong2 *>(smem);
+    } else {
+        K = a.K;
+        Xb = reinterpret_cast<const long long *>(a.X);
+        P = reinterpret_cast<const longlong2 *>(a.P);
+    }
+    const double H = a.H, NW = -a.W, X0 = a.X0;
+    const uint32_t R = a.R;
+    const uint64_t keep = l2_keep_policy();
+    const longlong2 *__restrict__ Zv = reinterpret_cast<const longlong2 *>(a.Z);
+    int2 *__restrict__ Iv = reinterpret_cast<int2 *>(a.I);
+    constexpr int NQ = 2 * VPT;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long b = tile * (long long)VPT * blockDim.x + threadIdx.x;
+        long long zb[NQ];
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const long long idx = b + (long long)v * blockDim.x;
+            longlong2 q = make_longlong2(0, 0);
+            if (idx < nvec) q = __ldcs(Zv + idx);
+            zb[2 * v] = q.x;
+            zb[2 * v + 1] = q.y;
+        }
+        uint32_t e[NQ];
+        long long xb[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) e[q] = cell_bits<FM>(zb[q], H, NW, X0, R);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if constexpr (CACHE) {
+                const longlong2 p = SMEM ? P[e[q]] : ld_keep(P + e[q], keep);
+                e[q] = (uint32_t)(p.x & 0xFFFFFFFFll);
+                xb[q] = p.y;
+            } else {
+                e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
+            }
+        }
+        if constexpr (!CACHE) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                xb[q] = 0;
+                if (e[q] & KNOT_FLAG) {
+                    const long long *px = Xb + (e[q] & ~KNOT_FLAG);
+                    xb[q] = SMEM ? *px : ld_keep(px, keep);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+            const long long idx = b + (long long)v * blockDim.x;
+            if (idx < nvec)
+                __stcs(Iv + idx, make_int2(correct_bits(zb[2 * v], e[2 * v], xb[2 * v], a.checked),
+                                           correct_bits(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], a.checked)));
+        }
+    }
+    if (blockIdx.x == 0) {  // the last m mod 2 queries
+        const long long q = nvec * 2 + threadIdx.x;
+        if (q < a.m) {
+            const long long zq = reinterpret_cast<const long long *>(a.Z)[q];
+            uint32_t e = cell_bits<FM>(zq, H, NW, X0, R);
+            long long xq = 0;
+            if constexpr (CACHE) {
+                const longlong2 p = P[e];
+                e = (uint32_t)(p.x & 0xFFFFFFFFll);
+                xq = p.y;
+            } else {
+                e = K[e];
+                if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
+            }
+            a.I[q] = correct_bits(zq, e, xq, a.checked);
+        }
+    }
+}
+
 struct SearchPlan {
     int form;      // FForm
     bool cache, smem, intops;

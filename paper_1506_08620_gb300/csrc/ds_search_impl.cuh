@@ -7,32 +7,43 @@
 
 namespace ds {
 
+template <int FM, bool CACHE, bool SMEM>
+static const void *pick_f64bits(int vpt)
+{
+    switch (vpt) {
+    case 2: return (const void *)k_search_f64bits<FM, CACHE, SMEM, 2>;
+    case 8: return (const void *)k_search_f64bits<FM, CACHE, SMEM, 8>;
+    default: return (const void *)k_search_f64bits<FM, CACHE, SMEM, 4>;
+    }
+}
+
 template <typename T, int FM, bool CACHE, bool SMEM>
-static const void *pick_vec4(bool intops)
+static const void *pick_vec4(bool intops, int vpt)
 {
     if constexpr (sizeof(T) == 8) {
-        if (intops) return (const void *)k_search_vec<T, FM, CACHE, SMEM, true, SEARCH_VPT>;
+        if (intops) return pick_f64bits<FM, CACHE, SMEM>(vpt);
     }
+    (void)vpt;
     (void)intops;
     return (const void *)k_search_vec<T, FM, CACHE, SMEM, false, SEARCH_VPT>;
 }
 template <typename T, int FM, bool CACHE>
-static const void *pick_vec3(bool smem, bool intops)
+static const void *pick_vec3(bool smem, bool intops, int vpt)
 {
-    return smem ? pick_vec4<T, FM, CACHE, true>(intops) : pick_vec4<T, FM, CACHE, false>(intops);
+    return smem ? pick_vec4<T, FM, CACHE, true>(intops, vpt) : pick_vec4<T, FM, CACHE, false>(intops, vpt);
 }
 template <typename T, int FM>
-static const void *pick_vec2(bool cache, bool smem, bool intops)
+static const void *pick_vec2(bool cache, bool smem, bool intops, int vpt)
 {
-    return cache ? pick_vec3<T, FM, true>(smem, intops) : pick_vec3<T, FM, false>(smem, intops);
+    return cache ? pick_vec3<T, FM, true>(smem, intops, vpt) : pick_vec3<T, FM, false>(smem, intops, vpt);
 }
 template <typename T>
 static const void *pick_vec(const SearchPlan &p)
 {
     switch (p.form) {
-    case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops);
-    case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops);
-    default: return pick_vec2<T, F_PLAIN>(p.cache, p.smem, p.intops);
+    case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops, p.vpt);
+    case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops, p.vpt);
+    default: return pick_vec2<T, F_PLAIN>(p.cache, p.smem, p.intops, p.vpt);
     }
 }
 

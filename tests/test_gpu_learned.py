@@ -78,7 +78,8 @@ def _cfg(ds, **kw):
     return ds.ds_learned_cfg_default(**base)
 
 
-def _learned_small(n_knots=(1 << 16) + 1, m=1 << 20, seed=None):
+def _learned_small(n_knots=(1 << 18) + 1, m=1 << 20, seed=None):
+    # at 2^18+1 knots the two-scale gaps already make R exceed 2^32
     return W.workload4(n_knots=n_knots, m=m, seed=seed)
 
 
@@ -113,7 +114,7 @@ def test_learned_single_array_is_exact_and_bound_holds(ds):
 def test_zero_bound_forces_the_certificate_and_stays_exact(ds):
     w = _learned_small(n_knots=20_001, m=200_000)
     X, Z = w["X"], _queries(w["X"], w["Z"], np.float64)
-    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds, flags=ds.DS_LEARNED_ZERO_BOUND))
+    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds, flags=ds.DS_LEARNED_ZERO_BOUND | ds.DS_LEARNED_FORCE))
     got = L.search(_cuda(Z)).cpu().numpy()
     assert np.array_equal(got, oracle.upper_bound(X, Z))
     assert L.info()["fallback_queries"] > 0
@@ -155,13 +156,30 @@ def _interp_tol(y, y64, Y0, Y1):
 def test_batched_learned_with_interpolation(ds):
     w = W.workload5(n_arrays=24, size_lo=1 << 10, size_hi=1 << 17, total_queries=1 << 21)
     Xcat, Ycat, x_off, Zcat, z_off = w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"], w["z_off"]
-    L = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=_cfg(ds))
+    # default selector: direct search exactly where ComputeHR succeeds with at
+    # most max_cells_per_knot cells per knot
+    cfg = _cfg(ds, steps=50)
+    Ld = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=cfg)
+    modes = []
+    for a in range(24):
+        Xa = Xcat[x_off[a]:x_off[a + 1]]
+        hr = oracle.compute_hr(Xa)
+        direct = hr["status"] == oracle.OR_OK and hr["R"] + 1 <= cfg.max_cells_per_knot * Xa.size
+        modes.append(ds.ds_learned_array(Ld, a)["mode"])
+        assert modes[-1] == (0 if direct else 1), a
+    assert 0 in modes and 1 in modes
+    Id, yd = Ld.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
+    Ld.free()
+    # every array through the learned predictor
+    L = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
     info = L.info()
-    assert info["n_learned"] + info["n_direct"] == 24 and info["n_learned"] > 0
+    assert info["n_learned"] == 24
     I, y = L.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
     I, y = I.cpu().numpy(), y.cpu().numpy()
     Iref, yref = oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)
     assert np.array_equal(I, Iref)
+    assert np.array_equal(Id.cpu().numpy(), Iref)
+    assert np.array_equal(yd.cpu().numpy(), y)
     arr = np.searchsorted(z_off, np.arange(Zcat.size), side="right") - 1
     gi = x_off[arr] + I
     assert np.all(_interp_tol(y, yref, Ycat[gi], Ycat[gi + 1]))
