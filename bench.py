@@ -131,6 +131,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def max_over_ranks(value, dist=None, device=None):
+    """The largest of `value` over all ranks (all ranks get it).  The only
+    collective of the multi-GPU run: every rank searches its own replica and
+    its own queries, so nothing else is exchanged."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_seed(W, workload_id, rank):
+    """Seed of a rank's replica workload: rank 0 uses the workload's own seed,
+    other ranks draw independent queries (and knots) of the same recipe."""
+    return None if rank == 0 else W.SEED_BASE + workload_id + 1000 * rank
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,7 +256,7 @@ def setup_direct(args, ds, W, torch, dev, rank):
     flags = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
              "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT}[args.variant]
     if args.workload in ("direct_f64", "direct_f64_sorted"):
-        w = W.workload2(seed=W.SEED_BASE + 2 + 1000 * rank if rank else None, m=args.queries or (1 << 27),
+        w = W.workload2(seed=rank_seed(W, 2, rank), m=args.queries or (1 << 27),
                         sort=args.workload.endswith("sorted"))
         X, Zh = w["X"], w["Z"]
         job.bytes_per_lookup, job.dtype_name = 8 + 4, "f64"
@@ -300,7 +318,7 @@ def setup_direct(args, ds, W, torch, dev, rank):
 
 def setup_batched(args, ds, W, torch, dev, rank):
     job = Job()
-    w = W.workload3(seed=W.SEED_BASE + 3 + 1000 * rank if rank else None, total_queries=args.queries or (1 << 28))
+    w = W.workload3(seed=rank_seed(W, 3, rank), total_queries=args.queries or (1 << 28))
     job.dtype_name = "f32"
     job.m = int(w["z_off"][-1])
     Xd, xo = torch.from_numpy(w["Xcat"]).to(dev), torch.from_numpy(w["x_off"]).to(dev)
@@ -343,13 +361,13 @@ def setup_learned(args, ds, W, torch, dev, rank):
     job = Job()
     five = args.workload == "learned_interp_f32"
     if five:
-        w = W.workload5(seed=W.SEED_BASE + 5 + 1000 * rank if rank else None, total_queries=args.queries or (1 << 28))
+        w = W.workload5(seed=rank_seed(W, 5, rank), total_queries=args.queries or (1 << 28))
         Xd, xo = torch.from_numpy(w["Xcat"]).to(dev), torch.from_numpy(w["x_off"]).to(dev)
         Yd = torch.from_numpy(w["Ycat"]).to(dev)
         Zh, zo = w["Zcat"], torch.from_numpy(w["z_off"]).to(dev)
         job.dtype_name = "f32"
     else:
-        w = W.workload4(seed=W.SEED_BASE + 4 + 1000 * rank if rank else None, m=args.queries or (1 << 27))
+        w = W.workload4(seed=rank_seed(W, 4, rank), m=args.queries or (1 << 27))
         Xd, xo, Yd, zo = torch.from_numpy(w["X"]).to(dev), None, None, None
         Zh = w["Z"]
         job.dtype_name = "f64"
@@ -469,9 +487,7 @@ def main():
     total_ms = ev[0].elapsed_time(ev[-1])
     clk = clocks.stop()
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, dist, dev)
         dist.barrier()
     ms_per_step = total_ms / args.steps
     value = world * m / (ms_per_step * 1e-3)
@@ -501,9 +517,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
     line["e2e"] = {"value": world * m / e2e_s, "unit": "lookups/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h}
     if rank == 0:

@@ -21,6 +21,25 @@ __global__ void k_hr_state_init(HRState *st, int count)
     st[a] = s;
 }
 
+__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P)
+{
+    const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < (long long)nblk; b += step) {
+        const unsigned long long j0 = (unsigned long long)b * PACK_CELLS;
+        const uint32_t base = K[j0] & ~KNOT_FLAG;
+        uint32_t w[3] = {0u, 0u, 0u};
+        for (int s = 0; s < PACK_CELLS; ++s) {
+            const unsigned long long j = j0 + s;
+            if (j > R) break;
+            const uint32_t e = K[j];
+            const uint32_t byte = ((e & ~KNOT_FLAG) - base) | ((e & KNOT_FLAG) ? 0x80u : 0u);
+            w[s >> 2] |= byte << ((s & 3) * 8);
+        }
+        P[b] = make_uint4(base, w[0], w[1], w[2]);
+    }
+}
+
 __global__ void k_clear_flags(uint32_t *p, long long count, int stride)
 {
     const long long step = (long long)gridDim.x * blockDim.x;
@@ -154,11 +173,26 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     plan.block = SEARCH_BLOCK;
     plan.vpt = SEARCH_VPT;
     if (sizeof(T) == 8 && plan.intops) {
-        if (const char *e = getenv("DS_F64_VPT")) plan.vpt = atoi(e) == 2 || atoi(e) == 8 ? atoi(e) : SEARCH_VPT;
+        plan.vpt = 2;  // measured best for the float64 kernel (more resident warps)
+        if (const char *e = getenv("DS_F64_VPT")) plan.vpt = atoi(e) == 4 || atoi(e) == 8 ? atoi(e) : 2;
     }
     const size_t image = cache ? idx->pair_bytes : idx->k_bytes + idx->x_bytes;
     plan.smem = !(flags & DS_NO_SMEM) && image <= smem_limit_bytes(props);
     idx->smem_bytes = plan.smem ? (uint32_t)image : 0;
+    plan.packed = false;
+    if (sizeof(T) == 8 && plan.intops && !plan.smem && !cache) {
+        const char *e = getenv("DS_PACKED");
+        if (!e || atoi(e) != 0) {
+            const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
+            idx->k16_bytes = (size_t)nblk * sizeof(uint4);
+            DS_TRY_CUDA(cudaMalloc(&idx->k16, idx->k16_bytes));
+            k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(K, R, idx->k16);
+            DS_TRY_CUDA(cudaGetLastError());
+            DS_TRY_CUDA(cudaStreamSynchronize(s));
+            idx->table_bytes += idx->k16_bytes;
+            plan.packed = true;
+        }
+    }
     DS_TRY(prepare_search<T>(&plan, idx->smem_bytes, props.num_sms));
     return DS_OK;
 }
@@ -230,6 +264,7 @@ static ds_status search_typed(const ds_index *idx, const void *Z, long long m, i
     SearchArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.K = reinterpret_cast<const uint32_t *>(idx->tab);
+    a.K16 = idx->k16;
     a.X = reinterpret_cast<const T *>(idx->tab + idx->k_bytes);
     a.P = reinterpret_cast<const Pair<T> *>(idx->pairs);
     a.smem_src = idx->plan.cache ? idx->pairs : (const void *)idx->tab;

@@ -160,6 +160,14 @@ __device__ __forceinline__ long long ld_keep(const long long *ptr, uint64_t pol)
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
     return v;
 }
+__device__ __forceinline__ uint4 ld_keep(const uint4 *ptr, uint64_t pol)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr), "l"(pol));
+    return v;
+}
 __device__ __forceinline__ longlong2 ld_keep(const longlong2 *ptr, uint64_t pol)
 {
     longlong2 v;

@@ -110,6 +110,7 @@ void free_index(ds_index *idx)
     destroy_pipe(idx->pipe);
     if (idx->tab) cudaFree(idx->tab);
     if (idx->pairs) cudaFree(idx->pairs);
+    if (idx->k16) cudaFree(idx->k16);
     if (idx->dev_err) cudaFree(idx->dev_err);
     idx->hdr.magic = 0;
     delete idx;

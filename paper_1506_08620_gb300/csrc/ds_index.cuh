@@ -19,6 +19,8 @@ struct ds_index {
     double build_ms;
     unsigned char *tab;   // [K: (R+1) uint32 (bit 31: cell holds a knot), padded to 16 B][X copy: N+1 values, padded]
     size_t k_bytes, x_bytes;
+    uint4 *k16;           // packed K (12 cells per 16 bytes) for the L2-resident float64 path
+    size_t k16_bytes;
     void *pairs;          // (R+1) Pair<T> when DS_CACHE_LAYOUT
     size_t pair_bytes;
     size_t table_bytes;
@@ -234,6 +236,9 @@ __global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, uint
         }
     }
 }
+
+// Packed copy of the flagged K: block b = {K_{12b}, 12 bytes (K_j - K_{12b}) | flag << 7}.
+__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P);
 
 // Clear the knot flag (bit 31) of every stride-th 32-bit word: turns a copy of
 // the flagged table into the plain K of Eq. indexdef.

@@ -13,8 +13,10 @@
 //
 // Per-array modes:
 //   MODE_DIRECT    Algorithm direct with the array's own H, W, R, K.
-//   MODE_LEARNED   predicted index, bounded window, fixed-depth bisection,
-//                  certificate, exact fall-back (defined with the learned form).
+//   MODE_LEARNED   predicted index, bounded window, certificate, exact
+//                  fall-back; the window is searched in two fixed-depth
+//                  levels: over every 32nd knot (a small, L2-resident copy),
+//                  then over at most 32 knots.
 //   MODE_BISECT    fixed-depth bisection over all knots (Algorithm
 //                  binaryoptnopad), the log-time fall-back where direct
 //                  search is infeasible.
@@ -46,7 +48,7 @@ struct __align__(16) ArrDesc {
     int32_t e_lo, e_hi;   // learned: recorded error bounds
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
-    int32_t pad_[2];
+    long long sg;         // learned: byte offset of the sampled knots S_k = X_{min(32 k, N)}, k = 0..N/32+1
 };
 static_assert(sizeof(ArrDesc) == 128, "ArrDesc layout");
 

@@ -63,23 +63,24 @@ __device__ __forceinline__ void window_of(int32_t pf, const ArrDesc &d, int32_t 
     *hi = (int32_t)h;
 }
 
-// Table read: shared memory (staged image) or global memory (read-only,
-// not allocated in L1; all arrays' tables together exceed L2, so no L2
-// priority is requested).
+// Table read: shared memory (staged image) or global memory through the
+// read-only path (L1-cached: a block works on one array at a time, whose
+// table is small enough to get L1 reuse; all tables together exceed L2, so
+// no L2 priority is requested).
 template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint32_t *p, uint64_t)
 {
     if constexpr (SM) return *p;
-    else return ld_na(p);
+    else return __ldg(p);
 }
 template <bool SM> __device__ __forceinline__ float tab_ld(const float *p, uint64_t)
 {
     if constexpr (SM) return *p;
-    else return __uint_as_float(ld_na(reinterpret_cast<const uint32_t *>(p)));
+    else return __ldg(p);
 }
 template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uint64_t)
 {
     if constexpr (SM) return *p;
-    else return __longlong_as_double(ld_na(reinterpret_cast<const long long *>(p)));
+    else return __ldg(p);
 }
 
 // ------------------------------------------------------------------ NQ queries of one array
@@ -119,31 +120,50 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         int nfail = 0;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            // certificate X_lo <= z < X_{hi+1}; otherwise the exact full search
-            const bool ok = !lt_exact<T>(z[q], xl[q]) && lt_exact<T>(z[q], xh[q]);
-            if (ok) {
-                n[q] = hi[q] + 1 - lo[q];
-            } else {
-                lo[q] = 0;
-                n[q] = d.n;
-                ++nfail;
-            }
             done[q] = false;
-        }
-        if (nfail) {
-            atomicAdd(a.fallbacks, (unsigned long long)nfail);
-            top = d.pbits;
-        } else {
-            top = d.wbits;
-        }
-        // the full search also needs the out-of-range answers
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (n[q] == d.n && lo[q] == 0) {
+            // certificate X_lo <= z < X_{hi+1}; otherwise the exact full search
+            if (!(!lt_exact<T>(z[q], xl[q]) && lt_exact<T>(z[q], xh[q]))) {
+                ++nfail;
+                lo[q] = 0;
+                hi[q] = d.n - 1;
                 if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
                 else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
             }
         }
+        if (nfail) atomicAdd(a.fallbacks, (unsigned long long)nfail);
+        // level 1: largest k in [lo/32, hi/32] with S_k = X_{32k} <= z
+        // (S_{lo/32} <= X_lo <= z and S_{hi/32+1} >= X_{hi+1} > z)
+        const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
+        const int32_t ws = nfail ? ((d.n - 1) >> 5) + 1 : ((d.e_lo + d.e_hi + 3) >> 5) + 2;
+        const int32_t top1 = 1 << (31 - __clz(ws));
+        int32_t k1[NQ], nk[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            k1[q] = lo[q] >> 5;
+            nk[q] = (hi[q] >> 5) - k1[q] + 1;
+        }
+        int32_t i1[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) i1[q] = 0;
+        for (int32_t k = top1; k > 0; k >>= 1) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int32_t rr = i1[q] | k;
+                const int32_t w = rr < nk[q] ? rr : nk[q];
+                if (!lt_exact<T>(z[q], tab_ld<SM>(S + k1[q] + w, pol))) i1[q] = rr;
+            }
+        }
+        // level 2: at most 32 knots
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t ks = k1[q] + (i1[q] < nk[q] ? i1[q] : nk[q] - 1);
+            const int32_t b0 = ks << 5;
+            const int32_t l2 = b0 > lo[q] ? b0 : lo[q];
+            const int32_t e2 = (b0 + 32 < hi[q] + 1) ? b0 + 32 : hi[q] + 1;
+            lo[q] = l2;
+            n[q] = e2 - l2;
+        }
+        top = 16;
     } else {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -394,9 +414,15 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
         const long long start = x_off[sg.arr];
         T *Xd = reinterpret_cast<T *>(blob + d.xg);
         const T H = (T)d.H, W = (T)d.W, X0 = (T)d.X0;
+        T *S = reinterpret_cast<T *>(blob + d.sg);
         for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
             const T x = Xcat[i];
-            Xd[i - start] = x;
+            const long long li = i - start;
+            Xd[li] = x;
+            if (d.mode == MODE_LEARNED) {  // S_k = X_{min(32 k, N)}, k = 0 .. N/32 + 1
+                if ((li & 31) == 0) S[li >> 5] = x;
+                if (li == d.n) S[(d.n >> 5) + 1] = x;
+            }
             if (d.mode == MODE_DIRECT) {
                 T v;
                 if (d.form == F_FMA) v = A::fma(H, x, -W);

@@ -25,7 +25,24 @@ enum FForm : int { F_PLAIN = 0, F_FMA = 1, F_PLAIN_X0ZERO = 2 };
 
 constexpr uint32_t KNOT_FLAG = 0x80000000u;
 
+// Packed table: K in 16-byte blocks of 12 cells, {K of the block's first
+// cell, 12 bytes (K_j - base) | knot flag << 7}.  Each cell holds at most one
+// knot (F is strictly increasing), so K grows by at most 1 per cell and the
+// difference fits 7 bits; 1.33 bytes per cell instead of 4 keeps large tables
+// L2-resident, and a lookup still reads one 16-byte sector.
+constexpr int PACK_CELLS = 12;
+
+__device__ __forceinline__ uint32_t unpack_cell(uint4 w, uint32_t j)
+{
+    const uint32_t b = __umulhi(j, 0xAAAAAAABu) >> 3;  // j / 12
+    const uint32_t s = j - b * PACK_CELLS;
+    const uint32_t word = s < 4 ? w.y : (s < 8 ? w.z : w.w);
+    const uint32_t byte = (word >> ((s & 3u) * 8u)) & 0xFFu;
+    return (w.x + (byte & 0x7Fu)) | ((byte & 0x80u) << 24);
+}
+
 template <typename T> struct SearchArgs {
+    const uint4 *K16;     // packed table (L2 path), or nullptr
     const uint32_t *K;    // R+1 cells (Eq. indexdef), flag in bit 31
     const T *X;           // N+1 knots
     const Pair<T> *P;     // R+1 (K_j | flag, X_{K_j}) pairs (cache layout)
@@ -244,7 +261,7 @@ __device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long l
     return i;
 }
 
-template <int FM, bool CACHE, bool SMEM, int VPT>
+template <int FM, bool CACHE, bool SMEM, int VPT, bool PACKED = false>
 __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, long long nvec, long long ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -268,17 +285,27 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
     const longlong2 *__restrict__ Zv = reinterpret_cast<const longlong2 *>(a.Z);
     int2 *__restrict__ Iv = reinterpret_cast<int2 *>(a.I);
     constexpr int NQ = 2 * VPT;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // software pipeline: the next tile's queries are loaded while this tile's
+    // gathers are in flight
+    long long zn[NQ];
+    auto load_tile = [&](long long tile, long long *dst) {
         const long long b = tile * (long long)VPT * blockDim.x + threadIdx.x;
-        long long zb[NQ];
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const long long idx = b + (long long)v * blockDim.x;
             longlong2 q = make_longlong2(0, 0);
-            if (idx < nvec) q = __ldcs(Zv + idx);
-            zb[2 * v] = q.x;
-            zb[2 * v + 1] = q.y;
+            if (tile < ntiles && idx < nvec) q = __ldcs(Zv + idx);
+            dst[2 * v] = q.x;
+            dst[2 * v + 1] = q.y;
         }
+    };
+    load_tile(blockIdx.x, zn);
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long b = tile * (long long)VPT * blockDim.x + threadIdx.x;
+        long long zb[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) zb[q] = zn[q];
+        load_tile(tile + gridDim.x, zn);
         uint32_t e[NQ];
         long long xb[NQ];
 #pragma unroll
@@ -289,6 +316,9 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 const longlong2 p = SMEM ? P[e[q]] : ld_keep(P + e[q], keep);
                 e[q] = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xb[q] = p.y;
+            } else if constexpr (PACKED) {
+                const uint32_t j = e[q];
+                e[q] = unpack_cell(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
             } else {
                 e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
             }
@@ -321,6 +351,9 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 const longlong2 p = P[e];
                 e = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xq = p.y;
+            } else if constexpr (PACKED) {
+                e = unpack_cell(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
+                if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
             } else {
                 e = K[e];
                 if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
@@ -332,7 +365,7 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
 
 struct SearchPlan {
     int form;      // FForm
-    bool cache, smem, intops;
+    bool cache, smem, intops, packed;
     int block;     // threads per block
     int vpt;       // vectors per thread per tile
     int grid_cap;  // resident blocks (one wave)

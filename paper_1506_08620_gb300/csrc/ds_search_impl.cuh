@@ -8,8 +8,13 @@
 namespace ds {
 
 template <int FM, bool CACHE, bool SMEM>
-static const void *pick_f64bits(int vpt)
+static const void *pick_f64bits(int vpt, bool packed)
 {
+    if constexpr (!CACHE && !SMEM) {
+        if (packed) return vpt == 2 ? (const void *)k_search_f64bits<FM, false, false, 2, true>
+                                    : (const void *)k_search_f64bits<FM, false, false, 4, true>;
+    }
+    (void)packed;
     switch (vpt) {
     case 2: return (const void *)k_search_f64bits<FM, CACHE, SMEM, 2>;
     case 8: return (const void *)k_search_f64bits<FM, CACHE, SMEM, 8>;
@@ -18,32 +23,35 @@ static const void *pick_f64bits(int vpt)
 }
 
 template <typename T, int FM, bool CACHE, bool SMEM>
-static const void *pick_vec4(bool intops, int vpt)
+static const void *pick_vec4(bool intops, int vpt, bool packed)
 {
     if constexpr (sizeof(T) == 8) {
-        if (intops) return pick_f64bits<FM, CACHE, SMEM>(vpt);
+        if (intops) return pick_f64bits<FM, CACHE, SMEM>(vpt, packed);
     }
     (void)vpt;
+    (void)packed;
     (void)intops;
     return (const void *)k_search_vec<T, FM, CACHE, SMEM, false, SEARCH_VPT>;
 }
 template <typename T, int FM, bool CACHE>
-static const void *pick_vec3(bool smem, bool intops, int vpt)
+static const void *pick_vec3(bool smem, bool intops, int vpt, bool packed)
 {
-    return smem ? pick_vec4<T, FM, CACHE, true>(intops, vpt) : pick_vec4<T, FM, CACHE, false>(intops, vpt);
+    return smem ? pick_vec4<T, FM, CACHE, true>(intops, vpt, packed)
+                : pick_vec4<T, FM, CACHE, false>(intops, vpt, packed);
 }
 template <typename T, int FM>
-static const void *pick_vec2(bool cache, bool smem, bool intops, int vpt)
+static const void *pick_vec2(bool cache, bool smem, bool intops, int vpt, bool packed)
 {
-    return cache ? pick_vec3<T, FM, true>(smem, intops, vpt) : pick_vec3<T, FM, false>(smem, intops, vpt);
+    return cache ? pick_vec3<T, FM, true>(smem, intops, vpt, packed)
+                 : pick_vec3<T, FM, false>(smem, intops, vpt, packed);
 }
 template <typename T>
 static const void *pick_vec(const SearchPlan &p)
 {
     switch (p.form) {
-    case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops, p.vpt);
-    case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops, p.vpt);
-    default: return pick_vec2<T, F_PLAIN>(p.cache, p.smem, p.intops, p.vpt);
+    case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops, p.vpt, p.packed);
+    case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops, p.vpt, p.packed);
+    default: return pick_vec2<T, F_PLAIN>(p.cache, p.smem, p.intops, p.vpt, p.packed);
     }
 }
 
