@@ -50,6 +50,15 @@ def lib():
         for nm in ("or_compute_hr_f64", "or_compute_hr_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _INT, _P, _P, _P, _P, _P, _P]
             getattr(L, nm).restype = _INT
+        for nm in ("or_compute_hr_gap2_f64", "or_compute_hr_gap2_f32"):
+            getattr(L, nm).argtypes = [_P, _I64, _INT, _P, _P, _P, _P, _P, _P]
+            getattr(L, nm).restype = _INT
+        for nm in ("or_fill_k_gap2_f64", "or_fill_k_gap2_f32"):
+            getattr(L, nm).argtypes = [_P, _I64, _D, _D, _U32, _INT, _P, _P]
+            getattr(L, nm).restype = _INT
+        for nm in ("or_direct_gap2_f64", "or_direct_gap2_f32"):
+            getattr(L, nm).argtypes = [_P, _P, _D, _D, _U32, _INT, _P, _I64, _P]
+            getattr(L, nm).restype = None
         for nm in ("or_fill_k_f64", "or_fill_k_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _D, _D, _U32, _INT, _P, _P]
             getattr(L, nm).restype = _INT
@@ -108,49 +117,52 @@ def upper_bound_batch(Xcat, x_off, Zcat, z_off):
     return out
 
 
-def compute_hr(X, fma=False):
-    """ComputeHR of Section 4.4 in the array's precision.
+def compute_hr(X, fma=False, gap2=False):
+    """ComputeHR of Section 4.4 in the array's precision (with gap2, its
+    DirectGap2 version of Section 4.7 over the pairs (i, i+2)).
 
     Returns a dict with status (OR_*), H, W, R, updates (number of growth
     steps), passes, bad (offending knot index or -1)."""
     X = np.ascontiguousarray(X)
     H = _D(); W = _D(); R = _U32(); upd = _I64(); passes = _I64(); bad = _I64()
-    st = getattr(lib(), "or_compute_hr_" + _suffix(X))(
+    st = getattr(lib(), ("or_compute_hr_gap2_" if gap2 else "or_compute_hr_") + _suffix(X))(
         _ptr(X), X.shape[0], int(bool(fma)), ctypes.byref(H), ctypes.byref(W), ctypes.byref(R),
         ctypes.byref(upd), ctypes.byref(passes), ctypes.byref(bad))
     return dict(status=st, H=H.value, W=W.value, R=R.value, updates=upd.value,
                 passes=passes.value, bad=bad.value)
 
 
-def fill_k(X, H, W, R, fma=False):
-    """Index table of Eq. indexdef (R+1 int32 entries) and F_i = f(X_i).
-    Returns (status, K, F)."""
+def fill_k(X, H, W, R, fma=False, gap2=False):
+    """Index table of Eq. indexdef (with gap2: Eq. kgeneral), R+1 int32
+    entries, and F_i = f(X_i).  Returns (status, K, F)."""
     X = np.ascontiguousarray(X)
     K = np.empty(int(R) + 1, dtype=np.int32)
     F = np.empty(X.shape[0], dtype=np.uint32)
-    st = getattr(lib(), "or_fill_k_" + _suffix(X))(
+    st = getattr(lib(), ("or_fill_k_gap2_" if gap2 else "or_fill_k_") + _suffix(X))(
         _ptr(X), X.shape[0], float(H), float(W), int(R), int(bool(fma)), _ptr(K), _ptr(F))
     return st, K, F
 
 
-def build_table(X, fma=False):
-    """ComputeHR followed by Eq. indexdef; returns (hr dict, K) or raises."""
-    hr = compute_hr(X, fma)
+def build_table(X, fma=False, gap2=False):
+    """ComputeHR followed by Eq. indexdef (or their DirectGap2 versions);
+    returns (hr dict, K) or raises."""
+    hr = compute_hr(X, fma, gap2)
     if hr["status"] != OR_OK:
         raise ValueError("array infeasible for direct search: status %d" % hr["status"])
-    st, K, _ = fill_k(X, hr["H"], hr["W"], hr["R"], fma)
+    st, K, _ = fill_k(X, hr["H"], hr["W"], hr["R"], fma, gap2)
     if st != OR_OK:
         raise ValueError("table construction failed: status %d" % st)
     return hr, K
 
 
-def direct(X, K, H, W, R, Z, fma=False):
-    """Algorithm "direct" on the CPU with a given (H, W, R, K)."""
+def direct(X, K, H, W, R, Z, fma=False, gap2=False):
+    """Algorithm "direct" (with gap2: Algorithm direct-2) on the CPU with a
+    given (H, W, R, K)."""
     X = np.ascontiguousarray(X)
     Z = np.ascontiguousarray(Z, dtype=X.dtype)
     K = np.ascontiguousarray(K, dtype=np.int32)
     out = np.empty(Z.shape[0], dtype=np.int32)
-    getattr(lib(), "or_direct_" + _suffix(X))(
+    getattr(lib(), ("or_direct_gap2_" if gap2 else "or_direct_") + _suffix(X))(
         _ptr(X), _ptr(K), float(H), float(W), int(R), int(bool(fma)), _ptr(Z), Z.shape[0], _ptr(out))
     return out
 

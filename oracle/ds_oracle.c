@@ -23,6 +23,8 @@
  *                      (Eq. fma) forms.
  *   or_fill_k_*        Eq. indexdef: K_0 = 0, K_j = i for f(X_{i-1}) < j <= f(X_i).
  *   or_direct_*        Algorithm "direct": j = f(z), t = K_j, i = t - [z < X_t].
+ *   or_*_gap2_*        DirectGap2 (Section 4.7): ComputeHR over pairs (i, i+2),
+ *                      K of Eq. kgeneral, Algorithm direct-2.
  *
  * Readings of the paper this file takes where the text is silent or garbled:
  *   - floor in f is truncation toward zero with negatives clamped to 0 and
@@ -357,5 +359,189 @@ void or_interp_f32(const float *X, const float *Y, int64_t n_knots, const float 
         if (i < 0 || i >= n_knots - 1) { y[q] = NAN; continue; }
         double x0 = X[i], x1 = X[i + 1], y0 = Y[i], y1 = Y[i + 1], z = Z[q];
         y[q] = y0 + (y1 - y0) * ((z - x0) / (x1 - x0));
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* DirectGap2 (Section 4.7): f need only satisfy f(X_{i+2}) > f(X_i)         */
+/* (Eq. f-monotonic-2); H > 1/min(X_{i+2} - X_i) (Eq. fcond11) taken in its  */
+/* rounded form m(1/min m(D_{i+2} - D_i)); the growth loop of ComputeHR runs */
+/* over the pairs (i, i+2) ("algorithm ComputeHR needs to be modified        */
+/* accordingly").  D_i == D_{i+1} is allowed; D_i == D_{i+2} is not.  With   */
+/* N = 1 the only pair is (0, 1).                                            */
+/* ------------------------------------------------------------------------ */
+int or_compute_hr_gap2_f64(const double *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
+    if (n_knots < 2) return OR_E_ARG;
+    const int64_t N = n_knots - 1;
+    const int64_t gap = N >= 2 ? 2 : 1;
+    for (int64_t i = 0; i <= N; ++i)
+        if (!isfinite(X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
+    for (int64_t i = 1; i <= N; ++i)
+        if (!(X[i - 1] < X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
+    const double X0 = X[0];
+    for (int64_t i = gap; i <= N; ++i) {
+        double Da = X[i - gap] - X0, Db = X[i] - X0;
+        if (Da == Db) { *bad_out = i; return OR_E_INDISTINGUISHABLE; }
+    }
+    double dmin = INFINITY;
+    for (int64_t i = gap; i <= N; ++i) {
+        double Db = X[i] - X0, Da = X[i - gap] - X0;
+        double g = Db - Da;
+        if (g < dmin) dmin = g;
+    }
+    double H = nextafter(1.0 / dmin, INFINITY);
+    double W = H * X0;
+#define OR_G64(x) (fma_form ? fval_fma_f64(H, W, (x)) : fval_plain_f64(H, X0, (x)))
+    if (!(OR_G64(X[N]) < 4294967296.0)) { *bad_out = N; return OR_E_OVERFLOW; }
+    double P = nextafter(H, INFINITY) - H;
+    int64_t updates = 0, passes = 0;
+    int changed;
+    do {
+        changed = 0;
+        ++passes;
+        for (int64_t i = gap; i <= N; ++i) {
+            while (trunc_u32(OR_G64(X[i - gap])) == trunc_u32(OR_G64(X[i]))) {
+                H = H + P;
+                W = H * X0;
+                if (!(OR_G64(X[N]) < 4294967296.0)) { *bad_out = i; *H_out = H; return OR_E_OVERFLOW; }
+                P = 2.0 * P;
+                ++updates;
+                changed = 1;
+            }
+        }
+    } while (changed && passes < OR_MAX_PASSES);
+    *H_out = H; *W_out = W; *updates_out = updates; *passes_out = passes;
+    if (changed) return OR_E_NO_CONVERGENCE;
+    *R_out = trunc_u32(OR_G64(X[N]));
+#undef OR_G64
+    return OR_OK;
+}
+
+int or_compute_hr_gap2_f32(const float *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
+    if (n_knots < 2) return OR_E_ARG;
+    const int64_t N = n_knots - 1;
+    const int64_t gap = N >= 2 ? 2 : 1;
+    for (int64_t i = 0; i <= N; ++i)
+        if (!isfinite(X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
+    for (int64_t i = 1; i <= N; ++i)
+        if (!(X[i - 1] < X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
+    const float X0 = X[0];
+    for (int64_t i = gap; i <= N; ++i) {
+        float Da = X[i - gap] - X0, Db = X[i] - X0;
+        if (Da == Db) { *bad_out = i; return OR_E_INDISTINGUISHABLE; }
+    }
+    float dmin = INFINITY;
+    for (int64_t i = gap; i <= N; ++i) {
+        float Db = X[i] - X0, Da = X[i - gap] - X0;
+        float g = Db - Da;
+        if (g < dmin) dmin = g;
+    }
+    float H = nextafterf(1.0f / dmin, INFINITY);
+    float W = H * X0;
+#define OR_G32(x) (fma_form ? fval_fma_f32(H, W, (x)) : fval_plain_f32(H, X0, (x)))
+    if (!((double)OR_G32(X[N]) < 4294967296.0)) { *bad_out = N; *H_out = H; return OR_E_OVERFLOW; }
+    float P = nextafterf(H, INFINITY) - H;
+    int64_t updates = 0, passes = 0;
+    int changed;
+    do {
+        changed = 0;
+        ++passes;
+        for (int64_t i = gap; i <= N; ++i) {
+            while (trunc_u32(OR_G32(X[i - gap])) == trunc_u32(OR_G32(X[i]))) {
+                H = H + P;
+                W = H * X0;
+                if (!((double)OR_G32(X[N]) < 4294967296.0)) { *bad_out = i; *H_out = H; return OR_E_OVERFLOW; }
+                P = 2.0f * P;
+                ++updates;
+                changed = 1;
+            }
+        }
+    } while (changed && passes < OR_MAX_PASSES);
+    *H_out = H; *W_out = W; *updates_out = updates; *passes_out = passes;
+    if (changed) return OR_E_NO_CONVERGENCE;
+    *R_out = trunc_u32(OR_G32(X[N]));
+#undef OR_G32
+    return OR_OK;
+}
+
+/* Eq. kgeneral written out: K_j = max{ i : F_i <= j }, j = 0..R (0 where no
+ * knot qualifies, which only cells below F_0 can be). */
+static void fill_k_general(const uint32_t *F, int64_t n_knots, uint32_t R, int32_t *K)
+{
+    int64_t i = -1;
+    for (uint64_t j = 0; j <= R; ++j) {
+        while (i + 1 < n_knots && F[i + 1] <= j) ++i;
+        K[j] = (int32_t)(i < 0 ? 0 : i);
+    }
+}
+
+int or_fill_k_gap2_f64(const double *X, int64_t n_knots, double H, double W, uint32_t R, int fma_form,
+                       int32_t *K, uint32_t *F)
+{
+    const int64_t N = n_knots - 1;
+    const double X0 = X[0];
+    for (int64_t i = 0; i <= N; ++i)
+        F[i] = trunc_u32(fma_form ? fval_fma_f64(H, W, X[i]) : fval_plain_f64(H, X0, X[i]));
+    for (int64_t i = 1; i <= N; ++i)
+        if (F[i - 1] > F[i]) return OR_E_BAD_TABLE;
+    for (int64_t i = 2; i <= N; ++i)
+        if (!(F[i - 2] < F[i])) return OR_E_BAD_TABLE;
+    if (F[N] != R) return OR_E_BAD_TABLE;
+    fill_k_general(F, n_knots, R, K);
+    return OR_OK;
+}
+
+int or_fill_k_gap2_f32(const float *X, int64_t n_knots, double H, double W, uint32_t R, int fma_form,
+                       int32_t *K, uint32_t *F)
+{
+    const int64_t N = n_knots - 1;
+    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
+    for (int64_t i = 0; i <= N; ++i)
+        F[i] = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, X[i]) : fval_plain_f32(Hf, X0, X[i]));
+    for (int64_t i = 1; i <= N; ++i)
+        if (F[i - 1] > F[i]) return OR_E_BAD_TABLE;
+    for (int64_t i = 2; i <= N; ++i)
+        if (!(F[i - 2] < F[i])) return OR_E_BAD_TABLE;
+    if (F[N] != R) return OR_E_BAD_TABLE;
+    fill_k_general(F, n_knots, R, K);
+    return OR_OK;
+}
+
+/* Algorithm direct-2: t = K_j, i = t - [z < X_t] - [z < X_{t-1}] with
+ * X_{-1} = X_0 (left padding); the result is clamped at -1 so that z < X_0
+ * answers -1 like the definition. */
+void or_direct_gap2_f64(const double *X, const int32_t *K, double H, double W, uint32_t R, int fma_form,
+                        const double *Z, int64_t m, int32_t *I)
+{
+    const double X0 = X[0];
+    for (int64_t q = 0; q < m; ++q) {
+        double z = Z[q];
+        uint32_t j = trunc_u32(fma_form ? fval_fma_f64(H, W, z) : fval_plain_f64(H, X0, z));
+        if (j > R) j = R;
+        int32_t t = K[j];
+        double xt = X[t], xp = t > 0 ? X[t - 1] : X0;
+        int32_t i = t - (z < xt ? 1 : 0) - (z < xp ? 1 : 0);
+        I[q] = i < -1 ? -1 : i;
+    }
+}
+
+void or_direct_gap2_f32(const float *X, const int32_t *K, double H, double W, uint32_t R, int fma_form,
+                        const float *Z, int64_t m, int32_t *I)
+{
+    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
+    for (int64_t q = 0; q < m; ++q) {
+        float z = Z[q];
+        uint32_t j = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, z) : fval_plain_f32(Hf, X0, z));
+        if (j > R) j = R;
+        int32_t t = K[j];
+        float xt = X[t], xp = t > 0 ? X[t - 1] : X0;
+        int32_t i = t - (z < xt ? 1 : 0) - (z < xp ? 1 : 0);
+        I[q] = i < -1 ? -1 : i;
     }
 }
