@@ -38,7 +38,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="direct_f64", choices=WORKLOADS)
-    p.add_argument("--variant", default="plain", choices=["plain", "fma", "cache", "fma_cache"])
+    p.add_argument("--variant", default="plain", choices=["plain", "fma", "cache", "fma_cache", "gap2", "fma_gap2"])
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     p.add_argument("--queries", type=int, default=0, help="override the query count (profiling runs)")
@@ -253,8 +253,9 @@ class Job:
 
 def setup_direct(args, ds, W, torch, dev, rank):
     job = Job()
-    flags = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
-             "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT}[args.variant]
+    variants = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
+                "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT, "gap2": ds.DS_GAP2, "fma_gap2": ds.DS_FMA | ds.DS_GAP2}
+    flags = variants[args.variant]
     if args.workload in ("direct_f64", "direct_f64_sorted"):
         w = W.workload2(seed=rank_seed(W, 2, rank), m=args.queries or (1 << 27),
                         sort=args.workload.endswith("sorted"))
@@ -299,12 +300,13 @@ def setup_direct(args, ds, W, torch, dev, rank):
 
     def extras(stream):
         res = {}
-        for name, fl in (("fma", ds.DS_FMA), ("cache", ds.DS_CACHE_LAYOUT),
-                         ("fma_cache", ds.DS_FMA | ds.DS_CACHE_LAYOUT), ("plain", 0)):
+        for name, fl in variants.items():
             if name == args.variant:
                 continue
             j = ds.ds_build(Xd, fl)
             res[name] = job.m / time_calls(torch, stream, lambda: ds.ds_search(j, Zd, out), 5)
+            if fl & ds.DS_GAP2:
+                res[name + "_table_bytes"] = j.info()["table_bytes"]
             j.free()
         if args.workload == "direct_f64":
             Zs = torch.sort(Zd).values

@@ -71,7 +71,11 @@ enum {
     DS_CACHE_LAYOUT = 2u, /* table of (K_j, X_{K_j}) pairs: Section 4.8, Algorithm directcache */
     DS_CHECKED = 4u,      /* NaN queries return -1 */
     DS_NO_SMEM = 8u,      /* never stage the table in shared memory (keep it L2/HBM resident) */
-    DS_STRICT = 16u       /* batched builds: an infeasible array is an error instead of a fallback */
+    DS_STRICT = 16u,      /* batched builds: an infeasible array is an error instead of a fallback */
+    DS_GAP2 = 32u         /* DirectGap2 (Section 4.7): f need only separate knots two apart
+                             (Eq. f-monotonic-2), K_j = max{i : f(X_i) <= j} (Eq. kgeneral), answers by
+                             Algorithm direct-2, i = t - [z < X_t] - [z < X_{t-1}]; a smaller table and
+                             feasible on more arrays; not combined with DS_CACHE_LAYOUT */
 };
 
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
@@ -116,10 +120,14 @@ typedef struct ds_info_t {
  * (Section 4.8).
  *   X_dev    n_knots = N+1 strictly increasing finite values of `dtype`; read
  *            once and copied (the handle does not keep the pointer).
- *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM.
+ *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2.
+ *            With DS_GAP2 (Section 4.7) ComputeHR separates the knot pairs
+ *            (i, i+2) instead of (i, i+1), K follows Eq. kgeneral and searches
+ *            use Algorithm direct-2; at most 2^30 knots, no DS_CACHE_LAYOUT.
  *   out      receives the handle (NULL on failure); release with ds_free.
  * Errors: DS_E_ARG, DS_E_NOT_INCREASING, DS_E_INDISTINGUISHABLE (Section 4.4
- * first counter-example), DS_E_OVERFLOW (second counter-example, Eq.
+ * first counter-example; with DS_GAP2, m(X_{i+2} - X_0) == m(X_i - X_0)),
+ * DS_E_OVERFLOW (second counter-example, Eq.
  * overflowexact), DS_E_NO_CONVERGENCE, DS_E_TABLE_TOO_LARGE (budget: half of
  * the free device memory, or the DS_TABLE_BUDGET_BYTES environment variable),
  * DS_E_NOMEM, DS_E_CUDA.  Synchronous: returns after the table is built. */
@@ -127,7 +135,8 @@ DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, ui
                    ds_index **out);
 
 /* Search m queries (Algorithm direct, Section 4.2): j = min(f(z), R),
- * t = K_j, I = t - [z < X_t].
+ * t = K_j, I = t - [z < X_t]; for a DS_GAP2 index (Algorithm direct-2,
+ * Section 4.7) I = t - [z < X_t] - [z < X_{t-1}], at least -1.
  *   Z_dev  m queries of the index's dtype; I_dev  m int32 results.
  * m == 0 is a no-op.  Asynchronous on `stream`; allocates nothing; safe to
  * capture in a CUDA graph. */
@@ -141,7 +150,8 @@ DS_API ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, in
 DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *I_host, void *stream);
 
 /* Read-only device views of the index's tables (for inspection and tests):
- * K (R+1 int32, Eq. indexdef), the library's copy of X (N+1 values), and,
+ * K (R+1 int32, Eq. indexdef or Eq. kgeneral, with the search's flag bits:
+ * bit 31, and bit 30 for DS_GAP2), the library's copy of X (N+1 values), and,
  * with DS_CACHE_LAYOUT, the (R+1) pairs (8 bytes for float32: int32 K_j then
  * float X_{K_j}; 16 bytes for float64: int32 K_j, 4 bytes of padding, double
  * X_{K_j}).  Any output pointer may be NULL. */
@@ -149,7 +159,7 @@ DS_API ds_status ds_index_tables(const ds_index *idx, const int32_t **K_dev, con
                           const void **pairs_dev);
 
 /* Copy the same tables into caller-owned device buffers (each may be NULL):
- * K_out (R+1 int32), X_out (N+1 values), pairs_out ((R+1) pairs, only with
+ * K_out (R+1 int32, flags cleared), X_out (N+1 values), pairs_out ((R+1) pairs, only with
  * DS_CACHE_LAYOUT).  Asynchronous on `stream`. */
 DS_API ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, void *X_out_dev, void *pairs_out_dev,
                                  void *stream);

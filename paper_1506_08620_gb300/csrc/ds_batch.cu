@@ -149,7 +149,7 @@ static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const
     DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState) * (size_t)A));
     const int sgrid = std::max(1, std::min(n_segs, props.num_sms * 8));
     const int agrid = (A + 127) / 128;
-    k_hr_state_init<<<agrid, 128, 0, s>>>(st, A);
+    k_hr_state_init<<<agrid, 128, 0, s>>>(st, A, 1);
     k_seg_validate<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, st);
     k_seg_hr_init<T, FMA><<<agrid, 128, 0, s>>>(Xcat, x_off_dev, A, st);
     hs.resize(A);

@@ -7,7 +7,7 @@
 
 namespace ds {
 
-__global__ void k_hr_state_init(HRState *st, int count)
+__global__ void k_hr_state_init(HRState *st, int count, int gap)
 {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= count) return;
@@ -18,33 +18,72 @@ __global__ void k_hr_state_init(HRState *st, int count)
     s.bad_order = NONE64;
     s.bad_indist = NONE64;
     s.min_gap_bits = NONE64;
+    s.gap = gap;
     st[a] = s;
 }
 
-__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P)
+__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P,
+                             uint32_t flag_mask)
 {
     const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
     const long long step = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < (long long)nblk; b += step) {
         const unsigned long long j0 = (unsigned long long)b * PACK_CELLS;
-        const uint32_t base = K[j0] & ~KNOT_FLAG;
+        const uint32_t base = K[j0] & ~flag_mask;
         uint32_t w[3] = {0u, 0u, 0u};
         for (int s = 0; s < PACK_CELLS; ++s) {
             const unsigned long long j = j0 + s;
             if (j > R) break;
             const uint32_t e = K[j];
-            const uint32_t byte = ((e & ~KNOT_FLAG) - base) | ((e & KNOT_FLAG) ? 0x80u : 0u);
+            const uint32_t byte = ((e & ~flag_mask) - base) | ((e & flag_mask) >> 24);
             w[s >> 2] |= byte << ((s & 3) * 8);
         }
         P[b] = make_uint4(base, w[0], w[1], w[2]);
     }
 }
 
-__global__ void k_clear_flags(uint32_t *p, long long count, int stride)
+__global__ void k_clear_flags(uint32_t *p, long long count, int stride, uint32_t flag_mask)
 {
     const long long step = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += step)
-        p[i * stride] &= ~KNOT_FLAG;
+        p[i * stride] &= ~flag_mask;
+}
+
+__global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_knots, unsigned long long R,
+                                 uint32_t *__restrict__ K)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long N = n_knots - 1;
+    const long long nchunks = (n_knots + 31) / 32;
+    for (long long c = warp; c < nchunks; c += nwarps) {
+        const long long i = c * 32 + lane;
+        const long long Fi = i <= N ? (long long)F[i] : (1ll << 32);  // lanes past X_N never qualify
+        const long long lo = c == 0 ? 0 : (long long)F[c * 32];
+        const long long hi = c + 1 == nchunks ? (long long)R + 1 : (long long)F[c * 32 + 32];
+        const long long before = c == 0 ? -1 : (long long)F[c * 32 - 1];  // F_{32c-1}
+        for (long long base = lo; base < hi; base += 32) {
+            const long long j = base + lane;
+            // largest lane k with F_{32c+k} <= j (lane 0 qualifies except in the
+            // cells below F_0, where K_j = 0)
+            int k = 0;
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const long long Fc = __shfl_sync(0xffffffffu, Fi, (k + s) & 31);
+                if (k + s <= 31 && Fc <= j) k += s;
+            }
+            const long long Fk = __shfl_sync(0xffffffffu, Fi, k);
+            const long long Fkm = __shfl_sync(0xffffffffu, Fi, (k + 31) & 31);
+            const long long Fprev = k == 0 ? before : Fkm;
+            if (j < hi) {
+                uint32_t e = (uint32_t)(c * 32 + k);
+                if (Fk >= j) e |= KNOT_FLAG;
+                if (Fprev == j) e |= KNOT_FLAG2;
+                K[j] = e;
+            }
+        }
+    }
 }
 
 static int grid_for(const DeviceProps &p, long long work, int block)
@@ -75,11 +114,11 @@ static bool f64_intops_default()
 // *host_st.  `st` is device scratch for one HRState.
 template <typename T, bool FMA>
 static ds_status run_compute_hr(const T *X, long long n_knots, HRState *st, HRState *host_st, cudaStream_t s,
-                                const DeviceProps &props)
+                                const DeviceProps &props, int gap)
 {
     const int block = 256;
     const int grid = grid_for(props, n_knots, block);
-    k_hr_state_init<<<1, 1, 0, s>>>(st, 1);
+    k_hr_state_init<<<1, 1, 0, s>>>(st, 1, gap);
     k_validate<T><<<grid, block, 0, s>>>(X, n_knots, st);
     k_hr_init<T, FMA><<<1, 1, 0, s>>>(X, n_knots, st);
     DS_TRY_CUDA(cudaGetLastError());
@@ -104,7 +143,7 @@ static const char *hr_message(int status)
 {
     switch (status) {
     case DS_E_NOT_INCREASING: return "knots are not strictly increasing finite values";
-    case DS_E_INDISTINGUISHABLE: return "m(X_i - X_0) == m(X_{i-1} - X_0): direct search infeasible";
+    case DS_E_INDISTINGUISHABLE: return "m(X_i - X_0) == m(X_{i-g} - X_0) (g = 1, or 2 for DirectGap2): direct search infeasible";
     case DS_E_OVERFLOW: return "m(H (X_N - X_0)) >= 2^32: direct search infeasible (Q = 32)";
     case DS_E_NO_CONVERGENCE: return "growth of H did not settle";
     default: return "";
@@ -119,7 +158,11 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     HRState *st = nullptr;
     DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
     HRState hs;
-    ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props);
+    const bool gap2 = (flags & DS_GAP2) != 0;
+    // DirectGap2 separates the pairs (i, i+2); with two knots the only pair is (0, 1)
+    const int gap = gap2 && n_knots >= 3 ? 2 : 1;
+    idx->gap2 = gap2;
+    ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props, gap);
     cudaFree(st);
     if (rc != DS_OK) return rc;
     idx->updates = hs.updates;
@@ -156,8 +199,11 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     const int block = 256;
     k_fill_F<T, FMA><<<grid_for(props, n_knots, block), block, 0, s>>>(Xc, n_knots, (T)hs.H, (T)hs.W, F);
     long long warps_work = (n_knots + 31) / 32 * 32;
-    k_fill_K<T><<<grid_for(props, warps_work, block), block, 0, s>>>(
-        F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
+    if (gap2)
+        k_fill_K_general<<<grid_for(props, warps_work, block), block, 0, s>>>(F, n_knots, R, K);
+    else
+        k_fill_K<T><<<grid_for(props, warps_work, block), block, 0, s>>>(
+            F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(s);
     cudaFree(F);
@@ -169,6 +215,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     SearchPlan &plan = idx->plan;
     plan.form = FMA ? F_FMA : (x0zero ? F_PLAIN_X0ZERO : F_PLAIN);
     plan.cache = cache;
+    plan.gap2 = gap2;
     plan.intops = sizeof(T) == 8 && f64_intops_default();
     plan.block = SEARCH_BLOCK;
     plan.vpt = SEARCH_VPT;
@@ -186,7 +233,8 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
             const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
             idx->k16_bytes = (size_t)nblk * sizeof(uint4);
             DS_TRY_CUDA(cudaMalloc(&idx->k16, idx->k16_bytes));
-            k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(K, R, idx->k16);
+            k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(
+                K, R, idx->k16, gap2 ? KNOT_FLAG | KNOT_FLAG2 : KNOT_FLAG);
             DS_TRY_CUDA(cudaGetLastError());
             DS_TRY_CUDA(cudaStreamSynchronize(s));
             idx->table_bytes += idx->k16_bytes;
@@ -320,7 +368,8 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
     const int grid = (int)((cells + 255) / 256 < idx->props.num_sms * 8 ? (cells + 255) / 256 : idx->props.num_sms * 8);
     if (K_out_dev) {
         DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(K_out_dev), cells, 1);
+        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(K_out_dev), cells, 1,
+                                               idx->gap2 ? ds::KNOT_FLAG | ds::KNOT_FLAG2 : ds::KNOT_FLAG);
         DS_TRY_CUDA(cudaGetLastError());
     }
     if (X_out_dev)
@@ -333,7 +382,8 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
         }
         DS_TRY_CUDA(cudaMemcpyAsync(pairs_out_dev, idx->pairs, (size_t)cells * (esz == 4 ? 8 : 16),
                                     cudaMemcpyDeviceToDevice, s));
-        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(pairs_out_dev), cells, esz == 4 ? 2 : 4);
+        ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(pairs_out_dev), cells, esz == 4 ? 2 : 4,
+                                               ds::KNOT_FLAG);
         DS_TRY_CUDA(cudaGetLastError());
     }
     return DS_OK;

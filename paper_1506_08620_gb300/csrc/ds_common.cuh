@@ -55,7 +55,8 @@ struct HRState {
     double H, W, P;
     unsigned long long R;
     long long updates, passes, cursor;
-    int status, done, grew, pad_;
+    int status, done, grew;
+    int gap;                             // pair distance: 1 (Direct) or 2 (DirectGap2)
     unsigned long long first_violation;  // atomicMin target of the pair scan
     unsigned long long bad_nonfinite;    // first knot that is NaN/Inf
     unsigned long long bad_order;        // first i with !(X_{i-1} < X_i)

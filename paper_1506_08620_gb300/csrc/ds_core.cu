@@ -191,13 +191,21 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
     }
     *out = nullptr;
     if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2))) {
         set_error("ds_build: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u)", X_dev, (long long)n_knots,
                   (int)dtype, flags);
         return DS_E_ARG;
     }
     if (n_knots > (1ll << 31) - 1) {
         set_error("ds_build: at most 2^31-1 knots (int32 results)");
+        return DS_E_ARG;
+    }
+    if ((flags & DS_GAP2) && (flags & DS_CACHE_LAYOUT)) {
+        set_error("ds_build: DS_GAP2 has no cache layout (its correction reads two knots)");
+        return DS_E_ARG;
+    }
+    if ((flags & DS_GAP2) && n_knots > (1ll << 30)) {
+        set_error("ds_build: DS_GAP2 takes at most 2^30 knots (two flag bits per table entry)");
         return DS_E_ARG;
     }
     return build_single(X_dev, n_knots, dtype, flags, (cudaStream_t)stream, out);

@@ -25,6 +25,7 @@ struct ds_index {
     size_t pair_bytes;
     size_t table_bytes;
     ds::SearchPlan plan;
+    int gap2;
     uint32_t smem_bytes;
     int *dev_err;
     ds::DeviceProps props;
@@ -34,15 +35,18 @@ struct ds_index {
 namespace ds {
 
 // ---------------------------------------------------------------- kernels
-__global__ void k_hr_state_init(HRState *st, int count);
+// gap: pair distance of the separation property (1 Direct, 2 DirectGap2).
+__global__ void k_hr_state_init(HRState *st, int count, int gap);
 
 // Validation and the minimum gap of the rounded differences D_i = m(X_i - X_0)
-// (Eq. distinguishable-exact, Eq. minhnumeric).
+// (Eq. distinguishable-exact, Eq. minhnumeric); with pair distance 2
+// (DirectGap2, Section 4.7) the differences D_i - D_{i-2} (Eq. fcond11).
 template <typename T>
 __global__ void k_validate(const T *__restrict__ X, long long n_knots, HRState *st)
 {
     using A = Arith<T>;
     const T X0 = X[0];
+    const int pg = st->gap;
     unsigned long long gmin = NONE64;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_knots; i += stride) {
@@ -51,7 +55,9 @@ __global__ void k_validate(const T *__restrict__ X, long long n_knots, HRState *
         if (i >= 1) {
             const T xp = X[i - 1];
             if (!(xp < xi)) atomicMin(&st->bad_order, (unsigned long long)i);
-            const T dp = A::sub(xp, X0), di = A::sub(xi, X0);
+        }
+        if (i >= pg) {
+            const T dp = A::sub(X[i - pg], X0), di = A::sub(xi, X0);
             if (dp == di) atomicMin(&st->bad_indist, (unsigned long long)i);
             const T gap = A::sub(di, dp);
             if (gap > T(0)) {
@@ -77,7 +83,7 @@ __device__ void hr_init_one(const T *X, long long n_knots, HRState *st)
     st->first_violation = NONE64;
     st->updates = 0;
     st->passes = 1;
-    st->cursor = 1;
+    st->cursor = st->gap;
     st->grew = 0;
     if (st->bad_nonfinite != NONE64 || st->bad_order != NONE64) {
         st->status = DS_E_NOT_INCREASING;
@@ -119,9 +125,10 @@ __global__ void k_hr_check(const T *__restrict__ X, long long n_knots, HRState *
     if (st->done) return;
     const T H = (T)st->H, W = (T)st->W, X0 = X[0];
     const long long c = st->cursor;
+    const int pg = st->gap;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = c + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_knots; i += stride) {
-        const uint32_t fa = A::trunc_u32(fval<T, FMA>(H, W, X0, X[i - 1]));
+        const uint32_t fa = A::trunc_u32(fval<T, FMA>(H, W, X0, X[i - pg]));
         const uint32_t fb = A::trunc_u32(fval<T, FMA>(H, W, X0, X[i]));
         if (fa == fb) atomicMin(&st->first_violation, (unsigned long long)i);
     }
@@ -148,14 +155,14 @@ __device__ void hr_grow_one(const T *X, long long n_knots, HRState *st)
             }
             st->passes += 1;
             st->grew = 0;
-            st->cursor = 1;
+            st->cursor = st->gap;
             return;
         }
         st->R = A::trunc_u32(fval<T, FMA>(H, W, X0, XN));
         st->done = 1;
         return;
     }
-    const T xa = X[v - 1], xb = X[v];
+    const T xa = X[v - st->gap], xb = X[v];
     while (A::trunc_u32(fval<T, FMA>(H, W, X0, xa)) == A::trunc_u32(fval<T, FMA>(H, W, X0, xb))) {
         H = A::add(H, P);
         W = A::mul(H, X0);
@@ -237,12 +244,21 @@ __global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, uint
     }
 }
 
-// Packed copy of the flagged K: block b = {K_{12b}, 12 bytes (K_j - K_{12b}) | flag << 7}.
-__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P);
+// K_j = max{ i : F_i <= j }, j = 0..R (Eq. kgeneral; 0 below F_0), for
+// DirectGap2, with bit 31 set when F_t >= j and bit 30 when F_{t-1} == j.
+// Warp c owns the cells [F_{32c}, F_{32c+32}) (chunk 0 from 0, the last chunk
+// up to R) and finds each cell's knot by a 5-step search over its 32 F values.
+__global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_knots, unsigned long long R,
+                                 uint32_t *__restrict__ K);
 
-// Clear the knot flag (bit 31) of every stride-th 32-bit word: turns a copy of
-// the flagged table into the plain K of Eq. indexdef.
-__global__ void k_clear_flags(uint32_t *p, long long count, int stride);
+// Packed copy of the flagged K: block b = {K_{12b}, 12 bytes (K_j - K_{12b}) | flags >> 24};
+// flag_mask selects the flag bits (bit 31, and bit 30 for DirectGap2).
+__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P,
+                             uint32_t flag_mask);
+
+// Clear the knot flags (flag_mask) of every stride-th 32-bit word: turns a copy
+// of the flagged table into the plain K of Eq. indexdef (or Eq. kgeneral).
+__global__ void k_clear_flags(uint32_t *p, long long count, int stride, uint32_t flag_mask);
 
 // host side, defined in ds_build.cu
 ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, cudaStream_t s,

@@ -14,6 +14,13 @@
 // f(z) = j < F_t = f(X_t), so z < X_t by the monotonicity of f (property
 // monotonic of Eq. fprop) and the answer is t - 1 without reading X_t; only
 // queries in a cell that holds a knot need the correcting comparison.
+//
+// DirectGap2 (Section 4.7) tables hold t = K_j = max{i : F_i <= j} (Eq.
+// kgeneral) with two flags: bit 31 when F_t >= j (knot t in the cell, or the
+// cells below F_0 where t = 0) and bit 30 when F_{t-1} == j (a second knot in
+// the cell).  Without bit 31, F_t < j = f(z) gives z > X_t and the answer is t;
+// Algorithm direct-2's comparisons i = t - [z < X_t] - [z < X_{t-1}] are made
+// only where the flags say they can be true.
 #pragma once
 
 #include "ds_common.cuh"
@@ -24,12 +31,16 @@ namespace ds {
 enum FForm : int { F_PLAIN = 0, F_FMA = 1, F_PLAIN_X0ZERO = 2 };
 
 constexpr uint32_t KNOT_FLAG = 0x80000000u;
+constexpr uint32_t KNOT_FLAG2 = 0x40000000u;  // DirectGap2: knot t-1 in the cell too
+constexpr uint32_t GAP2_T_MASK = 0x3FFFFFFFu;
 
 // Packed table: K in 16-byte blocks of 12 cells, {K of the block's first
-// cell, 12 bytes (K_j - base) | knot flag << 7}.  Each cell holds at most one
-// knot (F is strictly increasing), so K grows by at most 1 per cell and the
-// difference fits 7 bits; 1.33 bytes per cell instead of 4 keeps large tables
-// L2-resident, and a lookup still reads one 16-byte sector.
+// cell, 12 bytes (K_j - base) | flags << 6}.  A cell holds at most one knot
+// (Direct: F strictly increasing) or two (DirectGap2: F_{i+2} > F_i), so K
+// grows by at most 2 per cell and the difference (at most 22) fits 6 bits;
+// bits 6 and 7 carry the flags of bits 30 and 31.  1.33 bytes per cell instead
+// of 4 keeps large tables L2-resident, and a lookup still reads one 16-byte
+// sector.
 constexpr int PACK_CELLS = 12;
 
 __device__ __forceinline__ uint32_t unpack_cell(uint4 w, uint32_t j)
@@ -38,7 +49,7 @@ __device__ __forceinline__ uint32_t unpack_cell(uint4 w, uint32_t j)
     const uint32_t s = j - b * PACK_CELLS;
     const uint32_t word = s < 4 ? w.y : (s < 8 ? w.z : w.w);
     const uint32_t byte = (word >> ((s & 3u) * 8u)) & 0xFFu;
-    return (w.x + (byte & 0x7Fu)) | ((byte & 0x80u) << 24);
+    return (w.x + (byte & 0x3Fu)) | ((byte & 0xC0u) << 24);
 }
 
 template <typename T> struct SearchArgs {
@@ -136,20 +147,47 @@ __device__ __forceinline__ int32_t correct(T z, uint32_t e, T x, int checked)
     return i;
 }
 
-template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS>
+template <typename T, bool INTOPS>
+__device__ __forceinline__ bool z_less(T z, T x)
+{
+    if constexpr (INTOPS && sizeof(T) == 8) return okey((double)z) < okey((double)x);
+    else return z < x;
+}
+
+// DirectGap2 correction (Algorithm direct-2): i = t - [z < X_t] - [z < X_{t-1}]
+// with each comparison made only under its flag; x = X_t, xp = X_{t-1}.
+template <typename T, bool INTOPS>
+__device__ __forceinline__ int32_t correct_gap2(T z, uint32_t e, T x, T xp, int checked)
+{
+    int32_t i = (int32_t)(e & GAP2_T_MASK);
+    if (e & KNOT_FLAG) i -= (int32_t)z_less<T, INTOPS>(z, x);
+    if (e & KNOT_FLAG2) i -= (int32_t)z_less<T, INTOPS>(z, xp);
+    if (checked && is_nan<T>(z)) i = -1;
+    return i;
+}
+
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, bool GAP2 = false>
 __device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, const Pair<T> *P,
                                           const SearchArgs<T> &a)
 {
     const uint32_t j = cell_of<T, FM, INTOPS>(z, a);
     T x = T(0);
     const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x);
-    if constexpr (!CACHE) {
-        if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
+    if constexpr (GAP2) {
+        const int32_t t = (int32_t)(e & GAP2_T_MASK);
+        T xp = T(0);
+        if (e & KNOT_FLAG) x = gather_x<T, SMEM>(t, X);
+        if (e & KNOT_FLAG2) xp = gather_x<T, SMEM>(t - 1, X);
+        return correct_gap2<T, INTOPS>(z, e, x, xp, a.checked);
+    } else {
+        if constexpr (!CACHE) {
+            if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
+        }
+        return correct<T, INTOPS>(z, e, x, a.checked);
     }
-    return correct<T, INTOPS>(z, e, x, a.checked);
 }
 
-template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, int VPT>
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, int VPT, bool GAP2 = false>
 __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long nvec, long long ntiles)
 {
     using V = typename VecOf<T>::V;
@@ -196,14 +234,27 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q]);
-        if constexpr (!CACHE) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & ~KNOT_FLAG), X);
-        }
         int32_t r[NQ];
+        if constexpr (GAP2) {
+            T xp[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) r[q] = correct<T, INTOPS>(zs[q], e[q], x[q], a.checked);
+            for (int q = 0; q < NQ; ++q) {
+                const int32_t t = (int32_t)(e[q] & GAP2_T_MASK);
+                xp[q] = T(0);
+                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>(t, X);
+                if (e[q] & KNOT_FLAG2) xp[q] = gather_x<T, SMEM>(t - 1, X);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) r[q] = correct_gap2<T, INTOPS>(zs[q], e[q], x[q], xp[q], a.checked);
+        } else {
+            if constexpr (!CACHE) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+                    if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & ~KNOT_FLAG), X);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) r[q] = correct<T, INTOPS>(zs[q], e[q], x[q], a.checked);
+        }
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             const long long idx = b + (long long)v * blockDim.x;
@@ -218,17 +269,17 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
     // the last m mod L queries
     if (blockIdx.x == 0) {
         const long long q = nvec * L + threadIdx.x;
-        if (q < a.m) a.I[q] = lookup<T, FM, CACHE, SMEM, INTOPS>(a.Z[q], K, X, P, a);
+        if (q < a.m) a.I[q] = lookup<T, FM, CACHE, SMEM, INTOPS, GAP2>(a.Z[q], K, X, P, a);
     }
 }
 
 // Scalar path for queries or results that are not aligned for vector access.
-template <typename T, int FM, bool CACHE, bool INTOPS>
+template <typename T, int FM, bool CACHE, bool INTOPS, bool GAP2 = false>
 __global__ void __launch_bounds__(256) k_search_scalar(SearchArgs<T> a)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride)
-        a.I[q] = lookup<T, FM, CACHE, false, INTOPS>(a.Z[q], a.K, a.X, a.P, a);
+        a.I[q] = lookup<T, FM, CACHE, false, INTOPS, GAP2>(a.Z[q], a.K, a.X, a.P, a);
 }
 
 // Float64 lookups with the data kept as IEEE bit patterns (long long)
@@ -261,7 +312,18 @@ __device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long l
     return i;
 }
 
-template <int FM, bool CACHE, bool SMEM, int VPT, bool PACKED = false>
+__device__ __forceinline__ int32_t correct_bits_gap2(long long zb, uint32_t e, long long xb, long long xpb,
+                                                     int checked)
+{
+    const long long kz = okey_bits(zb);
+    int32_t i = (int32_t)(e & GAP2_T_MASK);
+    if (e & KNOT_FLAG) i -= (int32_t)(kz < okey_bits(xb));
+    if (e & KNOT_FLAG2) i -= (int32_t)(kz < okey_bits(xpb));
+    if (checked && ((unsigned long long)zb & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) i = -1;
+    return i;
+}
+
+template <int FM, bool CACHE, bool SMEM, int VPT, bool PACKED = false, bool GAP2 = false>
 __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, long long nvec, long long ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -323,22 +385,44 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
             }
         }
-        if constexpr (!CACHE) {
+        if constexpr (GAP2) {
+            long long xpb[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
+                const long long *px = Xb + (e[q] & GAP2_T_MASK);
                 xb[q] = 0;
-                if (e[q] & KNOT_FLAG) {
-                    const long long *px = Xb + (e[q] & ~KNOT_FLAG);
-                    xb[q] = SMEM ? *px : ld_keep(px, keep);
+                xpb[q] = 0;
+                if (e[q] & KNOT_FLAG) xb[q] = SMEM ? px[0] : ld_keep(px, keep);
+                if (e[q] & KNOT_FLAG2) xpb[q] = SMEM ? px[-1] : ld_keep(px - 1, keep);
+            }
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                const long long idx = b + (long long)v * blockDim.x;
+                if (idx < nvec)
+                    __stcs(Iv + idx,
+                           make_int2(correct_bits_gap2(zb[2 * v], e[2 * v], xb[2 * v], xpb[2 * v], a.checked),
+                                     correct_bits_gap2(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], xpb[2 * v + 1],
+                                                       a.checked)));
+            }
+        } else {
+            if constexpr (!CACHE) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    xb[q] = 0;
+                    if (e[q] & KNOT_FLAG) {
+                        const long long *px = Xb + (e[q] & ~KNOT_FLAG);
+                        xb[q] = SMEM ? *px : ld_keep(px, keep);
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-            const long long idx = b + (long long)v * blockDim.x;
-            if (idx < nvec)
-                __stcs(Iv + idx, make_int2(correct_bits(zb[2 * v], e[2 * v], xb[2 * v], a.checked),
-                                           correct_bits(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], a.checked)));
+            for (int v = 0; v < VPT; ++v) {
+                const long long idx = b + (long long)v * blockDim.x;
+                if (idx < nvec)
+                    __stcs(Iv + idx,
+                           make_int2(correct_bits(zb[2 * v], e[2 * v], xb[2 * v], a.checked),
+                                     correct_bits(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], a.checked)));
+            }
         }
     }
     if (blockIdx.x == 0) {  // the last m mod 2 queries
@@ -353,12 +437,19 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 xq = p.y;
             } else if constexpr (PACKED) {
                 e = unpack_cell(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
-                if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
             } else {
                 e = K[e];
-                if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
             }
-            a.I[q] = correct_bits(zq, e, xq, a.checked);
+            if constexpr (GAP2) {
+                const long long *px = Xb + (e & GAP2_T_MASK);
+                const long long xq0 = (e & KNOT_FLAG) ? px[0] : 0, xq1 = (e & KNOT_FLAG2) ? px[-1] : 0;
+                a.I[q] = correct_bits_gap2(zq, e, xq0, xq1, a.checked);
+            } else {
+                if constexpr (!CACHE) {
+                    if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
+                }
+                a.I[q] = correct_bits(zq, e, xq, a.checked);
+            }
         }
     }
 }
@@ -366,6 +457,7 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
 struct SearchPlan {
     int form;      // FForm
     bool cache, smem, intops, packed;
+    bool gap2;     // DirectGap2 table (Eq. kgeneral) and Algorithm direct-2
     int block;     // threads per block
     int vpt;       // vectors per thread per tile
     int grid_cap;  // resident blocks (one wave)

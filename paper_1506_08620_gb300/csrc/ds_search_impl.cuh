@@ -45,9 +45,38 @@ static const void *pick_vec2(bool cache, bool smem, bool intops, int vpt, bool p
     return cache ? pick_vec3<T, FM, true>(smem, intops, vpt, packed)
                  : pick_vec3<T, FM, false>(smem, intops, vpt, packed);
 }
+// DirectGap2 kernels: no cache layout; float64 on bit patterns with VPT 2 or 4.
+template <typename T, int FM, bool SMEM>
+static const void *pick_gap2_3(const SearchPlan &p)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (p.intops) {
+            if constexpr (!SMEM) {
+                if (p.packed) return p.vpt == 4 ? (const void *)k_search_f64bits<FM, false, false, 4, true, true>
+                                                : (const void *)k_search_f64bits<FM, false, false, 2, true, true>;
+            }
+            return p.vpt == 4 ? (const void *)k_search_f64bits<FM, false, SMEM, 4, false, true>
+                              : (const void *)k_search_f64bits<FM, false, SMEM, 2, false, true>;
+        }
+    }
+    return (const void *)k_search_vec<T, FM, false, SMEM, false, SEARCH_VPT, true>;
+}
+template <typename T, int FM>
+static const void *pick_gap2_2(const SearchPlan &p)
+{
+    return p.smem ? pick_gap2_3<T, FM, true>(p) : pick_gap2_3<T, FM, false>(p);
+}
+
 template <typename T>
 static const void *pick_vec(const SearchPlan &p)
 {
+    if (p.gap2) {
+        switch (p.form) {
+        case F_FMA: return pick_gap2_2<T, F_FMA>(p);
+        case F_PLAIN_X0ZERO: return pick_gap2_2<T, F_PLAIN_X0ZERO>(p);
+        default: return pick_gap2_2<T, F_PLAIN>(p);
+        }
+    }
     switch (p.form) {
     case F_FMA: return pick_vec2<T, F_FMA>(p.cache, p.smem, p.intops, p.vpt, p.packed);
     case F_PLAIN_X0ZERO: return pick_vec2<T, F_PLAIN_X0ZERO>(p.cache, p.smem, p.intops, p.vpt, p.packed);
@@ -69,9 +98,26 @@ static const void *pick_scalar2(bool cache, bool intops)
 {
     return cache ? pick_scalar3<T, FM, true>(intops) : pick_scalar3<T, FM, false>(intops);
 }
+template <typename T, int FM>
+static const void *pick_scalar_gap2(bool intops)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (intops) return (const void *)k_search_scalar<T, FM, false, true, true>;
+    }
+    (void)intops;
+    return (const void *)k_search_scalar<T, FM, false, false, true>;
+}
+
 template <typename T>
 static const void *pick_scalar(const SearchPlan &p)
 {
+    if (p.gap2) {
+        switch (p.form) {
+        case F_FMA: return pick_scalar_gap2<T, F_FMA>(p.intops);
+        case F_PLAIN_X0ZERO: return pick_scalar_gap2<T, F_PLAIN_X0ZERO>(p.intops);
+        default: return pick_scalar_gap2<T, F_PLAIN>(p.intops);
+        }
+    }
     switch (p.form) {
     case F_FMA: return pick_scalar2<T, F_FMA>(p.cache, p.intops);
     case F_PLAIN_X0ZERO: return pick_scalar2<T, F_PLAIN_X0ZERO>(p.cache, p.intops);

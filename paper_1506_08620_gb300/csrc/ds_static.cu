@@ -69,7 +69,7 @@ static ds_status static_build(const T *X, long long n_knots, int32_t *K_out, lon
     const int grid = (int)(want < props.num_sms * 8 ? (want < 1 ? 1 : want) : props.num_sms * 8);
 
     // ComputeHR: the state slot is re-initialised on every call
-    k_hr_state_init<<<1, 1, 0, s>>>(st, 1);
+    k_hr_state_init<<<1, 1, 0, s>>>(st, 1, 1);
     k_validate<T><<<grid, block, 0, s>>>(X, n_knots, st);
     k_hr_init<T, FMA><<<1, 1, 0, s>>>(X, n_knots, st);
     HRState hs;
@@ -105,7 +105,7 @@ static ds_status static_build(const T *X, long long n_knots, int32_t *K_out, lon
     const int wgrid = (int)(wwant < props.num_sms * 8 ? (wwant < 1 ? 1 : wwant) : props.num_sms * 8);
     k_fill_K<T><<<wgrid, block, 0, s>>>(F, n_knots, reinterpret_cast<uint32_t *>(K_out), nullptr, X);
     // the caller receives the plain K of Eq. indexdef
-    k_clear_flags<<<wgrid, block, 0, s>>>(reinterpret_cast<uint32_t *>(K_out), (long long)hs.R + 1, 1);
+    k_clear_flags<<<wgrid, block, 0, s>>>(reinterpret_cast<uint32_t *>(K_out), (long long)hs.R + 1, 1, KNOT_FLAG);
     DS_TRY_CUDA(cudaGetLastError());
     DS_TRY_CUDA(cudaStreamSynchronize(s));
     return DS_OK;
