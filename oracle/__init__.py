@@ -7,7 +7,8 @@ it, and it imports nothing from here.
 
 * ``ds_oracle.c`` (plain C, loaded with ctypes) holds the definition of the
   answer (Section 2), the brute-force scan it is pinned against, ComputeHR
-  (Section 4.4), the index table of Eq. indexdef and Algorithm "direct".
+  (Section 4.4), the index table of Eq. indexdef and Algorithm "direct", and
+  their DirectGap2 / Gap-q versions (Section 4.7, Eq. kgeneral).
 * ``mlp.py`` holds the float64 reference of the learned predictor (forward,
   loss, backward, Adam) used to check the GPU training kernels' gradients.
 * The fused-interpolation reference evaluates the interpolant in float64
@@ -53,11 +54,20 @@ def lib():
         for nm in ("or_compute_hr_gap2_f64", "or_compute_hr_gap2_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _INT, _P, _P, _P, _P, _P, _P]
             getattr(L, nm).restype = _INT
+        for nm in ("or_compute_hr_gapq_f64", "or_compute_hr_gapq_f32"):
+            getattr(L, nm).argtypes = [_P, _I64, _I32, _INT, _P, _P, _P, _P, _P, _P]
+            getattr(L, nm).restype = _INT
         for nm in ("or_fill_k_gap2_f64", "or_fill_k_gap2_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _D, _D, _U32, _INT, _P, _P]
             getattr(L, nm).restype = _INT
+        for nm in ("or_fill_k_gapq_f64", "or_fill_k_gapq_f32"):
+            getattr(L, nm).argtypes = [_P, _I64, _I32, _D, _D, _U32, _INT, _P, _P]
+            getattr(L, nm).restype = _INT
         for nm in ("or_direct_gap2_f64", "or_direct_gap2_f32"):
             getattr(L, nm).argtypes = [_P, _P, _D, _D, _U32, _INT, _P, _I64, _P]
+            getattr(L, nm).restype = None
+        for nm in ("or_direct_gapq_f64", "or_direct_gapq_f32"):
+            getattr(L, nm).argtypes = [_P, _P, _I32, _D, _D, _U32, _INT, _P, _I64, _P]
             getattr(L, nm).restype = None
         for nm in ("or_fill_k_f64", "or_fill_k_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _D, _D, _U32, _INT, _P, _P]
@@ -117,54 +127,92 @@ def upper_bound_batch(Xcat, x_off, Zcat, z_off):
     return out
 
 
-def compute_hr(X, fma=False, gap2=False):
-    """ComputeHR of Section 4.4 in the array's precision (with gap2, its
-    DirectGap2 version of Section 4.7 over the pairs (i, i+2)).
+def _q_of(gap2, q):
+    if gap2:
+        return 2
+    return 1 if q is None else int(q)
+
+
+def compute_hr(X, fma=False, gap2=False, q=None, general=False):
+    """ComputeHR of Section 4.4 in the array's precision.  With q >= 2 (gap2
+    is q = 2) its DirectGap2 / Gap-q version of Section 4.7 over the pairs
+    (i, i+q); general=True runs that version for q = 1 too.
 
     Returns a dict with status (OR_*), H, W, R, updates (number of growth
     steps), passes, bad (offending knot index or -1)."""
     X = np.ascontiguousarray(X)
+    q = _q_of(gap2, q)
     H = _D(); W = _D(); R = _U32(); upd = _I64(); passes = _I64(); bad = _I64()
-    st = getattr(lib(), ("or_compute_hr_gap2_" if gap2 else "or_compute_hr_") + _suffix(X))(
-        _ptr(X), X.shape[0], int(bool(fma)), ctypes.byref(H), ctypes.byref(W), ctypes.byref(R),
-        ctypes.byref(upd), ctypes.byref(passes), ctypes.byref(bad))
+    outs = (ctypes.byref(H), ctypes.byref(W), ctypes.byref(R), ctypes.byref(upd), ctypes.byref(passes),
+            ctypes.byref(bad))
+    if q == 1 and not general:
+        st = getattr(lib(), "or_compute_hr_" + _suffix(X))(_ptr(X), X.shape[0], int(bool(fma)), *outs)
+    else:
+        st = getattr(lib(), "or_compute_hr_gapq_" + _suffix(X))(_ptr(X), X.shape[0], q, int(bool(fma)), *outs)
     return dict(status=st, H=H.value, W=W.value, R=R.value, updates=upd.value,
                 passes=passes.value, bad=bad.value)
 
 
-def fill_k(X, H, W, R, fma=False, gap2=False):
-    """Index table of Eq. indexdef (with gap2: Eq. kgeneral), R+1 int32
-    entries, and F_i = f(X_i).  Returns (status, K, F)."""
+def fill_k(X, H, W, R, fma=False, gap2=False, q=None, general=False):
+    """Index table of Eq. indexdef (q = 1), or of Eq. kgeneral (q >= 2, or
+    general=True), R+1 int32 entries, and F_i = f(X_i).  Returns (status, K, F)."""
     X = np.ascontiguousarray(X)
+    q = _q_of(gap2, q)
     K = np.empty(int(R) + 1, dtype=np.int32)
     F = np.empty(X.shape[0], dtype=np.uint32)
-    st = getattr(lib(), ("or_fill_k_gap2_" if gap2 else "or_fill_k_") + _suffix(X))(
-        _ptr(X), X.shape[0], float(H), float(W), int(R), int(bool(fma)), _ptr(K), _ptr(F))
+    if q == 1 and not general:
+        st = getattr(lib(), "or_fill_k_" + _suffix(X))(
+            _ptr(X), X.shape[0], float(H), float(W), int(R), int(bool(fma)), _ptr(K), _ptr(F))
+    else:
+        st = getattr(lib(), "or_fill_k_gapq_" + _suffix(X))(
+            _ptr(X), X.shape[0], q, float(H), float(W), int(R), int(bool(fma)), _ptr(K), _ptr(F))
     return st, K, F
 
 
-def build_table(X, fma=False, gap2=False):
-    """ComputeHR followed by Eq. indexdef (or their DirectGap2 versions);
-    returns (hr dict, K) or raises."""
-    hr = compute_hr(X, fma, gap2)
+def build_table(X, fma=False, gap2=False, q=None, general=False):
+    """ComputeHR followed by its table (Eq. indexdef, or Eq. kgeneral for
+    q >= 2 or general=True); returns (hr dict, K) or raises."""
+    hr = compute_hr(X, fma, gap2, q, general)
     if hr["status"] != OR_OK:
         raise ValueError("array infeasible for direct search: status %d" % hr["status"])
-    st, K, _ = fill_k(X, hr["H"], hr["W"], hr["R"], fma, gap2)
+    st, K, _ = fill_k(X, hr["H"], hr["W"], hr["R"], fma, gap2, q, general)
     if st != OR_OK:
         raise ValueError("table construction failed: status %d" % st)
     return hr, K
 
 
-def direct(X, K, H, W, R, Z, fma=False, gap2=False):
-    """Algorithm "direct" (with gap2: Algorithm direct-2) on the CPU with a
-    given (H, W, R, K)."""
+def direct(X, K, H, W, R, Z, fma=False, gap2=False, q=None, general=False):
+    """Algorithm "direct" (q = 1), or Algorithm direct-2 and its q-comparison
+    generalisation (q >= 2, or general=True), on the CPU with a given (H, W, R, K)."""
     X = np.ascontiguousarray(X)
     Z = np.ascontiguousarray(Z, dtype=X.dtype)
     K = np.ascontiguousarray(K, dtype=np.int32)
+    q = _q_of(gap2, q)
     out = np.empty(Z.shape[0], dtype=np.int32)
-    getattr(lib(), ("or_direct_gap2_" if gap2 else "or_direct_") + _suffix(X))(
-        _ptr(X), _ptr(K), float(H), float(W), int(R), int(bool(fma)), _ptr(Z), Z.shape[0], _ptr(out))
+    if q == 1 and not general:
+        getattr(lib(), "or_direct_" + _suffix(X))(
+            _ptr(X), _ptr(K), float(H), float(W), int(R), int(bool(fma)), _ptr(Z), Z.shape[0], _ptr(out))
+    else:
+        getattr(lib(), "or_direct_gapq_" + _suffix(X))(
+            _ptr(X), _ptr(K), q, float(H), float(W), int(R), int(bool(fma)), _ptr(Z), Z.shape[0], _ptr(out))
     return out
+
+
+def table_bytes(X, R):
+    """Bytes of the index's table image: K ((R+1) int32) and X, each padded to 16 bytes."""
+    r16 = lambda b: (b + 15) // 16 * 16
+    return r16((int(R) + 1) * 4) + r16(X.shape[0] * X.dtype.itemsize)
+
+
+def choose_q(X, fma, budget_bytes, q_max):
+    """The paper's memory-budget use of Eq. f-monotonic-n (Section 4.7): the
+    smallest q in 1..q_max for which ComputeHR succeeds and the table fits
+    budget_bytes.  Returns (q, hr) or (0, None) if no q qualifies."""
+    for q in range(1, q_max + 1):
+        hr = compute_hr(X, fma, q=q)
+        if hr["status"] == OR_OK and table_bytes(X, hr["R"]) <= budget_bytes:
+            return q, hr
+    return 0, None
 
 
 def fvals(H, W, X0, Z, fma=False):

@@ -23,8 +23,10 @@
  *                      (Eq. fma) forms.
  *   or_fill_k_*        Eq. indexdef: K_0 = 0, K_j = i for f(X_{i-1}) < j <= f(X_i).
  *   or_direct_*        Algorithm "direct": j = f(z), t = K_j, i = t - [z < X_t].
- *   or_*_gap2_*        DirectGap2 (Section 4.7): ComputeHR over pairs (i, i+2),
- *                      K of Eq. kgeneral, Algorithm direct-2.
+ *   or_*_gapq_*        DirectGap2 and its q-knot generalisation (Section 4.7):
+ *                      ComputeHR over pairs (i, i+q), K of Eq. kgeneral,
+ *                      Algorithm direct-2 with q comparisons; or_*_gap2_* are
+ *                      the q = 2 case.
  *
  * Readings of the paper this file takes where the text is silent or garbled:
  *   - floor in f is truncation toward zero with negatives clamped to 0 and
@@ -363,20 +365,22 @@ void or_interp_f32(const float *X, const float *Y, int64_t n_knots, const float 
 }
 
 /* ------------------------------------------------------------------------ */
-/* DirectGap2 (Section 4.7): f need only satisfy f(X_{i+2}) > f(X_i)         */
-/* (Eq. f-monotonic-2); H > 1/min(X_{i+2} - X_i) (Eq. fcond11) taken in its  */
-/* rounded form m(1/min m(D_{i+2} - D_i)); the growth loop of ComputeHR runs */
-/* over the pairs (i, i+2) ("algorithm ComputeHR needs to be modified        */
-/* accordingly").  D_i == D_{i+1} is allowed; D_i == D_{i+2} is not.  With   */
-/* N = 1 the only pair is (0, 1).                                            */
+/* DirectGap2 and its generalisation (Section 4.7): f need only satisfy      */
+/* f(X_{i+q}) > f(X_i) (Eq. f-monotonic-2 for q = 2, Eq. f-monotonic-n in    */
+/* general), so H > 1/min(X_{i+q} - X_i) (Eq. fcond11 for q = 2), taken in   */
+/* its rounded form m(1/min m(D_{i+q} - D_i)), and the growth loop of        */
+/* ComputeHR runs over the pairs (i, i+q) ("algorithm ComputeHR needs to be  */
+/* modified accordingly").  D_i == D_{i+q} is not allowed; closer pairs may  */
+/* share a cell.  With fewer than q+1 knots the pair distance is N.  q = 1   */
+/* is ComputeHR itself.                                                      */
 /* ------------------------------------------------------------------------ */
-int or_compute_hr_gap2_f64(const double *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+int or_compute_hr_gapq_f64(const double *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
                            uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
 {
     *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
-    if (n_knots < 2) return OR_E_ARG;
+    if (n_knots < 2 || q < 1) return OR_E_ARG;
     const int64_t N = n_knots - 1;
-    const int64_t gap = N >= 2 ? 2 : 1;
+    const int64_t gap = N >= q ? q : N;
     for (int64_t i = 0; i <= N; ++i)
         if (!isfinite(X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
     for (int64_t i = 1; i <= N; ++i)
@@ -420,13 +424,13 @@ int or_compute_hr_gap2_f64(const double *X, int64_t n_knots, int fma_form, doubl
     return OR_OK;
 }
 
-int or_compute_hr_gap2_f32(const float *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+int or_compute_hr_gapq_f32(const float *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
                            uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
 {
     *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
-    if (n_knots < 2) return OR_E_ARG;
+    if (n_knots < 2 || q < 1) return OR_E_ARG;
     const int64_t N = n_knots - 1;
-    const int64_t gap = N >= 2 ? 2 : 1;
+    const int64_t gap = N >= q ? q : N;
     for (int64_t i = 0; i <= N; ++i)
         if (!isfinite(X[i])) { *bad_out = i; return OR_E_NOT_INCREASING; }
     for (int64_t i = 1; i <= N; ++i)
@@ -470,6 +474,18 @@ int or_compute_hr_gap2_f32(const float *X, int64_t n_knots, int fma_form, double
     return OR_OK;
 }
 
+int or_compute_hr_gap2_f64(const double *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    return or_compute_hr_gapq_f64(X, n_knots, 2, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out);
+}
+
+int or_compute_hr_gap2_f32(const float *X, int64_t n_knots, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    return or_compute_hr_gapq_f32(X, n_knots, 2, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out);
+}
+
 /* Eq. kgeneral written out: K_j = max{ i : F_i <= j }, j = 0..R (0 where no
  * knot qualifies, which only cells below F_0 can be). */
 static void fill_k_general(const uint32_t *F, int64_t n_knots, uint32_t R, int32_t *K)
@@ -481,67 +497,102 @@ static void fill_k_general(const uint32_t *F, int64_t n_knots, uint32_t R, int32
     }
 }
 
-int or_fill_k_gap2_f64(const double *X, int64_t n_knots, double H, double W, uint32_t R, int fma_form,
+/* F and the table of Eq. kgeneral for a given (H, W, R); checks that F is
+ * non-decreasing, that F_{i+q} > F_i (Eq. f-monotonic-n) and that F_N = R. */
+int or_fill_k_gapq_f64(const double *X, int64_t n_knots, int32_t q, double H, double W, uint32_t R, int fma_form,
                        int32_t *K, uint32_t *F)
 {
     const int64_t N = n_knots - 1;
     const double X0 = X[0];
+    if (q < 1) return OR_E_ARG;
     for (int64_t i = 0; i <= N; ++i)
         F[i] = trunc_u32(fma_form ? fval_fma_f64(H, W, X[i]) : fval_plain_f64(H, X0, X[i]));
     for (int64_t i = 1; i <= N; ++i)
         if (F[i - 1] > F[i]) return OR_E_BAD_TABLE;
-    for (int64_t i = 2; i <= N; ++i)
-        if (!(F[i - 2] < F[i])) return OR_E_BAD_TABLE;
+    for (int64_t i = q; i <= N; ++i)
+        if (!(F[i - q] < F[i])) return OR_E_BAD_TABLE;
     if (F[N] != R) return OR_E_BAD_TABLE;
     fill_k_general(F, n_knots, R, K);
     return OR_OK;
+}
+
+int or_fill_k_gapq_f32(const float *X, int64_t n_knots, int32_t q, double H, double W, uint32_t R, int fma_form,
+                       int32_t *K, uint32_t *F)
+{
+    const int64_t N = n_knots - 1;
+    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
+    if (q < 1) return OR_E_ARG;
+    for (int64_t i = 0; i <= N; ++i)
+        F[i] = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, X[i]) : fval_plain_f32(Hf, X0, X[i]));
+    for (int64_t i = 1; i <= N; ++i)
+        if (F[i - 1] > F[i]) return OR_E_BAD_TABLE;
+    for (int64_t i = q; i <= N; ++i)
+        if (!(F[i - q] < F[i])) return OR_E_BAD_TABLE;
+    if (F[N] != R) return OR_E_BAD_TABLE;
+    fill_k_general(F, n_knots, R, K);
+    return OR_OK;
+}
+
+int or_fill_k_gap2_f64(const double *X, int64_t n_knots, double H, double W, uint32_t R, int fma_form,
+                       int32_t *K, uint32_t *F)
+{
+    return or_fill_k_gapq_f64(X, n_knots, 2, H, W, R, fma_form, K, F);
 }
 
 int or_fill_k_gap2_f32(const float *X, int64_t n_knots, double H, double W, uint32_t R, int fma_form,
                        int32_t *K, uint32_t *F)
 {
-    const int64_t N = n_knots - 1;
-    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
-    for (int64_t i = 0; i <= N; ++i)
-        F[i] = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, X[i]) : fval_plain_f32(Hf, X0, X[i]));
-    for (int64_t i = 1; i <= N; ++i)
-        if (F[i - 1] > F[i]) return OR_E_BAD_TABLE;
-    for (int64_t i = 2; i <= N; ++i)
-        if (!(F[i - 2] < F[i])) return OR_E_BAD_TABLE;
-    if (F[N] != R) return OR_E_BAD_TABLE;
-    fill_k_general(F, n_knots, R, K);
-    return OR_OK;
+    return or_fill_k_gapq_f32(X, n_knots, 2, H, W, R, fma_form, K, F);
 }
 
-/* Algorithm direct-2: t = K_j, i = t - [z < X_t] - [z < X_{t-1}] with
- * X_{-1} = X_0 (left padding); the result is clamped at -1 so that z < X_0
- * answers -1 like the definition. */
-void or_direct_gap2_f64(const double *X, const int32_t *K, double H, double W, uint32_t R, int fma_form,
+/* Algorithm direct-2 and its q-knot generalisation: t = K_j,
+ * i = t - [z < X_t] - [z < X_{t-1}] - ... - [z < X_{t-q+1}], with the left
+ * padding X_{-1} = X_{-2} = ... = X_0; the result is clamped at -1 so that
+ * z < X_0 answers -1 like the definition. */
+void or_direct_gapq_f64(const double *X, const int32_t *K, int32_t q, double H, double W, uint32_t R, int fma_form,
                         const double *Z, int64_t m, int32_t *I)
 {
     const double X0 = X[0];
-    for (int64_t q = 0; q < m; ++q) {
-        double z = Z[q];
+    for (int64_t k = 0; k < m; ++k) {
+        double z = Z[k];
         uint32_t j = trunc_u32(fma_form ? fval_fma_f64(H, W, z) : fval_plain_f64(H, X0, z));
         if (j > R) j = R;
         int32_t t = K[j];
-        double xt = X[t], xp = t > 0 ? X[t - 1] : X0;
-        int32_t i = t - (z < xt ? 1 : 0) - (z < xp ? 1 : 0);
-        I[q] = i < -1 ? -1 : i;
+        int32_t i = t;
+        for (int32_t l = 0; l < q; ++l) {
+            double x = t - l >= 0 ? X[t - l] : X0;
+            if (z < x) --i;
+        }
+        I[k] = i < -1 ? -1 : i;
     }
+}
+
+void or_direct_gapq_f32(const float *X, const int32_t *K, int32_t q, double H, double W, uint32_t R, int fma_form,
+                        const float *Z, int64_t m, int32_t *I)
+{
+    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
+    for (int64_t k = 0; k < m; ++k) {
+        float z = Z[k];
+        uint32_t j = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, z) : fval_plain_f32(Hf, X0, z));
+        if (j > R) j = R;
+        int32_t t = K[j];
+        int32_t i = t;
+        for (int32_t l = 0; l < q; ++l) {
+            float x = t - l >= 0 ? X[t - l] : X0;
+            if (z < x) --i;
+        }
+        I[k] = i < -1 ? -1 : i;
+    }
+}
+
+void or_direct_gap2_f64(const double *X, const int32_t *K, double H, double W, uint32_t R, int fma_form,
+                        const double *Z, int64_t m, int32_t *I)
+{
+    or_direct_gapq_f64(X, K, 2, H, W, R, fma_form, Z, m, I);
 }
 
 void or_direct_gap2_f32(const float *X, const int32_t *K, double H, double W, uint32_t R, int fma_form,
                         const float *Z, int64_t m, int32_t *I)
 {
-    const float X0 = X[0], Hf = (float)H, Wf = (float)W;
-    for (int64_t q = 0; q < m; ++q) {
-        float z = Z[q];
-        uint32_t j = trunc_u32(fma_form ? fval_fma_f32(Hf, Wf, z) : fval_plain_f32(Hf, X0, z));
-        if (j > R) j = R;
-        int32_t t = K[j];
-        float xt = X[t], xp = t > 0 ? X[t - 1] : X0;
-        int32_t i = t - (z < xt ? 1 : 0) - (z < xp ? 1 : 0);
-        I[q] = i < -1 ? -1 : i;
-    }
+    or_direct_gapq_f32(X, K, 2, H, W, R, fma_form, Z, m, I);
 }
