@@ -75,7 +75,8 @@ enum {
     DS_GAP2 = 32u         /* DirectGap2 (Section 4.7): f need only separate knots two apart
                              (Eq. f-monotonic-2), K_j = max{i : f(X_i) <= j} (Eq. kgeneral), answers by
                              Algorithm direct-2, i = t - [z < X_t] - [z < X_{t-1}]; a smaller table and
-                             feasible on more arrays; not combined with DS_CACHE_LAYOUT */
+                             feasible on more arrays; not combined with DS_CACHE_LAYOUT; the same as
+                             ds_build_q with q = 2 */
 };
 
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
@@ -107,7 +108,7 @@ typedef struct ds_info_t {
     double final_loss;      /* learned: mean final training loss */
     uint64_t fallback_queries; /* learned: queries whose window certificate failed (since the build) */
     int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error */
-    int32_t reserved_;
+    int32_t gap_q;          /* single array: q of the table (1 Direct, 2 DirectGap2, ...); batched: largest q */
 } ds_info_t;
 
 /* ------------------------------------------------------------------------
@@ -123,7 +124,7 @@ typedef struct ds_info_t {
  *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2.
  *            With DS_GAP2 (Section 4.7) ComputeHR separates the knot pairs
  *            (i, i+2) instead of (i, i+1), K follows Eq. kgeneral and searches
- *            use Algorithm direct-2; at most 2^30 knots, no DS_CACHE_LAYOUT.
+ *            use Algorithm direct-2; at most 2^28 knots, no DS_CACHE_LAYOUT.
  *   out      receives the handle (NULL on failure); release with ds_free.
  * Errors: DS_E_ARG, DS_E_NOT_INCREASING, DS_E_INDISTINGUISHABLE (Section 4.4
  * first counter-example; with DS_GAP2, m(X_{i+2} - X_0) == m(X_i - X_0)),
@@ -134,9 +135,29 @@ typedef struct ds_info_t {
 DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, void *stream,
                    ds_index **out);
 
+/* Gap-q (Section 4.7, Eq. f-monotonic-n): f need only separate knots q apart,
+ * f(X_{i+q}) > f(X_i).  ComputeHR runs over the pairs (i, i+q) (pair distance
+ * N when N < q), K follows Eq. kgeneral, and a search compares z with the
+ * knots X_t, X_{t-1}, ..., X_{t-q+1} that share its cell.  A larger q gives a
+ * smaller table (about (X_N - X_0) / min(X_{i+q} - X_i) cells) for at most q
+ * comparisons per query.
+ *   q             1 (Direct: the table of Eq. indexdef, as ds_build), 2..15, or
+ *                 0 to choose, as the paper suggests for a memory budget, the
+ *                 smallest q in 1..15 for which ComputeHR succeeds and the table
+ *                 image (K and X, each padded to 16 bytes) fits budget_bytes.
+ *   budget_bytes  used when q == 0; <= 0 means the shared-memory staging limit
+ *                 of the search (so the table is staged per block).
+ *   flags         DS_FMA | DS_CHECKED | DS_NO_SMEM, and DS_CACHE_LAYOUT for q = 1.
+ * At most 2^28 knots for q >= 2.  ds_info reports the q built in gap_q.
+ * Errors: as ds_build; DS_E_TABLE_TOO_LARGE when q == 0 and no q qualifies.
+ * Synchronous. */
+DS_API ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, int32_t q,
+                            int64_t budget_bytes, void *stream, ds_index **out);
+
 /* Search m queries (Algorithm direct, Section 4.2): j = min(f(z), R),
  * t = K_j, I = t - [z < X_t]; for a DS_GAP2 index (Algorithm direct-2,
- * Section 4.7) I = t - [z < X_t] - [z < X_{t-1}], at least -1.
+ * Section 4.7) I = t - [z < X_t] - [z < X_{t-1}], and for a Gap-q index
+ * I = t - [z < X_t] - ... - [z < X_{t-q+1}], at least -1.
  *   Z_dev  m queries of the index's dtype; I_dev  m int32 results.
  * m == 0 is a no-op.  Asynchronous on `stream`; allocates nothing; safe to
  * capture in a CUDA graph. */
@@ -151,7 +172,8 @@ DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, in
 
 /* Read-only device views of the index's tables (for inspection and tests):
  * K (R+1 int32, Eq. indexdef or Eq. kgeneral, with the search's flag bits:
- * bit 31, and bit 30 for DS_GAP2), the library's copy of X (N+1 values), and,
+ * bit 31 for Eq. indexdef; for Eq. kgeneral, t in bits 0..27 and the count of
+ * the cell's knots t, t-1, ... in bits 28..31), the library's copy of X (N+1 values), and,
  * with DS_CACHE_LAYOUT, the (R+1) pairs (8 bytes for float32: int32 K_j then
  * float X_{K_j}; 16 bytes for float64: int32 K_j, 4 bytes of padding, double
  * X_{K_j}).  Any output pointer may be NULL. */

@@ -118,6 +118,14 @@ def ds_build(X, flags=0, stream=None):
     return Index(out.value, X.dtype)
 
 
+def ds_build_q(X, q, budget_bytes=0, flags=0, stream=None):
+    """Gap-q table of X (q = 1..15), or with q = 0 the smallest q whose table fits budget_bytes."""
+    out = ctypes.c_void_p()
+    check(lib().ds_build_q(_dev(X, "X"), X.numel(), _dtype(X), int(flags), int(q), int(budget_bytes),
+                           _stream(stream), ctypes.byref(out)), "ds_build_q")
+    return Index(out.value, X.dtype)
+
+
 def ds_search(idx, Z, out=None, stream=None):
     """int32 interval index of every query in Z (CUDA tensor of the index's dtype)."""
     if out is None:

@@ -55,7 +55,7 @@ class ds_info_t(ctypes.Structure):
         ("R", U64), ("table_bytes", I64), ("h_updates", I64), ("hr_passes", I64),
         ("build_ms", F64), ("smem_resident", I32), ("n_direct", I32), ("n_learned", I32),
         ("n_fallback", I32), ("max_window", I64), ("train_steps", I64), ("train_ms", F64),
-        ("final_loss", F64), ("fallback_queries", U64), ("device_error", I32), ("reserved_", I32),
+        ("final_loss", F64), ("fallback_queries", U64), ("device_error", I32), ("gap_q", I32),
     ]
 
     def as_dict(self):
@@ -76,6 +76,7 @@ class ds_learned_cfg(ctypes.Structure):
 
 _SIGS = {
     "ds_build": (ST, [P, I64, ST, U32, P, ctypes.POINTER(P)]),
+    "ds_build_q": (ST, [P, I64, ST, U32, ctypes.c_int32, I64, P, ctypes.POINTER(P)]),
     "ds_search": (ST, [P, P, I64, P, P]),
     "ds_search_host": (ST, [P, P, I64, P, P]),
     "ds_index_tables": (ST, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),

@@ -22,20 +22,21 @@ __global__ void k_hr_state_init(HRState *st, int count, int gap)
     st[a] = s;
 }
 
-__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P,
-                             uint32_t flag_mask)
+__global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P, bool gen)
 {
     const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
+    const uint32_t tmask = gen ? GEN_T_MASK : ~KNOT_FLAG;
     const long long step = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < (long long)nblk; b += step) {
         const unsigned long long j0 = (unsigned long long)b * PACK_CELLS;
-        const uint32_t base = K[j0] & ~flag_mask;
+        const uint32_t base = K[j0] & tmask;
         uint32_t w[3] = {0u, 0u, 0u};
         for (int s = 0; s < PACK_CELLS; ++s) {
             const unsigned long long j = j0 + s;
             if (j > R) break;
             const uint32_t e = K[j];
-            const uint32_t byte = ((e & ~flag_mask) - base) | ((e & flag_mask) >> 24);
+            const uint32_t d = (e & tmask) - base;
+            const uint32_t byte = gen ? d | ((e >> GEN_COUNT_SHIFT) << 6) : d | ((e & KNOT_FLAG) ? 0x80u : 0u);
             w[s >> 2] |= byte << ((s & 3) * 8);
         }
         P[b] = make_uint4(base, w[0], w[1], w[2]);
@@ -50,7 +51,7 @@ __global__ void k_clear_flags(uint32_t *p, long long count, int stride, uint32_t
 }
 
 __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_knots, unsigned long long R,
-                                 uint32_t *__restrict__ K)
+                                 uint32_t *__restrict__ K, int q)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -62,7 +63,6 @@ __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_kno
         const long long Fi = i <= N ? (long long)F[i] : (1ll << 32);  // lanes past X_N never qualify
         const long long lo = c == 0 ? 0 : (long long)F[c * 32];
         const long long hi = c + 1 == nchunks ? (long long)R + 1 : (long long)F[c * 32 + 32];
-        const long long before = c == 0 ? -1 : (long long)F[c * 32 - 1];  // F_{32c-1}
         for (long long base = lo; base < hi; base += 32) {
             const long long j = base + lane;
             // largest lane k with F_{32c+k} <= j (lane 0 qualifies except in the
@@ -73,14 +73,15 @@ __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_kno
                 const long long Fc = __shfl_sync(0xffffffffu, Fi, (k + s) & 31);
                 if (k + s <= 31 && Fc <= j) k += s;
             }
-            const long long Fk = __shfl_sync(0xffffffffu, Fi, k);
-            const long long Fkm = __shfl_sync(0xffffffffu, Fi, (k + 31) & 31);
-            const long long Fprev = k == 0 ? before : Fkm;
             if (j < hi) {
-                uint32_t e = (uint32_t)(c * 32 + k);
-                if (Fk >= j) e |= KNOT_FLAG;
-                if (Fprev == j) e |= KNOT_FLAG2;
-                K[j] = e;
+                const long long t = c * 32 + k;
+                // the knots t, t-1, ... in cell j: a run of F == j (F_0 > j below F_0), at most q
+                int cnt = 0;
+                for (int l = 0; l < q && t - l >= 0; ++l) {
+                    if ((long long)F[t - l] < j) break;
+                    ++cnt;
+                }
+                K[j] = (uint32_t)t | ((uint32_t)cnt << GEN_COUNT_SHIFT);
             }
         }
     }
@@ -151,17 +152,17 @@ static const char *hr_message(int status)
 }
 
 template <typename T, bool FMA>
-static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, cudaStream_t s, ds_index *idx,
+static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, int q, cudaStream_t s, ds_index *idx,
                              bool x0zero)
 {
     const DeviceProps &props = idx->props;
     HRState *st = nullptr;
     DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
     HRState hs;
-    const bool gap2 = (flags & DS_GAP2) != 0;
-    // DirectGap2 separates the pairs (i, i+2); with two knots the only pair is (0, 1)
-    const int gap = gap2 && n_knots >= 3 ? 2 : 1;
-    idx->gap2 = gap2;
+    // Gap-q separates the pairs (i, i+q); with fewer than q+1 knots the pair distance is N
+    const bool gen = q >= 2;
+    const int gap = (long long)q < n_knots - 1 ? q : (int)(n_knots - 1);
+    idx->q = q;
     ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props, gap);
     cudaFree(st);
     if (rc != DS_OK) return rc;
@@ -199,8 +200,8 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     const int block = 256;
     k_fill_F<T, FMA><<<grid_for(props, n_knots, block), block, 0, s>>>(Xc, n_knots, (T)hs.H, (T)hs.W, F);
     long long warps_work = (n_knots + 31) / 32 * 32;
-    if (gap2)
-        k_fill_K_general<<<grid_for(props, warps_work, block), block, 0, s>>>(F, n_knots, R, K);
+    if (gen)
+        k_fill_K_general<<<grid_for(props, warps_work, block), block, 0, s>>>(F, n_knots, R, K, q);
     else
         k_fill_K<T><<<grid_for(props, warps_work, block), block, 0, s>>>(
             F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
@@ -215,7 +216,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     SearchPlan &plan = idx->plan;
     plan.form = FMA ? F_FMA : (x0zero ? F_PLAIN_X0ZERO : F_PLAIN);
     plan.cache = cache;
-    plan.gap2 = gap2;
+    plan.gen = gen;
     plan.intops = sizeof(T) == 8 && f64_intops_default();
     plan.block = SEARCH_BLOCK;
     plan.vpt = SEARCH_VPT;
@@ -227,14 +228,13 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     plan.smem = !(flags & DS_NO_SMEM) && image <= smem_limit_bytes(props);
     idx->smem_bytes = plan.smem ? (uint32_t)image : 0;
     plan.packed = false;
-    if (sizeof(T) == 8 && plan.intops && !plan.smem && !cache) {
+    if (sizeof(T) == 8 && plan.intops && !plan.smem && !cache && q <= MAX_PACKED_Q) {
         const char *e = getenv("DS_PACKED");
         if (!e || atoi(e) != 0) {
             const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
             idx->k16_bytes = (size_t)nblk * sizeof(uint4);
             DS_TRY_CUDA(cudaMalloc(&idx->k16, idx->k16_bytes));
-            k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(
-                K, R, idx->k16, gap2 ? KNOT_FLAG | KNOT_FLAG2 : KNOT_FLAG);
+            k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(K, R, idx->k16, gen);
             DS_TRY_CUDA(cudaGetLastError());
             DS_TRY_CUDA(cudaStreamSynchronize(s));
             idx->table_bytes += idx->k16_bytes;
@@ -245,8 +245,42 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     return DS_OK;
 }
 
-ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, cudaStream_t s,
-                       ds_index **out)
+// Smallest q in 1..q_max for which ComputeHR over the pairs (i, i+q) succeeds
+// and the table image (K and X, each padded to 16 bytes) fits budget_bytes;
+// 0 if none does.
+template <typename T, bool FMA>
+static ds_status select_q(const T *X, long long n_knots, long long budget_bytes, int q_max, cudaStream_t s,
+                          const DeviceProps &props, int *q_out)
+{
+    *q_out = 0;
+    HRState *st = nullptr;
+    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
+    ds_status rc = DS_OK;
+    const size_t x_bytes = round_up((size_t)n_knots * sizeof(T), 16);
+    for (int q = 1; q <= q_max; ++q) {
+        const int gap = (long long)q < n_knots - 1 ? q : (int)(n_knots - 1);
+        HRState hs;
+        rc = run_compute_hr<T, FMA>(X, n_knots, st, &hs, s, props, gap);
+        if (rc != DS_OK) break;
+        if (hs.status == DS_E_NOT_INCREASING) {  // no q helps
+            rc = DS_E_NOT_INCREASING;
+            set_error("ds_build_q: %s (knot %lld)", hr_message(hs.status),
+                      (long long)(hs.bad_nonfinite != NONE64 ? hs.bad_nonfinite : hs.bad_order));
+            break;
+        }
+        if (hs.status != DS_OK) continue;
+        const size_t bytes = round_up((size_t)(hs.R + 1) * sizeof(int32_t), 16) + x_bytes;
+        if ((long long)bytes <= budget_bytes) {
+            *q_out = q;
+            break;
+        }
+    }
+    cudaFree(st);
+    return rc;
+}
+
+ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, int q,
+                       long long budget_bytes, cudaStream_t s, ds_index **out)
 {
     const double t0 = now_ms();
     ds_index *idx = new ds_index;
@@ -286,15 +320,31 @@ ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uin
             memcpy(&idx->XN, e2 + 8, 8);
         }
     }
+    const bool fma = (flags & DS_FMA) != 0;
+    if (rc == DS_OK && q == 0) {  // the memory-budget choice of q (Section 4.7)
+        if (budget_bytes <= 0) budget_bytes = (long long)smem_limit_bytes(idx->props);
+        if (dtype == DS_F32)
+            rc = fma ? select_q<float, true>((const float *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props, &q)
+                     : select_q<float, false>((const float *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props, &q);
+        else
+            rc = fma ? select_q<double, true>((const double *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props,
+                                              &q)
+                     : select_q<double, false>((const double *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props,
+                                               &q);
+        if (rc == DS_OK && q == 0) {
+            set_error("ds_build_q: no q in 1..%d gives a feasible table of at most %lld bytes", MAX_GAP_Q,
+                      budget_bytes);
+            rc = DS_E_TABLE_TOO_LARGE;
+        }
+    }
     if (rc == DS_OK) {
-        const bool fma = (flags & DS_FMA) != 0;
         const bool x0zero = idx->X0 == 0.0;
         if (dtype == DS_F32) {
-            rc = fma ? build_typed<float, true>((const float *)X_dev, n_knots, flags, s, idx, x0zero)
-                     : build_typed<float, false>((const float *)X_dev, n_knots, flags, s, idx, x0zero);
+            rc = fma ? build_typed<float, true>((const float *)X_dev, n_knots, flags, q, s, idx, x0zero)
+                     : build_typed<float, false>((const float *)X_dev, n_knots, flags, q, s, idx, x0zero);
         } else {
-            rc = fma ? build_typed<double, true>((const double *)X_dev, n_knots, flags, s, idx, x0zero)
-                     : build_typed<double, false>((const double *)X_dev, n_knots, flags, s, idx, x0zero);
+            rc = fma ? build_typed<double, true>((const double *)X_dev, n_knots, flags, q, s, idx, x0zero)
+                     : build_typed<double, false>((const double *)X_dev, n_knots, flags, q, s, idx, x0zero);
         }
     }
     if (rc != DS_OK) {
@@ -369,7 +419,7 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
     if (K_out_dev) {
         DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(K_out_dev), cells, 1,
-                                               idx->gap2 ? ds::KNOT_FLAG | ds::KNOT_FLAG2 : ds::KNOT_FLAG);
+                                               idx->q >= 2 ? ~ds::GEN_T_MASK : ds::KNOT_FLAG);
         DS_TRY_CUDA(cudaGetLastError());
     }
     if (X_out_dev)

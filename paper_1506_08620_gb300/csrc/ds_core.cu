@@ -134,6 +134,7 @@ ds_status info_index(const ds_index *idx, ds_info_t *o)
     o->build_ms = idx->build_ms;
     o->smem_resident = idx->plan.smem ? 1 : 0;
     o->n_direct = 1;
+    o->gap_q = idx->q;
     int err = 0;
     if (idx->dev_err && cudaMemcpy(&err, idx->dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
         o->device_error = err;
@@ -204,11 +205,37 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
         set_error("ds_build: DS_GAP2 has no cache layout (its correction reads two knots)");
         return DS_E_ARG;
     }
-    if ((flags & DS_GAP2) && n_knots > (1ll << 30)) {
-        set_error("ds_build: DS_GAP2 takes at most 2^30 knots (two flag bits per table entry)");
+    if ((flags & DS_GAP2) && n_knots > (1ll << 28)) {
+        set_error("ds_build: DS_GAP2 takes at most 2^28 knots (28-bit table entries)");
         return DS_E_ARG;
     }
-    return build_single(X_dev, n_knots, dtype, flags, (cudaStream_t)stream, out);
+    return build_single(X_dev, n_knots, dtype, flags, (flags & DS_GAP2) ? 2 : 1, 0, (cudaStream_t)stream, out);
+}
+
+ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, int32_t q,
+                     int64_t budget_bytes, void *stream, ds_index **out)
+{
+    clear_error();
+    if (!out) {
+        set_error("ds_build_q: out is NULL");
+        return DS_E_ARG;
+    }
+    *out = nullptr;
+    if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) || q < 0 || q > MAX_GAP_Q ||
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM))) {
+        set_error("ds_build_q: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u, q=%d)", X_dev,
+                  (long long)n_knots, (int)dtype, flags, q);
+        return DS_E_ARG;
+    }
+    if ((flags & DS_CACHE_LAYOUT) && q != 1) {
+        set_error("ds_build_q: the cache layout exists for q = 1 only");
+        return DS_E_ARG;
+    }
+    if (n_knots > (q == 1 ? (1ll << 31) - 1 : (1ll << 28))) {
+        set_error("ds_build_q: too many knots for q = %d", q);
+        return DS_E_ARG;
+    }
+    return build_single(X_dev, n_knots, dtype, flags, q, budget_bytes, (cudaStream_t)stream, out);
 }
 
 ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, int32_t *I_dev, void *stream)

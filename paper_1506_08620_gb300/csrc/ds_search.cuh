@@ -15,12 +15,14 @@
 // monotonic of Eq. fprop) and the answer is t - 1 without reading X_t; only
 // queries in a cell that holds a knot need the correcting comparison.
 //
-// DirectGap2 (Section 4.7) tables hold t = K_j = max{i : F_i <= j} (Eq.
-// kgeneral) with two flags: bit 31 when F_t >= j (knot t in the cell, or the
-// cells below F_0 where t = 0) and bit 30 when F_{t-1} == j (a second knot in
-// the cell).  Without bit 31, F_t < j = f(z) gives z > X_t and the answer is t;
-// Algorithm direct-2's comparisons i = t - [z < X_t] - [z < X_{t-1}] are made
-// only where the flags say they can be true.
+// DirectGap2 and Gap-q tables (Section 4.7: f(X_{i+q}) > f(X_i), Eq.
+// f-monotonic-n) hold t = K_j = max{i : F_i <= j} (Eq. kgeneral) in bits
+// 0..27 and, in bits 28..31, the count c of the knots t, t-1, ... that lie in
+// the cell (F == j; for the cells below F_0, t = 0 and c = 1), at most q.  A
+// knot t-l outside the cell has F_{t-l} < j = f(z), so z > X_{t-l}; the q
+// comparisons i = t - [z < X_t] - ... - [z < X_{t-q+1}] of Algorithm direct-2
+// and its generalisation therefore reduce to the first c, and since X
+// increases they stop at the first that fails.
 #pragma once
 
 #include "ds_common.cuh"
@@ -31,25 +33,29 @@ namespace ds {
 enum FForm : int { F_PLAIN = 0, F_FMA = 1, F_PLAIN_X0ZERO = 2 };
 
 constexpr uint32_t KNOT_FLAG = 0x80000000u;
-constexpr uint32_t KNOT_FLAG2 = 0x40000000u;  // DirectGap2: knot t-1 in the cell too
-constexpr uint32_t GAP2_T_MASK = 0x3FFFFFFFu;
+constexpr uint32_t GEN_T_MASK = 0x0FFFFFFFu;  // Eq. kgeneral tables: t in bits 0..27
+constexpr int GEN_COUNT_SHIFT = 28;           // ... and the knot count of the cell above
+constexpr int MAX_GAP_Q = 15;                 // largest q the 4-bit count can describe
+constexpr int MAX_PACKED_Q = 3;               // largest q the packed table can describe
 
 // Packed table: K in 16-byte blocks of 12 cells, {K of the block's first
-// cell, 12 bytes (K_j - base) | flags << 6}.  A cell holds at most one knot
-// (Direct: F strictly increasing) or two (DirectGap2: F_{i+2} > F_i), so K
-// grows by at most 2 per cell and the difference (at most 22) fits 6 bits;
-// bits 6 and 7 carry the flags of bits 30 and 31.  1.33 bytes per cell instead
-// of 4 keeps large tables L2-resident, and a lookup still reads one 16-byte
-// sector.
+// cell, 12 bytes, one per cell}.  Direct: a cell holds at most one knot (F is
+// strictly increasing), so K grows by at most 1 per cell; the byte is
+// (K_j - base) | flag << 7.  Eq. kgeneral with q <= 3: K grows by at most q
+// per cell, the difference (at most 33) fits 6 bits and the count (at most 3)
+// the other 2.  1.33 bytes per cell instead of 4 keeps large tables
+// L2-resident, and a lookup still reads one 16-byte sector.
 constexpr int PACK_CELLS = 12;
 
+template <bool GEN = false>
 __device__ __forceinline__ uint32_t unpack_cell(uint4 w, uint32_t j)
 {
     const uint32_t b = __umulhi(j, 0xAAAAAAABu) >> 3;  // j / 12
     const uint32_t s = j - b * PACK_CELLS;
     const uint32_t word = s < 4 ? w.y : (s < 8 ? w.z : w.w);
     const uint32_t byte = (word >> ((s & 3u) * 8u)) & 0xFFu;
-    return (w.x + (byte & 0x3Fu)) | ((byte & 0xC0u) << 24);
+    if constexpr (GEN) return (w.x + (byte & 0x3Fu)) | ((byte >> 6) << GEN_COUNT_SHIFT);
+    else return (w.x + (byte & 0x7Fu)) | ((byte & 0x80u) << 24);
 }
 
 template <typename T> struct SearchArgs {
@@ -154,31 +160,36 @@ __device__ __forceinline__ bool z_less(T z, T x)
     else return z < x;
 }
 
-// DirectGap2 correction (Algorithm direct-2): i = t - [z < X_t] - [z < X_{t-1}]
-// with each comparison made only under its flag; x = X_t, xp = X_{t-1}.
-template <typename T, bool INTOPS>
-__device__ __forceinline__ int32_t correct_gap2(T z, uint32_t e, T x, T xp, int checked)
+// Eq. kgeneral correction (Algorithm direct-2 and its q-knot form): x = X_t
+// (read by the caller when the count is nonzero); the further knots
+// X_{t-1}, ... of the cell are read only while the comparisons hold.
+template <typename T, bool INTOPS, bool SMEM>
+__device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, const T *X, int checked)
 {
-    int32_t i = (int32_t)(e & GAP2_T_MASK);
-    if (e & KNOT_FLAG) i -= (int32_t)z_less<T, INTOPS>(z, x);
-    if (e & KNOT_FLAG2) i -= (int32_t)z_less<T, INTOPS>(z, xp);
+    const int32_t t = (int32_t)(e & GEN_T_MASK);
+    const int32_t c = (int32_t)(e >> GEN_COUNT_SHIFT);
+    int32_t i = t;
+    if (c > 0 && z_less<T, INTOPS>(z, x)) {
+        --i;
+        for (int32_t l = 1; l < c; ++l) {
+            if (!z_less<T, INTOPS>(z, gather_x<T, SMEM>(t - l, X))) break;
+            --i;
+        }
+    }
     if (checked && is_nan<T>(z)) i = -1;
     return i;
 }
 
-template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, bool GAP2 = false>
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, bool GEN = false>
 __device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, const Pair<T> *P,
                                           const SearchArgs<T> &a)
 {
     const uint32_t j = cell_of<T, FM, INTOPS>(z, a);
     T x = T(0);
     const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x);
-    if constexpr (GAP2) {
-        const int32_t t = (int32_t)(e & GAP2_T_MASK);
-        T xp = T(0);
-        if (e & KNOT_FLAG) x = gather_x<T, SMEM>(t, X);
-        if (e & KNOT_FLAG2) xp = gather_x<T, SMEM>(t - 1, X);
-        return correct_gap2<T, INTOPS>(z, e, x, xp, a.checked);
+    if constexpr (GEN) {
+        if (e >> GEN_COUNT_SHIFT) x = gather_x<T, SMEM>((int32_t)(e & GEN_T_MASK), X);
+        return correct_gen<T, INTOPS, SMEM>(z, e, x, X, a.checked);
     } else {
         if constexpr (!CACHE) {
             if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
@@ -187,7 +198,7 @@ __device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, co
     }
 }
 
-template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, int VPT, bool GAP2 = false>
+template <typename T, int FM, bool CACHE, bool SMEM, bool INTOPS, int VPT, bool GEN = false>
 __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long nvec, long long ntiles)
 {
     using V = typename VecOf<T>::V;
@@ -235,17 +246,12 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
 #pragma unroll
         for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q]);
         int32_t r[NQ];
-        if constexpr (GAP2) {
-            T xp[NQ];
+        if constexpr (GEN) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int32_t t = (int32_t)(e[q] & GAP2_T_MASK);
-                xp[q] = T(0);
-                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>(t, X);
-                if (e[q] & KNOT_FLAG2) xp[q] = gather_x<T, SMEM>(t - 1, X);
-            }
+            for (int q = 0; q < NQ; ++q)
+                if (e[q] >> GEN_COUNT_SHIFT) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & GEN_T_MASK), X);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) r[q] = correct_gap2<T, INTOPS>(zs[q], e[q], x[q], xp[q], a.checked);
+            for (int q = 0; q < NQ; ++q) r[q] = correct_gen<T, INTOPS, SMEM>(zs[q], e[q], x[q], X, a.checked);
         } else {
             if constexpr (!CACHE) {
 #pragma unroll
@@ -269,17 +275,17 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
     // the last m mod L queries
     if (blockIdx.x == 0) {
         const long long q = nvec * L + threadIdx.x;
-        if (q < a.m) a.I[q] = lookup<T, FM, CACHE, SMEM, INTOPS, GAP2>(a.Z[q], K, X, P, a);
+        if (q < a.m) a.I[q] = lookup<T, FM, CACHE, SMEM, INTOPS, GEN>(a.Z[q], K, X, P, a);
     }
 }
 
 // Scalar path for queries or results that are not aligned for vector access.
-template <typename T, int FM, bool CACHE, bool INTOPS, bool GAP2 = false>
+template <typename T, int FM, bool CACHE, bool INTOPS, bool GEN = false>
 __global__ void __launch_bounds__(256) k_search_scalar(SearchArgs<T> a)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride)
-        a.I[q] = lookup<T, FM, CACHE, false, INTOPS, GAP2>(a.Z[q], a.K, a.X, a.P, a);
+        a.I[q] = lookup<T, FM, CACHE, false, INTOPS, GEN>(a.Z[q], a.K, a.X, a.P, a);
 }
 
 // Float64 lookups with the data kept as IEEE bit patterns (long long)
@@ -312,18 +318,29 @@ __device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long l
     return i;
 }
 
-__device__ __forceinline__ int32_t correct_bits_gap2(long long zb, uint32_t e, long long xb, long long xpb,
-                                                     int checked)
+// Eq. kgeneral correction on bit patterns; xb = bits of X_t (read by the
+// caller when the count is nonzero).
+template <bool SMEM>
+__device__ __forceinline__ int32_t correct_bits_gen(long long zb, uint32_t e, long long xb, const long long *Xb,
+                                                    uint64_t keep, int checked)
 {
     const long long kz = okey_bits(zb);
-    int32_t i = (int32_t)(e & GAP2_T_MASK);
-    if (e & KNOT_FLAG) i -= (int32_t)(kz < okey_bits(xb));
-    if (e & KNOT_FLAG2) i -= (int32_t)(kz < okey_bits(xpb));
+    const int32_t t = (int32_t)(e & GEN_T_MASK);
+    const int32_t c = (int32_t)(e >> GEN_COUNT_SHIFT);
+    int32_t i = t;
+    if (c > 0 && kz < okey_bits(xb)) {
+        --i;
+        for (int32_t l = 1; l < c; ++l) {
+            const long long *px = Xb + (t - l);
+            if (!(kz < okey_bits(SMEM ? *px : ld_keep(px, keep)))) break;
+            --i;
+        }
+    }
     if (checked && ((unsigned long long)zb & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) i = -1;
     return i;
 }
 
-template <int FM, bool CACHE, bool SMEM, int VPT, bool PACKED = false, bool GAP2 = false>
+template <int FM, bool CACHE, bool SMEM, int VPT, bool PACKED = false, bool GEN = false>
 __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, long long nvec, long long ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -380,29 +397,26 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 xb[q] = p.y;
             } else if constexpr (PACKED) {
                 const uint32_t j = e[q];
-                e[q] = unpack_cell(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
+                e[q] = unpack_cell<GEN>(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
             } else {
                 e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
             }
         }
-        if constexpr (GAP2) {
-            long long xpb[NQ];
+        if constexpr (GEN) {
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const long long *px = Xb + (e[q] & GAP2_T_MASK);
+                const long long *px = Xb + (e[q] & GEN_T_MASK);
                 xb[q] = 0;
-                xpb[q] = 0;
-                if (e[q] & KNOT_FLAG) xb[q] = SMEM ? px[0] : ld_keep(px, keep);
-                if (e[q] & KNOT_FLAG2) xpb[q] = SMEM ? px[-1] : ld_keep(px - 1, keep);
+                if (e[q] >> GEN_COUNT_SHIFT) xb[q] = SMEM ? *px : ld_keep(px, keep);
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = b + (long long)v * blockDim.x;
                 if (idx < nvec)
                     __stcs(Iv + idx,
-                           make_int2(correct_bits_gap2(zb[2 * v], e[2 * v], xb[2 * v], xpb[2 * v], a.checked),
-                                     correct_bits_gap2(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], xpb[2 * v + 1],
-                                                       a.checked)));
+                           make_int2(correct_bits_gen<SMEM>(zb[2 * v], e[2 * v], xb[2 * v], Xb, keep, a.checked),
+                                     correct_bits_gen<SMEM>(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], Xb, keep,
+                                                            a.checked)));
             }
         } else {
             if constexpr (!CACHE) {
@@ -436,14 +450,14 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 e = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xq = p.y;
             } else if constexpr (PACKED) {
-                e = unpack_cell(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
+                e = unpack_cell<GEN>(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
             } else {
                 e = K[e];
             }
-            if constexpr (GAP2) {
-                const long long *px = Xb + (e & GAP2_T_MASK);
-                const long long xq0 = (e & KNOT_FLAG) ? px[0] : 0, xq1 = (e & KNOT_FLAG2) ? px[-1] : 0;
-                a.I[q] = correct_bits_gap2(zq, e, xq0, xq1, a.checked);
+            if constexpr (GEN) {
+                const long long *px = Xb + (e & GEN_T_MASK);
+                const long long xq0 = (e >> GEN_COUNT_SHIFT) ? *px : 0;
+                a.I[q] = correct_bits_gen<true>(zq, e, xq0, Xb, keep, a.checked);
             } else {
                 if constexpr (!CACHE) {
                     if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
@@ -457,7 +471,7 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
 struct SearchPlan {
     int form;      // FForm
     bool cache, smem, intops, packed;
-    bool gap2;     // DirectGap2 table (Eq. kgeneral) and Algorithm direct-2
+    bool gen;      // Eq. kgeneral table (q >= 2) and Algorithm direct-2 / its q-knot form
     int block;     // threads per block
     int vpt;       // vectors per thread per tile
     int grid_cap;  // resident blocks (one wave)

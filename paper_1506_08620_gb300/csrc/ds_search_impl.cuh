@@ -45,9 +45,9 @@ static const void *pick_vec2(bool cache, bool smem, bool intops, int vpt, bool p
     return cache ? pick_vec3<T, FM, true>(smem, intops, vpt, packed)
                  : pick_vec3<T, FM, false>(smem, intops, vpt, packed);
 }
-// DirectGap2 kernels: no cache layout; float64 on bit patterns with VPT 2 or 4.
+// Eq. kgeneral kernels (q >= 2): no cache layout; float64 on bit patterns with VPT 2 or 4.
 template <typename T, int FM, bool SMEM>
-static const void *pick_gap2_3(const SearchPlan &p)
+static const void *pick_gen_3(const SearchPlan &p)
 {
     if constexpr (sizeof(T) == 8) {
         if (p.intops) {
@@ -62,19 +62,19 @@ static const void *pick_gap2_3(const SearchPlan &p)
     return (const void *)k_search_vec<T, FM, false, SMEM, false, SEARCH_VPT, true>;
 }
 template <typename T, int FM>
-static const void *pick_gap2_2(const SearchPlan &p)
+static const void *pick_gen_2(const SearchPlan &p)
 {
-    return p.smem ? pick_gap2_3<T, FM, true>(p) : pick_gap2_3<T, FM, false>(p);
+    return p.smem ? pick_gen_3<T, FM, true>(p) : pick_gen_3<T, FM, false>(p);
 }
 
 template <typename T>
 static const void *pick_vec(const SearchPlan &p)
 {
-    if (p.gap2) {
+    if (p.gen) {
         switch (p.form) {
-        case F_FMA: return pick_gap2_2<T, F_FMA>(p);
-        case F_PLAIN_X0ZERO: return pick_gap2_2<T, F_PLAIN_X0ZERO>(p);
-        default: return pick_gap2_2<T, F_PLAIN>(p);
+        case F_FMA: return pick_gen_2<T, F_FMA>(p);
+        case F_PLAIN_X0ZERO: return pick_gen_2<T, F_PLAIN_X0ZERO>(p);
+        default: return pick_gen_2<T, F_PLAIN>(p);
         }
     }
     switch (p.form) {
@@ -99,7 +99,7 @@ static const void *pick_scalar2(bool cache, bool intops)
     return cache ? pick_scalar3<T, FM, true>(intops) : pick_scalar3<T, FM, false>(intops);
 }
 template <typename T, int FM>
-static const void *pick_scalar_gap2(bool intops)
+static const void *pick_scalar_gen(bool intops)
 {
     if constexpr (sizeof(T) == 8) {
         if (intops) return (const void *)k_search_scalar<T, FM, false, true, true>;
@@ -111,11 +111,11 @@ static const void *pick_scalar_gap2(bool intops)
 template <typename T>
 static const void *pick_scalar(const SearchPlan &p)
 {
-    if (p.gap2) {
+    if (p.gen) {
         switch (p.form) {
-        case F_FMA: return pick_scalar_gap2<T, F_FMA>(p.intops);
-        case F_PLAIN_X0ZERO: return pick_scalar_gap2<T, F_PLAIN_X0ZERO>(p.intops);
-        default: return pick_scalar_gap2<T, F_PLAIN>(p.intops);
+        case F_FMA: return pick_scalar_gen<T, F_FMA>(p.intops);
+        case F_PLAIN_X0ZERO: return pick_scalar_gen<T, F_PLAIN_X0ZERO>(p.intops);
+        default: return pick_scalar_gen<T, F_PLAIN>(p.intops);
         }
     }
     switch (p.form) {
