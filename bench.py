@@ -28,7 +28,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = ("direct_f64", "direct_f64_sorted", "direct_f32", "batched_f32", "learned_f64", "learned_interp_f32")
+WORKLOADS = ("direct_f64", "direct_f64_sorted", "direct_f32", "batched_f32", "learned_f64", "learned_interp_f32",
+             "gapq_f64")
 
 
 def parse():
@@ -187,6 +188,8 @@ def reference_sample(args, n=1 << 20):
     from paper_1506_08620_gb300 import workloads as W
     if args.workload.startswith("direct_f64"):
         w = W.workload2(m=n, sort=args.workload.endswith("sorted"))
+    elif args.workload in ("learned_f64", "gapq_f64"):
+        w = W.workload4(m=n)
     elif args.workload == "direct_f32":
         w = W.workload1()
     else:
@@ -224,6 +227,9 @@ def workload_config(args):
         "learned_f64": {"workload": "learned index f64: 2^24+1 knots, gaps U[1e-3,1e-2] or (1%) U[1e3,1e4], "
                                     "2^27 uniform queries, 1-32-32-1 MLP + bounded window", "knots": (1 << 24) + 1,
                         "queries": 1 << 27},
+        "gapq_f64": {"workload": "Gap-q direct search f64 on the learned-index data: 2^24+1 knots, gaps "
+                                 "U[1e-3,1e-2] or (1%) U[1e3,1e4], 2^27 uniform queries; smallest q whose table "
+                                 "fits 4 GiB", "knots": (1 << 24) + 1, "queries": 1 << 27, "budget_bytes": 1 << 32},
         "learned_interp_f32": {"workload": "batched learned lookup + linear interpolation f32: 256 arrays of "
                                            "2^10..2^22 knots, mixed gap laws, 2^28 queries", "arrays": 256,
                                "queries": 1 << 28},
@@ -313,6 +319,53 @@ def setup_direct(args, ds, W, torch, dev, rank):
             res["sorted_queries_" + args.variant] = job.m / time_calls(torch, stream,
                                                                        lambda: ds.ds_search(idx, Zs, out), 5)
             del Zs
+        return res
+    job.extras = extras
+    return job
+
+
+def setup_gapq(args, ds, W, torch, dev, rank):
+    """Gap-q (Section 4.7) on the two-scale data where Direct overflows: the
+    network-free comparator of the learned index."""
+    job = Job()
+    w = W.workload4(seed=rank_seed(W, 4, rank), m=args.queries or (1 << 27))
+    X, Zh = w["X"], w["Z"]
+    job.bytes_per_lookup, job.dtype_name = 8 + 4, "f64"
+    job.m = Zh.size
+    Xd = torch.from_numpy(X).to(dev)
+    Zd = torch.from_numpy(Zh).to(dev)
+    out = torch.empty(job.m, dtype=torch.int32, device=dev)
+    budget = 1 << 32
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx = ds.ds_build_q(Xd, 0, budget, q_max=1024)
+    torch.cuda.synchronize()
+    job.build_ms = (time.perf_counter() - t0) * 1e3
+    info = idx.info()
+    job.table = {"q": info["gap_q"], "H": info["H"], "R": info["R"], "table_bytes": info["table_bytes"],
+                 "h_updates": info["h_updates"], "build_includes_choice_of_q": True}
+    job.kernel_key = "search_f64_gapq"
+    job.search = lambda: ds.ds_search(idx, Zd, out)
+    job.out = out
+    job.keep = (idx, Xd, Zd)
+    Zp = torch.from_numpy(Zh).pin_memory()
+    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
+
+    def e2e():
+        ds.ds_search_host(idx, Zp, Ip)
+        return Zp.numel() * Zp.element_size(), Ip.numel() * 4
+    job.e2e = e2e
+    job.e2e_out = Ip
+
+    def extras(stream):
+        res = {}
+        for q in (64, 128, 512, 1024):
+            if q == info["gap_q"]:
+                continue
+            j = ds.ds_build_q(Xd, q)
+            res["q%d" % q] = job.m / time_calls(torch, stream, lambda: ds.ds_search(j, Zd, out), 5)
+            res["q%d_table_bytes" % q] = j.info()["table_bytes"]
+            j.free()
         return res
     job.extras = extras
     return job
@@ -426,6 +479,12 @@ def setup_learned(args, ds, W, torch, dev, rank):
             res["linear_model"] = job.m / time_calls(torch, stream, lambda: ds.ds_learned_search(lin, Zd, out=out), 3)
             res["linear_model_max_window"] = lin.info()["max_window"]
             lin.free()
+            # no network at all: Gap-q direct search (Section 4.7), smallest q with a table of at most 4 GiB
+            gq = ds.ds_build_q(Xd, 0, 1 << 32, q_max=1024)
+            res["gapq_direct"] = job.m / time_calls(torch, stream, lambda: ds.ds_search(gq, Zd, out), 3)
+            res["gapq_q"] = gq.info()["gap_q"]
+            res["gapq_table_bytes"] = gq.info()["table_bytes"]
+            gq.free()
         return res
     job.extras = extras
     return job
@@ -465,6 +524,8 @@ def main():
         job = setup_batched(args, ds, W, torch, dev, rank)
     elif args.workload in ("learned_f64", "learned_interp_f32"):
         job = setup_learned(args, ds, W, torch, dev, rank)
+    elif args.workload == "gapq_f64":
+        job = setup_gapq(args, ds, W, torch, dev, rank)
     else:
         raise SystemExit("workload %s: not timed by this bench" % args.workload)
     m = job.m
@@ -529,8 +590,8 @@ def main():
         line["variants_lookups_per_s"] = job.extras(stream)
     if rank == 0:
         cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
-        if args.workload.startswith("direct") or args.workload == "learned_f64":
-            if args.workload == "learned_f64":
+        if args.workload.startswith("direct") or args.workload in ("learned_f64", "gapq_f64"):
+            if args.workload in ("learned_f64", "gapq_f64"):
                 cw = W.workload4(m=1 << 22)
             line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds)
         else:

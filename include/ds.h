@@ -124,7 +124,7 @@ typedef struct ds_info_t {
  *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2.
  *            With DS_GAP2 (Section 4.7) ComputeHR separates the knot pairs
  *            (i, i+2) instead of (i, i+1), K follows Eq. kgeneral and searches
- *            use Algorithm direct-2; at most 2^28 knots, no DS_CACHE_LAYOUT.
+ *            use Algorithm direct-2; at most 2^30 knots, no DS_CACHE_LAYOUT.
  *   out      receives the handle (NULL on failure); release with ds_free.
  * Errors: DS_E_ARG, DS_E_NOT_INCREASING, DS_E_INDISTINGUISHABLE (Section 4.4
  * first counter-example; with DS_GAP2, m(X_{i+2} - X_0) == m(X_i - X_0)),
@@ -137,27 +137,30 @@ DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, ui
 
 /* Gap-q (Section 4.7, Eq. f-monotonic-n): f need only separate knots q apart,
  * f(X_{i+q}) > f(X_i).  ComputeHR runs over the pairs (i, i+q) (pair distance
- * N when N < q), K follows Eq. kgeneral, and a search compares z with the
- * knots X_t, X_{t-1}, ..., X_{t-q+1} that share its cell.  A larger q gives a
- * smaller table (about (X_N - X_0) / min(X_{i+q} - X_i) cells) for at most q
- * comparisons per query.
- *   q             1 (Direct: the table of Eq. indexdef, as ds_build), 2..15, or
+ * N when N < q) and K follows Eq. kgeneral.  A search answers from the table
+ * alone when its cell holds no knot; otherwise it compares z with X_t and, if
+ * z < X_t, bisects the knots X_{t-q} < z .. X_{t-1} (at most ceil(log2 q) more
+ * comparisons; for q = 2 these are the comparisons of Algorithm direct-2).
+ * A larger q gives a smaller table (about (X_N - X_0) / min(X_{i+q} - X_i)
+ * cells), and arrays on which Direct is infeasible can become feasible.
+ *   q             1 (Direct: the table of Eq. indexdef, as ds_build), >= 2, or
  *                 0 to choose, as the paper suggests for a memory budget, the
- *                 smallest q in 1..15 for which ComputeHR succeeds and the table
- *                 image (K and X, each padded to 16 bytes) fits budget_bytes.
+ *                 smallest q in 1..q_max for which ComputeHR succeeds and the
+ *                 table image (K and X, each padded to 16 bytes) fits budget_bytes.
+ *   q_max         the largest q tried when q == 0 (ignored otherwise).
  *   budget_bytes  used when q == 0; <= 0 means the shared-memory staging limit
  *                 of the search (so the table is staged per block).
  *   flags         DS_FMA | DS_CHECKED | DS_NO_SMEM, and DS_CACHE_LAYOUT for q = 1.
- * At most 2^28 knots for q >= 2.  ds_info reports the q built in gap_q.
+ * At most 2^30 knots for q >= 2.  ds_info reports the q built in gap_q.
  * Errors: as ds_build; DS_E_TABLE_TOO_LARGE when q == 0 and no q qualifies.
  * Synchronous. */
 DS_API ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, int32_t q,
-                            int64_t budget_bytes, void *stream, ds_index **out);
+                            int32_t q_max, int64_t budget_bytes, void *stream, ds_index **out);
 
 /* Search m queries (Algorithm direct, Section 4.2): j = min(f(z), R),
  * t = K_j, I = t - [z < X_t]; for a DS_GAP2 index (Algorithm direct-2,
  * Section 4.7) I = t - [z < X_t] - [z < X_{t-1}], and for a Gap-q index
- * I = t - [z < X_t] - ... - [z < X_{t-q+1}], at least -1.
+ * I = t - [z < X_t] - ... - [z < X_{t-q+1}] (X_{-1} = ... = X_0), at least -1.
  *   Z_dev  m queries of the index's dtype; I_dev  m int32 results.
  * m == 0 is a no-op.  Asynchronous on `stream`; allocates nothing; safe to
  * capture in a CUDA graph. */
@@ -171,9 +174,10 @@ DS_API ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, in
 DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *I_host, void *stream);
 
 /* Read-only device views of the index's tables (for inspection and tests):
- * K (R+1 int32, Eq. indexdef or Eq. kgeneral, with the search's flag bits:
- * bit 31 for Eq. indexdef; for Eq. kgeneral, t in bits 0..27 and the count of
- * the cell's knots t, t-1, ... in bits 28..31), the library's copy of X (N+1 values), and,
+ * K (R+1 int32, Eq. indexdef or Eq. kgeneral, with the search's flags: bit 31
+ * set when knot K_j lies in cell j, or for Eq. kgeneral when j < f(X_0); for
+ * Eq. kgeneral bit 30 when knot K_j - 1 lies in cell j too), the library's copy
+ * of X (N+1 values), and,
  * with DS_CACHE_LAYOUT, the (R+1) pairs (8 bytes for float32: int32 K_j then
  * float X_{K_j}; 16 bytes for float64: int32 K_j, 4 bytes of padding, double
  * X_{K_j}).  Any output pointer may be NULL. */

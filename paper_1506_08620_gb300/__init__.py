@@ -118,10 +118,10 @@ def ds_build(X, flags=0, stream=None):
     return Index(out.value, X.dtype)
 
 
-def ds_build_q(X, q, budget_bytes=0, flags=0, stream=None):
-    """Gap-q table of X (q = 1..15), or with q = 0 the smallest q whose table fits budget_bytes."""
+def ds_build_q(X, q, budget_bytes=0, flags=0, q_max=64, stream=None):
+    """Gap-q table of X (q >= 1), or with q = 0 the smallest q in 1..q_max whose table fits budget_bytes."""
     out = ctypes.c_void_p()
-    check(lib().ds_build_q(_dev(X, "X"), X.numel(), _dtype(X), int(flags), int(q), int(budget_bytes),
+    check(lib().ds_build_q(_dev(X, "X"), X.numel(), _dtype(X), int(flags), int(q), int(q_max), int(budget_bytes),
                            _stream(stream), ctypes.byref(out)), "ds_build_q")
     return Index(out.value, X.dtype)
 

@@ -76,7 +76,7 @@ class ds_learned_cfg(ctypes.Structure):
 
 _SIGS = {
     "ds_build": (ST, [P, I64, ST, U32, P, ctypes.POINTER(P)]),
-    "ds_build_q": (ST, [P, I64, ST, U32, ctypes.c_int32, I64, P, ctypes.POINTER(P)]),
+    "ds_build_q": (ST, [P, I64, ST, U32, ctypes.c_int32, ctypes.c_int32, I64, P, ctypes.POINTER(P)]),
     "ds_search": (ST, [P, P, I64, P, P]),
     "ds_search_host": (ST, [P, P, I64, P, P]),
     "ds_index_tables": (ST, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),

@@ -25,18 +25,17 @@ __global__ void k_hr_state_init(HRState *st, int count, int gap)
 __global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P, bool gen)
 {
     const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
-    const uint32_t tmask = gen ? GEN_T_MASK : ~KNOT_FLAG;
+    const uint32_t flags = gen ? KNOT_FLAG | KNOT_FLAG2 : KNOT_FLAG;
     const long long step = (long long)gridDim.x * blockDim.x;
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < (long long)nblk; b += step) {
         const unsigned long long j0 = (unsigned long long)b * PACK_CELLS;
-        const uint32_t base = K[j0] & tmask;
+        const uint32_t base = K[j0] & ~flags;
         uint32_t w[3] = {0u, 0u, 0u};
         for (int s = 0; s < PACK_CELLS; ++s) {
             const unsigned long long j = j0 + s;
             if (j > R) break;
             const uint32_t e = K[j];
-            const uint32_t d = (e & tmask) - base;
-            const uint32_t byte = gen ? d | ((e >> GEN_COUNT_SHIFT) << 6) : d | ((e & KNOT_FLAG) ? 0x80u : 0u);
+            const uint32_t byte = ((e & ~flags) - base) | ((e & flags) >> 24);
             w[s >> 2] |= byte << ((s & 3) * 8);
         }
         P[b] = make_uint4(base, w[0], w[1], w[2]);
@@ -51,7 +50,7 @@ __global__ void k_clear_flags(uint32_t *p, long long count, int stride, uint32_t
 }
 
 __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_knots, unsigned long long R,
-                                 uint32_t *__restrict__ K, int q)
+                                 uint32_t *__restrict__ K)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -63,6 +62,7 @@ __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_kno
         const long long Fi = i <= N ? (long long)F[i] : (1ll << 32);  // lanes past X_N never qualify
         const long long lo = c == 0 ? 0 : (long long)F[c * 32];
         const long long hi = c + 1 == nchunks ? (long long)R + 1 : (long long)F[c * 32 + 32];
+        const long long before = c == 0 ? -1 : (long long)F[c * 32 - 1];  // F_{32c-1}
         for (long long base = lo; base < hi; base += 32) {
             const long long j = base + lane;
             // largest lane k with F_{32c+k} <= j (lane 0 qualifies except in the
@@ -73,16 +73,11 @@ __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_kno
                 const long long Fc = __shfl_sync(0xffffffffu, Fi, (k + s) & 31);
                 if (k + s <= 31 && Fc <= j) k += s;
             }
-            if (j < hi) {
-                const long long t = c * 32 + k;
-                // the knots t, t-1, ... in cell j: a run of F == j (F_0 > j below F_0), at most q
-                int cnt = 0;
-                for (int l = 0; l < q && t - l >= 0; ++l) {
-                    if ((long long)F[t - l] < j) break;
-                    ++cnt;
-                }
-                K[j] = (uint32_t)t | ((uint32_t)cnt << GEN_COUNT_SHIFT);
-            }
+            const long long Fk = __shfl_sync(0xffffffffu, Fi, k);
+            const long long Fkm = __shfl_sync(0xffffffffu, Fi, (k + 31) & 31);
+            const long long Fprev = k == 0 ? before : Fkm;  // F_{t-1}
+            if (j < hi)
+                K[j] = (uint32_t)(c * 32 + k) | (Fk >= j ? KNOT_FLAG : 0u) | (Fprev == j ? KNOT_FLAG2 : 0u);
         }
     }
 }
@@ -201,7 +196,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     k_fill_F<T, FMA><<<grid_for(props, n_knots, block), block, 0, s>>>(Xc, n_knots, (T)hs.H, (T)hs.W, F);
     long long warps_work = (n_knots + 31) / 32 * 32;
     if (gen)
-        k_fill_K_general<<<grid_for(props, warps_work, block), block, 0, s>>>(F, n_knots, R, K, q);
+        k_fill_K_general<<<grid_for(props, warps_work, block), block, 0, s>>>(F, n_knots, R, K);
     else
         k_fill_K<T><<<grid_for(props, warps_work, block), block, 0, s>>>(
             F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
@@ -279,7 +274,7 @@ static ds_status select_q(const T *X, long long n_knots, long long budget_bytes,
     return rc;
 }
 
-ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, int q,
+ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, int q, int q_max,
                        long long budget_bytes, cudaStream_t s, ds_index **out)
 {
     const double t0 = now_ms();
@@ -324,16 +319,15 @@ ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uin
     if (rc == DS_OK && q == 0) {  // the memory-budget choice of q (Section 4.7)
         if (budget_bytes <= 0) budget_bytes = (long long)smem_limit_bytes(idx->props);
         if (dtype == DS_F32)
-            rc = fma ? select_q<float, true>((const float *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props, &q)
-                     : select_q<float, false>((const float *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props, &q);
+            rc = fma ? select_q<float, true>((const float *)X_dev, n_knots, budget_bytes, q_max, s, idx->props, &q)
+                     : select_q<float, false>((const float *)X_dev, n_knots, budget_bytes, q_max, s, idx->props, &q);
         else
-            rc = fma ? select_q<double, true>((const double *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props,
+            rc = fma ? select_q<double, true>((const double *)X_dev, n_knots, budget_bytes, q_max, s, idx->props,
                                               &q)
-                     : select_q<double, false>((const double *)X_dev, n_knots, budget_bytes, MAX_GAP_Q, s, idx->props,
+                     : select_q<double, false>((const double *)X_dev, n_knots, budget_bytes, q_max, s, idx->props,
                                                &q);
         if (rc == DS_OK && q == 0) {
-            set_error("ds_build_q: no q in 1..%d gives a feasible table of at most %lld bytes", MAX_GAP_Q,
-                      budget_bytes);
+            set_error("ds_build_q: no q in 1..%d gives a feasible table of at most %lld bytes", q_max, budget_bytes);
             rc = DS_E_TABLE_TOO_LARGE;
         }
     }
@@ -372,6 +366,7 @@ static ds_status search_typed(const ds_index *idx, const void *Z, long long m, i
     a.W = (T)idx->W;
     a.X0 = (T)idx->X0;
     a.R = (uint32_t)idx->R;
+    a.q = idx->q;
     a.checked = (idx->flags & DS_CHECKED) != 0;
     a.Z = reinterpret_cast<const T *>(Z);
     a.I = I;
@@ -419,7 +414,7 @@ extern "C" ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, vo
     if (K_out_dev) {
         DS_TRY_CUDA(cudaMemcpyAsync(K_out_dev, idx->tab, (size_t)cells * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         ds::k_clear_flags<<<grid, 256, 0, s>>>(reinterpret_cast<uint32_t *>(K_out_dev), cells, 1,
-                                               idx->q >= 2 ? ~ds::GEN_T_MASK : ds::KNOT_FLAG);
+                                               idx->q >= 2 ? ds::KNOT_FLAG | ds::KNOT_FLAG2 : ds::KNOT_FLAG);
         DS_TRY_CUDA(cudaGetLastError());
     }
     if (X_out_dev)

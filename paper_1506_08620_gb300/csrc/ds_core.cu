@@ -205,14 +205,14 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
         set_error("ds_build: DS_GAP2 has no cache layout (its correction reads two knots)");
         return DS_E_ARG;
     }
-    if ((flags & DS_GAP2) && n_knots > (1ll << 28)) {
-        set_error("ds_build: DS_GAP2 takes at most 2^28 knots (28-bit table entries)");
+    if ((flags & DS_GAP2) && n_knots > (1ll << 30)) {
+        set_error("ds_build: DS_GAP2 takes at most 2^30 knots");
         return DS_E_ARG;
     }
-    return build_single(X_dev, n_knots, dtype, flags, (flags & DS_GAP2) ? 2 : 1, 0, (cudaStream_t)stream, out);
+    return build_single(X_dev, n_knots, dtype, flags, (flags & DS_GAP2) ? 2 : 1, 0, 0, (cudaStream_t)stream, out);
 }
 
-ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, int32_t q,
+ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags, int32_t q, int32_t q_max,
                      int64_t budget_bytes, void *stream, ds_index **out)
 {
     clear_error();
@@ -221,21 +221,21 @@ ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_
         return DS_E_ARG;
     }
     *out = nullptr;
-    if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) || q < 0 || q > MAX_GAP_Q ||
+    if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) || q < 0 || (q == 0 && q_max < 1) ||
         (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM))) {
-        set_error("ds_build_q: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u, q=%d)", X_dev,
-                  (long long)n_knots, (int)dtype, flags, q);
+        set_error("ds_build_q: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u, q=%d, q_max=%d)", X_dev,
+                  (long long)n_knots, (int)dtype, flags, q, q_max);
         return DS_E_ARG;
     }
     if ((flags & DS_CACHE_LAYOUT) && q != 1) {
         set_error("ds_build_q: the cache layout exists for q = 1 only");
         return DS_E_ARG;
     }
-    if (n_knots > (q == 1 ? (1ll << 31) - 1 : (1ll << 28))) {
-        set_error("ds_build_q: too many knots for q = %d", q);
+    if (n_knots > (q == 1 ? (1ll << 31) - 1 : (1ll << 30))) {
+        set_error("ds_build_q: too many knots for q = %d (at most 2^30 for an Eq. kgeneral table)", q);
         return DS_E_ARG;
     }
-    return build_single(X_dev, n_knots, dtype, flags, q, budget_bytes, (cudaStream_t)stream, out);
+    return build_single(X_dev, n_knots, dtype, flags, q, q_max, budget_bytes, (cudaStream_t)stream, out);
 }
 
 ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, int32_t *I_dev, void *stream)

@@ -245,15 +245,15 @@ __global__ void k_fill_K(const uint32_t *__restrict__ F, long long n_knots, uint
 }
 
 // K_j = max{ i : F_i <= j }, j = 0..R (Eq. kgeneral; 0 below F_0), for
-// DirectGap2 and Gap-q, with the count of the cell's knots t, t-1, ... (at
-// most q) in bits 28..31.  Warp c owns the cells [F_{32c}, F_{32c+32}) (chunk
-// 0 from 0, the last chunk up to R) and finds each cell's knot by a 5-step
-// search over its 32 F values.
+// DirectGap2 and Gap-q, with bit 31 set when F_{K_j} >= j and bit 30 when
+// F_{K_j - 1} == j.  Warp c owns the cells [F_{32c}, F_{32c+32}) (chunk 0 from
+// 0, the last chunk up to R) and finds each cell's knot by a 5-step search
+// over its 32 F values.
 __global__ void k_fill_K_general(const uint32_t *__restrict__ F, long long n_knots, unsigned long long R,
-                                 uint32_t *__restrict__ K, int q);
+                                 uint32_t *__restrict__ K);
 
-// Packed copy of a flagged K (Direct, or Eq. kgeneral with q <= 3 when gen):
-// block b = {K_{12b}, 12 bytes (K_j - K_{12b}) | flag or count}.
+// Packed copy of a flagged K (Direct, or Eq. kgeneral with q <= 5 when gen):
+// block b = {K_{12b}, 12 bytes (K_j - K_{12b}) | flags >> 24}.
 __global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long R, uint4 *__restrict__ P, bool gen);
 
 // Clear the knot flags (flag_mask) of every stride-th 32-bit word: turns a copy
@@ -261,9 +261,9 @@ __global__ void k_pack_cells(const uint32_t *__restrict__ K, unsigned long long 
 __global__ void k_clear_flags(uint32_t *p, long long count, int stride, uint32_t flag_mask);
 
 // host side, defined in ds_build.cu
-// q >= 1: the table of pair distance q (1: Direct); q == 0: the smallest q
-// whose table fits budget_bytes (<= 0: the shared-memory staging limit).
-ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, int q,
+// q >= 1: the table of pair distance q (1: Direct); q == 0: the smallest q in
+// 1..q_max whose table fits budget_bytes (<= 0: the shared-memory staging limit).
+ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uint32_t flags, int q, int q_max,
                        long long budget_bytes, cudaStream_t s, ds_index **out);
 void free_index(ds_index *idx);
 ds_status search_index(const ds_index *idx, const void *Z, long long m, int32_t *I, cudaStream_t s);

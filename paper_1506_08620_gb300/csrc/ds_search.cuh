@@ -17,12 +17,14 @@
 //
 // DirectGap2 and Gap-q tables (Section 4.7: f(X_{i+q}) > f(X_i), Eq.
 // f-monotonic-n) hold t = K_j = max{i : F_i <= j} (Eq. kgeneral) in bits
-// 0..27 and, in bits 28..31, the count c of the knots t, t-1, ... that lie in
-// the cell (F == j; for the cells below F_0, t = 0 and c = 1), at most q.  A
-// knot t-l outside the cell has F_{t-l} < j = f(z), so z > X_{t-l}; the q
-// comparisons i = t - [z < X_t] - ... - [z < X_{t-q+1}] of Algorithm direct-2
-// and its generalisation therefore reduce to the first c, and since X
-// increases they stop at the first that fails.
+// 0..29, bit 31 set when F_t >= j (knot t lies in the cell, or the cell is
+// below F_0 and t = 0) and bit 30 when F_{t-1} == j (knot t-1 lies in the cell
+// too).  Without bit 31, F_t < j = f(z) gives z > X_t and the answer is t;
+// without bit 30 the same argument gives z > X_{t-1}.  Otherwise the answer is
+// the largest i in [t - q, t] with X_i <= z (X_{t-q} < z because F_{t-q} <
+// F_t <= j; X_{-1} = -inf), found by a bisection after the comparisons with
+// X_t and X_{t-1}: for q = 2 exactly the comparisons of Algorithm direct-2,
+// each made only where the flags say it can be true.
 #pragma once
 
 #include "ds_common.cuh"
@@ -33,29 +35,26 @@ namespace ds {
 enum FForm : int { F_PLAIN = 0, F_FMA = 1, F_PLAIN_X0ZERO = 2 };
 
 constexpr uint32_t KNOT_FLAG = 0x80000000u;
-constexpr uint32_t GEN_T_MASK = 0x0FFFFFFFu;  // Eq. kgeneral tables: t in bits 0..27
-constexpr int GEN_COUNT_SHIFT = 28;           // ... and the knot count of the cell above
-constexpr int MAX_GAP_Q = 15;                 // largest q the 4-bit count can describe
-constexpr int MAX_PACKED_Q = 3;               // largest q the packed table can describe
+
+constexpr uint32_t KNOT_FLAG2 = 0x40000000u;  // Eq. kgeneral: knot t-1 in the cell as well
+constexpr uint32_t GEN_T_MASK = 0x3FFFFFFFu;  // Eq. kgeneral: t in bits 0..29
 
 // Packed table: K in 16-byte blocks of 12 cells, {K of the block's first
-// cell, 12 bytes, one per cell}.  Direct: a cell holds at most one knot (F is
-// strictly increasing), so K grows by at most 1 per cell; the byte is
-// (K_j - base) | flag << 7.  Eq. kgeneral with q <= 3: K grows by at most q
-// per cell, the difference (at most 33) fits 6 bits and the count (at most 3)
-// the other 2.  1.33 bytes per cell instead of 4 keeps large tables
-// L2-resident, and a lookup still reads one 16-byte sector.
+// cell, 12 bytes (K_j - base) | flags >> 24}.  K grows by at most 1 per cell
+// for Direct (F is strictly increasing) and at most q for Eq. kgeneral
+// (F_{i+q} > F_i), so the difference fits 6 bits for q <= 5; bits 6 and 7
+// carry the flags of bits 30 and 31.  1.33 bytes per cell instead of 4 keeps
+// large tables L2-resident, and a lookup still reads one 16-byte sector.
 constexpr int PACK_CELLS = 12;
+constexpr int MAX_PACKED_Q = 5;
 
-template <bool GEN = false>
 __device__ __forceinline__ uint32_t unpack_cell(uint4 w, uint32_t j)
 {
     const uint32_t b = __umulhi(j, 0xAAAAAAABu) >> 3;  // j / 12
     const uint32_t s = j - b * PACK_CELLS;
     const uint32_t word = s < 4 ? w.y : (s < 8 ? w.z : w.w);
     const uint32_t byte = (word >> ((s & 3u) * 8u)) & 0xFFu;
-    if constexpr (GEN) return (w.x + (byte & 0x3Fu)) | ((byte >> 6) << GEN_COUNT_SHIFT);
-    else return (w.x + (byte & 0x7Fu)) | ((byte & 0x80u) << 24);
+    return (w.x + (byte & 0x3Fu)) | ((byte & 0xC0u) << 24);
 }
 
 template <typename T> struct SearchArgs {
@@ -68,6 +67,7 @@ template <typename T> struct SearchArgs {
     uint32_t x_smem_off;  // byte offset of X inside the image
     T H, W, X0;
     uint32_t R;
+    int32_t q;            // pair distance of an Eq. kgeneral table (Gap-q); 1 for Direct
     int checked;          // NaN -> -1
     const T *Z;
     int32_t *I;
@@ -161,19 +161,24 @@ __device__ __forceinline__ bool z_less(T z, T x)
 }
 
 // Eq. kgeneral correction (Algorithm direct-2 and its q-knot form): x = X_t
-// (read by the caller when the count is nonzero); the further knots
-// X_{t-1}, ... of the cell are read only while the comparisons hold.
+// and xp = X_{t-1}, read by the caller under bits 31 and 30.  When
+// z < X_{t-1} the answer lies in [max(t - q, -1), t - 2] and is found by
+// bisection with X_{t-q} < z.
 template <typename T, bool INTOPS, bool SMEM>
-__device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, const T *X, int checked)
+__device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, T xp, const T *X, int32_t q, int checked)
 {
     const int32_t t = (int32_t)(e & GEN_T_MASK);
-    const int32_t c = (int32_t)(e >> GEN_COUNT_SHIFT);
     int32_t i = t;
-    if (c > 0 && z_less<T, INTOPS>(z, x)) {
-        --i;
-        for (int32_t l = 1; l < c; ++l) {
-            if (!z_less<T, INTOPS>(z, gather_x<T, SMEM>(t - l, X))) break;
-            --i;
+    if ((e & KNOT_FLAG) && z_less<T, INTOPS>(z, x)) {
+        i = t - 1;
+        if ((e & KNOT_FLAG2) && z_less<T, INTOPS>(z, xp)) {
+            int32_t a = t - q < -1 ? -1 : t - q, b = t - 1;  // X_a <= z < X_b
+            while (b - a > 1) {
+                const int32_t m = (a + b) >> 1;
+                if (z_less<T, INTOPS>(z, gather_x<T, SMEM>(m, X))) b = m;
+                else a = m;
+            }
+            i = a;
         }
     }
     if (checked && is_nan<T>(z)) i = -1;
@@ -188,8 +193,11 @@ __device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, co
     T x = T(0);
     const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x);
     if constexpr (GEN) {
-        if (e >> GEN_COUNT_SHIFT) x = gather_x<T, SMEM>((int32_t)(e & GEN_T_MASK), X);
-        return correct_gen<T, INTOPS, SMEM>(z, e, x, X, a.checked);
+        const int32_t t = (int32_t)(e & GEN_T_MASK);
+        T xp = T(0);
+        if (e & KNOT_FLAG) x = gather_x<T, SMEM>(t, X);
+        if (e & KNOT_FLAG2) xp = gather_x<T, SMEM>(t - 1, X);
+        return correct_gen<T, INTOPS, SMEM>(z, e, x, xp, X, a.q, a.checked);
     } else {
         if constexpr (!CACHE) {
             if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
@@ -247,11 +255,17 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
         for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q]);
         int32_t r[NQ];
         if constexpr (GEN) {
+            T xp[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int32_t t = (int32_t)(e[q] & GEN_T_MASK);
+                xp[q] = T(0);
+                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>(t, X);
+                if (e[q] & KNOT_FLAG2) xp[q] = gather_x<T, SMEM>(t - 1, X);
+            }
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
-                if (e[q] >> GEN_COUNT_SHIFT) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & GEN_T_MASK), X);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) r[q] = correct_gen<T, INTOPS, SMEM>(zs[q], e[q], x[q], X, a.checked);
+                r[q] = correct_gen<T, INTOPS, SMEM>(zs[q], e[q], x[q], xp[q], X, a.q, a.checked);
         } else {
             if constexpr (!CACHE) {
 #pragma unroll
@@ -318,22 +332,26 @@ __device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long l
     return i;
 }
 
-// Eq. kgeneral correction on bit patterns; xb = bits of X_t (read by the
-// caller when the count is nonzero).
+// Eq. kgeneral correction on bit patterns; xb, xpb = bits of X_t, X_{t-1}
+// (read by the caller under bits 31 and 30).
 template <bool SMEM>
-__device__ __forceinline__ int32_t correct_bits_gen(long long zb, uint32_t e, long long xb, const long long *Xb,
-                                                    uint64_t keep, int checked)
+__device__ __forceinline__ int32_t correct_bits_gen(long long zb, uint32_t e, long long xb, long long xpb,
+                                                    const long long *Xb, uint64_t keep, int32_t q, int checked)
 {
     const long long kz = okey_bits(zb);
     const int32_t t = (int32_t)(e & GEN_T_MASK);
-    const int32_t c = (int32_t)(e >> GEN_COUNT_SHIFT);
     int32_t i = t;
-    if (c > 0 && kz < okey_bits(xb)) {
-        --i;
-        for (int32_t l = 1; l < c; ++l) {
-            const long long *px = Xb + (t - l);
-            if (!(kz < okey_bits(SMEM ? *px : ld_keep(px, keep)))) break;
-            --i;
+    if ((e & KNOT_FLAG) && kz < okey_bits(xb)) {
+        i = t - 1;
+        if ((e & KNOT_FLAG2) && kz < okey_bits(xpb)) {
+            int32_t a = t - q < -1 ? -1 : t - q, b = t - 1;  // X_a <= z < X_b
+            while (b - a > 1) {
+                const int32_t m = (a + b) >> 1;
+                const long long *px = Xb + m;
+                if (kz < okey_bits(SMEM ? *px : ld_keep(px, keep))) b = m;
+                else a = m;
+            }
+            i = a;
         }
     }
     if (checked && ((unsigned long long)zb & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) i = -1;
@@ -397,26 +415,29 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 xb[q] = p.y;
             } else if constexpr (PACKED) {
                 const uint32_t j = e[q];
-                e[q] = unpack_cell<GEN>(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
+                e[q] = unpack_cell(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
             } else {
                 e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
             }
         }
         if constexpr (GEN) {
+            long long xpb[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const long long *px = Xb + (e[q] & GEN_T_MASK);
                 xb[q] = 0;
-                if (e[q] >> GEN_COUNT_SHIFT) xb[q] = SMEM ? *px : ld_keep(px, keep);
+                xpb[q] = 0;
+                if (e[q] & KNOT_FLAG) xb[q] = SMEM ? px[0] : ld_keep(px, keep);
+                if (e[q] & KNOT_FLAG2) xpb[q] = SMEM ? px[-1] : ld_keep(px - 1, keep);
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = b + (long long)v * blockDim.x;
                 if (idx < nvec)
-                    __stcs(Iv + idx,
-                           make_int2(correct_bits_gen<SMEM>(zb[2 * v], e[2 * v], xb[2 * v], Xb, keep, a.checked),
-                                     correct_bits_gen<SMEM>(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1], Xb, keep,
-                                                            a.checked)));
+                    __stcs(Iv + idx, make_int2(correct_bits_gen<SMEM>(zb[2 * v], e[2 * v], xb[2 * v], xpb[2 * v], Xb,
+                                                                      keep, a.q, a.checked),
+                                               correct_bits_gen<SMEM>(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1],
+                                                                      xpb[2 * v + 1], Xb, keep, a.q, a.checked)));
             }
         } else {
             if constexpr (!CACHE) {
@@ -450,14 +471,14 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 e = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xq = p.y;
             } else if constexpr (PACKED) {
-                e = unpack_cell<GEN>(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
+                e = unpack_cell(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
             } else {
                 e = K[e];
             }
             if constexpr (GEN) {
                 const long long *px = Xb + (e & GEN_T_MASK);
-                const long long xq0 = (e >> GEN_COUNT_SHIFT) ? *px : 0;
-                a.I[q] = correct_bits_gen<true>(zq, e, xq0, Xb, keep, a.checked);
+                const long long xq0 = (e & KNOT_FLAG) ? px[0] : 0, xq1 = (e & KNOT_FLAG2) ? px[-1] : 0;
+                a.I[q] = correct_bits_gen<true>(zq, e, xq0, xq1, Xb, keep, a.q, a.checked);
             } else {
                 if constexpr (!CACHE) {
                     if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];

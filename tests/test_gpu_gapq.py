@@ -55,7 +55,7 @@ def _queries(X, g, n=3000):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-@pytest.mark.parametrize("q", [1, 3, 4, 8, 15])
+@pytest.mark.parametrize("q", [1, 3, 4, 8, 15, 40])
 def test_gapq_tables_bit_identical(ds, dtype, q):
     for fma in (False, True):
         for name, X in _arrays(dtype):
@@ -75,7 +75,7 @@ def test_gapq_tables_bit_identical(ds, dtype, q):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-@pytest.mark.parametrize("q", [3, 5, 8])
+@pytest.mark.parametrize("q", [3, 5, 11, 12, 40])
 @pytest.mark.parametrize("flags", [0, 1, 8, 9], ids=["smem", "smem_fma", "l2", "l2_fma"])
 @pytest.mark.parametrize("variant", ["bits_packed", "bits", "float"])
 def test_gapq_search_matches_definition(ds, dtype, q, flags, variant, monkeypatch):
@@ -103,13 +103,13 @@ def test_budget_choice_of_q_matches_oracle(ds, dtype):
         x_bytes = (X.nbytes + 15) // 16 * 16
         for fma in (False, True):
             for budget in (x_bytes + 4 * n, x_bytes + 16 * n, x_bytes + 64 * n):
-                q_ref, hr = oracle.choose_q(X, fma, budget, 15)
+                q_ref, hr = oracle.choose_q(X, fma, budget, 24)
                 if q_ref == 0:
                     with pytest.raises(ds.DsError):
-                        ds.ds_build_q(_cuda(X), 0, budget, flags=ds.DS_FMA if fma else 0)
+                        ds.ds_build_q(_cuda(X), 0, budget, flags=ds.DS_FMA if fma else 0, q_max=24)
                     continue
                 chosen.add(q_ref)
-                idx = ds.ds_build_q(_cuda(X), 0, budget, flags=ds.DS_FMA if fma else 0)
+                idx = ds.ds_build_q(_cuda(X), 0, budget, flags=ds.DS_FMA if fma else 0, q_max=24)
                 info = idx.info()
                 assert info["gap_q"] == q_ref and info["R"] == hr["R"] and info["H"] == hr["H"]
                 Z = _queries(X, g, 2000)
@@ -136,19 +136,20 @@ def test_default_budget_is_the_shared_memory_stage(ds):
 def test_gapq_statuses(ds):
     from paper_1506_08620_gb300 import _abi
 
-    def status(X, q, budget=0, flags=0):
+    def status(X, q, budget=0, flags=0, q_max=64):
         try:
-            ds.ds_build_q(_cuda(X), q, budget, flags).free()
+            ds.ds_build_q(_cuda(X), q, budget, flags, q_max).free()
             return _abi.DS_OK
         except ds.DsError as e:
             return e.status
 
     X = np.linspace(0, 1, 1000).astype(np.float32)
-    assert status(X, 16) == _abi.DS_E_ARG
+    assert status(X, 1000) == _abi.DS_OK  # q above N: pair distance N
     assert status(X, -1) == _abi.DS_E_ARG
     assert status(X, 3, flags=ds.DS_CACHE_LAYOUT) == _abi.DS_E_ARG
     assert status(X, 1, flags=ds.DS_CACHE_LAYOUT) == _abi.DS_OK
     assert status(X, 0, budget=100) == _abi.DS_E_TABLE_TOO_LARGE
+    assert status(X, 0, q_max=0) == _abi.DS_E_ARG
     assert status(np.array([0.0, 2.0, 1.0]), 0) == _abi.DS_E_NOT_INCREASING
     # infeasible for Direct and DirectGap2 (m(X_3 - X_0) == m(X_1 - X_0)), feasible for q = 3
     Y = np.array([-1e9, 0, 1, 2], dtype=np.float32)
@@ -156,4 +157,26 @@ def test_gapq_statuses(ds):
     assert oracle.compute_hr(Y, q=3)["status"] == oracle.OR_OK and status(Y, 3) == _abi.DS_OK
     idx = ds.ds_build_q(_cuda(Y), 0, 1 << 20)
     assert idx.info()["gap_q"] == 3
+    idx.free()
+
+
+def test_large_q_makes_the_two_scale_gap_law_feasible(ds):
+    # workload 4's gap law (99% U[1e-3,1e-2], 1% U[1e3,1e4]) on 2^18 + 1 knots:
+    # Direct overflows (R >= 2^32); a large q gives a feasible table
+    w = W.workload4(n_knots=(1 << 18) + 1, m=1 << 20, seed=1)
+    X, Z = w["X"], w["Z"]
+    assert oracle.compute_hr(X)["status"] == oracle.OR_E_OVERFLOW
+    q_ref, hr = oracle.choose_q(X, False, 1 << 30, 256)
+    assert q_ref > 1
+    idx = ds.ds_build_q(_cuda(X), 0, 1 << 30, q_max=256)
+    info = idx.info()
+    assert info["gap_q"] == q_ref and info["R"] == hr["R"] and info["H"] == hr["H"]
+    st, K_ref, _ = oracle.fill_k(X, hr["H"], hr["W"], hr["R"], q=q_ref)
+    K, _, _ = ds.ds_index_export(idx)
+    assert np.array_equal(K.cpu().numpy(), K_ref)
+    # uniform queries (mostly in the wide gaps) and queries inside the dense clusters
+    g = np.random.default_rng(2)
+    Zc = np.concatenate([Z, W.adversarial_queries(X), W.midpoints(X)])
+    got = ds.ds_search(idx, _cuda(Zc)).cpu().numpy()
+    assert np.array_equal(got, oracle.upper_bound(X, Zc))
     idx.free()
