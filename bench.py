@@ -407,6 +407,17 @@ def setup_batched(args, ds, W, torch, dev, rank):
         return Zp.numel() * 4, Ip.numel() * 4
     job.e2e = e2e
     job.e2e_out = Ip
+
+    def extras(stream):
+        # the same engine without knot fingerprints in K (every query in a cell
+        # holding a knot reads the knot), autotuned the same way
+        nf = ds.ds_batch_build(Xd, xo, ds.DS_NO_FINGERPRINT)
+        t = ds.ds_batch_autotune(nf, Zd, zo, out)
+        res = {"no_fingerprint": job.m / time_calls(torch, stream, lambda: ds.ds_batch_search(nf, Zd, zo, out), 5),
+               "no_fingerprint_tune": t}
+        nf.free()
+        return res
+    job.extras = extras
     return job
 
 

@@ -72,11 +72,14 @@ enum {
     DS_CHECKED = 4u,      /* NaN queries return -1 */
     DS_NO_SMEM = 8u,      /* never stage the table in shared memory (keep it L2/HBM resident) */
     DS_STRICT = 16u,      /* batched builds: an infeasible array is an error instead of a fallback */
-    DS_GAP2 = 32u         /* DirectGap2 (Section 4.7): f need only separate knots two apart
+    DS_GAP2 = 32u,        /* DirectGap2 (Section 4.7): f need only separate knots two apart
                              (Eq. f-monotonic-2), K_j = max{i : f(X_i) <= j} (Eq. kgeneral), answers by
                              Algorithm direct-2, i = t - [z < X_t] - [z < X_{t-1}]; a smaller table and
                              feasible on more arrays; not combined with DS_CACHE_LAYOUT; the same as
                              ds_build_q with q = 2 */
+    DS_NO_FINGERPRINT = 64u /* batched builds: K entries of arrays with at most 2^24 knots carry no
+                             7-bit fingerprint of f(X_t), so every query in a cell holding a knot
+                             reads the knot (the paper's correcting comparison, always made) */
 };
 
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
@@ -201,7 +204,11 @@ DS_API ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, void *
  * on which direct search is infeasible is served by the fixed-depth bisection
  * of Algorithm binaryopt (the log-time fall-back the Conclusion names) unless
  * DS_STRICT is set, in which case the build fails with that array's status.
- * Synchronous. */
+ * Flags: DS_FMA | DS_CHECKED | DS_STRICT | DS_NO_SMEM | DS_NO_FINGERPRINT.
+ * For arrays of at most 2^24 knots each flagged K entry also carries a 7-bit
+ * fingerprint of its knot's cell position (not in the paper), so that a query
+ * reads the knot only when the fingerprints are equal; DS_NO_FINGERPRINT turns
+ * this off.  Synchronous. */
 DS_API ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, ds_dtype dtype,
                          uint32_t flags, void *stream, ds_batch **out);
 

@@ -31,6 +31,7 @@ DS_CHECKED = 4
 DS_NO_SMEM = 8
 DS_STRICT = 16
 DS_GAP2 = 32
+DS_NO_FINGERPRINT = 64
 
 DS_LEARNED_FORCE = 1
 DS_LEARNED_LINEAR = 2

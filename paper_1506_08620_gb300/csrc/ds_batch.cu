@@ -58,9 +58,9 @@ __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_
     if (threadIdx.x == 0) *counter = 0;
 }
 
-__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
-                             const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
-                             unsigned char *blob)
+__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
+                             const long long *__restrict__ x_off, const long long *__restrict__ kc_off, int n_arrays,
+                             const ArrDesc *__restrict__ desc, unsigned char *blob)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -92,7 +92,12 @@ __global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const long long *__
                 if ((long long)Fc < j) k += s;
             }
             const uint32_t Fk = __shfl_sync(0xffffffffu, Fi, k);
-            if (j <= last) K[j] = (uint32_t)(lc * 32 + k) | ((long long)Fk == j ? KNOT_FLAG : 0u);
+            if (j <= last) {
+                const long long t = lc * 32 + k;
+                uint32_t e = (uint32_t)t;
+                if ((long long)Fk == j) e |= KNOT_FLAG | (d.aux ? (uint32_t)G[start + t] << FP_SHIFT : 0u);
+                K[j] = e;
+            }
         }
     }
 }
@@ -196,6 +201,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
     ds_status rc = DS_OK;
     std::vector<HRState> hs;
     uint32_t *F = nullptr;
+    uint8_t *G = nullptr;
     long long *kc_dev = nullptr;
     do {
         if (cudaMemcpyAsync(segs_dev, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice, s) !=
@@ -267,6 +273,12 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
             // X0 and XN are read back below
         }
         if (rc != DS_OK) break;
+        // fingerprints in K: for all direct arrays or none (t needs 24 bits at most)
+        e->fingerprints = !(flags & DS_NO_FINGERPRINT) && e->n_direct > 0;
+        for (int a = 0; a < A; ++a)
+            if (e->desc_host[a].mode == MODE_DIRECT && x_off[a + 1] - x_off[a] > FP_MAX_KNOTS) e->fingerprints = false;
+        for (int a = 0; a < A; ++a)
+            if (e->desc_host[a].mode == MODE_DIRECT) e->desc_host[a].aux = e->fingerprints ? 1 : 0;
         // knots X_0, X_N per array (for the descriptors)
         {
             std::vector<T> ends(2 * (size_t)A);
@@ -298,6 +310,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
         if (cudaMalloc(&e->blob, std::max<size_t>(off, 16)) != cudaSuccess ||
             cudaMalloc(&e->desc_dev, sizeof(ArrDesc) * (size_t)A) != cudaSuccess ||
             cudaMalloc(&F, sizeof(uint32_t) * std::max<long long>(x_off[A], 1)) != cudaSuccess ||
+            cudaMalloc(&G, std::max<long long>(x_off[A], 1)) != cudaSuccess ||
             cudaMalloc(&kc_dev, sizeof(long long) * (size_t)(A + 1)) != cudaSuccess) {
             set_error("batched build: device allocation failed");
             rc = DS_E_NOMEM;
@@ -307,11 +320,11 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
         cudaMemcpyAsync(e->desc_dev, e->desc_host.data(), sizeof(ArrDesc) * (size_t)A, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(kc_dev, kc.data(), sizeof(long long) * (size_t)(A + 1), cudaMemcpyHostToDevice, s);
         const int sgrid = std::max(1, std::min(n_segs, e->props.num_sms * 8));
-        k_seg_copy_fill_F<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, e->desc_dev, e->blob, F);
+        k_seg_copy_fill_F<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, e->desc_dev, e->blob, F, G);
         const long long kchunks = kc[A];
         if (kchunks > 0) {
             const long long kgrid = std::min<long long>((kchunks * 32 + 255) / 256, (long long)e->props.num_sms * 16);
-            k_seg_fill_K<<<(int)kgrid, 256, 0, s>>>(F, x_off_dev, kc_dev, A, e->desc_dev, e->blob);
+            k_seg_fill_K<<<(int)kgrid, 256, 0, s>>>(F, G, x_off_dev, kc_dev, A, e->desc_dev, e->blob);
         }
         cudaError_t ce = cudaGetLastError();
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -323,6 +336,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
     } while (0);
     cudaFree(segs_dev);
     if (F) cudaFree(F);
+    if (G) cudaFree(G);
     if (kc_dev) cudaFree(kc_dev);
     if (hs_out) *hs_out = hs;
     return rc;
@@ -373,36 +387,40 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
 }
 
 // ---------------------------------------------------------------- launch
-template <typename T, int VPT, bool INTERP, bool DO>
+template <typename T, int VPT, bool INTERP, int KIND>
 static const void *pick4(bool vec)
 {
-    return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, DO>
-               : (const void *)k_batch_search<T, VPT, INTERP, false, DO>;
+    return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, KIND>
+               : (const void *)k_batch_search<T, VPT, INTERP, false, KIND>;
 }
 template <typename T, int VPT, bool INTERP>
-static const void *pick3(bool vec, bool direct_only)
+static const void *pick3(bool vec, int kind)
 {
-    return direct_only ? pick4<T, VPT, INTERP, true>(vec) : pick4<T, VPT, INTERP, false>(vec);
+    switch (kind) {
+    case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec);
+    case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec);
+    default: return pick4<T, VPT, INTERP, KIND_ALL>(vec);
+    }
 }
 template <typename T, int VPT>
-static const void *pick2(bool interp, bool vec, bool direct_only)
+static const void *pick2(bool interp, bool vec, int kind)
 {
-    return interp ? pick3<T, VPT, true>(vec, direct_only) : pick3<T, VPT, false>(vec, direct_only);
+    return interp ? pick3<T, VPT, true>(vec, kind) : pick3<T, VPT, false>(vec, kind);
 }
 template <typename T>
-static const void *pick1(int vpt, bool interp, bool vec, bool direct_only)
+static const void *pick1(int vpt, bool interp, bool vec, int kind)
 {
     switch (vpt) {
-    case 1: return pick2<T, 1>(interp, vec, direct_only);
-    case 2: return pick2<T, 2>(interp, vec, direct_only);
-    default: return pick2<T, 4>(interp, vec, direct_only);
+    case 1: return pick2<T, 1>(interp, vec, kind);
+    case 2: return pick2<T, 2>(interp, vec, kind);
+    default: return pick2<T, 4>(interp, vec, kind);
     }
 }
 static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec)
 {
     const bool direct_only = e->n_learned == 0 && e->n_fallback == 0;
-    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, direct_only)
-                              : pick1<double>(vpt, interp, vec, direct_only);
+    const int kind = !direct_only ? KIND_ALL : (e->fingerprints ? KIND_DIRECT_FP : KIND_DIRECT);
+    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, kind) : pick1<double>(vpt, interp, vec, kind);
 }
 
 static int clamp_block(int b) { return b == 128 || b == 512 ? b : 256; }
@@ -625,7 +643,7 @@ ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t
     }
     *out = nullptr;
     if (!Xcat_dev || !x_off_dev || n_arrays < 1 || (dtype != DS_F32 && dtype != DS_F64) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CHECKED | DS_STRICT | DS_NO_SMEM))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CHECKED | DS_STRICT | DS_NO_SMEM | DS_NO_FINGERPRINT))) {
         ds::set_error("ds_batch_build: bad argument");
         return DS_E_ARG;
     }

@@ -118,6 +118,62 @@ __device__ __forceinline__ uint32_t trunc_u32_bits(double v)
     return (uint32_t)(mant >> (52 - e));
 }
 
+// Cell j = trunc(v) (as trunc_u32 / cvt.rzi.u32: negatives and NaN -> 0,
+// saturated at 2^32 - 1) and fingerprint g = floor(128 (v - trunc(v))), the
+// top 7 bits of the fractional part, 0 for negatives and NaN and 128 for
+// v >= 2^32, computed exactly from the bit pattern.  Within one cell g is a
+// non-decreasing function of v, so g(v) < g(w) implies v < w and g(v) > g(w)
+// implies v > w: comparing fingerprints decides most comparisons of a query
+// with the knot of its cell without reading the knot.
+constexpr uint32_t FP_BITS = 7;
+constexpr uint32_t FP_ABOVE = 128;  // fingerprint of a value past the last cell
+
+__device__ __forceinline__ uint32_t cell_fp_bits(double v, uint32_t *g)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF) - 1023;
+    if ((long long)b < 0 || e < -7 || (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) {
+        *g = 0u;
+        return 0u;
+    }
+    if (e >= 32) {
+        *g = FP_ABOVE;
+        return 0xFFFFFFFFu;
+    }
+    const unsigned long long mant = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+    *g = (uint32_t)(mant >> (45 - e)) & 0x7Fu;
+    return e < 0 ? 0u : (uint32_t)(mant >> (52 - e));
+}
+
+__device__ __forceinline__ uint32_t cell_fp_bits(float v, uint32_t *g)
+{
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFF) - 127;
+    if ((int32_t)b < 0 || e < -7 || (b & 0x7FFFFFFFu) > 0x7F800000u) {
+        *g = 0u;
+        return 0u;
+    }
+    if (e >= 32) {
+        *g = FP_ABOVE;
+        return 0xFFFFFFFFu;
+    }
+    const uint32_t mant = (b & 0x007FFFFFu) | (1u << 23);
+    if (e < 0) {
+        *g = mant >> (16 - e);
+        return 0u;
+    }
+    if (e <= 16) {
+        *g = (mant >> (16 - e)) & 0x7Fu;
+        return mant >> (23 - e);
+    }
+    if (e <= 23) {
+        *g = (mant << (e - 16)) & 0x7Fu;
+        return mant >> (23 - e);
+    }
+    *g = 0u;
+    return mant << (e - 23);
+}
+
 // Signed integer key ordering doubles like their values (+0 and -0 equal);
 // for non-NaN a, b:  a < b  <=>  okey(a) < okey(b).
 __device__ __forceinline__ long long okey(double v)

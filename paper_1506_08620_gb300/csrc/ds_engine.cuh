@@ -36,6 +36,7 @@ struct Engine {
     long long h_updates = 0;
     unsigned long long R_total = 0;
     int n_direct = 0, n_learned = 0, n_fallback = 0;
+    bool fingerprints = false;  // every direct array's K carries knot fingerprints
     double build_ms = 0;
 };
 

@@ -710,7 +710,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             long long w = (long long)d.e_lo + d.e_hi + 3;
             long long t = 1;
             while (t * 2 <= w) t *= 2;
-            d.wbits = (int32_t)t;
+            d.aux = (int32_t)t;
             L->max_window = std::max(L->max_window, w);
         }
         ce = cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);

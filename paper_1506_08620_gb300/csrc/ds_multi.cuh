@@ -40,7 +40,8 @@ struct __align__(16) ArrDesc {
     uint32_t R;           // direct: largest cell
     int32_t form;         // direct: FForm
     int32_t pbits;        // bisection over all knots: 2^floor(log2 N)
-    int32_t wbits;        // learned: 2^floor(log2(window width))
+    int32_t aux;          // learned: 2^floor(log2(window width)); direct: 1 if K entries carry
+                          // fingerprints (bits 24..30, t in bits 0..23)
     double H, W, X0;      // direct: parameters in the array's precision (held exactly)
     double XN;            // last knot
     float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32)
@@ -96,6 +97,29 @@ __device__ __forceinline__ uint32_t cell_rt(T z, const ArrDesc &d)
     else j = A::trunc_u32(v);
     return min(j, d.R);
 }
+
+// Cell and fingerprint of a query (cell_fp_bits); a query past the last
+// cell gets FP_ABOVE, larger than any knot's fingerprint in cell R.
+template <typename T>
+__device__ __forceinline__ uint32_t cell_rt_fp(T z, const ArrDesc &d, uint32_t *g)
+{
+    using A = Arith<T>;
+    const T H = (T)d.H;
+    T v;
+    if (d.form == F_FMA) v = A::fma(H, z, -(T)d.W);
+    else if (d.form == F_PLAIN_X0ZERO) v = A::mul(H, z);
+    else v = A::mul(H, A::sub(z, (T)d.X0));
+    const uint32_t j = cell_fp_bits(v, g);
+    if (j > d.R) {
+        *g = FP_ABOVE;
+        return d.R;
+    }
+    return j;
+}
+
+constexpr uint32_t FP_T_MASK = 0x00FFFFFFu;  // t of a K entry that carries a fingerprint
+constexpr int FP_SHIFT = 24;
+constexpr long long FP_MAX_KNOTS = 1ll << 24;
 
 template <typename T> __device__ __forceinline__ bool lt_exact(T a, T b)
 {

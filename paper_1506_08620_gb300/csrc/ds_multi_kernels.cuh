@@ -84,13 +84,41 @@ template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uin
 }
 
 // ------------------------------------------------------------------ NQ queries of one array
-template <typename T, int NQ, bool DIRECT_ONLY, bool SM>
+// Kernel kinds: every mode (fingerprints decided per array at run time), or
+// direct arrays only, without or with fingerprints (the other paths compiled
+// out, which keeps the register count low).
+enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2 };
+
+template <typename T, int NQ, int KIND, bool SM>
 __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
                                              const T *z, int32_t *r, uint64_t pol)
 {
-    if (DIRECT_ONLY || d.mode == MODE_DIRECT) {
+    if (KIND != KIND_ALL || d.mode == MODE_DIRECT) {
         uint32_t e[NQ];
         T x[NQ];
+        if (KIND == KIND_DIRECT_FP || (KIND == KIND_ALL && d.aux)) {
+            // entries carry the fingerprint of their knot: the knot is read only
+            // when the query's fingerprint equals it (about 1 in 128)
+            uint32_t g[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) e[q] = tab_ld<SM>(K + cell_rt_fp<T>(z[q], d, &g[q]), pol);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const uint32_t ge = (e[q] >> FP_SHIFT) & 0x7Fu;
+                const bool need = (e[q] & KNOT_FLAG) && g[q] == ge;
+                x[q] = need ? tab_ld<SM>(X + (e[q] & FP_T_MASK), pol) : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int32_t t = (int32_t)(e[q] & FP_T_MASK);
+                const uint32_t ge = (e[q] >> FP_SHIFT) & 0x7Fu;
+                bool lt = true;  // no knot in the cell: z < X_t (Eq. indexdef)
+                if (e[q] & KNOT_FLAG) lt = g[q] != ge ? g[q] < ge : lt_exact<T>(z[q], x[q]);
+                r[q] = t - (int32_t)lt;
+                if (a.checked && is_nan<T>(z[q])) r[q] = -1;
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) e[q] = tab_ld<SM>(K + cell_rt<T>(z[q], d), pol);
 #pragma unroll
@@ -194,7 +222,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
     }
 }
 
-template <typename T, int VPT, bool INTERP, bool VEC, bool DIRECT_ONLY, bool SM>
+template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool SM>
 __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
                                               long long zs, long long ze, uint64_t pol)
 {
@@ -212,14 +240,14 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     for (long long q = zs + threadIdx.x; q < va; q += blockDim.x) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1, DIRECT_ONLY, SM>(a, d, K, X, &z, &r, pol);
+        answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
     for (long long q = vb + threadIdx.x; q < ze; q += blockDim.x) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1, DIRECT_ONLY, SM>(a, d, K, X, &z, &r, pol);
+        answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
@@ -239,7 +267,7 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
             }
             const T *zs4 = reinterpret_cast<const T *>(zv);
             int32_t r[NQ];
-            answer_block<T, NQ, DIRECT_ONLY, SM>(a, d, K, X, zs4, r, pol);
+            answer_block<T, NQ, KIND, SM>(a, d, K, X, zs4, r, pol);
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = base + (long long)v * blockDim.x;
@@ -259,9 +287,8 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     }
 }
 
-// DIRECT_ONLY: every array of the handle is in direct mode (the learned and
-// bisection paths are compiled out, which keeps the register count low).
-template <typename T, int VPT, bool INTERP, bool VEC, bool DIRECT_ONLY>
+// KIND: BatchKind (KIND_DIRECT*: every array of the handle is in direct mode).
+template <typename T, int VPT, bool INTERP, bool VEC, int KIND>
 __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -314,8 +341,8 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
             K = reinterpret_cast<const uint32_t *>(a.blob + d.img);
             X = reinterpret_cast<const T *>(a.blob + d.xg);
         }
-        if (use_smem) process_chunk<T, VPT, INTERP, VEC, DIRECT_ONLY, true>(a, d, K, X, zs, ze, pol);
-        else process_chunk<T, VPT, INTERP, VEC, DIRECT_ONLY, false>(a, d, K, X, zs, ze, pol);
+        if (use_smem) process_chunk<T, VPT, INTERP, VEC, KIND, true>(a, d, K, X, zs, ze, pol);
+        else process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, K, X, zs, ze, pol);
         __syncthreads();
     }
 }
@@ -401,11 +428,11 @@ __global__ void k_seg_hr_grow(const T *Xcat, const long long *x_off, int n_array
 }
 
 // Copy every array's knots into its place in the blob; cells F_i of the
-// knots of direct arrays into F (packed like Xcat).
+// knots of direct arrays into F and their fingerprints into G (packed like Xcat).
 template <typename T>
 __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *__restrict__ x_off,
                                   const Segment *__restrict__ segs, int n_segs, const ArrDesc *__restrict__ desc,
-                                  unsigned char *blob, uint32_t *__restrict__ F)
+                                  unsigned char *blob, uint32_t *__restrict__ F, uint8_t *__restrict__ G)
 {
     using A = Arith<T>;
     for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
@@ -427,16 +454,20 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
                 T v;
                 if (d.form == F_FMA) v = A::fma(H, x, -W);
                 else v = A::mul(H, A::sub(x, X0));
-                F[i] = A::trunc_u32(v);
+                uint32_t g;
+                F[i] = cell_fp_bits(v, &g);
+                G[i] = (uint8_t)(g & 0x7Fu);
             }
         }
     }
 }
 
-// Flagged K of every direct array (as k_fill_K); warps walk 32-knot chunks of
-// all direct arrays, chunk -> array through the chunk offsets kc_off.
-__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
-                             const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
-                             unsigned char *blob);
+// Flagged K of every direct array (as k_fill_K), with the knot's fingerprint
+// from G in bits 24..30 of flagged entries when the array's descriptor asks
+// for it; warps walk 32-knot chunks of all direct arrays, chunk -> array
+// through the chunk offsets kc_off.
+__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
+                             const long long *__restrict__ x_off, const long long *__restrict__ kc_off, int n_arrays,
+                             const ArrDesc *__restrict__ desc, unsigned char *blob);
 
 }  // namespace ds

@@ -168,3 +168,38 @@ def test_workload3_full_size_autotuned(ds):
     assert bool((gi + 1 < xo[arr_all + 1]).all())
     assert bool((Xd[gi] <= Zd).all()) and bool((Zd < Xd[gi + 1]).all())
     b.free()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("fma", [False, True])
+def test_fingerprints_across_cell_ranges(ds, dtype, fma):
+    # arrays whose largest cell R spans every exponent range of f(z): fractional
+    # bits below 2^17 cells, fewer of them up to 2^24, none above (float32)
+    g = np.random.default_rng(21)
+    arrays = []
+    for cells_per_knot, n in ((3, 100), (40, 2000), (200, 3000), (2000, 4000), (20000, 2000), (2e5, 1000)):
+        X0 = 0.0 if len(arrays) % 2 == 0 else g.uniform(-1e3, 1e3)
+        gaps = g.uniform(0.5, 1.5, n - 1)
+        gaps[g.integers(0, n - 1)] = 1.0 / cells_per_knot  # one narrow gap sets H
+        arrays.append(W.knots_from_gaps(X0, gaps, dtype))
+    x_off = W.csr([a.size for a in arrays])
+    Xcat = np.concatenate(arrays)
+    Zs = []
+    for a in arrays:
+        inf = dtype(np.inf)
+        Zs.append(np.concatenate([W.adversarial_queries(a), W.midpoints(a), W.uniform_queries(g, a[0], a[-1], 20000, dtype),
+                                  np.array([a[-1], -inf, inf, np.nextafter(a[0], -inf), a[-1] * 2 + 1], dtype=dtype)]))
+    z_off = W.csr([z.size for z in Zs])
+    Zcat = np.concatenate(Zs)
+    ref = oracle.upper_bound_batch(Xcat, x_off, Zcat, z_off)
+    flags = ds.DS_FMA if fma else 0
+    Rs = []
+    for extra in (0, ds.DS_NO_FINGERPRINT):
+        b = ds.ds_batch_build(_cuda(Xcat), _cuda(x_off), flags | extra)
+        Rs = [ds.ds_batch_array(b, a)["R"] for a in range(len(arrays))]
+        for smem in (0, 96 * 1024):
+            ds.ds_batch_set_tune(b, 256, 4, smem)
+            got = ds.ds_batch_search(b, _cuda(Zcat), _cuda(z_off)).cpu().numpy()
+            assert np.array_equal(got, ref), (extra, smem, int(np.count_nonzero(got != ref)))
+        b.free()
+    assert max(Rs) > (1 << 24) and min(Rs) < (1 << 10)
