@@ -240,3 +240,22 @@ def test_search_in_cuda_graph(ds):
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), oracle.upper_bound(X, Z))
     idx.free()
+
+
+@pytest.mark.parametrize("flags", [8, 9], ids=["l2", "l2_fma"])
+def test_packed_float64_tables_across_cell_ranges(ds, flags):
+    # the packed L2 table on arrays whose cells span small to very large f
+    # values (R up to ~1.5e9), X_0 zero and not
+    g = np.random.default_rng(33)
+    fl = flags
+    for k, (cells_per_knot, n) in enumerate(((3, 100), (40, 2000), (700, 3000), (2e4, 3000), (1e6, 1500))):
+        X0 = 0.0 if k % 2 == 0 else g.uniform(-1e3, 1e3)
+        gaps = g.uniform(0.5, 1.5, n - 1)
+        gaps[g.integers(0, n - 1)] = 1.0 / cells_per_knot
+        X = W.knots_from_gaps(X0, gaps, np.float64)
+        Z = _queries(X, g, 20000)
+        idx = ds.ds_build(_cuda(X), fl)
+        got = ds.ds_search(idx, _cuda(Z)).cpu().numpy()
+        ref = oracle.upper_bound(X, Z)
+        assert np.array_equal(got, ref), (k, int(np.count_nonzero(got != ref)))
+        idx.free()
