@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = ("direct_f64", "direct_f64_sorted", "direct_f32", "batched_f32", "learned_f64", "learned_interp_f32",
-             "gapq_f64")
+             "gapq_f64", "paper_tables")
 
 
 def parse():
@@ -190,6 +190,8 @@ def reference_sample(args, n=1 << 20):
         w = W.workload2(m=n, sort=args.workload.endswith("sorted"))
     elif args.workload in ("learned_f64", "gapq_f64"):
         w = W.workload4(m=n)
+    elif args.workload == "paper_tables":
+        w = W.paper_layout(PAPER_SIZES[-1], n, np.float64)
     elif args.workload == "direct_f32":
         w = W.workload1()
     else:
@@ -230,6 +232,10 @@ def workload_config(args):
         "gapq_f64": {"workload": "Gap-q direct search f64 on the learned-index data: 2^24+1 knots, gaps "
                                  "U[1e-3,1e-2] or (1%) U[1e3,1e4], 2^27 uniform queries; smallest q whose table "
                                  "fits 4 GiB", "knots": (1 << 24) + 1, "queries": 1 << 27, "budget_bytes": 1 << 32},
+        "paper_tables": {"workload": "direct search vs the logarithmic searches of Section 3 on the paper's layout "
+                                     "(gaps U[1,5], queries at interval midpoints), N+1 = 15 .. 1048575, f32 and f64, "
+                                     "2^26 queries per launch; the timed step is Direct f64 at 1048575 knots",
+                         "queries": 1 << 26},
         "learned_interp_f32": {"workload": "batched learned lookup + linear interpolation f32: 256 arrays of "
                                            "2^10..2^22 knots, mixed gap laws, 2^28 queries", "arrays": 256,
                                "queries": 1 << 28},
@@ -366,6 +372,71 @@ def setup_gapq(args, ds, W, torch, dev, rank):
             res["q%d" % q] = job.m / time_calls(torch, stream, lambda: ds.ds_search(j, Zd, out), 5)
             res["q%d_table_bytes" % q] = j.info()["table_bytes"]
             j.free()
+        return res
+    job.extras = extras
+    return job
+
+
+PAPER_SIZES = (15, 255, 4095, 65535, 1048575)
+
+
+def setup_paper_tables(args, ds, W, torch, dev, rank):
+    """The paper's throughput tables (size of X against method) on this GPU:
+    direct search in its variants and the logarithmic searches, same queries."""
+    job = Job()
+    m = args.queries or (1 << 26)
+    last = {}
+
+    def layout(n, dtype):
+        w = W.paper_layout(n, m, dtype, seed=rank_seed(W, 0, rank))
+        return torch.from_numpy(w["X"]).to(dev), torch.from_numpy(w["Z"]).to(dev)
+
+    X, Z = layout(PAPER_SIZES[-1], np.float64)
+    out = torch.empty(m, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx = ds.ds_build(X)
+    torch.cuda.synchronize()
+    job.build_ms = (time.perf_counter() - t0) * 1e3
+    info = idx.info()
+    job.m = m
+    job.bytes_per_lookup, job.dtype_name = 8 + 4, "f64"
+    job.table = {"H": info["H"], "R": info["R"], "table_bytes": info["table_bytes"]}
+    job.kernel_key = "search_f64_paper_layout"
+    job.search = lambda: ds.ds_search(idx, Z, out)
+    job.out = out
+    job.keep = (idx, X, Z)
+    Zp = Z.cpu().pin_memory()
+    Ip = torch.empty(m, dtype=torch.int32).pin_memory()
+
+    def e2e():
+        ds.ds_search_host(idx, Zp, Ip)
+        return Zp.numel() * 8, Ip.numel() * 4
+    job.e2e = e2e
+    job.e2e_out = Ip
+
+    def extras(stream):
+        direct = {"direct": 0, "direct_fma": ds.DS_FMA, "direct_cache": ds.DS_CACHE_LAYOUT, "direct_gap2": ds.DS_GAP2}
+        res = {}
+        for dtype in (np.float32, np.float64):
+            tab = {}
+            for n in PAPER_SIZES:
+                Xn, Zn = layout(n, dtype)
+                o = torch.empty(m, dtype=torch.int32, device=dev)
+                row = {}
+                for name, fl in direct.items():
+                    h = ds.ds_build(Xn, fl)
+                    row[name] = m / time_calls(torch, stream, lambda: ds.ds_search(h, Zn, o), 5) / 1e9
+                    h.free()
+                for meth, name in enumerate(ds.DS_LS_NAMES):
+                    h = ds.ds_lsearch_build(Xn, meth)
+                    row[name] = m / time_calls(torch, stream, lambda: ds.ds_lsearch_search(h, Zn, o), 5) / 1e9
+                    h.free()
+                row["direct_over_classic"] = row["direct"] / row["classic"]
+                row["direct_over_best_log"] = row["direct"] / max(row[k] for k in ds.DS_LS_NAMES)
+                tab[str(n)] = row
+                del Xn, Zn, o
+            res["G_lookups_per_s_" + ("f32" if dtype == np.float32 else "f64")] = tab
         return res
     job.extras = extras
     return job
@@ -537,6 +608,8 @@ def main():
         job = setup_learned(args, ds, W, torch, dev, rank)
     elif args.workload == "gapq_f64":
         job = setup_gapq(args, ds, W, torch, dev, rank)
+    elif args.workload == "paper_tables":
+        job = setup_paper_tables(args, ds, W, torch, dev, rank)
     else:
         raise SystemExit("workload %s: not timed by this bench" % args.workload)
     m = job.m
@@ -601,9 +674,11 @@ def main():
         line["variants_lookups_per_s"] = job.extras(stream)
     if rank == 0:
         cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
-        if args.workload.startswith("direct") or args.workload in ("learned_f64", "gapq_f64"):
+        if args.workload.startswith("direct") or args.workload in ("learned_f64", "gapq_f64", "paper_tables"):
             if args.workload in ("learned_f64", "gapq_f64"):
                 cw = W.workload4(m=1 << 22)
+            if args.workload == "paper_tables":
+                cw = W.paper_layout(PAPER_SIZES[-1], 1 << 24, np.float64)
             line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds)
         else:
             line["cpu_baseline"] = cpu_baseline_batched(W, args.cpu_seconds)

@@ -85,10 +85,11 @@ enum {
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
 typedef struct ds_batch ds_batch;     /* many independent knot arrays (CSR) */
 typedef struct ds_learned ds_learned; /* learned-index form (one or many arrays) */
+typedef struct ds_lsearch ds_lsearch; /* one knot array laid out for a logarithmic search (Section 3) */
 
 /* Summary of a handle.  Fields that do not apply are 0. */
 typedef struct ds_info_t {
-    int32_t kind;           /* 1 = ds_index, 2 = ds_batch, 3 = ds_learned */
+    int32_t kind;           /* 1 = ds_index, 2 = ds_batch, 3 = ds_learned, 4 = ds_lsearch */
     int32_t dtype;          /* ds_dtype */
     uint32_t flags;
     int32_t n_arrays;
@@ -192,6 +193,44 @@ DS_API ds_status ds_index_tables(const ds_index *idx, const int32_t **K_dev, con
  * DS_CACHE_LAYOUT).  Asynchronous on `stream`. */
 DS_API ds_status ds_index_export(const ds_index *idx, int32_t *K_out_dev, void *X_out_dev, void *pairs_out_dev,
                                  void *stream);
+
+/* ------------------------------------------------------------------------
+ * Logarithmic searches (Section 3): the comparators of direct search.
+ * ------------------------------------------------------------------------ */
+
+typedef enum ds_lsearch_method {
+    DS_LS_CLASSIC = 0,        /* Algorithm naivealg: low/high bisection, data-dependent trip count */
+    DS_LS_CLASSICMOD = 1,     /* the same with conditional assignments, ceil(log2 N) iterations */
+    DS_LS_LEADBIT = 2,        /* Algorithm binaryopt: leading-bit search, X padded with X_N to size Q */
+    DS_LS_LEADBIT_NOPAD = 3,  /* Algorithm binaryoptnopad: min(r, N) after the first U iterations */
+    DS_LS_OFFSET = 4,         /* Algorithm naiveoffset: start index and size (Knuth's Algorithm U) */
+    DS_LS_EYTZINGER = 5       /* Algorithm eytzinger: breadth-first layout padded to 2^L - 1 */
+} ds_lsearch_method;
+
+/* Constants of a method for N+1 = n_knots knots, as the paper defines them
+ * (host only, no device call):
+ *   CLASSICMOD  consts[0] = ceil(log2 N) iterations
+ *   LEADBIT     consts[0] = P = 2^floor(log2 N), consts[1] = Q = 1 + s_ubar,
+ *               s_u = sum_{k=1..u} P / 2^(k-1), ubar = inf{u : s_u >= N}
+ *   LEADBIT_NOPAD consts[0] = P, consts[1] = U = sup{u : s_u <= N}
+ *   OFFSET      consts[0..2] = F = floor((N+1)/2), S = N+1-F, J = floor(log2(N+1))
+ *   EYTZINGER   consts[0] = L = 1 + floor(log2(N+2))
+ * *layout_len = elements of the method's layout (N+1, Q, or 2^L - 1). */
+DS_API ds_status ds_lsearch_constants(int32_t method, int64_t n_knots, int64_t consts[4], int64_t *layout_len);
+
+/* Lay out one knot array for `method` (a copy of X, right-padded with X_N for
+ * LEADBIT, breadth-first for EYTZINGER; float64 knots are stored as
+ * order-preserving integer keys).  X_dev: n_knots (2..2^30) strictly
+ * increasing values (not validated: the methods are exact only on sorted X);
+ * the layout may hold at most 2^30 elements (DS_E_ARG otherwise).
+ * flags: DS_CHECKED | DS_NO_SMEM.  Synchronous. */
+DS_API ds_status ds_lsearch_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, int32_t method,
+                                  uint32_t flags, void *stream, ds_lsearch **out);
+
+/* The same answers as ds_search (the largest i with X_i <= z; -1 below X_0
+ * and for NaN, N at or above X_N) by the handle's logarithmic method.
+ * Asynchronous; allocates nothing. */
+DS_API ds_status ds_lsearch_search(const ds_lsearch *h, const void *Z_dev, int64_t m, int32_t *I_dev, void *stream);
 
 /* ------------------------------------------------------------------------
  * Many independent arrays ("vectorial problem" of Section 2, batched).

@@ -12,8 +12,9 @@ import torch
 
 from . import _abi
 from ._abi import (DS_CACHE_LAYOUT, DS_CHECKED, DS_F32, DS_F64, DS_FMA, DS_LEARNED_FORCE,  # noqa: F401
-                   DS_GAP2, DS_LEARNED_LINEAR, DS_LEARNED_ZERO_BOUND, DS_NO_FINGERPRINT, DS_NO_SMEM, DS_OK, DS_STRICT,
-                   DsError, check, lib)
+                   DS_GAP2, DS_LEARNED_LINEAR, DS_LEARNED_ZERO_BOUND, DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_EYTZINGER,
+                   DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_NAMES, DS_LS_OFFSET, DS_NO_FINGERPRINT, DS_NO_SMEM, DS_OK,
+                   DS_STRICT, DsError, check, lib)
 
 __all__ = [
     "ds_build", "ds_search", "ds_search_host", "ds_index_export", "ds_batch_build", "ds_batch_search",
@@ -101,6 +102,14 @@ class Batch(_Handle):
         return ds_batch_search(self, Zcat, z_off, out, stream)
 
 
+class LSearch(_Handle):
+    """One array laid out for a logarithmic search (``ds_lsearch``)."""
+    kind = "ds_lsearch"
+
+    def search(self, Z, out=None, stream=None):
+        return ds_lsearch_search(self, Z, out, stream)
+
+
 class Learned(_Handle):
     """Learned-index form (``ds_learned``)."""
     kind = "ds_learned"
@@ -159,6 +168,31 @@ def ds_index_export(idx, stream=None):
         pp = _dev(pairs, "pairs")
     check(lib().ds_index_export(idx.ptr, _dev(K, "K"), _dev(X, "X"), pp, _stream(stream)), "ds_index_export")
     return K, X, pairs
+
+
+# ---------------------------------------------------------------- logarithmic searches
+def ds_lsearch_constants(method, n_knots):
+    """(consts[4], layout_len) of a logarithmic method (host only)."""
+    c = (_abi.I64 * 4)()
+    n = _abi.I64()
+    check(lib().ds_lsearch_constants(int(method), int(n_knots), c, ctypes.byref(n)), "ds_lsearch_constants")
+    return list(c), n.value
+
+
+def ds_lsearch_build(X, method, flags=0, stream=None):
+    """Lay out knot array X (CUDA tensor) for a logarithmic method (DS_LS_*)."""
+    out = ctypes.c_void_p()
+    check(lib().ds_lsearch_build(_dev(X, "X"), X.numel(), _dtype(X), int(method), int(flags), _stream(stream),
+                                 ctypes.byref(out)), "ds_lsearch_build")
+    return LSearch(out.value, X.dtype)
+
+
+def ds_lsearch_search(h, Z, out=None, stream=None):
+    if out is None:
+        out = torch.empty(Z.numel(), dtype=torch.int32, device=Z.device)
+    check(lib().ds_lsearch_search(h.ptr, _dev(Z, "Z", h.dtype), Z.numel(), _dev(out, "out", torch.int32),
+                                  _stream(stream)), "ds_lsearch_search")
+    return out
 
 
 # ---------------------------------------------------------------- batched

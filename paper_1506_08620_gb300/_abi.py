@@ -32,6 +32,8 @@ DS_NO_SMEM = 8
 DS_STRICT = 16
 DS_GAP2 = 32
 DS_NO_FINGERPRINT = 64
+DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_OFFSET, DS_LS_EYTZINGER = range(6)
+DS_LS_NAMES = ("classic", "classicmod", "leadbit", "leadbit_nopad", "offset", "eytzinger")
 
 DS_LEARNED_FORCE = 1
 DS_LEARNED_LINEAR = 2
@@ -78,6 +80,9 @@ class ds_learned_cfg(ctypes.Structure):
 _SIGS = {
     "ds_build": (ST, [P, I64, ST, U32, P, ctypes.POINTER(P)]),
     "ds_build_q": (ST, [P, I64, ST, U32, ctypes.c_int32, ctypes.c_int32, I64, P, ctypes.POINTER(P)]),
+    "ds_lsearch_constants": (ST, [ctypes.c_int32, I64, P, ctypes.POINTER(I64)]),
+    "ds_lsearch_build": (ST, [P, I64, ST, ctypes.c_int32, U32, P, ctypes.POINTER(P)]),
+    "ds_lsearch_search": (ST, [P, P, I64, P, P]),
     "ds_search": (ST, [P, P, I64, P, P]),
     "ds_search_host": (ST, [P, P, I64, P, P]),
     "ds_index_tables": (ST, [P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P)]),

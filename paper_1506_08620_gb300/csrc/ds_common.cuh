@@ -37,7 +37,7 @@ void clear_error();
     } while (0)
 
 // ------------------------------------------------------------------ handles
-enum Kind : int32_t { KIND_INDEX = 1, KIND_BATCH = 2, KIND_LEARNED = 3 };
+enum Kind : int32_t { KIND_INDEX = 1, KIND_BATCH = 2, KIND_LEARNED = 3, KIND_LSEARCH = 4 };
 constexpr int32_t HANDLE_MAGIC = 0x0D5E5C;
 
 struct HandleHeader {

@@ -146,6 +146,8 @@ void free_batch(ds_batch *b);
 ds_status info_batch(const ds_batch *b, ds_info_t *out);
 void free_learned(ds_learned *L);
 ds_status info_learned(const ds_learned *L, ds_info_t *out);
+void free_lsearch(ds_lsearch *h);
+ds_status info_lsearch(const ds_lsearch *h, ds_info_t *out);
 
 }  // namespace ds
 
@@ -295,6 +297,7 @@ ds_status ds_info(const void *handle, ds_info_t *out)
     case KIND_INDEX: return info_index(reinterpret_cast<const ds_index *>(handle), out);
     case KIND_BATCH: return info_batch(reinterpret_cast<const ds_batch *>(handle), out);
     case KIND_LEARNED: return info_learned(reinterpret_cast<const ds_learned *>(handle), out);
+    case KIND_LSEARCH: return info_lsearch(reinterpret_cast<const ds_lsearch *>(handle), out);
     }
     return DS_E_ARG;
 }
@@ -306,6 +309,7 @@ void ds_free(void *handle)
     case KIND_INDEX: free_index(reinterpret_cast<ds_index *>(handle)); break;
     case KIND_BATCH: free_batch(reinterpret_cast<ds_batch *>(handle)); break;
     case KIND_LEARNED: free_learned(reinterpret_cast<ds_learned *>(handle)); break;
+    case KIND_LSEARCH: free_lsearch(reinterpret_cast<ds_lsearch *>(handle)); break;
     }
 }
 
