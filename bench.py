@@ -324,7 +324,14 @@ def setup_direct(args, ds, W, torch, dev, rank):
             Zs = torch.sort(Zd).values
             res["sorted_queries_" + args.variant] = job.m / time_calls(torch, stream,
                                                                        lambda: ds.ds_search(idx, Zs, out), 5)
+            # the O(M + N) merge of sorted queries into X (no table)
+            res["sorted_queries_merge"] = job.m / time_calls(torch, stream,
+                                                             lambda: ds.ds_search_sorted(Xd, Zs, out), 5)
             del Zs
+            # counts per interval, fused with the search (N+2 uint64 counters)
+            counts = torch.zeros(Xd.numel() + 1, dtype=torch.int64, device=dev)
+            res["histogram"] = job.m / time_calls(torch, stream, lambda: ds.ds_histogram(idx, Zd, counts), 5)
+            del counts
         return res
     job.extras = extras
     return job

@@ -177,6 +177,25 @@ DS_API ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, in
  * call and keeps them in the handle. */
 DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *I_host, void *stream);
 
+/* Sorted queries (the O(M + N) case of Section 1.2): merge Z into X instead
+ * of searching each query.  The merged order places X_i before z when
+ * X_i <= z; a query merged after a knots gets I = a - 1, the same answer as
+ * ds_search (the largest i with X_i <= z; -1 below X_0, N at or above X_N).
+ *   X_dev  n_knots (1 .. 2^31-1) strictly increasing values of `dtype`.
+ *   Z_dev  m queries in non-decreasing order, no NaN; for other inputs the
+ *          results are unspecified but every access stays in bounds.
+ * Needs no index handle and no table; allocates nothing; asynchronous. */
+DS_API ds_status ds_search_sorted(const void *X_dev, int64_t n_knots, ds_dtype dtype, const void *Z_dev, int64_t m,
+                                  int32_t *I_dev, void *stream);
+
+/* Counts of the samples in each interval (the distribution use case of
+ * Section 1.2), by the index's direct search fused with counting:
+ * counts_dev[i + 1] += #{z : answer(z) = i} for i = -1 .. N, so bin 0 counts
+ * z < X_0 (and NaN), bin N+1 counts z >= X_N.  counts_dev: N+2 uint64, added
+ * to (not cleared).  Shared-memory counters when N+2 of them fit in 96 KB,
+ * otherwise global atomics.  Asynchronous; allocates nothing. */
+DS_API ds_status ds_histogram(const ds_index *idx, const void *Z_dev, int64_t m, uint64_t *counts_dev, void *stream);
+
 /* Read-only device views of the index's tables (for inspection and tests):
  * K (R+1 int32, Eq. indexdef or Eq. kgeneral, with the search's flags: bit 31
  * set when knot K_j lies in cell j, or for Eq. kgeneral when j < f(X_0); for

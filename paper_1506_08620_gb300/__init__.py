@@ -144,6 +144,24 @@ def ds_search(idx, Z, out=None, stream=None):
     return out
 
 
+def ds_search_sorted(X, Z, out=None, stream=None):
+    """Answers for non-decreasing queries Z by merging them into X (CUDA tensors, same dtype)."""
+    if out is None:
+        out = torch.empty(Z.numel(), dtype=torch.int32, device=Z.device)
+    check(lib().ds_search_sorted(_dev(X, "X"), X.numel(), _dtype(X), _dev(Z, "Z", X.dtype), Z.numel(),
+                                 _dev(out, "out", torch.int32), _stream(stream)), "ds_search_sorted")
+    return out
+
+
+def ds_histogram(idx, Z, counts=None, stream=None):
+    """Counts (int64, N+2 bins: below X_0, each interval, at or above X_N) of the queries Z."""
+    if counts is None:
+        counts = torch.zeros(int(ds_info(idx)["n_knots"]) + 1, dtype=torch.int64, device=Z.device)
+    check(lib().ds_histogram(idx.ptr, _dev(Z, "Z", idx.dtype), Z.numel(), _dev(counts, "counts", torch.int64),
+                             _stream(stream)), "ds_histogram")
+    return counts
+
+
 def ds_search_host(idx, Z, out=None, stream=None):
     """Search with host buffers (pinned CPU tensors); copies run inside the call."""
     if out is None:
