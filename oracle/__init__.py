@@ -57,6 +57,9 @@ def lib():
         for nm in ("or_compute_hr_gapq_f64", "or_compute_hr_gapq_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _I32, _INT, _P, _P, _P, _P, _P, _P]
             getattr(L, nm).restype = _INT
+        for nm in ("or_compute_hr_refined_f64", "or_compute_hr_refined_f32"):
+            getattr(L, nm).argtypes = [_P, _I64, _I32, _INT, _P, _P, _P, _P, _P, _P, _P]
+            getattr(L, nm).restype = _INT
         for nm in ("or_fill_k_gap2_f64", "or_fill_k_gap2_f32"):
             getattr(L, nm).argtypes = [_P, _I64, _D, _D, _U32, _INT, _P, _P]
             getattr(L, nm).restype = _INT
@@ -151,6 +154,19 @@ def compute_hr(X, fma=False, gap2=False, q=None, general=False):
         st = getattr(lib(), "or_compute_hr_gapq_" + _suffix(X))(_ptr(X), X.shape[0], q, int(bool(fma)), *outs)
     return dict(status=st, H=H.value, W=W.value, R=R.value, updates=upd.value,
                 passes=passes.value, bad=bad.value)
+
+
+def compute_hr_refined(X, fma=False, q=1):
+    """ComputeHR over the pairs (i, i+q), then, if H had to grow, the bisection
+    of [last infeasible H, final H] proposed at the end of Section 4.4.
+    Returns the dict of compute_hr plus `probes` (feasibility checks made)."""
+    X = np.ascontiguousarray(X)
+    H = _D(); W = _D(); R = _U32(); upd = _I64(); passes = _I64(); bad = _I64(); probes = _I64()
+    st = getattr(lib(), "or_compute_hr_refined_" + _suffix(X))(
+        _ptr(X), X.shape[0], int(q), int(bool(fma)), ctypes.byref(H), ctypes.byref(W), ctypes.byref(R),
+        ctypes.byref(upd), ctypes.byref(passes), ctypes.byref(bad), ctypes.byref(probes))
+    return dict(status=st, H=H.value, W=W.value, R=R.value, updates=upd.value, passes=passes.value, bad=bad.value,
+                probes=probes.value)
 
 
 def fill_k(X, H, W, R, fma=False, gap2=False, q=None, general=False):

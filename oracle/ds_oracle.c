@@ -23,6 +23,8 @@
  *                      (Eq. fma) forms.
  *   or_fill_k_*        Eq. indexdef: K_0 = 0, K_j = i for f(X_{i-1}) < j <= f(X_i).
  *   or_direct_*        Algorithm "direct": j = f(z), t = K_j, i = t - [z < X_t].
+ *   or_compute_hr_refined_*  ComputeHR followed by the bisection of H that the end
+ *                      of Section 4.4 proposes (not implemented in the paper).
  *   or_*_gapq_*        DirectGap2 and its q-knot generalisation (Section 4.7):
  *                      ComputeHR over pairs (i, i+q), K of Eq. kgeneral,
  *                      Algorithm direct-2 with q comparisons; or_*_gap2_* are
@@ -374,8 +376,9 @@ void or_interp_f32(const float *X, const float *Y, int64_t n_knots, const float 
 /* share a cell.  With fewer than q+1 knots the pair distance is N.  q = 1   */
 /* is ComputeHR itself.                                                      */
 /* ------------------------------------------------------------------------ */
-int or_compute_hr_gapq_f64(const double *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
-                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+static int compute_hr_gapq_track_f64(const double *X, int64_t n_knots, int32_t q, int fma_form, double *H_out,
+                                       double *W_out, uint32_t *R_out, int64_t *updates_out, int64_t *passes_out,
+                                       int64_t *bad_out, double *H_inf_out)
 {
     *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
     if (n_knots < 2 || q < 1) return OR_E_ARG;
@@ -408,6 +411,7 @@ int or_compute_hr_gapq_f64(const double *X, int64_t n_knots, int32_t q, int fma_
         ++passes;
         for (int64_t i = gap; i <= N; ++i) {
             while (trunc_u32(OR_G64(X[i - gap])) == trunc_u32(OR_G64(X[i]))) {
+                if (H_inf_out) *H_inf_out = H; /* the last H found infeasible */
                 H = H + P;
                 W = H * X0;
                 if (!(OR_G64(X[N]) < 4294967296.0)) { *bad_out = i; *H_out = H; return OR_E_OVERFLOW; }
@@ -424,8 +428,9 @@ int or_compute_hr_gapq_f64(const double *X, int64_t n_knots, int32_t q, int fma_
     return OR_OK;
 }
 
-int or_compute_hr_gapq_f32(const float *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
-                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+static int compute_hr_gapq_track_f32(const float *X, int64_t n_knots, int32_t q, int fma_form, double *H_out,
+                                       double *W_out, uint32_t *R_out, int64_t *updates_out, int64_t *passes_out,
+                                       int64_t *bad_out, double *H_inf_out)
 {
     *H_out = 0; *W_out = 0; *R_out = 0; *updates_out = 0; *passes_out = 0; *bad_out = -1;
     if (n_knots < 2 || q < 1) return OR_E_ARG;
@@ -458,6 +463,7 @@ int or_compute_hr_gapq_f32(const float *X, int64_t n_knots, int32_t q, int fma_f
         ++passes;
         for (int64_t i = gap; i <= N; ++i) {
             while (trunc_u32(OR_G32(X[i - gap])) == trunc_u32(OR_G32(X[i]))) {
+                if (H_inf_out) *H_inf_out = H; /* the last H found infeasible */
                 H = H + P;
                 W = H * X0;
                 if (!((double)OR_G32(X[N]) < 4294967296.0)) { *bad_out = i; *H_out = H; return OR_E_OVERFLOW; }
@@ -471,6 +477,113 @@ int or_compute_hr_gapq_f32(const float *X, int64_t n_knots, int32_t q, int fma_f
     if (changed) return OR_E_NO_CONVERGENCE;
     *R_out = trunc_u32(OR_G32(X[N]));
 #undef OR_G32
+    return OR_OK;
+}
+
+int or_compute_hr_gapq_f64(const double *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    return compute_hr_gapq_track_f64(X, n_knots, q, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out,
+                                     0);
+}
+
+int or_compute_hr_gapq_f32(const float *X, int64_t n_knots, int32_t q, int fma_form, double *H_out, double *W_out,
+                           uint32_t *R_out, int64_t *updates_out, int64_t *passes_out, int64_t *bad_out)
+{
+    return compute_hr_gapq_track_f32(X, n_knots, q, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out,
+                                     0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Refinement of H by bisection (end of Section 4.4): when ComputeHR had to  */
+/* grow H, the last value found infeasible and the final, feasible one bound */
+/* an interval; bisect it for the smallest feasible H it can reach.  Each    */
+/* probe checks the whole array (every pair (i, i+q) and the overflow test). */
+/* The midpoint is taken on the bit patterns (positive floats order like     */
+/* their patterns), so the steps are exact integer arithmetic.               */
+/* ------------------------------------------------------------------------ */
+static int feasible_f64(const double *X, int64_t n_knots, int64_t gap, int fma_form, double H)
+{
+    const int64_t N = n_knots - 1;
+    const double X0 = X[0], W = H * X0;
+#define OR_P64(x) (fma_form ? fval_fma_f64(H, W, (x)) : fval_plain_f64(H, X0, (x)))
+    if (!(OR_P64(X[N]) < 4294967296.0)) return 0;
+    for (int64_t i = gap; i <= N; ++i)
+        if (trunc_u32(OR_P64(X[i - gap])) == trunc_u32(OR_P64(X[i]))) return 0;
+#undef OR_P64
+    return 1;
+}
+
+static int feasible_f32(const float *X, int64_t n_knots, int64_t gap, int fma_form, float H)
+{
+    const int64_t N = n_knots - 1;
+    const float X0 = X[0], W = H * X0;
+#define OR_P32(x) (fma_form ? fval_fma_f32(H, W, (x)) : fval_plain_f32(H, X0, (x)))
+    if (!((double)OR_P32(X[N]) < 4294967296.0)) return 0;
+    for (int64_t i = gap; i <= N; ++i)
+        if (trunc_u32(OR_P32(X[i - gap])) == trunc_u32(OR_P32(X[i]))) return 0;
+#undef OR_P32
+    return 1;
+}
+
+int or_compute_hr_refined_f64(const double *X, int64_t n_knots, int32_t q, int fma_form, double *H_out,
+                              double *W_out, uint32_t *R_out, int64_t *updates_out, int64_t *passes_out,
+                              int64_t *bad_out, int64_t *probes_out)
+{
+    double H_inf = 0;
+    *probes_out = 0;
+    int st = compute_hr_gapq_track_f64(X, n_knots, q, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out,
+                                       &H_inf);
+    if (st != OR_OK || *updates_out == 0) return st;
+    const int64_t N = n_knots - 1, gap = N >= q ? q : N;
+    uint64_t lo, hi;
+    double Hf = *H_out;
+    memcpy(&lo, &H_inf, 8);
+    memcpy(&hi, &Hf, 8);
+    while (hi - lo > 1) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        double Hm;
+        memcpy(&Hm, &mid, 8);
+        ++*probes_out;
+        if (feasible_f64(X, n_knots, gap, fma_form, Hm)) hi = mid;
+        else lo = mid;
+    }
+    memcpy(&Hf, &hi, 8);
+    const double X0 = X[0], W = Hf * X0;
+    *H_out = Hf;
+    *W_out = W;
+    *R_out = trunc_u32(fma_form ? fval_fma_f64(Hf, W, X[N]) : fval_plain_f64(Hf, X0, X[N]));
+    return OR_OK;
+}
+
+int or_compute_hr_refined_f32(const float *X, int64_t n_knots, int32_t q, int fma_form, double *H_out,
+                              double *W_out, uint32_t *R_out, int64_t *updates_out, int64_t *passes_out,
+                              int64_t *bad_out, int64_t *probes_out)
+{
+    double H_inf = 0;
+    *probes_out = 0;
+    int st = compute_hr_gapq_track_f32(X, n_knots, q, fma_form, H_out, W_out, R_out, updates_out, passes_out, bad_out,
+                                       &H_inf);
+    if (st != OR_OK || *updates_out == 0) return st;
+    const int64_t N = n_knots - 1, gap = N >= q ? q : N;
+    const float Hi = (float)H_inf, Hfe = (float)*H_out;
+    uint32_t lo, hi;
+    memcpy(&lo, &Hi, 4);
+    memcpy(&hi, &Hfe, 4);
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        float Hm;
+        memcpy(&Hm, &mid, 4);
+        ++*probes_out;
+        if (feasible_f32(X, n_knots, gap, fma_form, Hm)) hi = mid;
+        else lo = mid;
+    }
+    float Hf;
+    memcpy(&Hf, &hi, 4);
+    const float X0 = X[0], W = Hf * X0;
+    *H_out = Hf;
+    *W_out = W;
+    *R_out = trunc_u32(fma_form ? fval_fma_f32(Hf, W, X[N]) : fval_plain_f32(Hf, X0, X[N]));
     return OR_OK;
 }
 
