@@ -77,9 +77,12 @@ enum {
                              Algorithm direct-2, i = t - [z < X_t] - [z < X_{t-1}]; a smaller table and
                              feasible on more arrays; not combined with DS_CACHE_LAYOUT; the same as
                              ds_build_q with q = 2 */
-    DS_NO_FINGERPRINT = 64u /* batched builds: K entries of arrays with at most 2^24 knots carry no
+    DS_NO_FINGERPRINT = 64u, /* batched builds: K entries of arrays with at most 2^24 knots carry no
                              7-bit fingerprint of f(X_t), so every query in a cell holding a knot
                              reads the knot (the paper's correcting comparison, always made) */
+    DS_REFINE_H = 128u    /* single-array builds: when ComputeHR had to grow H, bisect the interval
+                             between the last infeasible H and the final one for a smaller feasible
+                             H (end of Section 4.4; every probe checks the whole array) */
 };
 
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */
@@ -125,7 +128,7 @@ typedef struct ds_info_t {
  * (Section 4.8).
  *   X_dev    n_knots = N+1 strictly increasing finite values of `dtype`; read
  *            once and copied (the handle does not keep the pointer).
- *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2.
+ *   flags    DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H.
  *            With DS_GAP2 (Section 4.7) ComputeHR separates the knot pairs
  *            (i, i+2) instead of (i, i+1), K follows Eq. kgeneral and searches
  *            use Algorithm direct-2; at most 2^30 knots, no DS_CACHE_LAYOUT.
@@ -154,7 +157,7 @@ DS_API ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, ui
  *   q_max         the largest q tried when q == 0 (ignored otherwise).
  *   budget_bytes  used when q == 0; <= 0 means the shared-memory staging limit
  *                 of the search (so the table is staged per block).
- *   flags         DS_FMA | DS_CHECKED | DS_NO_SMEM, and DS_CACHE_LAYOUT for q = 1.
+ *   flags         DS_FMA | DS_CHECKED | DS_NO_SMEM | DS_REFINE_H, and DS_CACHE_LAYOUT for q = 1.
  * At most 2^30 knots for q >= 2.  ds_info reports the q built in gap_q.
  * Errors: as ds_build; DS_E_TABLE_TOO_LARGE when q == 0 and no q qualifies.
  * Synchronous. */

@@ -135,6 +135,47 @@ static ds_status run_compute_hr(const T *X, long long n_knots, HRState *st, HRSt
     return DS_OK;
 }
 
+// Refinement of H (end of Section 4.4): bisect [last infeasible H, final H]
+// on the bit patterns (positive floats order like them), each probe checking
+// every pair and the overflow test; hs receives the smallest feasible H
+// reached, its W and R.
+template <typename T, bool FMA>
+static ds_status refine_h(const T *X, long long n_knots, HRState *st, HRState *hs, cudaStream_t s,
+                          const DeviceProps &props)
+{
+    using A = Arith<T>;
+    using B = typename A::Bits;
+    const int block = 256;
+    const int grid = grid_for(props, n_knots, block);
+    T lo_h = (T)hs->H_inf, hi_h = (T)hs->H;
+    B lo, hi;
+    memcpy(&lo, &lo_h, sizeof(T));
+    memcpy(&hi, &hi_h, sizeof(T));
+    HRState probe;
+    while (hi - lo > 1) {
+        const B mid = lo + (hi - lo) / 2;
+        T Hm;
+        memcpy(&Hm, &mid, sizeof(T));
+        k_hr_probe<T, FMA><<<1, 1, 0, s>>>(X, n_knots, Hm, st);
+        k_hr_check<T, FMA><<<grid, block, 0, s>>>(X, n_knots, st);
+        DS_TRY_CUDA(cudaGetLastError());
+        DS_TRY_CUDA(cudaMemcpyAsync(&probe, st, sizeof(HRState), cudaMemcpyDeviceToHost, s));
+        DS_TRY_CUDA(cudaStreamSynchronize(s));
+        if (probe.status == DS_OK && probe.first_violation == NONE64) hi = mid;
+        else lo = mid;
+    }
+    T Hf;
+    memcpy(&Hf, &hi, sizeof(T));
+    k_hr_probe<T, FMA><<<1, 1, 0, s>>>(X, n_knots, Hf, st);
+    DS_TRY_CUDA(cudaGetLastError());
+    DS_TRY_CUDA(cudaMemcpyAsync(&probe, st, sizeof(HRState), cudaMemcpyDeviceToHost, s));
+    DS_TRY_CUDA(cudaStreamSynchronize(s));
+    hs->H = probe.H;
+    hs->W = probe.W;
+    hs->R = probe.R;
+    return DS_OK;
+}
+
 static const char *hr_message(int status)
 {
     switch (status) {
@@ -159,6 +200,8 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     const int gap = (long long)q < n_knots - 1 ? q : (int)(n_knots - 1);
     idx->q = q;
     ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props, gap);
+    if (rc == DS_OK && hs.status == DS_OK && hs.updates > 0 && (flags & DS_REFINE_H))
+        rc = refine_h<T, FMA>(X_user, n_knots, st, &hs, s, props);
     cudaFree(st);
     if (rc != DS_OK) return rc;
     idx->updates = hs.updates;

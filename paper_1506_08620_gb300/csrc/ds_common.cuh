@@ -53,6 +53,7 @@ enum DeviceErr : int32_t { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 
 // values exactly.
 struct HRState {
     double H, W, P;
+    double H_inf;                        // the last H found infeasible by the growth loop
     unsigned long long R;
     long long updates, passes, cursor;
     int status, done, grew;

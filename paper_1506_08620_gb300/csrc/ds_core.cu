@@ -194,7 +194,7 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
     }
     *out = nullptr;
     if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H))) {
         set_error("ds_build: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u)", X_dev, (long long)n_knots,
                   (int)dtype, flags);
         return DS_E_ARG;
@@ -224,7 +224,7 @@ ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_
     }
     *out = nullptr;
     if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) || q < 0 || (q == 0 && q_max < 1) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_REFINE_H))) {
         set_error("ds_build_q: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u, q=%d, q_max=%d)", X_dev,
                   (long long)n_knots, (int)dtype, flags, q, q_max);
         return DS_E_ARG;

@@ -164,6 +164,7 @@ __device__ void hr_grow_one(const T *X, long long n_knots, HRState *st)
     }
     const T xa = X[v - st->gap], xb = X[v];
     while (A::trunc_u32(fval<T, FMA>(H, W, X0, xa)) == A::trunc_u32(fval<T, FMA>(H, W, X0, xb))) {
+        st->H_inf = (double)H;
         H = A::add(H, P);
         W = A::mul(H, X0);
         if (!(fval<T, FMA>(H, W, X0, XN) < T(4294967296.0))) {
@@ -186,6 +187,25 @@ template <typename T, bool FMA>
 __global__ void k_hr_grow(const T *X, long long n_knots, HRState *st)
 {
     hr_grow_one<T, FMA>(X, n_knots, st);
+}
+
+// One probe of the refinement of H (end of Section 4.4): state for a pair
+// scan by k_hr_check with this H (W = m(H X_0), cursor at the pair distance);
+// the overflow test of Eq. overflowexact marks the probe done and infeasible.
+template <typename T, bool FMA>
+__global__ void k_hr_probe(const T *X, long long n_knots, T H, HRState *st)
+{
+    using A = Arith<T>;
+    const T X0 = X[0], XN = X[n_knots - 1];
+    const T W = A::mul(H, X0);
+    st->H = (double)H;
+    st->W = (double)W;
+    st->first_violation = NONE64;
+    st->cursor = st->gap;
+    const bool over = !(fval<T, FMA>(H, W, X0, XN) < T(4294967296.0));
+    st->status = over ? DS_E_OVERFLOW : DS_OK;
+    st->done = over ? 1 : 0;
+    st->R = over ? 0 : A::trunc_u32(fval<T, FMA>(H, W, X0, XN));
 }
 
 // F_i = f(X_i) truncated (the cells of the knots).
