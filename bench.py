@@ -43,8 +43,12 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     p.add_argument("--queries", type=int, default=0, help="override the query count (profiling runs)")
-    p.add_argument("--tune", default="auto", choices=["auto", "default"],
-                   help="batched/learned launch configuration: autotuned, or the library default")
+    p.add_argument("--tune", default="auto",
+                   help="batched/learned launch configuration: auto (autotuned), default (the library's), "
+                        "or block,items,smem_limit")
+    p.add_argument("--record-traffic", default="", metavar="NCU_CSV",
+                   help="write the timed kernel's DRAM bytes per launch from an ncu CSV to profiles/traffic.json "
+                        "(no GPU needed; give the --workload/--variant/--queries of the captured run)")
     return p.parse_args()
 
 
@@ -57,25 +61,76 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
+# the sources each timed kernel is compiled from (a capture stays valid while they are unchanged)
+_COMMON = ["ds_common.cuh", "ds_search.cuh", "ds_index.cuh", "ds.h"]
+KERNEL_SOURCES = {
+    "search": _COMMON + ["ds_search_impl.cuh", "ds_search_f32.cu", "ds_search_f64.cu", "ds_build.cu"],
+    "batch": _COMMON + ["ds_multi.cuh", "ds_multi_kernels.cuh", "ds_engine.cuh", "ds_batch.cu"],
+    "learned": _COMMON + ["ds_multi.cuh", "ds_multi_kernels.cuh", "ds_engine.cuh", "ds_batch.cu", "ds_learned.cu"],
+}
+
+
+def source_hash(kernel_key):
+    family = kernel_key.split("_")[0]
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1506_08620_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES.get(family, KERNEL_SOURCES["search"]):
+        path = os.path.join(ROOT, "include", f) if f.endswith(".h") else \
+            os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", f)
+        h.update(open(path, "rb").read())
     return h.hexdigest()[:16]
+
+
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def traffic_for(kernel_key):
     """Per-launch DRAM bytes from a committed ncu capture, if it was taken on the
     current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(TRAFFIC_PATH):
         return None
-    d = json.load(open(path))
+    d = json.load(open(TRAFFIC_PATH))
     e = d.get(kernel_key)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel_key):
         return None
     return e.get("bytes_per_launch")
+
+
+def kernel_key_of(args):
+    if args.workload.startswith("direct"):
+        return "search_%s_%s" % ("f32" if args.workload == "direct_f32" else "f64", args.variant)
+    return {"gapq_f64": "search_f64_gapq", "paper_tables": "search_f64_paper_layout",
+            "batched_f32": "batch_search_f32", "learned_f64": "learned_search_f64",
+            "learned_interp_f32": "learned_search_f32"}[args.workload]
+
+
+def record_traffic(args):
+    """Per-launch DRAM traffic of the timed kernel from an ncu CSV (--metrics
+    dram__bytes_read.sum,dram__bytes_write.sum of a run with --queries Q),
+    scaled to the full workload by the query count, into profiles/traffic.json."""
+    import csv
+    scale_unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per_launch = {}
+    with open(args.record_traffic) as f:
+        lines = [l for l in f if l.startswith('"')]
+    for row in csv.DictReader(lines):
+        if row.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        v = float(row["Metric Value"].replace(",", "")) * scale_unit.get(row.get("Metric Unit", "byte"), 1)
+        per_launch[row["ID"]] = per_launch.get(row["ID"], 0.0) + v
+    if not per_launch or not args.queries:
+        raise SystemExit("record-traffic: no dram__bytes rows in %s, or --queries not given" % args.record_traffic)
+    captured = float(np.mean(list(per_launch.values())))
+    full = workload_config(argparse.Namespace(**{**vars(args), "queries": 0}))["queries"]
+    key = kernel_key_of(args)
+    d = json.load(open(TRAFFIC_PATH)) if os.path.exists(TRAFFIC_PATH) else {}
+    d[key] = {"bytes_per_launch": captured * full / args.queries, "captured_bytes_per_launch": captured,
+              "captured_queries": args.queries, "full_queries": full, "launches": len(per_launch),
+              "scaled": "traffic grows in proportion to the queries (tables L2-resident)",
+              "source_hash": source_hash(key)}
+    with open(TRAFFIC_PATH, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+        f.write("\n")
+    print(json.dumps({key: d[key]}))
 
 
 class Clocks:
@@ -463,7 +518,14 @@ def setup_batched(args, ds, W, torch, dev, rank):
     torch.cuda.synchronize()
     job.build_ms = (time.perf_counter() - t0) * 1e3
     info = b.info()
-    tune = ds.ds_batch_autotune(b, Zd, zo, out) if args.tune == "auto" else ds.ds_batch_get_tune(b)
+    if args.tune == "auto":
+        tune = ds.ds_batch_autotune(b, Zd, zo, out)
+    elif args.tune == "default":
+        tune = ds.ds_batch_get_tune(b)
+    else:
+        blk, items, smem = (int(v) for v in args.tune.split(","))
+        ds.ds_batch_set_tune(b, blk, items, smem)
+        tune = ds.ds_batch_get_tune(b)
     job.bytes_per_lookup = 8 + info["table_bytes"] / job.m
     job.table = {"arrays": info["n_arrays"], "R_total": info["R"], "table_bytes": info["table_bytes"],
                  "tune": tune}
@@ -593,6 +655,8 @@ def time_calls(torch, stream, fn, n):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        return record_traffic(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

@@ -284,7 +284,8 @@ DS_API ds_status ds_batch_search(const ds_batch *b, const void *Zcat_dev, const 
 typedef struct ds_tune_t {
     int32_t block;       /* threads per block (multiple of 32) */
     int32_t items;       /* queries per thread per tile */
-    int32_t smem_limit;  /* largest per-array table (bytes) staged in shared memory; 0 = never */
+    int32_t smem_limit;  /* largest per-array table (bytes) staged in shared memory; 0 = never (blocks
+                            claim chunks); -1 = never, and each warp claims its own chunks */
     int32_t blocks_per_sm;
     float ms;            /* measured time of the chosen configuration (autotune output) */
 } ds_tune_t;

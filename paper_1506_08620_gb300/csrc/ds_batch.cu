@@ -387,40 +387,44 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
 }
 
 // ---------------------------------------------------------------- launch
+// Warp-claimed kernels exist for the vector path (the scalar path, for
+// misaligned buffers, always claims per block).
 template <typename T, int VPT, bool INTERP, int KIND>
-static const void *pick4(bool vec)
+static const void *pick4(bool vec, bool warps)
 {
+    if (vec && warps) return (const void *)k_batch_search<T, VPT, INTERP, true, KIND, true>;
     return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, KIND>
                : (const void *)k_batch_search<T, VPT, INTERP, false, KIND>;
 }
 template <typename T, int VPT, bool INTERP>
-static const void *pick3(bool vec, int kind)
+static const void *pick3(bool vec, bool warps, int kind)
 {
     switch (kind) {
-    case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec);
-    case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec);
-    default: return pick4<T, VPT, INTERP, KIND_ALL>(vec);
+    case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec, warps);
+    case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps);
+    default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps);
     }
 }
 template <typename T, int VPT>
-static const void *pick2(bool interp, bool vec, int kind)
+static const void *pick2(bool interp, bool vec, bool warps, int kind)
 {
-    return interp ? pick3<T, VPT, true>(vec, kind) : pick3<T, VPT, false>(vec, kind);
+    return interp ? pick3<T, VPT, true>(vec, warps, kind) : pick3<T, VPT, false>(vec, warps, kind);
 }
 template <typename T>
-static const void *pick1(int vpt, bool interp, bool vec, int kind)
+static const void *pick1(int vpt, bool interp, bool vec, bool warps, int kind)
 {
     switch (vpt) {
-    case 1: return pick2<T, 1>(interp, vec, kind);
-    case 2: return pick2<T, 2>(interp, vec, kind);
-    default: return pick2<T, 4>(interp, vec, kind);
+    case 1: return pick2<T, 1>(interp, vec, warps, kind);
+    case 2: return pick2<T, 2>(interp, vec, warps, kind);
+    default: return pick2<T, 4>(interp, vec, warps, kind);
     }
 }
-static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec)
+static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps)
 {
     const bool direct_only = e->n_learned == 0 && e->n_fallback == 0;
     const int kind = !direct_only ? KIND_ALL : (e->fingerprints ? KIND_DIRECT_FP : KIND_DIRECT);
-    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, kind) : pick1<double>(vpt, interp, vec, kind);
+    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, warps, kind)
+                              : pick1<double>(vpt, interp, vec, warps, kind);
 }
 
 static int clamp_block(int b) { return b == 128 || b == 512 ? b : 256; }
@@ -429,7 +433,7 @@ static int clamp_vpt(int v) { return v == 1 || v == 2 ? v : 4; }
 // Resident blocks for a configuration (and the shared-memory opt-in).
 static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid)
 {
-    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec);
+    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0);
     const int smem = std::max(0, t.smem_limit);
     if (smem > 0) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
@@ -454,10 +458,11 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
     int grid = 0;
     DS_TRY(occupancy(e, t, interp, vec, &grid));
     const int block = clamp_block(t.block), vpt = clamp_vpt(t.items);
-    const long long chunk = (long long)block * vpt * L * CHUNK_TILES;
+    const bool warps = vec && t.smem_limit < 0;  // nothing staged, and warps claim their own chunks
+    const long long chunk = (long long)(warps ? 32 : block) * vpt * L * (warps ? CHUNK_TILES_WARP : CHUNK_TILES);
     k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->chunk_off, e->counter);
     DS_TRY_CUDA(cudaGetLastError());
-    const void *fn = pick_kernel(e, vpt, interp, vec);
+    const void *fn = pick_kernel(e, vpt, interp, vec, warps);
     if (e->dtype == DS_F32) {
         BatchArgs<float> a;
         memset(&a, 0, sizeof(a));
@@ -533,7 +538,7 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
 {
     const int blocks[] = {128, 256, 512};
     const int items[] = {1, 2, 4};
-    const int smems[] = {0, 24 * 1024, 48 * 1024, 96 * 1024, 200 * 1024};
+    const int smems[] = {-1, 0, 24 * 1024, 48 * 1024, 96 * 1024, 200 * 1024};
     cudaEvent_t e0, e1;
     DS_TRY_CUDA(cudaEventCreate(&e0));
     DS_TRY_CUDA(cudaEventCreate(&e1));
@@ -688,7 +693,7 @@ ds_status ds_batch_autotune(ds_batch *b, const void *Zcat_dev, const int64_t *z_
 
 ds_status ds_batch_set_tune(ds_batch *b, const ds_tune_t *cfg)
 {
-    if (!batch_ok(b) || !cfg || cfg->smem_limit < 0 || cfg->smem_limit > b->eng.props.max_smem_optin - 2048) {
+    if (!batch_ok(b) || !cfg || cfg->smem_limit < -1 || cfg->smem_limit > b->eng.props.max_smem_optin - 2048) {
         ds::set_error("ds_batch_set_tune: bad argument");
         return DS_E_ARG;
     }

@@ -11,7 +11,8 @@
 namespace ds {
 
 constexpr long long SEG_KNOTS = 1 << 16;  // knots per build segment
-constexpr int CHUNK_TILES = 8;            // tiles per search chunk
+constexpr int CHUNK_TILES = 8;            // tiles per search chunk claimed by a block
+constexpr int CHUNK_TILES_WARP = 32;      // tiles per search chunk claimed by a warp
 
 struct Engine {
     int dtype = 0;

@@ -222,9 +222,11 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
     }
 }
 
+// Queries [zs, ze) of one array by `nthr` threads (a block, or a warp); `tid`
+// is the thread's rank among them.
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool SM>
 __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
-                                              long long zs, long long ze, uint64_t pol)
+                                              long long zs, long long ze, uint64_t pol, int tid, int nthr)
 {
     constexpr int L = VecOf<T>::L;
     long long va, vb;
@@ -237,14 +239,14 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         vb = ze;
     }
     // scalar head and tail
-    for (long long q = zs + threadIdx.x; q < va; q += blockDim.x) {
+    for (long long q = zs + tid; q < va; q += nthr) {
         T z = a.Z[q];
         int32_t r;
         answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
-    for (long long q = vb + threadIdx.x; q < ze; q += blockDim.x) {
+    for (long long q = vb + tid; q < ze; q += nthr) {
         T z = a.Z[q];
         int32_t r;
         answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
@@ -258,11 +260,11 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         const long long v0 = va / L, nv = (vb - va) / L;
         const V *Zv = reinterpret_cast<const V *>(a.Z) + v0;
         IV *Iv = reinterpret_cast<IV *>(a.I) + v0;
-        for (long long base = threadIdx.x; base < nv; base += (long long)VPT * blockDim.x) {
+        for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
             V zv[VPT];
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                const long long idx = base + (long long)v * blockDim.x;
+                const long long idx = base + (long long)v * nthr;
                 zv[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
             }
             const T *zs4 = reinterpret_cast<const T *>(zv);
@@ -270,7 +272,7 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
             answer_block<T, NQ, KIND, SM>(a, d, K, X, zs4, r, pol);
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                const long long idx = base + (long long)v * blockDim.x;
+                const long long idx = base + (long long)v * nthr;
                 if (idx < nv) {
                     IV o;
                     if constexpr (L == 4) o = make_int4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
@@ -288,9 +290,44 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
 }
 
 // KIND: BatchKind (KIND_DIRECT*: every array of the handle is in direct mode).
-template <typename T, int VPT, bool INTERP, bool VEC, int KIND>
+// WARPS: no table is staged (a.smem_limit == 0) and every warp claims its own
+// chunks, so no block-wide barrier is needed; otherwise the block claims a
+// chunk and stages its array's image for all of its warps.
+template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false>
 __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
 {
+    if constexpr (WARPS) {
+        const int lane = threadIdx.x & 31;
+        const long long total = a.chunk_off[a.n_arrays];
+        for (;;) {
+            long long c = 0;
+            int arr = -1;
+            if (lane == 0) {
+                c = (long long)atomicAdd(a.counter, 1ull);
+                if (c < total) {
+                    int lo = 0, hi = a.n_arrays - 1;  // largest array with chunk_off <= c
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (a.chunk_off[mid] <= c) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    arr = lo;
+                }
+            }
+            c = __shfl_sync(0xffffffffu, c, 0);
+            arr = __shfl_sync(0xffffffffu, arr, 0);
+            if (arr < 0) break;
+            const ArrDesc d = a.desc[arr];
+            const long long zb = q_begin(a.z_off, arr);
+            const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
+            const long long zs = zb + (c - a.chunk_off[arr]) * a.chunk;
+            const long long ze = zs + a.chunk < zend ? zs + a.chunk : zend;
+            process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, reinterpret_cast<const uint32_t *>(a.blob + d.img),
+                                                            reinterpret_cast<const T *>(a.blob + d.xg), zs, ze, 0,
+                                                            lane, 32);
+        }
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ long long s_c;
@@ -341,8 +378,8 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
             K = reinterpret_cast<const uint32_t *>(a.blob + d.img);
             X = reinterpret_cast<const T *>(a.blob + d.xg);
         }
-        if (use_smem) process_chunk<T, VPT, INTERP, VEC, KIND, true>(a, d, K, X, zs, ze, pol);
-        else process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, K, X, zs, ze, pol);
+        if (use_smem) process_chunk<T, VPT, INTERP, VEC, KIND, true>(a, d, K, X, zs, ze, pol, threadIdx.x, blockDim.x);
+        else process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, K, X, zs, ze, pol, threadIdx.x, blockDim.x);
         __syncthreads();
     }
 }

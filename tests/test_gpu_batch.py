@@ -52,7 +52,7 @@ def test_small_batch_all_tunings(ds, fma):
     ref = oracle.upper_bound_batch(w["Xcat"], w["x_off"], w["Zcat"], w["z_off"])
     for block in (128, 256, 512):
         for items in (1, 2, 4):
-            for smem in (0, 24 * 1024, 96 * 1024):
+            for smem in (-1, 0, 24 * 1024, 96 * 1024):
                 ds.ds_batch_set_tune(b, block, items, smem)
                 out = ds.ds_batch_search(b, Zd, zo)
                 got = out.cpu().numpy()
@@ -197,7 +197,7 @@ def test_fingerprints_across_cell_ranges(ds, dtype, fma):
     for extra in (0, ds.DS_NO_FINGERPRINT):
         b = ds.ds_batch_build(_cuda(Xcat), _cuda(x_off), flags | extra)
         Rs = [ds.ds_batch_array(b, a)["R"] for a in range(len(arrays))]
-        for smem in (0, 96 * 1024):
+        for smem in (-1, 0, 96 * 1024):
             ds.ds_batch_set_tune(b, 256, 4, smem)
             got = ds.ds_batch_search(b, _cuda(Zcat), _cuda(z_off)).cpu().numpy()
             assert np.array_equal(got, ref), (extra, smem, int(np.count_nonzero(got != ref)))
