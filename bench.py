@@ -62,7 +62,7 @@ def peaks():
 
 
 # the sources each timed kernel is compiled from (a capture stays valid while they are unchanged)
-_COMMON = ["ds_common.cuh", "ds_search.cuh", "ds_index.cuh", "ds.h"]
+_COMMON = ["ds_common.cuh", "ds_search.cuh", "ds_index.cuh"]
 KERNEL_SOURCES = {
     "search": _COMMON + ["ds_search_impl.cuh", "ds_search_f32.cu", "ds_search_f64.cu", "ds_build.cu"],
     "batch": _COMMON + ["ds_multi.cuh", "ds_multi_kernels.cuh", "ds_engine.cuh", "ds_batch.cu"],
@@ -74,9 +74,7 @@ def source_hash(kernel_key):
     family = kernel_key.split("_")[0]
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(family, KERNEL_SOURCES["search"]):
-        path = os.path.join(ROOT, "include", f) if f.endswith(".h") else \
-            os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", f)
-        h.update(open(path, "rb").read())
+        h.update(open(os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -20,6 +20,18 @@
 
 namespace ds {
 
+// Comparison key of the merge: floats compare as themselves, doubles as their
+// order-preserving integer keys (integer comparisons instead of the FP64 pipe).
+template <typename T> struct MergeKey;
+template <> struct MergeKey<float> {
+    using K = float;
+    static __device__ __forceinline__ float of(float v) { return v; }
+};
+template <> struct MergeKey<double> {
+    using K = long long;
+    static __device__ __forceinline__ long long of(double v) { return okey(v); }
+};
+
 constexpr int MP_BLOCK = 256;
 constexpr int MP_ITEMS = 11;  // odd: fewer shared-memory bank conflicts in the per-thread merges
 constexpr int MP_TILE = MP_BLOCK * MP_ITEMS;
@@ -33,7 +45,7 @@ __device__ __forceinline__ long long merge_split(const T *X, long long NX, const
     while (lo < hi) {
         const long long mid = (lo + hi) >> 1;
         // X[mid] before Z[d - mid - 1]: the cut takes more knots
-        if (!(Z[d - mid - 1] < X[mid])) lo = mid + 1;
+        if (!(MergeKey<T>::of(Z[d - mid - 1]) < MergeKey<T>::of(X[mid]))) lo = mid + 1;
         else hi = mid;
     }
     return lo;
@@ -44,9 +56,10 @@ __global__ void __launch_bounds__(MP_BLOCK) k_merge_search(const T *__restrict__
                                                            const T *__restrict__ Z, long long M,
                                                            int32_t *__restrict__ I)
 {
+    using K = typename MergeKey<T>::K;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *sX = reinterpret_cast<T *>(smem);
-    T *sZ = sX + MP_TILE;
+    K *sX = reinterpret_cast<K *>(smem);
+    K *sZ = sX + MP_TILE;
     int32_t *sI = reinterpret_cast<int32_t *>(sZ + MP_TILE);
     __shared__ long long cuts[MP_BLOCK + 1];
     const long long total = NX + M;
@@ -80,7 +93,7 @@ __global__ void __launch_bounds__(MP_BLOCK) k_merge_search(const T *__restrict__
         };
         // software pipeline: tile j + 1's knots and queries are loaded into
         // registers while tile j is merged
-        T vz[MP_ITEMS], vx[MP_ITEMS];
+        K vz[MP_ITEMS], vx[MP_ITEMS];
         auto load_regs = [&](int j) {
             long long a0, b0;
             int nx, nz;
@@ -88,8 +101,8 @@ __global__ void __launch_bounds__(MP_BLOCK) k_merge_search(const T *__restrict__
 #pragma unroll
             for (int u = 0; u < MP_ITEMS; ++u) {
                 const int k = threadIdx.x + u * MP_BLOCK;
-                vz[u] = k < nz ? __ldcs(Z + b0 + k) : T(0);
-                vx[u] = k < nx ? X[a0 + k] : T(0);
+                vz[u] = MergeKey<T>::of(k < nz ? __ldcs(Z + b0 + k) : T(0));
+                vx[u] = MergeKey<T>::of(k < nx ? X[a0 + k] : T(0));
             }
         };
         if (n > 0) load_regs(0);
@@ -147,11 +160,24 @@ __global__ void __launch_bounds__(256) k_histogram(SearchArgs<T> a, unsigned lon
         for (long long k = threadIdx.x; k < nbins; k += blockDim.x) h[k] = 0u;
         __syncthreads();
     }
-    constexpr bool INTOPS = sizeof(T) == 8;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < a.m; q += stride) {
-        const T z = __ldcs(a.Z + q);
-        const int32_t i = lookup<T, FM, false, false, INTOPS, GEN>(z, a.K, a.X, a.P, a);
+        int32_t i;
+        if constexpr (sizeof(T) == 8) {
+            // doubles as bit patterns: one FP64 instruction per query (as k_search_f64bits)
+            const long long zb = __ldcs(reinterpret_cast<const long long *>(a.Z) + q);
+            const long long *Xb = reinterpret_cast<const long long *>(a.X);
+            const uint32_t e = __ldg(a.K + cell_bits<FM>(zb, (double)a.H, -(double)a.W, (double)a.X0, a.R));
+            if constexpr (GEN) {
+                const long long *px = Xb + (e & GEN_T_MASK);
+                const long long xb = (e & KNOT_FLAG) ? __ldg(px) : 0, xpb = (e & KNOT_FLAG2) ? __ldg(px - 1) : 0;
+                i = correct_bits_gen<true>(zb, e, xb, xpb, Xb, 0, a.q, 1);  // plain loads in the bisection
+            } else {
+                i = correct_bits(zb, e, (e & KNOT_FLAG) ? __ldg(Xb + (e & ~KNOT_FLAG)) : 0, 1);
+            }
+        } else {
+            i = lookup<T, FM, false, false, false, GEN>(__ldcs(a.Z + q), a.K, a.X, a.P, a);
+        }
         const long long bin = i + 1;
         if constexpr (SMH) atomicAdd(&h[bin], 1u);
         else atomicAdd(&counts[bin], 1ull);
@@ -221,7 +247,7 @@ static ds_status merge_typed(const void *X, long long NX, const void *Z, long lo
     int dev = 0, sms = 0, occ = 0;
     DS_TRY_CUDA(cudaGetDevice(&dev));
     DS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t sbytes = 2 * (size_t)MP_TILE * sizeof(T) + (size_t)MP_TILE * sizeof(int32_t);
+    const size_t sbytes = 2 * (size_t)MP_TILE * sizeof(typename MergeKey<T>::K) + (size_t)MP_TILE * sizeof(int32_t);
     DS_TRY_CUDA(cudaFuncSetAttribute(k_merge_search<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes));
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_merge_search<T>, MP_BLOCK, sbytes));
     const long long ntiles = (NX + M + MP_TILE - 1) / MP_TILE;
