@@ -262,9 +262,9 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 const size_t xb = round_up((size_t)nk * sizeof(T), 16);
                 d.img_bytes = d.mode == MODE_BISECT && xb <= 0xFFFFFFF0u ? (uint32_t)xb : 0u;
                 off += xb;
-                if (d.mode == MODE_LEARNED) {  // every 32nd knot, for the two-level window search
+                if (d.mode == MODE_LEARNED) {  // every SG_STRIDE-th knot, for the two-level window search
                     d.sg = (long long)off;
-                    off += round_up((size_t)((d.n >> 5) + 2) * sizeof(T), 16);
+                    off += round_up((size_t)((d.n >> SG_SHIFT) + 2) * sizeof(T), 16);
                 }
                 if (d.mode == MODE_BISECT) e->n_fallback += 1;
                 else e->n_learned += 1;

@@ -159,16 +159,16 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
             }
         }
         if (nfail) atomicAdd(a.fallbacks, (unsigned long long)nfail);
-        // level 1: largest k in [lo/32, hi/32] with S_k = X_{32k} <= z
+        // level 1: largest k in [lo/SG, hi/SG] with S_k = X_{SG k} <= z
         // (S_{lo/32} <= X_lo <= z and S_{hi/32+1} >= X_{hi+1} > z)
         const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
-        const int32_t ws = nfail ? ((d.n - 1) >> 5) + 1 : ((d.e_lo + d.e_hi + 3) >> 5) + 2;
+        const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
         const int32_t top1 = 1 << (31 - __clz(ws));
         int32_t k1[NQ], nk[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            k1[q] = lo[q] >> 5;
-            nk[q] = (hi[q] >> 5) - k1[q] + 1;
+            k1[q] = lo[q] >> SG_SHIFT;
+            nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
         }
         int32_t i1[NQ];
 #pragma unroll
@@ -181,17 +181,17 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
                 if (!lt_exact<T>(z[q], tab_ld<SM>(S + k1[q] + w, pol))) i1[q] = rr;
             }
         }
-        // level 2: at most 32 knots
+        // level 2: at most SG_STRIDE knots
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int32_t ks = k1[q] + (i1[q] < nk[q] ? i1[q] : nk[q] - 1);
-            const int32_t b0 = ks << 5;
+            const int32_t b0 = ks << SG_SHIFT;
             const int32_t l2 = b0 > lo[q] ? b0 : lo[q];
-            const int32_t e2 = (b0 + 32 < hi[q] + 1) ? b0 + 32 : hi[q] + 1;
+            const int32_t e2 = (b0 + SG_STRIDE < hi[q] + 1) ? b0 + SG_STRIDE : hi[q] + 1;
             lo[q] = l2;
             n[q] = e2 - l2;
         }
-        top = 16;
+        top = SG_STRIDE / 2;
     } else {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -483,9 +483,9 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
             const T x = Xcat[i];
             const long long li = i - start;
             Xd[li] = x;
-            if (d.mode == MODE_LEARNED) {  // S_k = X_{min(32 k, N)}, k = 0 .. N/32 + 1
-                if ((li & 31) == 0) S[li >> 5] = x;
-                if (li == d.n) S[(d.n >> 5) + 1] = x;
+            if (d.mode == MODE_LEARNED) {  // S_k = X_{min(SG k, N)}, k = 0 .. N/SG + 1
+                if ((li & (SG_STRIDE - 1)) == 0) S[li >> SG_SHIFT] = x;
+                if (li == d.n) S[(d.n >> SG_SHIFT) + 1] = x;
             }
             if (d.mode == MODE_DIRECT) {
                 T v;
