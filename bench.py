@@ -373,6 +373,16 @@ def setup_direct(args, ds, W, torch, dev, rank):
             if fl & ds.DS_GAP2:
                 res[name + "_table_bytes"] = j.info()["table_bytes"]
             j.free()
+        # end to end through the chunked copy pipeline instead of in-place host access
+        os.environ["DS_HOST_PIPE"] = "1"
+        try:
+            ds.ds_search_host(idx, Zp, Ip)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                ds.ds_search_host(idx, Zp, Ip)
+            res["e2e_copy_pipeline"] = job.m / ((time.perf_counter() - t0) / 3)
+        finally:
+            del os.environ["DS_HOST_PIPE"]
         if args.workload == "direct_f64":
             Zs = torch.sort(Zd).values
             res["sorted_queries_" + args.variant] = job.m / time_calls(torch, stream,

@@ -173,11 +173,14 @@ DS_API ds_status ds_build_q(const void *X_dev, int64_t n_knots, ds_dtype dtype, 
  * capture in a CUDA graph. */
 DS_API ds_status ds_search(const ds_index *idx, const void *Z_dev, int64_t m, int32_t *I_dev, void *stream);
 
-/* The same search with HOST buffers: copies queries in and results out in
- * pipelined chunks (host->device, search, device->host on separate streams).
- * Z_host / I_host should be pinned; the call returns when the last result has
- * been written to I_host.  Allocates its device staging buffers on the first
- * call and keeps them in the handle. */
+/* The same search with HOST buffers.  When both are pinned and mapped
+ * (cudaHostAlloc, cudaHostRegister) the search kernel reads the queries from
+ * and writes the results to host memory directly over the CPU-GPU link, with no
+ * staging; otherwise (or with the environment variable DS_HOST_PIPE=1) queries
+ * are copied in and results out in pipelined chunks (host->device, search,
+ * device->host on separate streams), with device staging buffers allocated on
+ * the first call and kept in the handle.  Returns when the last result has
+ * been written to I_host. */
 DS_API ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *I_host, void *stream);
 
 /* Sorted queries (the O(M + N) case of Section 1.2): merge Z into X instead

@@ -260,10 +260,30 @@ ds_status ds_search_host(ds_index *idx, const void *Z_host, int64_t m, int32_t *
         set_error("ds_search_host: null pointer or negative size");
         return DS_E_ARG;
     }
+    cudaStream_t us = (cudaStream_t)stream;
+    // Pinned, mapped host buffers (cudaHostAlloc, cudaHostRegister): the search
+    // kernel streams the queries from host memory and writes the results there
+    // itself, over the CPU-GPU link (NVLink-C2C on Grace-Blackwell), with no
+    // staging copies; the table gathers stay in device memory.
+    const char *pipe_env = getenv("DS_HOST_PIPE");
+    const bool force_pipe = pipe_env && atoi(pipe_env) != 0;
+    if (!force_pipe) {
+        cudaPointerAttributes az, ai;
+        if (cudaPointerGetAttributes(&az, Z_host) == cudaSuccess && az.type == cudaMemoryTypeHost &&
+            az.devicePointer && az.hostPointer && cudaPointerGetAttributes(&ai, I_host) == cudaSuccess &&
+            ai.type == cudaMemoryTypeHost && ai.devicePointer && ai.hostPointer) {
+            // the attributes may describe the enclosing allocation: keep the pointers' offsets into it
+            const char *zd = (const char *)az.devicePointer + ((const char *)Z_host - (const char *)az.hostPointer);
+            char *id = (char *)ai.devicePointer + ((const char *)I_host - (const char *)ai.hostPointer);
+            DS_TRY(search_index(idx, zd, m, reinterpret_cast<int32_t *>(id), us));
+            DS_TRY_CUDA(cudaStreamSynchronize(us));
+            return DS_OK;
+        }
+        cudaGetLastError();  // pageable memory: not an error, take the copy pipeline
+    }
     const size_t esz = idx->dtype == DS_F32 ? 4 : 8;
     if (!idx->pipe) DS_TRY(make_pipe(&idx->pipe, esz));
     HostPipe *p = idx->pipe;
-    cudaStream_t us = (cudaStream_t)stream;
     DS_TRY_CUDA(cudaEventRecord(p->ev_start, us));
     DS_TRY_CUDA(cudaStreamWaitEvent(p->s_in, p->ev_start, 0));
     const char *zh = reinterpret_cast<const char *>(Z_host);

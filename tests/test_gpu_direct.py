@@ -209,15 +209,30 @@ def test_error_statuses(ds):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_search_host_buffers(ds, dtype, monkeypatch):
+@pytest.mark.parametrize("mode", ["direct", "pipeline", "pageable"])
+def test_search_host_buffers(ds, dtype, mode, monkeypatch):
+    # pinned buffers are read and written by the kernel in place; DS_HOST_PIPE=1
+    # and pageable buffers take the chunked copy pipeline
     monkeypatch.setenv("DS_PIPE_CHUNK", str(100_003))
+    if mode == "pipeline":
+        monkeypatch.setenv("DS_HOST_PIPE", "1")
     g = np.random.default_rng(6)
     X = W.knots_from_gaps(1.0, g.lognormal(0, 0.5, 50_000), dtype)
     Z = W.uniform_queries(g, X[0], X[-1], 1_000_001, dtype)
     idx = ds.ds_build(_cuda(X), ds.DS_FMA)
-    Zh = torch.from_numpy(Z).pin_memory()
-    out = ds.ds_search_host(idx, Zh)
+    if mode == "pageable":
+        Zh = torch.from_numpy(Z.copy())
+        out = torch.full((Z.size,), -7, dtype=torch.int32)
+        ds.ds_search_host(idx, Zh, out)
+    else:
+        Zh = torch.from_numpy(Z).pin_memory()
+        out = ds.ds_search_host(idx, Zh)
     assert np.array_equal(out.numpy(), oracle.upper_bound(X, Z))
+    # misaligned views of pinned memory (scalar kernel path)
+    if mode == "direct":
+        out2 = torch.full((Z.size,), -7, dtype=torch.int32).pin_memory()
+        ds.ds_search_host(idx, Zh[1:], out2[1:])
+        assert np.array_equal(out2.numpy()[1:], oracle.upper_bound(X, Z[1:])) and out2[0] == -7
     idx.free()
 
 
