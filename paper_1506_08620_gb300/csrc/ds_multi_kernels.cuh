@@ -260,13 +260,22 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         const long long v0 = va / L, nv = (vb - va) / L;
         const V *Zv = reinterpret_cast<const V *>(a.Z) + v0;
         IV *Iv = reinterpret_cast<IV *>(a.I) + v0;
-        for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
-            V zv[VPT];
+        // software pipeline: the next tile's queries are loaded while this
+        // tile's table gathers are in flight
+        V zn[VPT];
+        auto load_tile = [&](long long base) {
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = base + (long long)v * nthr;
-                zv[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
+                zn[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
             }
+        };
+        if (tid < nv) load_tile(tid);
+        for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
+            V zv[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) zv[v] = zn[v];
+            if (base + (long long)VPT * nthr < nv) load_tile(base + (long long)VPT * nthr);
             const T *zs4 = reinterpret_cast<const T *>(zv);
             int32_t r[NQ];
             answer_block<T, NQ, KIND, SM>(a, d, K, X, zs4, r, pol);
@@ -289,6 +298,40 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     }
 }
 
+// The array owning chunk c: the largest a with chunk_off[a] <= c (arrays
+// without queries share their offset with the next one, so the largest is the
+// owner).  Called by all 32 lanes of a warp: a 32-way search, each step
+// comparing 32 evenly spaced offsets with one ballot (3 dependent loads for
+// 4096 arrays instead of 12 for bisection).
+__device__ __forceinline__ int owner_of_chunk(const long long *chunk_off, int n_arrays, long long c)
+{
+    const int lane = threadIdx.x & 31;
+    int lo = 0, n = n_arrays;  // the owner lies in [lo, lo + n); chunk_off[lo] <= c
+    while (n > 1) {
+        const int step = (n + 31) >> 5;
+        const int p = lo + lane * step;
+        const bool ok = p < lo + n && chunk_off[p] <= c;
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        const int k = 31 - __clz(mask);  // lane 0 always qualifies
+        const int nlo = lo + k * step;
+        n = (lo + n - nlo) < step ? (lo + n - nlo) : step;
+        lo = nlo;
+    }
+    return lo;
+}
+
+// Claim the next chunk for the calling warp: (chunk, owning array), array -1
+// when none is left.  All 32 lanes call; every lane gets the result.
+__device__ __forceinline__ void claim_chunk(unsigned long long *counter, const long long *chunk_off, int n_arrays,
+                                            long long *c_out, int *arr_out)
+{
+    long long c = 0;
+    if ((threadIdx.x & 31) == 0) c = (long long)atomicAdd(counter, 1ull);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    *c_out = c;
+    *arr_out = c < chunk_off[n_arrays] ? owner_of_chunk(chunk_off, n_arrays, c) : -1;
+}
+
 // KIND: BatchKind (KIND_DIRECT*: every array of the handle is in direct mode).
 // WARPS: no table is staged (a.smem_limit == 0) and every warp claims its own
 // chunks, so no block-wide barrier is needed; otherwise the block claims a
@@ -298,24 +341,10 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
 {
     if constexpr (WARPS) {
         const int lane = threadIdx.x & 31;
-        const long long total = a.chunk_off[a.n_arrays];
         for (;;) {
-            long long c = 0;
-            int arr = -1;
-            if (lane == 0) {
-                c = (long long)atomicAdd(a.counter, 1ull);
-                if (c < total) {
-                    int lo = 0, hi = a.n_arrays - 1;  // largest array with chunk_off <= c
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (a.chunk_off[mid] <= c) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    arr = lo;
-                }
-            }
-            c = __shfl_sync(0xffffffffu, c, 0);
-            arr = __shfl_sync(0xffffffffu, arr, 0);
+            long long c;
+            int arr;
+            claim_chunk(a.counter, a.chunk_off, a.n_arrays, &c, &arr);
             if (arr < 0) break;
             const ArrDesc d = a.desc[arr];
             const long long zb = q_begin(a.z_off, arr);
@@ -330,34 +359,37 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
     }
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ long long s_c;
-    __shared__ int s_a;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    // the block's next chunk, claimed by warp 0 while the current one is worked
+    // on; two slots, read at the start of iteration k from slot k & 1
+    __shared__ long long s_c[2];
+    __shared__ int s_a[2];
+    if (threadIdx.x < 32) {
+        long long c0;
+        int a0;
+        claim_chunk(a.counter, a.chunk_off, a.n_arrays, &c0, &a0);
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            s_c[0] = c0;
+            s_a[0] = a0;
+        }
+    }
     __syncthreads();
     uint32_t parity = 0;
     int staged = -1;
     const uint64_t pol = 0;
-    const long long total = a.chunk_off[a.n_arrays];
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const long long c = (long long)atomicAdd(a.counter, 1ull);
-            int arr = -1;
-            if (c < total) {
-                int lo = 0, hi = a.n_arrays - 1;  // largest array with chunk_off <= c
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (a.chunk_off[mid] <= c) lo = mid;
-                    else hi = mid - 1;
-                }
-                arr = lo;
-            }
-            s_c = c;
-            s_a = arr;
-        }
-        __syncthreads();
-        const long long c = s_c;
-        const int arr = s_a;
+    for (int it = 0;; ++it) {
+        const long long c = s_c[it & 1];
+        const int arr = s_a[it & 1];
         if (arr < 0) break;
+        if (threadIdx.x < 32) {
+            long long cn;
+            int an;
+            claim_chunk(a.counter, a.chunk_off, a.n_arrays, &cn, &an);
+            if (threadIdx.x == 0) {
+                s_c[(it + 1) & 1] = cn;
+                s_a[(it + 1) & 1] = an;
+            }
+        }
         const ArrDesc d = a.desc[arr];
         const long long zb = q_begin(a.z_off, arr);
         const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
