@@ -600,6 +600,8 @@ def setup_learned(args, ds, W, torch, dev, rank):
     job.bytes_per_lookup = (esz + 4 + (4 if five else 0))
     job.table = {k: info[k] for k in ("n_arrays", "n_direct", "n_learned", "n_fallback", "max_window",
                                       "train_steps", "train_ms", "final_loss", "table_bytes")}
+    if args.tune == "auto":  # the same engine autotuner as the batched form
+        job.table["tune"] = ds.ds_learned_autotune(L, Zd, zo, out)
     job.kernel_key = "learned_search_%s" % job.dtype_name
     job.launches_per_step = 2
     if five:
@@ -635,6 +637,8 @@ def setup_learned(args, ds, W, torch, dev, rank):
         res["fallback_queries_per_step"] = L.info()["fallback_queries"] - f0
         if not five:  # the model without the network, same search path
             lin = ds.ds_learned_build(Xd, cfg=ds.ds_learned_cfg_default(flags=ds.DS_LEARNED_LINEAR))
+            if args.tune == "auto":
+                ds.ds_learned_autotune(lin, Zd, None, out)
             res["linear_model"] = job.m / time_calls(torch, stream, lambda: ds.ds_learned_search(lin, Zd, out=out), 3)
             res["linear_model_max_window"] = lin.info()["max_window"]
             lin.free()

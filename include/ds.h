@@ -355,6 +355,13 @@ DS_API ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev
 DS_API ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
                             const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream);
 
+/* Time the launch configurations of ds_batch_autotune on these queries (the
+ * same engine serves the learned form), keep the fastest in the handle and
+ * return it in *best.  Single array: z_off_dev = NULL and m queries.  The
+ * outputs are overwritten with valid results.  Synchronous. */
+DS_API ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
+                                     int32_t *Icat_dev, void *stream, ds_tune_t *best);
+
 /* Host copy of array a's network parameters (1153 floats: W1[32] b1[32]
  * W2[32][32] b2[32] w3[32] b3) and its recorded error bounds: every knot i
  * satisfies floor(p(X_i)) - e_lo <= i <= floor(p(X_i)) + e_hi.  mode: 0 direct,

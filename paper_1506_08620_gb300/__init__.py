@@ -297,6 +297,17 @@ def ds_learned_search(L, Z, z_off=None, Y=None, out=None, y_out=None, stream=Non
     return (out, y_out) if Y is not None else out
 
 
+def ds_learned_autotune(L, Z, z_off=None, out=None, stream=None):
+    """Autotune the learned handle's launch configuration on these queries; returns the chosen one."""
+    if out is None:
+        out = torch.empty(Z.numel(), dtype=torch.int32, device=Z.device)
+    best = _abi.ds_tune_t()
+    zo = _dev(z_off, "z_off", torch.int64) if z_off is not None else None
+    check(lib().ds_learned_autotune(L.ptr, _dev(Z, "Z", L.dtype), zo, Z.numel(), _dev(out, "out", torch.int32),
+                                    _stream(stream), ctypes.byref(best)), "ds_learned_autotune")
+    return best.as_dict()
+
+
 def ds_learned_array(L, a):
     theta = torch.empty(1153, dtype=torch.float32)
     e_lo = ctypes.c_int32(); e_hi = ctypes.c_int32(); mode = ctypes.c_int32()

@@ -854,6 +854,17 @@ ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int
                              z_off_dev ? 0 : m, Ycat_dev, y_out_dev, Icat_dev, (cudaStream_t)stream);
 }
 
+ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
+                              int32_t *Icat_dev, void *stream, ds_tune_t *best)
+{
+    if (!learned_ok(L) || !Zcat_dev || !Icat_dev || (!z_off_dev && (m < 1 || L->eng.n_arrays != 1))) {
+        ds::set_error("ds_learned_autotune: bad argument");
+        return DS_E_ARG;
+    }
+    return ds::engine_autotune(&L->eng, Zcat_dev, (const long long *)z_off_dev, z_off_dev ? 0 : m, Icat_dev,
+                               (cudaStream_t)stream, best);
+}
+
 ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, int32_t *e_lo, int32_t *e_hi,
                            int32_t *mode)
 {

@@ -260,8 +260,10 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         const long long v0 = va / L, nv = (vb - va) / L;
         const V *Zv = reinterpret_cast<const V *>(a.Z) + v0;
         IV *Iv = reinterpret_cast<IV *>(a.I) + v0;
-        // software pipeline: the next tile's queries are loaded while this
-        // tile's table gathers are in flight
+        // direct-only kernels: software pipeline, the next tile's queries are
+        // loaded while this tile's table gathers are in flight (the general
+        // kernel is at its register limit already)
+        constexpr bool PREFETCH = KIND != KIND_ALL;
         V zn[VPT];
         auto load_tile = [&](long long base) {
 #pragma unroll
@@ -270,12 +272,18 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
                 zn[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
             }
         };
-        if (tid < nv) load_tile(tid);
+        if (PREFETCH && tid < nv) load_tile(tid);
         for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
             V zv[VPT];
+            if constexpr (PREFETCH) {
 #pragma unroll
-            for (int v = 0; v < VPT; ++v) zv[v] = zn[v];
-            if (base + (long long)VPT * nthr < nv) load_tile(base + (long long)VPT * nthr);
+                for (int v = 0; v < VPT; ++v) zv[v] = zn[v];
+                if (base + (long long)VPT * nthr < nv) load_tile(base + (long long)VPT * nthr);
+            } else {
+                load_tile(base);
+#pragma unroll
+                for (int v = 0; v < VPT; ++v) zv[v] = zn[v];
+            }
             const T *zs4 = reinterpret_cast<const T *>(zv);
             int32_t r[NQ];
             answer_block<T, NQ, KIND, SM>(a, d, K, X, zs4, r, pol);

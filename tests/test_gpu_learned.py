@@ -231,3 +231,23 @@ def test_workload5_full_size(ds):
     gi = xo[arr_all] + I.long()
     assert bool((Xd[gi] <= Zd).all()) and bool((Zd < Xd[gi + 1]).all())
     L.free()
+
+
+def test_autotuned_learned_stays_exact(ds):
+    # the autotuner tries every launch configuration (block and warp claims,
+    # staging limits) on these queries; the answers of the one it keeps, and of
+    # the batched interpolating form after its own tuning, stay exact
+    w = _learned_small(n_knots=50_001, m=400_000)
+    X, Z = w["X"], _queries(w["X"], w["Z"], np.float64)
+    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
+    tune = ds.ds_learned_autotune(L, _cuda(Z))
+    assert tune["block"] in (128, 256, 512) and tune["ms"] > 0
+    assert np.array_equal(L.search(_cuda(Z)).cpu().numpy(), oracle.upper_bound(X, Z))
+    L.free()
+    w5 = W.workload5(n_arrays=24, size_lo=1 << 10, size_hi=1 << 16, total_queries=1 << 20)
+    Xcat, Ycat, x_off, Zcat, z_off = w5["Xcat"], w5["Ycat"], w5["x_off"], w5["Zcat"], w5["z_off"]
+    L5 = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=_cfg(ds, steps=50))
+    ds.ds_learned_autotune(L5, _cuda(Zcat), _cuda(z_off))
+    I, _ = L5.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
+    assert np.array_equal(I.cpu().numpy(), oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)[0])
+    L5.free()
