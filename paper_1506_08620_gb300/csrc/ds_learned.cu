@@ -58,56 +58,20 @@ __device__ __forceinline__ uint32_t below(uint32_t x, uint32_t n) { return (uint
 // ------------------------------------------------------------------ network
 __device__ __forceinline__ float relu(float a) { return a > 0.f ? a : 0.f; }
 
-// Forward and backward of one sample; returns out and fills the per-sample
-// vectors the gradient needs.  dscale = 2 / (batch size).
-__device__ __forceinline__ float mlp_sample(const float *th, float u, float y, float dscale, float *h1, float *da1,
-                                            float *da2, float *h2, float *dout)
-{
-    float a1[HID], a2[HID];
-#pragma unroll
-    for (int m = 0; m < HID; ++m) {
-        a1[m] = __fmaf_rn(th[OW1 + m], u, th[OB1 + m]);
-        h1[m] = relu(a1[m]);
-    }
-#pragma unroll
-    for (int n = 0; n < HID; ++n) {
-        float acc = th[OB2 + n];
-#pragma unroll
-        for (int m = 0; m < HID; ++m) acc = __fmaf_rn(th[OW2 + n * HID + m], h1[m], acc);
-        a2[n] = acc;
-        h2[n] = relu(acc);
-    }
-    float out = th[OB3];
-#pragma unroll
-    for (int n = 0; n < HID; ++n) out = __fmaf_rn(th[OW3 + n], h2[n], out);
-    const float d = dscale * (out - y);
-    *dout = d;
-#pragma unroll
-    for (int n = 0; n < HID; ++n) da2[n] = a2[n] > 0.f ? d * th[OW3 + n] : 0.f;
-#pragma unroll
-    for (int m = 0; m < HID; ++m) {
-        float acc = 0.f;
-#pragma unroll
-        for (int n = 0; n < HID; ++n) acc = __fmaf_rn(th[OW2 + n * HID + m], da2[n], acc);
-        da1[m] = a1[m] > 0.f ? acc : 0.f;
-    }
-    return out;
-}
+// Shared-memory image of the parameters: theta, then W2 transposed (W2T[m][n]
+// = W2[n][m]), so that both the forward layer (column m of W2 times h1_m) and
+// the backward product (row m of W2T times da2) read 32 consecutive floats.
+constexpr size_t W2T_OFF = TH_BYTES;
+constexpr size_t PARAM_SMEM = TH_BYTES + HID * HID * sizeof(float);
 
-__device__ __forceinline__ float mlp_forward1(const float *th, float u)
+__device__ __forceinline__ void load_params(const float *theta, float *sm)
 {
-    float h1[HID];
-#pragma unroll
-    for (int m = 0; m < HID; ++m) h1[m] = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
-    float out = th[OB3];
-#pragma unroll
-    for (int n = 0; n < HID; ++n) {
-        float acc = th[OB2 + n];
-#pragma unroll
-        for (int m = 0; m < HID; ++m) acc = __fmaf_rn(th[OW2 + n * HID + m], h1[m], acc);
-        out = __fmaf_rn(th[OW3 + n], relu(acc), out);
+    float *w2t = sm + W2T_OFF / sizeof(float);
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) sm[p] = theta[p];
+    for (int p = threadIdx.x; p < HID * HID; p += blockDim.x) {
+        const int n = p / HID, m = p % HID;
+        w2t[m * HID + n] = theta[OW2 + p];
     }
-    return out;
 }
 
 // Shared-memory tile of one block's samples and the block's gradient sum.
@@ -116,23 +80,138 @@ struct GradTile {
     float H1[TB][HID + 1], DA1[TB][HID + 1], DA2[TB][HID + 1], H2[TB][HID + 1];
 };
 
+// Forward and backward of one sample (the calling thread's), written straight
+// into its row of the tile; returns out.  dscale = 2 / (batch size).  Layer 2
+// is accumulated as sum_m h1_m * W2[:, m] with the 32 outputs in registers;
+// the loops over m stay rolled (unrolling them lets the scheduler hoist all
+// 256 weight loads, which spills), and h1 lives in the tile row.
+__device__ __forceinline__ float mlp_sample(const float *sm, float u, float y, float dscale, GradTile &t)
+{
+    const float *th = sm;
+    const float4 *w2t = reinterpret_cast<const float4 *>(sm + W2T_OFF / sizeof(float));
+    const int s = threadIdx.x;
+    float a2[HID];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) a2[n] = th[OB2 + n];
+#pragma unroll 1
+    for (int m = 0; m < HID; ++m) {
+        const float h = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
+        t.H1[s][m] = h;
+#pragma unroll
+        for (int q = 0; q < HID / 4; ++q) {
+            const float4 w = w2t[m * (HID / 4) + q];
+            a2[4 * q + 0] = __fmaf_rn(w.x, h, a2[4 * q + 0]);
+            a2[4 * q + 1] = __fmaf_rn(w.y, h, a2[4 * q + 1]);
+            a2[4 * q + 2] = __fmaf_rn(w.z, h, a2[4 * q + 2]);
+            a2[4 * q + 3] = __fmaf_rn(w.w, h, a2[4 * q + 3]);
+        }
+    }
+    float out = th[OB3];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) {
+        const float h2 = relu(a2[n]);
+        t.H2[s][n] = h2;
+        out = __fmaf_rn(th[OW3 + n], h2, out);
+    }
+    const float d = dscale * (out - y);
+    // da2 replaces a2 (a2 > 0 exactly where h2 > 0)
+#pragma unroll
+    for (int n = 0; n < HID; ++n) {
+        a2[n] = a2[n] > 0.f ? d * th[OW3 + n] : 0.f;
+        t.DA2[s][n] = a2[n];
+    }
+#pragma unroll 1
+    for (int m = 0; m < HID; ++m) {
+        float acc = 0.f;
+#pragma unroll
+        for (int q = 0; q < HID / 4; ++q) {
+            const float4 w = w2t[m * (HID / 4) + q];
+            acc = __fmaf_rn(w.x, a2[4 * q + 0], acc);
+            acc = __fmaf_rn(w.y, a2[4 * q + 1], acc);
+            acc = __fmaf_rn(w.z, a2[4 * q + 2], acc);
+            acc = __fmaf_rn(w.w, a2[4 * q + 3], acc);
+        }
+        t.DA1[s][m] = t.H1[s][m] > 0.f ? acc : 0.f;  // a1 > 0 exactly where h1 > 0
+    }
+    t.U[s] = u;
+    t.DOUT[s] = d;
+    const float r = out - y;
+    t.LOSS[s] = r * r;
+    return out;
+}
+
+__device__ __forceinline__ float mlp_forward1(const float *sm, float u)
+{
+    const float *th = sm;
+    const float4 *w2t = reinterpret_cast<const float4 *>(sm + W2T_OFF / sizeof(float));
+    float a2[HID];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) a2[n] = th[OB2 + n];
+#pragma unroll 1
+    for (int m = 0; m < HID; ++m) {
+        const float h = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
+#pragma unroll
+        for (int q = 0; q < HID / 4; ++q) {
+            const float4 w = w2t[m * (HID / 4) + q];
+            a2[4 * q + 0] = __fmaf_rn(w.x, h, a2[4 * q + 0]);
+            a2[4 * q + 1] = __fmaf_rn(w.y, h, a2[4 * q + 1]);
+            a2[4 * q + 2] = __fmaf_rn(w.z, h, a2[4 * q + 2]);
+            a2[4 * q + 3] = __fmaf_rn(w.w, h, a2[4 * q + 3]);
+        }
+    }
+    float out = th[OB3];
+#pragma unroll
+    for (int n = 0; n < HID; ++n) out = __fmaf_rn(th[OW3 + n], relu(a2[n]), out);
+    return out;
+}
+
+// Sum of the per-sample gradients of the tile's `count` samples, in parameter
+// order.  The 32x32 block of W2 is a product DA2^T H1 over the samples: each
+// thread of a 128-thread block owns 4 rows x 2 columns of it; the other 129
+// parameters take one thread each.
 __device__ __forceinline__ void tile_gradient(const GradTile &t, int count, float *gout)
 {
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int base = 0; base < HID * HID; base += 8 * blockDim.x) {
+        const int cell = base / 8 + tid;  // 4 x 2 block index
+        if (cell < HID * HID / 8) {
+            const int n0 = (cell / (HID / 2)) * 4, m0 = (cell % (HID / 2)) * 2;
+            float g[4][2] = {};
+            for (int s = 0; s < count; ++s) {
+                const float h0 = t.H1[s][m0], h1 = t.H1[s][m0 + 1];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float dn = t.DA2[s][n0 + k];
+                    g[k][0] = __fmaf_rn(dn, h0, g[k][0]);
+                    g[k][1] = __fmaf_rn(dn, h1, g[k][1]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                gout[OW2 + (n0 + k) * HID + m0] = g[k][0];
+                gout[OW2 + (n0 + k) * HID + m0 + 1] = g[k][1];
+            }
+        }
+    }
+    // W1, b1, b2, W3, b3: 129 sums over the samples
+    for (int q = tid; q < 4 * HID + 1; q += blockDim.x) {
         float acc = 0.f;
-        if (p < OB1) {
-            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DA1[s][p], t.U[s], acc);
-        } else if (p < OW2) {
-            for (int s = 0; s < count; ++s) acc += t.DA1[s][p - OB1];
-        } else if (p < OB2) {
-            const int n = (p - OW2) / HID, m = (p - OW2) % HID;
-            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DA2[s][n], t.H1[s][m], acc);
-        } else if (p < OW3) {
-            for (int s = 0; s < count; ++s) acc += t.DA2[s][p - OB2];
-        } else if (p < OB3) {
-            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DOUT[s], t.H2[s][p - OW3], acc);
-        } else {
+        int p;
+        if (q < HID) {  // W1[m] = sum DA1[s][m] u_s
+            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DA1[s][q], t.U[s], acc);
+            p = OW1 + q;
+        } else if (q < 2 * HID) {  // b1
+            for (int s = 0; s < count; ++s) acc += t.DA1[s][q - HID];
+            p = OB1 + q - HID;
+        } else if (q < 3 * HID) {  // b2
+            for (int s = 0; s < count; ++s) acc += t.DA2[s][q - 2 * HID];
+            p = OB2 + q - 2 * HID;
+        } else if (q < 4 * HID) {  // W3[n] = sum DOUT[s] H2[s][n]
+            for (int s = 0; s < count; ++s) acc = __fmaf_rn(t.DOUT[s], t.H2[s][q - 3 * HID], acc);
+            p = OW3 + q - 3 * HID;
+        } else {  // b3
             for (int s = 0; s < count; ++s) acc += t.DOUT[s];
+            p = OB3;
         }
         gout[p] = acc;
     }
@@ -145,40 +224,19 @@ __device__ __forceinline__ float tile_loss(const GradTile &t, int count)
     return l;
 }
 
-__device__ __forceinline__ void store_sample(GradTile &t, float u, float y, float out, float dout, const float *h1,
-                                             const float *da1, const float *da2, const float *h2)
-{
-    const int s = threadIdx.x;
-    t.U[s] = u;
-    t.DOUT[s] = dout;
-    const float r = out - y;
-    t.LOSS[s] = r * r;
-#pragma unroll
-    for (int m = 0; m < HID; ++m) {
-        t.H1[s][m] = h1[m];
-        t.DA1[s][m] = da1[m];
-        t.DA2[s][m] = da2[m];
-        t.H2[s][m] = h2[m];
-    }
-}
-
 // Gradient of the mean squared error over explicit samples: block b writes
 // the sum over its samples into partial[b][*] and partial_loss[b].
 __global__ void __launch_bounds__(TB) k_grad_explicit(const float *theta, const float *u, const float *y, long long n,
                                                       float *partial, float *partial_loss)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float *th = reinterpret_cast<float *>(sm_raw);
-    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + TH_BYTES);
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    float *sm = reinterpret_cast<float *>(sm_raw);
+    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + PARAM_SMEM);
+    load_params(theta, sm);
     __syncthreads();
     const long long i = (long long)blockIdx.x * TB + threadIdx.x;
     const int count = (int)min((long long)TB, n - (long long)blockIdx.x * TB);
-    if (i < n) {
-        float h1[HID], da1[HID], da2[HID], h2[HID], dout;
-        const float out = mlp_sample(th, u[i], y[i], 2.0f / (float)n, h1, da1, da2, h2, &dout);
-        store_sample(t, u[i], y[i], out, dout, h1, da1, da2, h2);
-    }
+    if (i < n) mlp_sample(sm, u[i], y[i], 2.0f / (float)n, t);
     __syncthreads();
     tile_gradient(t, count, partial + (size_t)blockIdx.x * NP);
     if (threadIdx.x == 0) partial_loss[blockIdx.x] = tile_loss(t, count);
@@ -218,11 +276,11 @@ __global__ void k_adam_explicit(float *theta, float *m, float *v, const float *g
 
 __global__ void k_forward(const float *theta, const float *u, long long n, float *out)
 {
-    __shared__ float th[NP];
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    __shared__ __align__(16) float sm[PARAM_SMEM / sizeof(float)];
+    load_params(theta, sm);
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        out[i] = mlp_forward1(th, u[i]);
+        out[i] = mlp_forward1(sm, u[i]);
 }
 
 // ------------------------------------------------------------------ training on an array
@@ -248,11 +306,10 @@ template <typename T>
 __global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm_raw[];
-    float *th = reinterpret_cast<float *>(sm_raw);
-    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + TH_BYTES);
+    float *sm = reinterpret_cast<float *>(sm_raw);
+    GradTile &t = *reinterpret_cast<GradTile *>(sm_raw + PARAM_SMEM);
     const int model = blockIdx.y;
-    const float *theta = a.theta + (size_t)model * NP;
-    for (int p = threadIdx.x; p < NP; p += blockDim.x) th[p] = theta[p];
+    load_params(a.theta + (size_t)model * NP, sm);
     const ArrDesc d = a.desc[a.model_arr[model]];
     const T *X = reinterpret_cast<const T *>(a.blob + d.xg);
     const int step = a.step[model];
@@ -269,10 +326,8 @@ __global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
         u = pred_u<T>(X[i], d);
         y = (float)i / (float)d.n;
     }
-    float h1[HID], da1[HID], da2[HID], h2[HID], dout;
     const float res = y - u;  // the network's target: deviation from the linear model
-    const float out = mlp_sample(th, u, res, 2.0f / (float)(a.gb * TB), h1, da1, da2, h2, &dout);
-    store_sample(t, u, res, out, dout, h1, da1, da2, h2);
+    mlp_sample(sm, u, res, 2.0f / (float)(a.gb * TB), t);
     __syncthreads();
     tile_gradient(t, TB, a.partial + ((size_t)model * a.gb + blockIdx.x) * NP);
     if (threadIdx.x == 0) a.partial_loss[(size_t)model * a.gb + blockIdx.x] = tile_loss(t, TB);
@@ -611,7 +666,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             ta.desc = e.desc_dev; ta.blob = e.blob; ta.model_arr = model_arr; ta.pool = pool; ta.pool_off = pool_off_d;
             ta.theta = theta; ta.m = mom; ta.v = vel; ta.partial = part; ta.partial_loss = plos; ta.loss = loss;
             ta.step = step; ta.gb = gb; ta.steps = cfg.steps; ta.lr = cfg.lr; ta.seed_lo = slo; ta.seed_hi = shi;
-            const size_t smem = TH_BYTES + sizeof(GradTile);
+            const size_t smem = PARAM_SMEM + sizeof(GradTile);
             ce = cudaFuncSetAttribute(k_train_grad<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -909,7 +964,7 @@ ds_status ds_mlp_loss_grad(const float *theta_dev, const float *u_dev, const flo
     float *part = nullptr, *plos = nullptr;
     DS_TRY_CUDA(cudaMallocAsync(&part, sizeof(float) * (size_t)nb * ds::NP, s));
     cudaError_t ce = cudaMallocAsync(&plos, sizeof(float) * (size_t)nb, s);
-    const size_t smem = ds::TH_BYTES + sizeof(ds::GradTile);
+    const size_t smem = ds::PARAM_SMEM + sizeof(ds::GradTile);
     if (ce == cudaSuccess)
         ce = cudaFuncSetAttribute(ds::k_grad_explicit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ce == cudaSuccess) {
