@@ -274,3 +274,34 @@ def test_packed_float64_tables_across_cell_ranges(ds, flags):
         ref = oracle.upper_bound(X, Z)
         assert np.array_equal(got, ref), (k, int(np.count_nonzero(got != ref)))
         idx.free()
+
+
+@pytest.mark.slow
+def test_table_near_the_32_bit_cell_limit(ds):
+    # one narrow gap sets H so that R = trunc(m(H D_N)) is close to 2^32 - 1:
+    # a 16 GB table; cells and the clamp at R work in the top of the uint32 range
+    g = np.random.default_rng(71)
+    gaps = g.uniform(0.5, 1.5, 1000)
+    gaps[500] = 1.0 / 3.9e6
+    X = W.knots_from_gaps(0.0, gaps, np.float64)
+    hr = oracle.compute_hr(X)
+    assert hr["status"] == oracle.OR_OK and hr["R"] > 3.5e9
+    idx = ds.ds_build(_cuda(X))
+    info = idx.info()
+    assert info["H"] == hr["H"] and info["R"] == hr["R"]
+    Z = _queries(X, g, 1_000_000)
+    assert np.array_equal(ds.ds_search(idx, _cuda(Z)).cpu().numpy(), oracle.upper_bound(X, Z))
+    idx.free()
+
+
+@pytest.mark.slow
+def test_array_of_2p28_knots(ds):
+    # indices near 2^28 in the int32 results; sampled queries and the array's ends
+    g = np.random.default_rng(72)
+    X = W.knots_from_gaps(-5.0, g.uniform(0.5, 1.5, 1 << 28), np.float64)
+    idx = ds.ds_build(_cuda(X))
+    assert idx.info()["R"] == oracle.compute_hr(X)["R"]
+    Z = np.concatenate([W.uniform_queries(g, X[0], X[-1], 1 << 20, np.float64), X[-1000:],
+                        np.nextafter(X[-1000:], -np.inf), X[:1000], np.array([np.inf, -np.inf, X[-1] + 1.0])])
+    assert np.array_equal(ds.ds_search(idx, _cuda(Z)).cpu().numpy(), oracle.upper_bound(X, Z))
+    idx.free()
