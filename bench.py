@@ -557,7 +557,7 @@ def setup_batched(args, ds, W, torch, dev, rank):
     job.e2e_out = Ip
 
     def extras(stream):
-        # the same engine without knot fingerprints in K (every query in a cell
+        # the same engine without the knot fingerprints (every query in a cell
         # holding a knot reads the knot), autotuned the same way
         nf = ds.ds_batch_build(Xd, xo, ds.DS_NO_FINGERPRINT)
         t = ds.ds_batch_autotune(nf, Zd, zo, out)

@@ -12,18 +12,23 @@ namespace ds {
 
 // ---------------------------------------------------------------- kernels
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
-                              long long *chunk_off, unsigned long long *counter)
+                              const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
+                              unsigned long long *counter)
 {
+    // chunks of the array at claim position p
+    auto chunks_at = [&](int p) -> long long {
+        const int a = order ? order[p] : p;
+        long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
+        q = q < 0 ? 0 : q;
+        const long long c = chunk_len(desc[a], chunk, smem_limit);
+        return (q + c - 1) / c;
+    };
     __shared__ long long warp_sum[32];
     const int per = (n_arrays + blockDim.x - 1) / blockDim.x;
     const int a0 = threadIdx.x * per;
     const int a1 = min(a0 + per, n_arrays);
     long long local = 0;
-    for (int a = a0; a < a1; ++a) {
-        long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
-        q = q < 0 ? 0 : q;
-        local += (q + chunk - 1) / chunk;
-    }
+    for (int a = a0; a < a1; ++a) local += chunks_at(a);
     // block-wide exclusive scan of `local`
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     long long incl = local;
@@ -49,18 +54,16 @@ __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_
     long long prefix = warp_sum[wid] + incl - local;
     for (int a = a0; a < a1; ++a) {
         chunk_off[a] = prefix;
-        long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
-        q = q < 0 ? 0 : q;
-        prefix += (q + chunk - 1) / chunk;
+        prefix += chunks_at(a);
     }
     if (a1 == n_arrays && a0 < a1) chunk_off[n_arrays] = prefix;
     if (n_arrays <= 0 && threadIdx.x == 0) chunk_off[0] = 0;
     if (threadIdx.x == 0) *counter = 0;
 }
 
-__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
-                             const long long *__restrict__ x_off, const long long *__restrict__ kc_off, int n_arrays,
-                             const ArrDesc *__restrict__ desc, unsigned char *blob)
+__global__ void k_seg_rank_base(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
+                                const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
+                                unsigned char *blob)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -78,26 +81,39 @@ __global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const uint8_t *__re
         const long long lc = c - kc_off[arr];
         const long long start = x_off[arr];
         const long long N = d.n;
-        uint32_t *K = reinterpret_cast<uint32_t *>(blob + d.img);
+        uint32_t *Wd = reinterpret_cast<uint32_t *>(blob + d.img);  // two words per group
         const long long i = lc * 32 + lane;
         const uint32_t Fi = F[start + (i <= N ? i : N)];
         const long long prev = lc == 0 ? -1 : (long long)F[start + lc * 32 - 1];
         const long long last = (long long)__shfl_sync(0xffffffffu, Fi, 31);
-        for (long long base = prev + 1; base <= last; base += 32) {
-            const long long j = base + lane;
+        // groups g with prev < 8 g <= last: K_{8 g} is the first lane with F >= 8 g
+        const long long g_first = (prev + 1 + 7) >> RANK_SHIFT, g_last = last >> RANK_SHIFT;
+        for (long long gb = g_first; gb <= g_last; gb += 32) {
+            const long long g = gb + lane;
+            const long long j = g << RANK_SHIFT;
             int k = 0;
 #pragma unroll
             for (int s = 16; s >= 1; s >>= 1) {
                 const uint32_t Fc = __shfl_sync(0xffffffffu, Fi, k + s - 1);
                 if ((long long)Fc < j) k += s;
             }
-            const uint32_t Fk = __shfl_sync(0xffffffffu, Fi, k);
-            if (j <= last) {
-                const long long t = lc * 32 + k;
-                uint32_t e = (uint32_t)t;
-                if ((long long)Fk == j) e |= KNOT_FLAG | (d.aux ? (uint32_t)G[start + t] << FP_SHIFT : 0u);
-                K[j] = e;
-            }
+            if (g <= g_last) Wd[2 * g] = (uint32_t)(lc * 32 + k);
+        }
+    }
+}
+
+__global__ void k_seg_rank_bits(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
+                                const Segment *__restrict__ segs, int n_segs, const long long *__restrict__ x_off,
+                                const ArrDesc *__restrict__ desc, unsigned char *blob)
+{
+    for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
+        const Segment sg = segs[s];
+        const ArrDesc d = desc[sg.arr];
+        if (d.mode != MODE_DIRECT) continue;
+        uint32_t *Wd = reinterpret_cast<uint32_t *>(blob + d.img);
+        for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
+            const uint32_t f = F[i], b = f & 7u;
+            atomicOr(&Wd[2 * (long long)(f >> RANK_SHIFT) + 1], (1u << b) | (((uint32_t)G[i] & 7u) << (8u + 3u * b)));
         }
     }
 }
@@ -110,6 +126,7 @@ void engine_free(Engine *e)
     if (e->desc_dev) cudaFree(e->desc_dev);
     if (e->blob) cudaFree(e->blob);
     if (e->chunk_off) cudaFree(e->chunk_off);
+    if (e->order) cudaFree(e->order);
     if (e->counter) cudaFree(e->counter);
     if (e->dev_err) cudaFree(e->dev_err);
     if (e->seg_x) cudaFree(e->seg_x);
@@ -244,13 +261,14 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 d.R = (uint32_t)hs[a].R;
                 d.H = hs[a].H;
                 d.W = hs[a].W;
-                const size_t kb = round_up(((size_t)hs[a].R + 1) * 4, 16);
-                d.x_in_img = (uint32_t)std::min<size_t>(kb, 0xFFFFFFFFu);
+                // the image is the rank table (8 bytes per 8 cells); the knots
+                // follow it and stay in global memory
+                const size_t kb = round_up((((size_t)hs[a].R >> RANK_SHIFT) + 1) * 8, 16);
+                d.x_in_img = NO_X_IN_IMG;
                 d.xg = (long long)(off + kb);
                 const size_t xb = round_up((size_t)nk * sizeof(T), 16);
-                const size_t ib = kb + xb;
-                d.img_bytes = ib <= 0xFFFFFFF0u ? (uint32_t)ib : 0u;
-                off += ib;
+                d.img_bytes = kb <= 0xFFFFFFF0u ? (uint32_t)kb : 0u;
+                off += kb + xb;
                 kc[a + 1] = (nk + 31) / 32;
                 e->n_direct += 1;
                 e->R_total += (unsigned long long)hs[a].R + 1;
@@ -273,10 +291,8 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
             // X0 and XN are read back below
         }
         if (rc != DS_OK) break;
-        // fingerprints in K: for all direct arrays or none (t needs 24 bits at most)
+        // knot fingerprints of the rank tables: used unless turned off
         e->fingerprints = !(flags & DS_NO_FINGERPRINT) && e->n_direct > 0;
-        for (int a = 0; a < A; ++a)
-            if (e->desc_host[a].mode == MODE_DIRECT && x_off[a + 1] - x_off[a] > FP_MAX_KNOTS) e->fingerprints = false;
         for (int a = 0; a < A; ++a)
             if (e->desc_host[a].mode == MODE_DIRECT) e->desc_host[a].aux = e->fingerprints ? 1 : 0;
         // knots X_0, X_N per array (for the descriptors)
@@ -324,7 +340,8 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
         const long long kchunks = kc[A];
         if (kchunks > 0) {
             const long long kgrid = std::min<long long>((kchunks * 32 + 255) / 256, (long long)e->props.num_sms * 16);
-            k_seg_fill_K<<<(int)kgrid, 256, 0, s>>>(F, G, x_off_dev, kc_dev, A, e->desc_dev, e->blob);
+            k_seg_rank_base<<<(int)kgrid, 256, 0, s>>>(F, x_off_dev, kc_dev, A, e->desc_dev, e->blob);
+            k_seg_rank_bits<<<sgrid, 256, 0, s>>>(F, G, segs_dev, n_segs, x_off_dev, e->desc_dev, e->blob);
         }
         cudaError_t ce = cudaGetLastError();
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -370,6 +387,15 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
     e->n_knots = x_off[n_arrays];
     if (x_off_host) *x_off_host = x_off;
     DS_TRY_CUDA(cudaMalloc(&e->chunk_off, sizeof(long long) * (size_t)(n_arrays + 1)));
+    {  // claim order: the arrays with the most knots first (longest-processing-time first)
+        std::vector<int> order(n_arrays);
+        for (int a = 0; a < n_arrays; ++a) order[a] = a;
+        std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+            return x_off[p + 1] - x_off[p] > x_off[q + 1] - x_off[q];
+        });
+        DS_TRY_CUDA(cudaMalloc(&e->order, sizeof(int) * (size_t)std::max(n_arrays, 1)));
+        DS_TRY_CUDA(cudaMemcpy(e->order, order.data(), sizeof(int) * (size_t)n_arrays, cudaMemcpyHostToDevice));
+    }
     DS_TRY_CUDA(cudaMalloc(&e->counter, 2 * sizeof(unsigned long long)));
     DS_TRY_CUDA(cudaMemset(e->counter, 0, 2 * sizeof(unsigned long long)));
     DS_TRY_CUDA(cudaMalloc(&e->dev_err, sizeof(int)));
@@ -388,56 +414,68 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
 
 // ---------------------------------------------------------------- launch
 // Warp-claimed kernels exist for the vector path (the scalar path, for
-// misaligned buffers, always claims per block).
+// misaligned buffers, always claims per block); 1024-thread blocks for the
+// direct kinds at one vector per thread, block-claimed.
 template <typename T, int VPT, bool INTERP, int KIND>
-static const void *pick4(bool vec, bool warps)
+static const void *pick4(bool vec, bool warps, bool big)
 {
+    if constexpr (VPT == 1 && KIND != KIND_ALL)
+        if (vec && !warps && big) return (const void *)k_batch_search<T, 1, INTERP, true, KIND, false, 1024>;
     if (vec && warps) return (const void *)k_batch_search<T, VPT, INTERP, true, KIND, true>;
     return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, KIND>
                : (const void *)k_batch_search<T, VPT, INTERP, false, KIND>;
 }
 template <typename T, int VPT, bool INTERP>
-static const void *pick3(bool vec, bool warps, int kind)
+static const void *pick3(bool vec, bool warps, bool big, int kind)
 {
     switch (kind) {
-    case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec, warps);
-    case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps);
-    default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps);
+    case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec, warps, big);
+    case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
+    default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps, big);
     }
 }
 template <typename T, int VPT>
-static const void *pick2(bool interp, bool vec, bool warps, int kind)
+static const void *pick2(bool interp, bool vec, bool warps, bool big, int kind)
 {
-    return interp ? pick3<T, VPT, true>(vec, warps, kind) : pick3<T, VPT, false>(vec, warps, kind);
+    return interp ? pick3<T, VPT, true>(vec, warps, big, kind) : pick3<T, VPT, false>(vec, warps, big, kind);
 }
 template <typename T>
-static const void *pick1(int vpt, bool interp, bool vec, bool warps, int kind)
+static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, int kind)
 {
     switch (vpt) {
-    case 1: return pick2<T, 1>(interp, vec, warps, kind);
-    case 2: return pick2<T, 2>(interp, vec, warps, kind);
-    default: return pick2<T, 4>(interp, vec, warps, kind);
+    case 1: return pick2<T, 1>(interp, vec, warps, big, kind);
+    case 2: return pick2<T, 2>(interp, vec, warps, big, kind);
+    default: return pick2<T, 4>(interp, vec, warps, big, kind);
     }
 }
-static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps)
+static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0; }
+static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big)
 {
-    const bool direct_only = e->n_learned == 0 && e->n_fallback == 0;
-    const int kind = !direct_only ? KIND_ALL : (e->fingerprints ? KIND_DIRECT_FP : KIND_DIRECT);
-    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, warps, kind)
-                              : pick1<double>(vpt, interp, vec, warps, kind);
+    const int kind = !direct_only(e) ? KIND_ALL : (e->fingerprints ? KIND_DIRECT_FP : KIND_DIRECT);
+    return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, warps, big, kind)
+                              : pick1<double>(vpt, interp, vec, warps, big, kind);
 }
 
-static int clamp_block(int b) { return b == 128 || b == 512 ? b : 256; }
 static int clamp_vpt(int v) { return v == 1 || v == 2 ? v : 4; }
+// The block size a configuration runs with: 128, 256 or 512, or 1024 where a
+// 1024-thread kernel exists (direct arrays only, one vector per thread, block
+// claims, aligned buffers); a 1024 request falls back to 512 elsewhere.
+static int eff_block(const Engine *e, const ds_tune_t &t, bool vec)
+{
+    if (t.block == 1024)
+        return direct_only(e) && clamp_vpt(t.items) == 1 && vec && t.smem_limit >= 0 ? 1024 : 512;
+    return t.block == 128 || t.block == 512 ? t.block : 256;
+}
 
 // Resident blocks for a configuration (and the shared-memory opt-in).
 static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid)
 {
-    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0);
+    const int block = eff_block(e, t, vec);
+    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0, block == 1024);
     const int smem = std::max(0, t.smem_limit);
     if (smem > 0) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int occ = 0;
-    DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, clamp_block(t.block), smem));
+    DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
     if (occ < 1) {
         set_error("batched search: configuration cannot be resident (block %d, smem %d)", t.block, smem);
         return DS_E_ARG;
@@ -457,19 +495,21 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
                      (!interp || (uintptr_t)y_out % esz == 0);
     int grid = 0;
     DS_TRY(occupancy(e, t, interp, vec, &grid));
-    const int block = clamp_block(t.block), vpt = clamp_vpt(t.items);
+    const int block = eff_block(e, t, vec), vpt = clamp_vpt(t.items);
     const bool warps = vec && t.smem_limit < 0;  // nothing staged, and warps claim their own chunks
     const long long chunk = (long long)(warps ? 32 : block) * vpt * L * (warps ? CHUNK_TILES_WARP : CHUNK_TILES);
-    k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->chunk_off, e->counter);
+    const uint32_t smem_limit = (uint32_t)std::max(0, t.smem_limit);
+    k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->desc_dev, e->order, smem_limit,
+                                     e->chunk_off, e->counter);
     DS_TRY_CUDA(cudaGetLastError());
-    const void *fn = pick_kernel(e, vpt, interp, vec, warps);
+    const void *fn = pick_kernel(e, vpt, interp, vec, warps, block == 1024);
     if (e->dtype == DS_F32) {
         BatchArgs<float> a;
         memset(&a, 0, sizeof(a));
         a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
         a.Z = (const float *)Z; a.I = I; a.Y = (const float *)Y; a.y_out = (float *)y_out;
-        a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1; a.chunk = chunk;
-        a.smem_limit = (uint32_t)std::max(0, t.smem_limit); a.checked = (e->flags & DS_CHECKED) != 0;
+        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1;
+        a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
         a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
         void *args[] = {&a};
         DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
@@ -478,8 +518,8 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
         memset(&a, 0, sizeof(a));
         a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
         a.Z = (const double *)Z; a.I = I; a.Y = (const double *)Y; a.y_out = (double *)y_out;
-        a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1; a.chunk = chunk;
-        a.smem_limit = (uint32_t)std::max(0, t.smem_limit); a.checked = (e->flags & DS_CHECKED) != 0;
+        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1;
+        a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
         a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
         void *args[] = {&a};
         DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
@@ -536,9 +576,9 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
 ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
                           cudaStream_t s, ds_tune_t *best_out)
 {
-    const int blocks[] = {128, 256, 512};
+    const int blocks[] = {128, 256, 512, 1024};
     const int items[] = {1, 2, 4};
-    const int smems[] = {-1, 0, 24 * 1024, 48 * 1024, 96 * 1024, 200 * 1024};
+    const int smems[] = {-1, 0, 24 * 1024, 48 * 1024, 96 * 1024, 136 * 1024, 200 * 1024};
     cudaEvent_t e0, e1;
     DS_TRY_CUDA(cudaEventCreate(&e0));
     DS_TRY_CUDA(cudaEventCreate(&e1));
@@ -550,6 +590,7 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
         for (int it : items)
             for (int sm : smems) {
                 if (sm > e->props.max_smem_optin - 2048) continue;
+                if (b == 1024 && (it != 1 || sm < 0 || !direct_only(e))) continue;  // runs as 512
                 ds_tune_t t;
                 memset(&t, 0, sizeof(t));
                 t.block = b;
@@ -698,7 +739,7 @@ ds_status ds_batch_set_tune(ds_batch *b, const ds_tune_t *cfg)
         return DS_E_ARG;
     }
     ds_tune_t t = *cfg;
-    t.block = t.block == 128 || t.block == 512 ? t.block : 256;
+    t.block = t.block == 128 || t.block == 512 || t.block == 1024 ? t.block : 256;
     t.items = t.items == 1 || t.items == 2 ? t.items : 4;
     int grid = 0;
     DS_TRY(ds::occupancy(&b->eng, t, false, true, &grid));

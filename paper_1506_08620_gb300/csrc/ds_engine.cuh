@@ -26,6 +26,7 @@ struct Engine {
     size_t blob_bytes = 0;
     size_t table_bytes = 0;
     long long *chunk_off = nullptr;
+    int *order = nullptr;  // claim order of the arrays: most knots first
     unsigned long long *counter = nullptr;  // [0] chunk counter, [1] certificate failures
     int *dev_err = nullptr;
     float *seg_x = nullptr, *seg_a = nullptr, *seg_b = nullptr;
@@ -37,7 +38,7 @@ struct Engine {
     long long h_updates = 0;
     unsigned long long R_total = 0;
     int n_direct = 0, n_learned = 0, n_fallback = 0;
-    bool fingerprints = false;  // every direct array's K carries knot fingerprints
+    bool fingerprints = false;  // the knot fingerprints of the rank tables are used
     double build_ms = 0;
 };
 

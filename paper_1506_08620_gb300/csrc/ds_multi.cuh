@@ -5,14 +5,15 @@
 // array.  A small planning kernel turns the query offsets z_off into chunk
 // offsets on the device (so the whole search is stream-ordered and can be
 // captured in a CUDA graph); persistent blocks then claim chunks with an
-// atomic counter.  A block that claims a chunk of an array whose image (its
-// K table and knots, or the learned predictor's tables) fits the shared-memory
-// budget stages that image with a bulk asynchronous copy, unless it already
-// holds it from its previous chunk; other arrays are read from global memory,
-// where the array being worked on stays L2-resident.
+// atomic counter.  A block that claims a chunk of an array whose image (the
+// rank table of a direct array, or the knots of a bisected one) fits the
+// shared-memory budget stages that image with a bulk asynchronous copy, unless
+// it already holds it from its previous chunk; other arrays are read from
+// global memory, where the array being worked on stays L2-resident.
 //
 // Per-array modes:
-//   MODE_DIRECT    Algorithm direct with the array's own H, W, R, K.
+//   MODE_DIRECT    Algorithm direct with the array's own H, W, R; K is held
+//                  as a rank table (below), one byte per cell.
 //   MODE_LEARNED   predicted index, bounded window, certificate, exact
 //                  fall-back; the window is searched in two fixed-depth
 //                  levels: over every 32nd knot (a small, L2-resident copy),
@@ -35,20 +36,22 @@ enum ArrMode : int32_t { MODE_DIRECT = 0, MODE_LEARNED = 1, MODE_BISECT = 2 };
 constexpr int SG_SHIFT = 5;
 constexpr int SG_STRIDE = 1 << SG_SHIFT;
 
+constexpr uint32_t NO_X_IN_IMG = 0xFFFFFFFFu;  // the image does not hold the knots
+
 // 128 bytes per array.
 struct __align__(16) ArrDesc {
-    long long img;        // byte offset of the staged image in the blob
+    long long img;        // byte offset of the staged image in the blob (direct: the rank table)
     long long xg;         // byte offset of the knots in the blob
     long long yoff;       // element offset of the array's knot values Y in the caller's Ycat
     uint32_t img_bytes;   // bytes of the image (multiple of 16), 0 if nothing to stage
-    uint32_t x_in_img;    // byte offset of the knots inside the image (direct mode)
+    uint32_t x_in_img;    // byte offset of the knots inside the image, or NO_X_IN_IMG
     int32_t n;            // N: the array has N+1 knots
     int32_t mode;         // ArrMode
     uint32_t R;           // direct: largest cell
     int32_t form;         // direct: FForm
     int32_t pbits;        // bisection over all knots: 2^floor(log2 N)
-    int32_t aux;          // learned: 2^floor(log2(window width)); direct: 1 if K entries carry
-                          // fingerprints (bits 24..30, t in bits 0..23)
+    int32_t aux;          // learned: 2^floor(log2(window width)); direct: 1 if the knot
+                          // fingerprints of the rank table are used
     double H, W, X0;      // direct: parameters in the array's precision (held exactly)
     double XN;            // last knot
     float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32)
@@ -70,10 +73,11 @@ template <typename T> struct BatchArgs {
     int32_t *I;
     const T *Y;                 // knot values (interpolation) or nullptr
     T *y_out;
-    long long *chunk_off;       // n_arrays+1 chunk offsets (written by the planner)
+    const int *order;           // claim order: position p serves array order[p] (nullptr: p itself)
+    long long *chunk_off;       // n_arrays+1 chunk offsets by position (written by the planner)
     unsigned long long *counter;// chunk counter (reset by the planner)
     unsigned long long *fallbacks; // learned: certificate failures
-    long long chunk;            // queries per chunk
+    long long chunk;            // queries per chunk of an array that is not staged (chunk_len)
     uint32_t smem_limit;        // largest image staged in shared memory
     int checked;
     int *err;
@@ -83,50 +87,121 @@ template <typename T> struct BatchArgs {
     const float *seg_b;
 };
 
-// Chunk offsets from the query offsets; resets the chunk counter.  One block.
+// Queries per chunk of an array.  A block stages the image of every chunk it
+// claims (its previous chunk is almost always of another array), so a staged
+// array gets chunks of about STAGE_Q_PER_BYTE queries per image byte, between
+// `base` and STAGE_MAX_CHUNKS * base, a multiple of `base`; the claim order
+// serves the largest arrays first, so the long chunks do not end the launch.
+constexpr long long STAGE_Q_PER_BYTE = 2;
+constexpr long long STAGE_MAX_CHUNKS = 8;
+
+__host__ __device__ __forceinline__ long long chunk_len(const ArrDesc &d, long long base, uint32_t smem_limit)
+{
+    if (d.img_bytes == 0 || d.img_bytes > smem_limit) return base;
+    const long long want = (long long)d.img_bytes * STAGE_Q_PER_BYTE;
+    const long long n = (want + base - 1) / base;
+    return (n < 1 ? 1 : (n > STAGE_MAX_CHUNKS ? STAGE_MAX_CHUNKS : n)) * base;
+}
+
+// Chunk offsets from the query offsets, in claim order; resets the chunk
+// counter.  One block.
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
-                              long long *chunk_off, unsigned long long *counter);
+                              const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
+                              unsigned long long *counter);
 
 __device__ __forceinline__ long long q_begin(const long long *z_off, int a) { return z_off ? z_off[a] : 0; }
 
 // ------------------------------------------------------------------ per-query pieces
-template <typename T>
-__device__ __forceinline__ uint32_t cell_rt(T z, const ArrDesc &d)
+// Cell j = trunc(v) (negative and NaN -> 0, saturated at 2^32 - 1) and the
+// knot fingerprint g = floor(8 (v - j)), the top 3 bits of the fractional
+// part of v.  Within one cell g is a non-decreasing function of v, so
+// g(v) < g(w) implies v < w and g(v) > g(w) implies v > w.  float: in float
+// arithmetic, where v - j is exact (j <= v < j + 1, Sterbenz) and so is the
+// product by 8 (negative and NaN v give g = 0); double: from the bit pattern
+// (cell_fp_bits), which keeps the scarce FP64 pipe free.
+constexpr uint32_t RANK_FP_ABOVE = 8;  // fingerprint of a query past the last cell
+
+__device__ __forceinline__ uint32_t cell_fp3(float v, uint32_t *g)
 {
-    using A = Arith<T>;
-    const T H = (T)d.H;
-    T v;
-    if (d.form == F_FMA) v = A::fma(H, z, -(T)d.W);
-    else if (d.form == F_PLAIN_X0ZERO) v = A::mul(H, z);
-    else v = A::mul(H, A::sub(z, (T)d.X0));
-    uint32_t j;
-    if constexpr (sizeof(T) == 8) j = trunc_u32_bits((double)v);
-    else j = A::trunc_u32(v);
-    return min(j, d.R);
+    const uint32_t j = __float2uint_rz(v);
+    *g = __float2uint_rz(__fmul_rn(__fsub_rn(v, __uint2float_rn(j)), 8.0f));
+    return j;
+}
+__device__ __forceinline__ uint32_t cell_fp3(double v, uint32_t *g)
+{
+    uint32_t g7;
+    const uint32_t j = cell_fp_bits(v, &g7);
+    *g = g7 >> 4;
+    return j;
 }
 
-// Cell and fingerprint of a query (cell_fp_bits); a query past the last
-// cell gets FP_ABOVE, larger than any knot's fingerprint in cell R.
+// f of a direct array for its queries and knots.  float: both forms as one
+// subtraction and one fused multiply-add, f = m(H m(z - x0) + c), with
+// (x0, c) = (X_0, 0) for Eq. f (H y + 0 rounds like the product H y) and
+// (0, -W) for the FMA form (z - 0 = z); double keeps one FP64 operation per
+// query where the form allows it.
+template <typename T> struct CellF;
+template <> struct CellF<float> {
+    float H, x0, c;
+    __device__ __forceinline__ explicit CellF(const ArrDesc &d)
+        : H((float)d.H), x0(d.form == F_FMA ? 0.0f : (float)d.X0), c(d.form == F_FMA ? -(float)d.W : 0.0f)
+    {
+    }
+    __device__ __forceinline__ float operator()(float z) const { return __fmaf_rn(H, __fsub_rn(z, x0), c); }
+};
+template <> struct CellF<double> {
+    double H, W, X0;
+    int form;
+    __device__ __forceinline__ explicit CellF(const ArrDesc &d) : H(d.H), W(d.W), X0(d.X0), form(d.form) {}
+    __device__ __forceinline__ double operator()(double z) const
+    {
+        if (form == F_FMA) return __fma_rn(H, z, -W);
+        if (form == F_PLAIN_X0ZERO) return __dmul_rn(H, z);
+        return __dmul_rn(H, __dsub_rn(z, X0));
+    }
+};
+
+// Cell and fingerprint of a query; a query past the last cell R gets cell R
+// and fingerprint RANK_FP_ABOVE, above every knot's.
 template <typename T>
-__device__ __forceinline__ uint32_t cell_rt_fp(T z, const ArrDesc &d, uint32_t *g)
+__device__ __forceinline__ uint32_t cell_q(const CellF<T> &f, uint32_t R, T z, uint32_t *g)
 {
-    using A = Arith<T>;
-    const T H = (T)d.H;
-    T v;
-    if (d.form == F_FMA) v = A::fma(H, z, -(T)d.W);
-    else if (d.form == F_PLAIN_X0ZERO) v = A::mul(H, z);
-    else v = A::mul(H, A::sub(z, (T)d.X0));
-    const uint32_t j = cell_fp_bits(v, g);
-    if (j > d.R) {
-        *g = FP_ABOVE;
-        return d.R;
+    const uint32_t j = cell_fp3(f(z), g);
+    if (j > R) {
+        *g = RANK_FP_ABOVE;
+        return R;
     }
     return j;
 }
 
-constexpr uint32_t FP_T_MASK = 0x00FFFFFFu;  // t of a K entry that carries a fingerprint
-constexpr int FP_SHIFT = 24;
-constexpr long long FP_MAX_KNOTS = 1ll << 24;
+// ------------------------------------------------------------------ rank table
+// With pairs (i, i+1) ComputeHR makes F strictly increasing, so a cell holds at
+// most one knot and K_j = min{i : F_i >= j} = #{i : F_i < j} (Eq. indexdef):
+// K is the rank function of the set of cells that hold a knot.  A direct
+// array's table stores it in one 8-byte word per group of 8 cells:
+//   x            K_{8 g}, the knots in cells before the group
+//   y bits 0..7  bit b set when cell 8 g + b holds a knot
+//   y bits 8..31 3 bits per cell: the fingerprint (cell_fp3) of its knot
+// so K_j = K_{8 g} + popc(knot bits below b).  One byte per cell (a quarter
+// of a 32-bit K), and one gather answers a query except when its cell holds a
+// knot whose fingerprint equals the query's.
+constexpr int RANK_SHIFT = 3;  // 8 cells per word
+
+struct RankHit {
+    uint32_t t;     // K_j
+    uint32_t knot;  // 1 if cell j holds knot t (F_t == j)
+    uint32_t kf;    // that knot's fingerprint
+};
+
+__device__ __forceinline__ RankHit rank_decode(uint2 w, uint32_t j)
+{
+    RankHit h;
+    const uint32_t b = j & 7u;
+    h.t = w.x + __popc(w.y & ((1u << b) - 1u));
+    h.knot = (w.y >> b) & 1u;
+    h.kf = (w.y >> (8u + 3u * b)) & 7u;
+    return h;
+}
 
 template <typename T> __device__ __forceinline__ bool lt_exact(T a, T b)
 {

@@ -82,6 +82,11 @@ template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uin
     if constexpr (SM) return *p;
     else return __ldg(p);
 }
+template <bool SM> __device__ __forceinline__ uint2 tab_ld(const uint2 *p, uint64_t)
+{
+    if constexpr (SM) return *p;
+    else return __ldg(p);
+}
 
 // ------------------------------------------------------------------ NQ queries of one array
 // Kernel kinds: every mode (fingerprints decided per array at run time), or
@@ -89,42 +94,41 @@ template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uin
 // out, which keeps the register count low).
 enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2 };
 
+// Rt: the array's rank table (shared or global memory); X: its knots (global
+// memory for direct arrays, shared or global for bisected ones).
 template <typename T, int NQ, int KIND, bool SM>
-__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
+__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint2 *Rt, const T *X,
                                              const T *z, int32_t *r, uint64_t pol)
 {
     if (KIND != KIND_ALL || d.mode == MODE_DIRECT) {
-        uint32_t e[NQ];
+        // one rank-table word per query, then X_t only for queries whose cell
+        // holds a knot and, with fingerprints, whose fingerprint equals the
+        // knot's (otherwise the fingerprints order z and X_t: within a cell
+        // the fingerprint is a non-decreasing function of f, Eq. fprop)
+        const bool fp = KIND == KIND_DIRECT_FP || (KIND == KIND_ALL && d.aux);
+        const CellF<T> f(d);
+        uint32_t g[NQ], j[NQ];
+        uint2 w[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            j[q] = cell_q<T>(f, d.R, z[q], &g[q]);
+            w[q] = tab_ld<SM>(Rt + (j[q] >> RANK_SHIFT), pol);
+        }
+        RankHit h[NQ];
         T x[NQ];
-        if (KIND == KIND_DIRECT_FP || (KIND == KIND_ALL && d.aux)) {
-            // entries carry the fingerprint of their knot: the knot is read only
-            // when the query's fingerprint equals it (about 1 in 128)
-            uint32_t g[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) e[q] = tab_ld<SM>(K + cell_rt_fp<T>(z[q], d, &g[q]), pol);
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const uint32_t ge = (e[q] >> FP_SHIFT) & 0x7Fu;
-                const bool need = (e[q] & KNOT_FLAG) && g[q] == ge;
-                x[q] = need ? tab_ld<SM>(X + (e[q] & FP_T_MASK), pol) : T(0);
-            }
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int32_t t = (int32_t)(e[q] & FP_T_MASK);
-                const uint32_t ge = (e[q] >> FP_SHIFT) & 0x7Fu;
-                bool lt = true;  // no knot in the cell: z < X_t (Eq. indexdef)
-                if (e[q] & KNOT_FLAG) lt = g[q] != ge ? g[q] < ge : lt_exact<T>(z[q], x[q]);
-                r[q] = t - (int32_t)lt;
-                if (a.checked && is_nan<T>(z[q])) r[q] = -1;
-            }
-            return;
+        for (int q = 0; q < NQ; ++q) {
+            h[q] = rank_decode(w[q], j[q]);
+            const bool need = h[q].knot && (!fp || g[q] == h[q].kf);
+            x[q] = need ? tab_ld<false>(X + h[q].t, pol) : T(0);
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) e[q] = tab_ld<SM>(K + cell_rt<T>(z[q], d), pol);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) x[q] = (e[q] & KNOT_FLAG) ? tab_ld<SM>(X + (e[q] & ~KNOT_FLAG), pol) : T(0);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) r[q] = correct<T, true>(z[q], e[q], x[q], a.checked);
+        for (int q = 0; q < NQ; ++q) {
+            bool lt = true;  // no knot in the cell: z < X_t (Eq. indexdef)
+            if (h[q].knot) lt = (fp && g[q] != h[q].kf) ? g[q] < h[q].kf : lt_exact<T>(z[q], x[q]);
+            r[q] = (int32_t)h[q].t - (int32_t)lt;
+            if (a.checked && is_nan<T>(z[q])) r[q] = -1;
+        }
         return;
     }
     int32_t lo[NQ], n[NQ], top;
@@ -225,7 +229,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
 // Queries [zs, ze) of one array by `nthr` threads (a block, or a warp); `tid`
 // is the thread's rank among them.
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool SM>
-__device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint32_t *K, const T *X,
+__device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint2 *K, const T *X,
                                               long long zs, long long ze, uint64_t pol, int tid, int nthr)
 {
     constexpr int L = VecOf<T>::L;
@@ -328,38 +332,52 @@ __device__ __forceinline__ int owner_of_chunk(const long long *chunk_off, int n_
     return lo;
 }
 
-// Claim the next chunk for the calling warp: (chunk, owning array), array -1
-// when none is left.  All 32 lanes call; every lane gets the result.
+// Claim the next chunk for the calling warp: (chunk, claim position of its
+// array), position -1 when none is left.  All 32 lanes call; every lane gets
+// the result.
 __device__ __forceinline__ void claim_chunk(unsigned long long *counter, const long long *chunk_off, int n_arrays,
-                                            long long *c_out, int *arr_out)
+                                            long long *c_out, int *pos_out)
 {
     long long c = 0;
     if ((threadIdx.x & 31) == 0) c = (long long)atomicAdd(counter, 1ull);
     c = __shfl_sync(0xffffffffu, c, 0);
     *c_out = c;
-    *arr_out = c < chunk_off[n_arrays] ? owner_of_chunk(chunk_off, n_arrays, c) : -1;
+    *pos_out = c < chunk_off[n_arrays] ? owner_of_chunk(chunk_off, n_arrays, c) : -1;
+}
+
+// Queries [zs, ze) of chunk c, claimed at position p (array arr).
+template <typename T>
+__device__ __forceinline__ void chunk_range(const BatchArgs<T> &a, const ArrDesc &d, int arr, int p, long long c,
+                                            long long *zs, long long *ze)
+{
+    const long long zb = q_begin(a.z_off, arr);
+    const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
+    const long long len = chunk_len(d, a.chunk, a.smem_limit);
+    *zs = zb + (c - a.chunk_off[p]) * len;
+    *ze = *zs + len < zend ? *zs + len : zend;
 }
 
 // KIND: BatchKind (KIND_DIRECT*: every array of the handle is in direct mode).
 // WARPS: no table is staged (a.smem_limit == 0) and every warp claims its own
 // chunks, so no block-wide barrier is needed; otherwise the block claims a
 // chunk and stages its array's image for all of its warps.
-template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false>
-__global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
+// MAXB: the largest block the kernel is compiled for (1024 only for the
+// direct kinds at one vector per thread, which fit 64 registers).
+template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false, int MAXB = 512>
+__global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
 {
     if constexpr (WARPS) {
         const int lane = threadIdx.x & 31;
         for (;;) {
             long long c;
-            int arr;
-            claim_chunk(a.counter, a.chunk_off, a.n_arrays, &c, &arr);
-            if (arr < 0) break;
+            int p;
+            claim_chunk(a.counter, a.chunk_off, a.n_arrays, &c, &p);
+            if (p < 0) break;
+            const int arr = a.order ? a.order[p] : p;
             const ArrDesc d = a.desc[arr];
-            const long long zb = q_begin(a.z_off, arr);
-            const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
-            const long long zs = zb + (c - a.chunk_off[arr]) * a.chunk;
-            const long long ze = zs + a.chunk < zend ? zs + a.chunk : zend;
-            process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, reinterpret_cast<const uint32_t *>(a.blob + d.img),
+            long long zs, ze;
+            chunk_range(a, d, arr, p, c, &zs, &ze);
+            process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, reinterpret_cast<const uint2 *>(a.blob + d.img),
                                                             reinterpret_cast<const T *>(a.blob + d.xg), zs, ze, 0,
                                                             lane, 32);
         }
@@ -387,8 +405,9 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
     const uint64_t pol = 0;
     for (int it = 0;; ++it) {
         const long long c = s_c[it & 1];
-        const int arr = s_a[it & 1];
-        if (arr < 0) break;
+        const int p = s_a[it & 1];
+        if (p < 0) break;
+        const int arr = a.order ? a.order[p] : p;
         if (threadIdx.x < 32) {
             long long cn;
             int an;
@@ -399,25 +418,17 @@ __global__ void __launch_bounds__(512) k_batch_search(BatchArgs<T> a)
             }
         }
         const ArrDesc d = a.desc[arr];
-        const long long zb = q_begin(a.z_off, arr);
-        const long long zend = a.z_off ? a.z_off[arr + 1] : a.m_single;
-        const long long zs = zb + (c - a.chunk_off[arr]) * a.chunk;
-        const long long ze = zs + a.chunk < zend ? zs + a.chunk : zend;
+        long long zs, ze;
+        chunk_range(a, d, arr, p, c, &zs, &ze);
         const bool use_smem = d.img_bytes > 0 && d.img_bytes <= a.smem_limit;
         if (use_smem && staged != arr) {
             if (!stage_again(smem, a.blob + d.img, d.img_bytes, &bar, parity, a.err)) return;
             parity ^= 1u;
             staged = arr;
         }
-        const uint32_t *K;
-        const T *X;
-        if (use_smem) {
-            K = reinterpret_cast<const uint32_t *>(smem);
-            X = reinterpret_cast<const T *>(smem + d.x_in_img);
-        } else {
-            K = reinterpret_cast<const uint32_t *>(a.blob + d.img);
-            X = reinterpret_cast<const T *>(a.blob + d.xg);
-        }
+        const uint2 *K = reinterpret_cast<const uint2 *>(use_smem ? smem : a.blob + d.img);
+        const T *X = reinterpret_cast<const T *>(use_smem && d.x_in_img != NO_X_IN_IMG ? smem + d.x_in_img
+                                                                                       : a.blob + d.xg);
         if (use_smem) process_chunk<T, VPT, INTERP, VEC, KIND, true>(a, d, K, X, zs, ze, pol, threadIdx.x, blockDim.x);
         else process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, K, X, zs, ze, pol, threadIdx.x, blockDim.x);
         __syncthreads();
@@ -511,13 +522,11 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
                                   const Segment *__restrict__ segs, int n_segs, const ArrDesc *__restrict__ desc,
                                   unsigned char *blob, uint32_t *__restrict__ F, uint8_t *__restrict__ G)
 {
-    using A = Arith<T>;
     for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
         const Segment sg = segs[s];
         const ArrDesc d = desc[sg.arr];
         const long long start = x_off[sg.arr];
         T *Xd = reinterpret_cast<T *>(blob + d.xg);
-        const T H = (T)d.H, W = (T)d.W, X0 = (T)d.X0;
         T *S = reinterpret_cast<T *>(blob + d.sg);
         for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
             const T x = Xcat[i];
@@ -527,24 +536,25 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
                 if ((li & (SG_STRIDE - 1)) == 0) S[li >> SG_SHIFT] = x;
                 if (li == d.n) S[(d.n >> SG_SHIFT) + 1] = x;
             }
-            if (d.mode == MODE_DIRECT) {
-                T v;
-                if (d.form == F_FMA) v = A::fma(H, x, -W);
-                else v = A::mul(H, A::sub(x, X0));
+            if (d.mode == MODE_DIRECT) {  // f and fingerprint exactly as a query computes them
                 uint32_t g;
-                F[i] = cell_fp_bits(v, &g);
-                G[i] = (uint8_t)(g & 0x7Fu);
+                F[i] = cell_fp3(CellF<T>(d)(x), &g);
+                G[i] = (uint8_t)g;
             }
         }
     }
 }
 
-// Flagged K of every direct array (as k_fill_K), with the knot's fingerprint
-// from G in bits 24..30 of flagged entries when the array's descriptor asks
-// for it; warps walk 32-knot chunks of all direct arrays, chunk -> array
-// through the chunk offsets kc_off.
-__global__ void k_seg_fill_K(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
-                             const long long *__restrict__ x_off, const long long *__restrict__ kc_off, int n_arrays,
-                             const ArrDesc *__restrict__ desc, unsigned char *blob);
+// Rank tables of every direct array, in two passes (the blob is zeroed
+// first).  k_seg_rank_base writes K_{8 g} of every group: warps walk 32-knot
+// chunks of all direct arrays (chunk -> array through the chunk offsets
+// kc_off) and write the groups whose first cell lies in the chunk's cell span.
+// k_seg_rank_bits sets, for every knot, its cell's bit and fingerprint.
+__global__ void k_seg_rank_base(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
+                                const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
+                                unsigned char *blob);
+__global__ void k_seg_rank_bits(const uint32_t *__restrict__ F, const uint8_t *__restrict__ G,
+                                const Segment *__restrict__ segs, int n_segs, const long long *__restrict__ x_off,
+                                const ArrDesc *__restrict__ desc, unsigned char *blob);
 
 }  // namespace ds

@@ -50,7 +50,7 @@ def test_small_batch_all_tunings(ds, fma):
     b = ds.ds_batch_build(Xd, xo, ds.DS_FMA if fma else 0)
     _check_params(ds, b, w, fma)
     ref = oracle.upper_bound_batch(w["Xcat"], w["x_off"], w["Zcat"], w["z_off"])
-    for block in (128, 256, 512):
+    for block in (128, 256, 512, 1024):
         for items in (1, 2, 4):
             for smem in (-1, 0, 24 * 1024, 96 * 1024):
                 ds.ds_batch_set_tune(b, block, items, smem)
@@ -149,7 +149,7 @@ def test_workload3_full_size_autotuned(ds):
     info = b.info()
     assert info["n_direct"] == 4096 and info["n_fallback"] == 0
     best = ds.ds_batch_autotune(b, Zd, zo)
-    assert best["ms"] > 0 and best["block"] in (128, 256, 512)
+    assert best["ms"] > 0 and best["block"] in (128, 256, 512, 1024)
     out = ds.ds_batch_search(b, Zd, zo)
     # sampled exact check against the oracle, one by one per array
     g = np.random.default_rng(12)
