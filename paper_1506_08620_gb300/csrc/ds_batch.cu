@@ -86,8 +86,8 @@ __global__ void k_seg_rank_base(const uint32_t *__restrict__ F, const long long 
         const uint32_t Fi = F[start + (i <= N ? i : N)];
         const long long prev = lc == 0 ? -1 : (long long)F[start + lc * 32 - 1];
         const long long last = (long long)__shfl_sync(0xffffffffu, Fi, 31);
-        // groups g with prev < 8 g <= last: K_{8 g} is the first lane with F >= 8 g
-        const long long g_first = (prev + 1 + 7) >> RANK_SHIFT, g_last = last >> RANK_SHIFT;
+        // groups g with prev < 32 g <= last: K_{32 g} is the first lane with F >= 32 g
+        const long long g_first = (prev + 32) >> RANK_SHIFT, g_last = last >> RANK_SHIFT;
         for (long long gb = g_first; gb <= g_last; gb += 32) {
             const long long g = gb + lane;
             const long long j = g << RANK_SHIFT;
@@ -111,9 +111,12 @@ __global__ void k_seg_rank_bits(const uint32_t *__restrict__ F, const uint8_t *_
         const ArrDesc d = desc[sg.arr];
         if (d.mode != MODE_DIRECT) continue;
         uint32_t *Wd = reinterpret_cast<uint32_t *>(blob + d.img);
+        uint8_t *Gd = blob + d.img + d.g_in_img;
+        const long long start = x_off[sg.arr];
         for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
-            const uint32_t f = F[i], b = f & 7u;
-            atomicOr(&Wd[2 * (long long)(f >> RANK_SHIFT) + 1], (1u << b) | (((uint32_t)G[i] & 7u) << (8u + 3u * b)));
+            const uint32_t f = F[i];
+            atomicOr(&Wd[2 * (long long)(f >> RANK_SHIFT) + 1], 1u << (f & 31u));
+            Gd[i - start] = G[i];
         }
     }
 }
@@ -261,14 +264,15 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 d.R = (uint32_t)hs[a].R;
                 d.H = hs[a].H;
                 d.W = hs[a].W;
-                // the image is the rank table (8 bytes per 8 cells); the knots
-                // follow it and stay in global memory
-                const size_t kb = round_up((((size_t)hs[a].R >> RANK_SHIFT) + 1) * 8, 16);
+                // the image is the rank words and the knot fingerprints; the
+                // knots follow it and stay in global memory
+                const size_t kb = rank_bytes((uint32_t)hs[a].R), gb = round_up((size_t)nk, 16);
                 d.x_in_img = NO_X_IN_IMG;
-                d.xg = (long long)(off + kb);
+                d.g_in_img = (uint32_t)std::min<size_t>(kb, 0xFFFFFFFFu);
+                d.xg = (long long)(off + kb + gb);
                 const size_t xb = round_up((size_t)nk * sizeof(T), 16);
-                d.img_bytes = kb <= 0xFFFFFFF0u ? (uint32_t)kb : 0u;
-                off += kb + xb;
+                d.img_bytes = kb + gb <= 0xFFFFFFF0u ? (uint32_t)(kb + gb) : 0u;
+                off += kb + gb + xb;
                 kc[a + 1] = (nk + 31) / 32;
                 e->n_direct += 1;
                 e->R_total += (unsigned long long)hs[a].R + 1;

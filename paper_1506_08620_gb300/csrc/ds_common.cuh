@@ -120,20 +120,20 @@ __device__ __forceinline__ uint32_t trunc_u32_bits(double v)
 }
 
 // Cell j = trunc(v) (as trunc_u32 / cvt.rzi.u32: negatives and NaN -> 0,
-// saturated at 2^32 - 1) and fingerprint g = floor(128 (v - trunc(v))), the
-// top 7 bits of the fractional part, 0 for negatives and NaN and 128 for
-// v >= 2^32, computed exactly from the bit pattern.  Within one cell g is a
-// non-decreasing function of v, so g(v) < g(w) implies v < w and g(v) > g(w)
-// implies v > w: comparing fingerprints decides most comparisons of a query
-// with the knot of its cell without reading the knot.
-constexpr uint32_t FP_BITS = 7;
-constexpr uint32_t FP_ABOVE = 128;  // fingerprint of a value past the last cell
+// saturated at 2^32 - 1) and fingerprint g = floor(256 (v - trunc(v))), the
+// top 8 bits of the fractional part, 0 for negatives and NaN and FP_ABOVE for
+// v >= 2^32, computed exactly from the bit pattern of a double.  Within one
+// cell g is a non-decreasing function of v, so g(v) < g(w) implies v < w and
+// g(v) > g(w) implies v > w: comparing fingerprints decides most comparisons
+// of a query with the knot of its cell without reading the knot.
+constexpr uint32_t FP_BITS = 8;
+constexpr uint32_t FP_ABOVE = 1u << FP_BITS;  // fingerprint of a value past the last cell
 
 __device__ __forceinline__ uint32_t cell_fp_bits(double v, uint32_t *g)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7FF) - 1023;
-    if ((long long)b < 0 || e < -7 || (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) {
+    if ((long long)b < 0 || e < -(int)FP_BITS || (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) {
         *g = 0u;
         return 0u;
     }
@@ -142,37 +142,8 @@ __device__ __forceinline__ uint32_t cell_fp_bits(double v, uint32_t *g)
         return 0xFFFFFFFFu;
     }
     const unsigned long long mant = (b & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-    *g = (uint32_t)(mant >> (45 - e)) & 0x7Fu;
+    *g = (uint32_t)(mant >> (52 - (int)FP_BITS - e)) & (FP_ABOVE - 1u);
     return e < 0 ? 0u : (uint32_t)(mant >> (52 - e));
-}
-
-__device__ __forceinline__ uint32_t cell_fp_bits(float v, uint32_t *g)
-{
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFF) - 127;
-    if ((int32_t)b < 0 || e < -7 || (b & 0x7FFFFFFFu) > 0x7F800000u) {
-        *g = 0u;
-        return 0u;
-    }
-    if (e >= 32) {
-        *g = FP_ABOVE;
-        return 0xFFFFFFFFu;
-    }
-    const uint32_t mant = (b & 0x007FFFFFu) | (1u << 23);
-    if (e < 0) {
-        *g = mant >> (16 - e);
-        return 0u;
-    }
-    if (e <= 16) {
-        *g = (mant >> (16 - e)) & 0x7Fu;
-        return mant >> (23 - e);
-    }
-    if (e <= 23) {
-        *g = (mant << (e - 16)) & 0x7Fu;
-        return mant >> (23 - e);
-    }
-    *g = 0u;
-    return mant << (e - 23);
 }
 
 // Signed integer key ordering doubles like their values (+0 and -0 equal);
@@ -232,6 +203,22 @@ __device__ __forceinline__ longlong2 ld_keep(const longlong2 *ptr, uint64_t pol)
     asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.b64 {%0, %1}, [%2], %3;"
         : "=l"(v.x), "=l"(v.y)
         : "l"(ptr), "l"(pol));
+    return v;
+}
+
+// The same mark in L2, with L1 allocation (a block works on one array's table
+// at a time, so its cells are reused in L1).
+__device__ __forceinline__ uint2 ld_keep_l1(const uint2 *ptr, uint64_t pol)
+{
+    uint2 v;
+    asm("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(ptr), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_keep_l1(const uint8_t *ptr, uint64_t pol)
+{
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;" : "=r"(v) : "l"(ptr), "l"(pol));
     return v;
 }
 

@@ -13,7 +13,7 @@
 //
 // Per-array modes:
 //   MODE_DIRECT    Algorithm direct with the array's own H, W, R; K is held
-//                  as a rank table (below), one byte per cell.
+//                  as a rank table with knot fingerprints (below).
 //   MODE_LEARNED   predicted index, bounded window, certificate, exact
 //                  fall-back; the window is searched in two fixed-depth
 //                  levels: over every 32nd knot (a small, L2-resident copy),
@@ -60,6 +60,8 @@ struct __align__(16) ArrDesc {
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
     long long sg;         // learned: byte offset of the sampled knots S_k = X_{min(32 k, N)}, k = 0..N/32+1
+    uint32_t g_in_img;    // direct: byte offset of the knot fingerprints inside the image
+    uint32_t pad_;
 };
 static_assert(sizeof(ArrDesc) == 128, "ArrDesc layout");
 
@@ -113,27 +115,19 @@ __device__ __forceinline__ long long q_begin(const long long *z_off, int a) { re
 
 // ------------------------------------------------------------------ per-query pieces
 // Cell j = trunc(v) (negative and NaN -> 0, saturated at 2^32 - 1) and the
-// knot fingerprint g = floor(8 (v - j)), the top 3 bits of the fractional
-// part of v.  Within one cell g is a non-decreasing function of v, so
-// g(v) < g(w) implies v < w and g(v) > g(w) implies v > w.  float: in float
-// arithmetic, where v - j is exact (j <= v < j + 1, Sterbenz) and so is the
-// product by 8 (negative and NaN v give g = 0); double: from the bit pattern
-// (cell_fp_bits), which keeps the scarce FP64 pipe free.
-constexpr uint32_t RANK_FP_ABOVE = 8;  // fingerprint of a query past the last cell
-
-__device__ __forceinline__ uint32_t cell_fp3(float v, uint32_t *g)
+// knot fingerprint g = floor(256 (v - j)), the top 8 bits of the fractional
+// part of v (FP_ABOVE for v >= 2^32).  Within one cell g is a non-decreasing
+// function of v, so g(v) < g(w) implies v < w and g(v) > g(w) implies v > w.
+// float: in float arithmetic, where v - j is exact (j <= v < j + 1, Sterbenz)
+// and so is the product by 256 (negative and NaN v give g = 0); double: from
+// the bit pattern (cell_fp_bits), which keeps the scarce FP64 pipe free.
+__device__ __forceinline__ uint32_t cell_fp(float v, uint32_t *g)
 {
     const uint32_t j = __float2uint_rz(v);
-    *g = __float2uint_rz(__fmul_rn(__fsub_rn(v, __uint2float_rn(j)), 8.0f));
+    *g = __float2uint_rz(__fmul_rn(__fsub_rn(v, __uint2float_rn(j)), (float)FP_ABOVE));
     return j;
 }
-__device__ __forceinline__ uint32_t cell_fp3(double v, uint32_t *g)
-{
-    uint32_t g7;
-    const uint32_t j = cell_fp_bits(v, &g7);
-    *g = g7 >> 4;
-    return j;
-}
+__device__ __forceinline__ uint32_t cell_fp(double v, uint32_t *g) { return cell_fp_bits(v, g); }
 
 // f of a direct array for its queries and knots.  float: both forms as one
 // subtraction and one fused multiply-add, f = m(H m(z - x0) + c), with
@@ -162,13 +156,13 @@ template <> struct CellF<double> {
 };
 
 // Cell and fingerprint of a query; a query past the last cell R gets cell R
-// and fingerprint RANK_FP_ABOVE, above every knot's.
+// and fingerprint FP_ABOVE, above every knot's.
 template <typename T>
 __device__ __forceinline__ uint32_t cell_q(const CellF<T> &f, uint32_t R, T z, uint32_t *g)
 {
-    const uint32_t j = cell_fp3(f(z), g);
+    const uint32_t j = cell_fp(f(z), g);
     if (j > R) {
-        *g = RANK_FP_ABOVE;
+        *g = FP_ABOVE;
         return R;
     }
     return j;
@@ -178,29 +172,33 @@ __device__ __forceinline__ uint32_t cell_q(const CellF<T> &f, uint32_t R, T z, u
 // With pairs (i, i+1) ComputeHR makes F strictly increasing, so a cell holds at
 // most one knot and K_j = min{i : F_i >= j} = #{i : F_i < j} (Eq. indexdef):
 // K is the rank function of the set of cells that hold a knot.  A direct
-// array's table stores it in one 8-byte word per group of 8 cells:
-//   x            K_{8 g}, the knots in cells before the group
-//   y bits 0..7  bit b set when cell 8 g + b holds a knot
-//   y bits 8..31 3 bits per cell: the fingerprint (cell_fp3) of its knot
-// so K_j = K_{8 g} + popc(knot bits below b).  One byte per cell (a quarter
-// of a 32-bit K), and one gather answers a query except when its cell holds a
-// knot whose fingerprint equals the query's.
-constexpr int RANK_SHIFT = 3;  // 8 cells per word
+// array's image stores it as one 8-byte word per group of 32 cells,
+//   x  K_{32 g}, the knots in cells before the group
+//   y  bit b set when cell 32 g + b holds a knot
+// so K_j = K_{32 g} + popc(y below bit b) (a quarter of a byte per cell),
+// followed by one byte per knot, the knot's fingerprint (cell_fp).  A query
+// reads one word; if its cell holds a knot, that knot's fingerprint; and the
+// knot itself only when the two fingerprints are equal (about 1 in 256).
+constexpr int RANK_SHIFT = 5;  // 32 cells per word
 
 struct RankHit {
     uint32_t t;     // K_j
     uint32_t knot;  // 1 if cell j holds knot t (F_t == j)
-    uint32_t kf;    // that knot's fingerprint
 };
 
 __device__ __forceinline__ RankHit rank_decode(uint2 w, uint32_t j)
 {
     RankHit h;
-    const uint32_t b = j & 7u;
+    const uint32_t b = j & 31u;
     h.t = w.x + __popc(w.y & ((1u << b) - 1u));
     h.knot = (w.y >> b) & 1u;
-    h.kf = (w.y >> (8u + 3u * b)) & 7u;
     return h;
+}
+
+// Bytes of a direct array's rank words (16-byte multiple).
+__host__ __device__ __forceinline__ size_t rank_bytes(uint32_t R)
+{
+    return (((size_t)(R >> RANK_SHIFT) + 1) * 8 + 15) / 16 * 16;
 }
 
 template <typename T> __device__ __forceinline__ bool lt_exact(T a, T b)

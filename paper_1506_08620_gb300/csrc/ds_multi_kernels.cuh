@@ -65,8 +65,9 @@ __device__ __forceinline__ void window_of(int32_t pf, const ArrDesc &d, int32_t 
 
 // Table read: shared memory (staged image) or global memory through the
 // read-only path (L1-cached: a block works on one array at a time, whose
-// table is small enough to get L1 reuse; all tables together exceed L2, so
-// no L2 priority is requested).
+// table is small enough to get L1 reuse).  Rank words and knot fingerprints
+// are marked evict-last in L2 with the policy `pol`, so they stay resident
+// under the query stream; knots and learned tables keep the default policy.
 template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint32_t *p, uint64_t)
 {
     if constexpr (SM) return *p;
@@ -82,10 +83,15 @@ template <bool SM> __device__ __forceinline__ double tab_ld(const double *p, uin
     if constexpr (SM) return *p;
     else return __ldg(p);
 }
-template <bool SM> __device__ __forceinline__ uint2 tab_ld(const uint2 *p, uint64_t)
+template <bool SM> __device__ __forceinline__ uint2 tab_ld(const uint2 *p, uint64_t pol)
 {
     if constexpr (SM) return *p;
-    else return __ldg(p);
+    else return ld_keep_l1(p, pol);
+}
+template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint8_t *p, uint64_t pol)
+{
+    if constexpr (SM) return *p;
+    else return ld_keep_l1(p, pol);
 }
 
 // ------------------------------------------------------------------ NQ queries of one array
@@ -94,18 +100,21 @@ template <bool SM> __device__ __forceinline__ uint2 tab_ld(const uint2 *p, uint6
 // out, which keeps the register count low).
 enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2 };
 
-// Rt: the array's rank table (shared or global memory); X: its knots (global
-// memory for direct arrays, shared or global for bisected ones).
+// img: the array's image (shared or global memory: for a direct array its
+// rank words and knot fingerprints); X: its knots (global memory for direct
+// arrays, shared or global for bisected ones).
 template <typename T, int NQ, int KIND, bool SM>
-__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const uint2 *Rt, const T *X,
-                                             const T *z, int32_t *r, uint64_t pol)
+__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const unsigned char *img,
+                                             const T *X, const T *z, int32_t *r, uint64_t pol)
 {
     if (KIND != KIND_ALL || d.mode == MODE_DIRECT) {
-        // one rank-table word per query, then X_t only for queries whose cell
-        // holds a knot and, with fingerprints, whose fingerprint equals the
-        // knot's (otherwise the fingerprints order z and X_t: within a cell
-        // the fingerprint is a non-decreasing function of f, Eq. fprop)
+        // one rank word per query; for a cell holding a knot, the knot's
+        // fingerprint; the knot X_t itself only when the two fingerprints are
+        // equal (otherwise they order z and X_t: within a cell the fingerprint
+        // is a non-decreasing function of f, Eq. fprop)
         const bool fp = KIND == KIND_DIRECT_FP || (KIND == KIND_ALL && d.aux);
+        const uint2 *Rt = reinterpret_cast<const uint2 *>(img);
+        const uint8_t *Gt = img + d.g_in_img;
         const CellF<T> f(d);
         uint32_t g[NQ], j[NQ];
         uint2 w[NQ];
@@ -115,17 +124,22 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
             w[q] = tab_ld<SM>(Rt + (j[q] >> RANK_SHIFT), pol);
         }
         RankHit h[NQ];
-        T x[NQ];
+        uint32_t kf[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             h[q] = rank_decode(w[q], j[q]);
-            const bool need = h[q].knot && (!fp || g[q] == h[q].kf);
+            kf[q] = fp && h[q].knot ? tab_ld<SM>(Gt + h[q].t, pol) : 0u;
+        }
+        T x[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const bool need = h[q].knot && (!fp || g[q] == kf[q]);
             x[q] = need ? tab_ld<false>(X + h[q].t, pol) : T(0);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             bool lt = true;  // no knot in the cell: z < X_t (Eq. indexdef)
-            if (h[q].knot) lt = (fp && g[q] != h[q].kf) ? g[q] < h[q].kf : lt_exact<T>(z[q], x[q]);
+            if (h[q].knot) lt = (fp && g[q] != kf[q]) ? g[q] < kf[q] : lt_exact<T>(z[q], x[q]);
             r[q] = (int32_t)h[q].t - (int32_t)lt;
             if (a.checked && is_nan<T>(z[q])) r[q] = -1;
         }
@@ -229,7 +243,8 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
 // Queries [zs, ze) of one array by `nthr` threads (a block, or a warp); `tid`
 // is the thread's rank among them.
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool SM>
-__device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const uint2 *K, const T *X,
+__device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const unsigned char *K,
+                                              const T *X,
                                               long long zs, long long ze, uint64_t pol, int tid, int nthr)
 {
     constexpr int L = VecOf<T>::L;
@@ -377,9 +392,9 @@ __global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
             const ArrDesc d = a.desc[arr];
             long long zs, ze;
             chunk_range(a, d, arr, p, c, &zs, &ze);
-            process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, reinterpret_cast<const uint2 *>(a.blob + d.img),
-                                                            reinterpret_cast<const T *>(a.blob + d.xg), zs, ze, 0,
-                                                            lane, 32);
+            process_chunk<T, VPT, INTERP, VEC, KIND, false>(a, d, a.blob + d.img,
+                                                            reinterpret_cast<const T *>(a.blob + d.xg), zs, ze,
+                                                            l2_keep_policy(), lane, 32);
         }
         return;
     }
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
     __syncthreads();
     uint32_t parity = 0;
     int staged = -1;
-    const uint64_t pol = 0;
+    const uint64_t pol = l2_keep_policy();
     for (int it = 0;; ++it) {
         const long long c = s_c[it & 1];
         const int p = s_a[it & 1];
@@ -426,7 +441,7 @@ __global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
             parity ^= 1u;
             staged = arr;
         }
-        const uint2 *K = reinterpret_cast<const uint2 *>(use_smem ? smem : a.blob + d.img);
+        const unsigned char *K = use_smem ? smem : a.blob + d.img;
         const T *X = reinterpret_cast<const T *>(use_smem && d.x_in_img != NO_X_IN_IMG ? smem + d.x_in_img
                                                                                        : a.blob + d.xg);
         if (use_smem) process_chunk<T, VPT, INTERP, VEC, KIND, true>(a, d, K, X, zs, ze, pol, threadIdx.x, blockDim.x);
@@ -538,18 +553,19 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
             }
             if (d.mode == MODE_DIRECT) {  // f and fingerprint exactly as a query computes them
                 uint32_t g;
-                F[i] = cell_fp3(CellF<T>(d)(x), &g);
+                F[i] = cell_fp(CellF<T>(d)(x), &g);
                 G[i] = (uint8_t)g;
             }
         }
     }
 }
 
-// Rank tables of every direct array, in two passes (the blob is zeroed
-// first).  k_seg_rank_base writes K_{8 g} of every group: warps walk 32-knot
-// chunks of all direct arrays (chunk -> array through the chunk offsets
-// kc_off) and write the groups whose first cell lies in the chunk's cell span.
-// k_seg_rank_bits sets, for every knot, its cell's bit and fingerprint.
+// Rank words and knot fingerprints of every direct array, in two passes (the
+// blob is zeroed first).  k_seg_rank_base writes K_{32 g} of every group:
+// warps walk 32-knot chunks of all direct arrays (chunk -> array through the
+// chunk offsets kc_off) and write the groups whose first cell lies in the
+// chunk's cell span.  k_seg_rank_bits sets, for every knot, its cell's bit,
+// and stores its fingerprint.
 __global__ void k_seg_rank_base(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
                                 const long long *__restrict__ kc_off, int n_arrays, const ArrDesc *__restrict__ desc,
                                 unsigned char *blob);
