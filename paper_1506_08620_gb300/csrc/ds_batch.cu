@@ -299,6 +299,10 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
         e->fingerprints = !(flags & DS_NO_FINGERPRINT) && e->n_direct > 0;
         for (int a = 0; a < A; ++a)
             if (e->desc_host[a].mode == MODE_DIRECT) e->desc_host[a].aux = e->fingerprints ? 1 : 0;
+        // the one-conversion cell form: float, every direct array with R < 2^24 - 1
+        e->fast_cells = sizeof(T) == 4 && e->n_direct > 0;
+        for (int a = 0; a < A; ++a)
+            if (e->desc_host[a].mode == MODE_DIRECT && e->desc_host[a].R > FASTF_MAX_R) e->fast_cells = false;
         // knots X_0, X_N per array (for the descriptors)
         {
             std::vector<T> ends(2 * (size_t)A);
@@ -435,6 +439,9 @@ static const void *pick3(bool vec, bool warps, bool big, int kind)
     switch (kind) {
     case KIND_DIRECT: return pick4<T, VPT, INTERP, KIND_DIRECT>(vec, warps, big);
     case KIND_DIRECT_FP: return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
+    case KIND_DIRECT_FPF:
+        if constexpr (sizeof(T) == 4) return pick4<T, VPT, INTERP, KIND_DIRECT_FPF>(vec, warps, big);
+        else return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
     default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps, big);
     }
 }
@@ -455,7 +462,10 @@ static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, i
 static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0; }
 static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big)
 {
-    const int kind = !direct_only(e) ? KIND_ALL : (e->fingerprints ? KIND_DIRECT_FP : KIND_DIRECT);
+    const int kind = !direct_only(e) ? KIND_ALL
+                     : !e->fingerprints ? KIND_DIRECT
+                     : e->fast_cells    ? KIND_DIRECT_FPF
+                                        : KIND_DIRECT_FP;
     return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, warps, big, kind)
                               : pick1<double>(vpt, interp, vec, warps, big, kind);
 }

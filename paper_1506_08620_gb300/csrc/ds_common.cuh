@@ -281,6 +281,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // Bounded wait: gives up after `limit` polls (each poll may suspend the
 // thread for a hardware-defined time), returns false on timeout.
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned address and
+// size; no shared memory, registers or barrier involved).
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
     for (uint32_t it = 0; it < limit; ++it)

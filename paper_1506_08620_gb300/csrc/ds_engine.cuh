@@ -39,6 +39,7 @@ struct Engine {
     unsigned long long R_total = 0;
     int n_direct = 0, n_learned = 0, n_fallback = 0;
     bool fingerprints = false;  // the knot fingerprints of the rank tables are used
+    bool fast_cells = false;    // float, every direct R < 2^24 - 1: one conversion per query
     double build_ms = 0;
 };
 

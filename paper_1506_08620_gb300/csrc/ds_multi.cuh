@@ -142,6 +142,13 @@ template <> struct CellF<float> {
     {
     }
     __device__ __forceinline__ float operator()(float z) const { return __fmaf_rn(H, __fsub_rn(z, x0), c); }
+    // 2^FP_BITS f(z), exactly: scaling by a power of two commutes with the
+    // rounding of the fused multiply-add, except where f(z) is subnormal, and
+    // there both give cell 0 and fingerprint 0
+    __device__ __forceinline__ float scaled(float z) const
+    {
+        return __fmaf_rn(H * (float)FP_ABOVE, __fsub_rn(z, x0), c * (float)FP_ABOVE);
+    }
 };
 template <> struct CellF<double> {
     double H, W, X0;
@@ -156,17 +163,27 @@ template <> struct CellF<double> {
 };
 
 // Cell and fingerprint of a query; a query past the last cell R gets cell R
-// and fingerprint FP_ABOVE, above every knot's.
-template <typename T>
+// and fingerprint FP_ABOVE, above every knot's.  FASTF (float, R < 2^24 - 1):
+// both from one conversion, q = trunc(2^FP_BITS f(z)) = 2^FP_BITS j + g, which
+// stays below 2^32 up to cell 2^24 - 1 and saturates above, past R.
+template <typename T, bool FASTF = false>
 __device__ __forceinline__ uint32_t cell_q(const CellF<T> &f, uint32_t R, T z, uint32_t *g)
 {
-    const uint32_t j = cell_fp(f(z), g);
+    uint32_t j;
+    if constexpr (FASTF) {
+        const uint32_t q = __float2uint_rz(f.scaled(z));
+        j = q >> FP_BITS;
+        *g = q & (FP_ABOVE - 1u);
+    } else {
+        j = cell_fp(f(z), g);
+    }
     if (j > R) {
         *g = FP_ABOVE;
         return R;
     }
     return j;
 }
+constexpr uint32_t FASTF_MAX_R = (1u << 24) - 2;  // largest R of the one-conversion form
 
 // ------------------------------------------------------------------ rank table
 // With pairs (i, i+1) ComputeHR makes F strictly increasing, so a cell holds at
@@ -189,9 +206,10 @@ struct RankHit {
 __device__ __forceinline__ RankHit rank_decode(uint2 w, uint32_t j)
 {
     RankHit h;
-    const uint32_t b = j & 31u;
-    h.t = w.x + __popc(w.y & ((1u << b) - 1u));
-    h.knot = (w.y >> b) & 1u;
+    uint32_t below;  // the b = j mod 32 low bits set
+    asm("bmsk.clamp.b32 %0, 0, %1;" : "=r"(below) : "r"(j & 31u));
+    h.t = w.x + __popc(w.y & below);
+    h.knot = (w.y >> (j & 31u)) & 1u;
     return h;
 }
 

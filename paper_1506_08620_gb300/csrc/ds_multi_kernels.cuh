@@ -97,30 +97,31 @@ template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint8_t *p, 
 // ------------------------------------------------------------------ NQ queries of one array
 // Kernel kinds: every mode (fingerprints decided per array at run time), or
 // direct arrays only, without or with fingerprints (the other paths compiled
-// out, which keeps the register count low).
-enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2 };
+// out, which keeps the register count low), or with fingerprints and the
+// one-conversion cell form (float arrays, every R < 2^24 - 1).
+enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3 };
 
 // img: the array's image (shared or global memory: for a direct array its
 // rank words and knot fingerprints); X: its knots (global memory for direct
 // arrays, shared or global for bisected ones).
-template <typename T, int NQ, int KIND, bool SM>
-__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const unsigned char *img,
-                                             const T *X, const T *z, int32_t *r, uint64_t pol)
+template <typename T, int NQ, int KIND, bool SM, bool FASTF>
+__device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const CellF<T> &f,
+                                             const unsigned char *img, const T *X, const T *z, int32_t *r,
+                                             uint64_t pol)
 {
     if (KIND != KIND_ALL || d.mode == MODE_DIRECT) {
         // one rank word per query; for a cell holding a knot, the knot's
         // fingerprint; the knot X_t itself only when the two fingerprints are
         // equal (otherwise they order z and X_t: within a cell the fingerprint
         // is a non-decreasing function of f, Eq. fprop)
-        const bool fp = KIND == KIND_DIRECT_FP || (KIND == KIND_ALL && d.aux);
+        const bool fp = KIND == KIND_DIRECT_FP || KIND == KIND_DIRECT_FPF || (KIND == KIND_ALL && d.aux);
         const uint2 *Rt = reinterpret_cast<const uint2 *>(img);
         const uint8_t *Gt = img + d.g_in_img;
-        const CellF<T> f(d);
         uint32_t g[NQ], j[NQ];
         uint2 w[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
-            j[q] = cell_q<T>(f, d.R, z[q], &g[q]);
+            j[q] = cell_q<T, FASTF>(f, d.R, z[q], &g[q]);
             w[q] = tab_ld<SM>(Rt + (j[q] >> RANK_SHIFT), pol);
         }
         RankHit h[NQ];
@@ -240,13 +241,17 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
     }
 }
 
+// Tiles by which the bulk L2 prefetch of the query stream runs ahead.
+constexpr int QP_DIST = 4;
+
 // Queries [zs, ze) of one array by `nthr` threads (a block, or a warp); `tid`
 // is the thread's rank among them.
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool SM>
 __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDesc &d, const unsigned char *K,
-                                              const T *X,
-                                              long long zs, long long ze, uint64_t pol, int tid, int nthr)
+                                              const T *X, long long zs, long long ze, uint64_t pol, int tid, int nthr)
 {
+    constexpr bool FASTF = KIND == KIND_DIRECT_FPF;
+    const CellF<T> f(d);  // once per chunk
     constexpr int L = VecOf<T>::L;
     long long va, vb;
     if constexpr (VEC) {
@@ -261,14 +266,14 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
     for (long long q = zs + tid; q < va; q += nthr) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
+        answer_block<T, 1, KIND, SM, FASTF>(a, d, f, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
     for (long long q = vb + tid; q < ze; q += nthr) {
         T z = a.Z[q];
         int32_t r;
-        answer_block<T, 1, KIND, SM>(a, d, K, X, &z, &r, pol);
+        answer_block<T, 1, KIND, SM, FASTF>(a, d, f, K, X, &z, &r, pol);
         a.I[q] = r;
         interp_store<T, INTERP>(a, d, X, q, z, r);
     }
@@ -291,8 +296,20 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
                 zn[v] = idx < nv ? __ldcs(Zv + idx) : Zv[0];
             }
         };
+        // the query stream is also prefetched into L2, QP_DIST tiles ahead of
+        // its loads, by bulk prefetches of whole tiles (no registers held)
+        const long long tile = (long long)VPT * nthr;
+        auto prefetch_l2 = [&](long long first) {
+            if (first < nv) {
+                const long long n = nv - first < tile ? nv - first : tile;
+                bulk_prefetch_l2(Zv + first, (uint32_t)(n * (long long)sizeof(V)));
+            }
+        };
+        if (PREFETCH && tid == 0)
+            for (int k = 1; k <= QP_DIST; ++k) prefetch_l2((long long)k * tile);
         if (PREFETCH && tid < nv) load_tile(tid);
         for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
+            if (PREFETCH && tid == 0) prefetch_l2(base + (long long)(QP_DIST + 1) * tile);
             V zv[VPT];
             if constexpr (PREFETCH) {
 #pragma unroll
@@ -305,7 +322,7 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
             }
             const T *zs4 = reinterpret_cast<const T *>(zv);
             int32_t r[NQ];
-            answer_block<T, NQ, KIND, SM>(a, d, K, X, zs4, r, pol);
+            answer_block<T, NQ, KIND, SM, FASTF>(a, d, f, K, X, zs4, r, pol);
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = base + (long long)v * nthr;
