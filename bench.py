@@ -123,7 +123,8 @@ def record_traffic(args):
     d = json.load(open(TRAFFIC_PATH)) if os.path.exists(TRAFFIC_PATH) else {}
     d[key] = {"bytes_per_launch": captured * full / args.queries, "captured_bytes_per_launch": captured,
               "captured_queries": args.queries, "full_queries": full, "launches": len(per_launch),
-              "scaled": "traffic grows in proportion to the queries (tables L2-resident)",
+              "scaled": ("captured at the full workload" if args.queries == full else
+                         "traffic grows in proportion to the queries (tables L2-resident)"),
               "source_hash": source_hash(key)}
     with open(TRAFFIC_PATH, "w") as f:
         json.dump(d, f, indent=1, sort_keys=True)

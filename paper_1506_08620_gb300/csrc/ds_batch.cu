@@ -11,6 +11,42 @@
 namespace ds {
 
 // ---------------------------------------------------------------- kernels
+// Exclusive prefix sum of v over the block; *total gets the block's sum.
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *total)
+{
+    __shared__ long long warp_sum[33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) / 32;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_sum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const long long w = lane < nw ? warp_sum[lane] : 0;
+        long long inc2 = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc2, o);
+            if (lane >= o) inc2 += y;
+        }
+        if (lane < nw) warp_sum[lane] = inc2 - w;
+        if (lane == 31) warp_sum[32] = inc2;
+    }
+    __syncthreads();
+    const long long r = warp_sum[wid] + incl - v;
+    *total = warp_sum[32];
+    __syncthreads();  // warp_sum is reused by the next call
+    return r;
+}
+
+// Positions are taken in rounds of one per thread (coalesced loads); up to
+// PLAN_ROUNDS rounds the per-array loads of all rounds are issued together
+// before the first scan.
+constexpr int PLAN_ROUNDS = 8;
+
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
                               const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
                               unsigned long long *counter)
@@ -23,42 +59,38 @@ __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_
         const long long c = chunk_len(desc[a], chunk, smem_limit);
         return (q + c - 1) / c;
     };
-    __shared__ long long warp_sum[32];
-    const int per = (n_arrays + blockDim.x - 1) / blockDim.x;
-    const int a0 = threadIdx.x * per;
-    const int a1 = min(a0 + per, n_arrays);
-    long long local = 0;
-    for (int a = a0; a < a1; ++a) local += chunks_at(a);
-    // block-wide exclusive scan of `local`
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    long long incl = local;
+    const int B = blockDim.x, rounds = (n_arrays + B - 1) / B;
+    long long carry = 0;
+    if (rounds <= PLAN_ROUNDS) {
+        long long cnt[PLAN_ROUNDS];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) warp_sum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        const int nw = (blockDim.x + 31) / 32;
-        long long v = lane < nw ? warp_sum[lane] : 0;
-        long long inc2 = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, inc2, o);
-            if (lane >= o) inc2 += y;
+        for (int k = 0; k < PLAN_ROUNDS; ++k) {
+            const int p = k * B + threadIdx.x;
+            cnt[k] = k < rounds && p < n_arrays ? chunks_at(p) : 0;
         }
-        if (lane < nw) warp_sum[lane] = inc2 - v;
+#pragma unroll
+        for (int k = 0; k < PLAN_ROUNDS; ++k) {
+            if (k < rounds) {
+                long long total;
+                const long long ex = block_exclusive_scan(cnt[k], &total);
+                const int p = k * B + threadIdx.x;
+                if (p < n_arrays) chunk_off[p] = carry + ex;
+                carry += total;
+            }
+        }
+    } else {
+        for (int k = 0; k < rounds; ++k) {
+            const int p = k * B + threadIdx.x;
+            long long total;
+            const long long ex = block_exclusive_scan(p < n_arrays ? chunks_at(p) : 0, &total);
+            if (p < n_arrays) chunk_off[p] = carry + ex;
+            carry += total;
+        }
     }
-    __syncthreads();
-    long long prefix = warp_sum[wid] + incl - local;
-    for (int a = a0; a < a1; ++a) {
-        chunk_off[a] = prefix;
-        prefix += chunks_at(a);
+    if (threadIdx.x == 0) {
+        chunk_off[n_arrays > 0 ? n_arrays : 0] = carry;
+        *counter = 0;
     }
-    if (a1 == n_arrays && a0 < a1) chunk_off[n_arrays] = prefix;
-    if (n_arrays <= 0 && threadIdx.x == 0) chunk_off[0] = 0;
-    if (threadIdx.x == 0) *counter = 0;
 }
 
 __global__ void k_seg_rank_base(const uint32_t *__restrict__ F, const long long *__restrict__ x_off,
