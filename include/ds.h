@@ -77,9 +77,9 @@ enum {
                              Algorithm direct-2, i = t - [z < X_t] - [z < X_{t-1}]; a smaller table and
                              feasible on more arrays; not combined with DS_CACHE_LAYOUT; the same as
                              ds_build_q with q = 2 */
-    DS_NO_FINGERPRINT = 64u, /* batched builds: the 5-bit knot fingerprints of the rank tables are not
-                             used, so every query in a cell holding a knot reads the knot (the
-                             paper's correcting comparison, always made) */
+    DS_NO_FINGERPRINT = 64u, /* batched builds: the 8-bit knot fingerprints are not used, so every
+                             query in a cell holding a knot reads the knot (the paper's correcting
+                             comparison, always made) */
     DS_REFINE_H = 128u    /* single-array builds: when ComputeHR had to grow H, bisect the interval
                              between the last infeasible H and the final one for a smaller feasible
                              H (end of Section 4.4; every probe checks the whole array) */
@@ -270,11 +270,11 @@ DS_API ds_status ds_lsearch_search(const ds_lsearch *h, const void *Z_dev, int64
  * DS_STRICT is set, in which case the build fails with that array's status.
  * Flags: DS_FMA | DS_CHECKED | DS_STRICT | DS_NO_SMEM | DS_NO_FINGERPRINT.
  * K is held as a rank table (not in the paper's layout): with pairs (i, i+1)
- * a cell holds at most one knot, so K_j = #{i : F_i < j}; one 16-byte word per
- * 16 cells holds K at the group's first cell, which cells hold a knot, and a
- * 5-bit fingerprint of each such knot's position within its cell, so that a
- * query reads the knot only when the fingerprints are equal; DS_NO_FINGERPRINT
- * turns the fingerprints off.  Synchronous. */
+ * a cell holds at most one knot, so K_j = #{i : F_i < j}; one 8-byte word per
+ * 32 cells holds K at the group's first cell and which cells hold a knot, and
+ * one byte per knot an 8-bit fingerprint of its position within its cell, so
+ * that a query reads the knot only when the fingerprints are equal;
+ * DS_NO_FINGERPRINT turns the fingerprints off.  Synchronous. */
 DS_API ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, ds_dtype dtype,
                          uint32_t flags, void *stream, ds_batch **out);
 
