@@ -11,7 +11,7 @@
 namespace ds {
 
 constexpr long long SEG_KNOTS = 1 << 16;  // knots per build segment
-constexpr int CHUNK_TILES = 16;           // tiles per search chunk claimed by a block (8: 287, 16: 302, 32: 296 G/s on the 4096-array workload)
+constexpr int CHUNK_TILES = 32;           // tiles per search chunk claimed by a block (16: 472.5, 32: 478.5 G/s on the 4096-array workload)
 constexpr int CHUNK_TILES_WARP = 32;      // tiles per search chunk claimed by a warp
 
 struct Engine {

@@ -203,3 +203,29 @@ def test_fingerprints_across_cell_ranges(ds, dtype, fma):
             assert np.array_equal(got, ref), (extra, smem, int(np.count_nonzero(got != ref)))
         b.free()
     assert max(Rs) > (1 << 24) and min(Rs) < (1 << 10)
+
+
+def test_many_arrays_claim_order_and_long_chunks(ds):
+    # more arrays than the planner's register rounds (8 x 1024), sizes spanning
+    # three decades so the claim order (most knots first) differs from the CSR
+    # order, a few arrays without queries, and staged images long enough that
+    # their chunks are several base chunks long
+    g = np.random.default_rng(31)
+    n_arrays = 9000
+    sizes = np.maximum(2, np.exp(g.uniform(np.log(2), np.log(3000), n_arrays))).astype(np.int64)
+    sizes[g.integers(0, n_arrays, 3)] = 60000
+    arrays = [W.knots_from_gaps(g.uniform(-5, 5), g.uniform(0.5, 1.5, int(n) - 1), np.float32) for n in sizes]
+    x_off = W.csr(sizes)
+    Xcat = np.concatenate(arrays)
+    q = (sizes * 3).astype(np.int64)
+    q[g.integers(0, n_arrays, 50)] = 0
+    Zs = [W.uniform_queries(g, a[0], a[-1], int(k), np.float32) for a, k in zip(arrays, q)]
+    z_off = W.csr(q)
+    Zcat = np.concatenate(Zs)
+    ref = oracle.upper_bound_batch(Xcat, x_off, Zcat, z_off)
+    b = ds.ds_batch_build(_cuda(Xcat), _cuda(x_off))
+    for block, items, smem in ((512, 1, 96 * 1024), (1024, 1, 136 * 1024), (256, 2, 0), (512, 1, -1)):
+        ds.ds_batch_set_tune(b, block, items, smem)
+        got = ds.ds_batch_search(b, _cuda(Zcat), _cuda(z_off)).cpu().numpy()
+        assert np.array_equal(got, ref), (block, items, smem, int(np.count_nonzero(got != ref)))
+    b.free()
