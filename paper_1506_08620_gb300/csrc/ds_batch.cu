@@ -459,7 +459,7 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
 template <typename T, int VPT, bool INTERP, int KIND>
 static const void *pick4(bool vec, bool warps, bool big)
 {
-    if constexpr (VPT == 1 && KIND != KIND_ALL)
+    if constexpr (VPT == 1 && direct_kind(KIND))
         if (vec && !warps && big) return (const void *)k_batch_search<T, 1, INTERP, true, KIND, false, 1024>;
     if (vec && warps) return (const void *)k_batch_search<T, VPT, INTERP, true, KIND, true>;
     return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, KIND>
@@ -474,6 +474,7 @@ static const void *pick3(bool vec, bool warps, bool big, int kind)
     case KIND_DIRECT_FPF:
         if constexpr (sizeof(T) == 4) return pick4<T, VPT, INTERP, KIND_DIRECT_FPF>(vec, warps, big);
         else return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
+    case KIND_LEARNED_ONLY: return pick4<T, VPT, INTERP, KIND_LEARNED_ONLY>(vec, warps, big);
     default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps, big);
     }
 }
@@ -494,7 +495,7 @@ static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, i
 static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0; }
 static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big)
 {
-    const int kind = !direct_only(e) ? KIND_ALL
+    const int kind = !direct_only(e) ? (e->n_direct == 0 && e->n_fallback == 0 ? KIND_LEARNED_ONLY : KIND_ALL)
                      : !e->fingerprints ? KIND_DIRECT
                      : e->fast_cells    ? KIND_DIRECT_FPF
                                         : KIND_DIRECT_FP;

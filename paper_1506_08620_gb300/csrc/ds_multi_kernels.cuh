@@ -98,8 +98,13 @@ template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint8_t *p, 
 // Kernel kinds: every mode (fingerprints decided per array at run time), or
 // direct arrays only, without or with fingerprints (the other paths compiled
 // out, which keeps the register count low), or with fingerprints and the
-// one-conversion cell form (float arrays, every R < 2^24 - 1).
-enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3 };
+// one-conversion cell form (float arrays, every R < 2^24 - 1), or learned
+// arrays only.
+enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3, KIND_LEARNED_ONLY = 4 };
+__host__ __device__ constexpr bool direct_kind(int k)
+{
+    return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
+}
 
 // img: the array's image (shared or global memory: for a direct array its
 // rank words and knot fingerprints); X: its knots (global memory for direct
@@ -109,7 +114,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
                                              const unsigned char *img, const T *X, const T *z, int32_t *r,
                                              uint64_t pol)
 {
-    if (KIND != KIND_ALL || d.mode == MODE_DIRECT) {
+    if (direct_kind(KIND) || (KIND == KIND_ALL && d.mode == MODE_DIRECT)) {
         // one rank word per query; for a cell holding a knot, the knot's
         // fingerprint; the knot X_t itself only when the two fingerprints are
         // equal (otherwise they order z and X_t: within a cell the fingerprint
@@ -148,7 +153,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
     }
     int32_t lo[NQ], n[NQ], top;
     bool done[NQ];
-    if (d.mode == MODE_LEARNED) {
+    if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {
         const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
         int stop = 1;
         while (stop * 2 <= d.seg_n) stop *= 2;
@@ -287,7 +292,7 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         // direct-only kernels: software pipeline, the next tile's queries are
         // loaded while this tile's table gathers are in flight (the general
         // kernel is at its register limit already)
-        constexpr bool PREFETCH = KIND != KIND_ALL;
+        constexpr bool PREFETCH = direct_kind(KIND);
         V zn[VPT];
         auto load_tile = [&](long long base) {
 #pragma unroll
