@@ -316,9 +316,9 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 const size_t xb = round_up((size_t)nk * sizeof(T), 16);
                 d.img_bytes = d.mode == MODE_BISECT && xb <= 0xFFFFFFF0u ? (uint32_t)xb : 0u;
                 off += xb;
-                if (d.mode == MODE_LEARNED) {  // every SG_STRIDE-th knot, for the two-level window search
+                if (d.mode == MODE_LEARNED) {  // the sampled knots S and S1 of the window search
                     d.sg = (long long)off;
-                    off += round_up((size_t)((d.n >> SG_SHIFT) + 2) * sizeof(T), 16);
+                    off += sample_bytes(d.n, sizeof(T)) + sample1_bytes(d.n, sizeof(T));
                 }
                 if (d.mode == MODE_BISECT) e->n_fallback += 1;
                 else e->n_learned += 1;
@@ -544,7 +544,8 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
     DS_TRY(occupancy(e, t, interp, vec, &grid));
     const int block = eff_block(e, t, vec), vpt = clamp_vpt(t.items);
     const bool warps = vec && t.smem_limit < 0;  // nothing staged, and warps claim their own chunks
-    const long long chunk = (long long)(warps ? 32 : block) * vpt * L * (warps ? CHUNK_TILES_WARP : CHUNK_TILES);
+    const int tiles = warps ? CHUNK_TILES_WARP : direct_only(e) ? CHUNK_TILES_DIRECT : CHUNK_TILES;
+    const long long chunk = (long long)(warps ? 32 : block) * vpt * L * tiles;
     const uint32_t smem_limit = (uint32_t)std::max(0, t.smem_limit);
     k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->desc_dev, e->order, smem_limit,
                                      e->chunk_off, e->counter);

@@ -11,7 +11,10 @@
 namespace ds {
 
 constexpr long long SEG_KNOTS = 1 << 16;  // knots per build segment
-constexpr int CHUNK_TILES = 32;           // tiles per search chunk claimed by a block (16: 472.5, 32: 478.5 G/s on the 4096-array workload)
+// tiles per search chunk claimed by a block: direct-only handles 32 (16: 472.5,
+// 32: 478.5 G/s on the 4096-array workload), others 16 (the learned workloads)
+constexpr int CHUNK_TILES_DIRECT = 32;
+constexpr int CHUNK_TILES = 16;
 constexpr int CHUNK_TILES_WARP = 32;      // tiles per search chunk claimed by a warp
 
 struct Engine {

@@ -15,9 +15,9 @@
 //   MODE_DIRECT    Algorithm direct with the array's own H, W, R; K is held
 //                  as a rank table with knot fingerprints (below).
 //   MODE_LEARNED   predicted index, bounded window, certificate, exact
-//                  fall-back; the window is searched in two fixed-depth
-//                  levels: over every 32nd knot (a small, L2-resident copy),
-//                  then over at most 32 knots.
+//                  fall-back; the window is searched in three fixed-depth
+//                  levels: over every 1024th knot (L1-resident), over at most
+//                  32 of every 32nd knot, then over at most 32 knots.
 //   MODE_BISECT    fixed-depth bisection over all knots (Algorithm
 //                  binaryoptnopad), the log-time fall-back where direct
 //                  search is infeasible.
@@ -35,6 +35,23 @@ enum ArrMode : int32_t { MODE_DIRECT = 0, MODE_LEARNED = 1, MODE_BISECT = 2 };
 // from 146 to 181 bytes).
 constexpr int SG_SHIFT = 5;
 constexpr int SG_STRIDE = 1 << SG_SHIFT;
+// A second sample level, every SG_STRIDE-th sample: S1_k = X_{min(k * SG_STRIDE^2, N)},
+// small enough to stay in L1 (128 KB for 2^24 float64 knots).  The window is
+// searched over S1, then over at most SG_STRIDE samples, then over at most
+// SG_STRIDE knots: the last two are contiguous 256-byte runs, so a query's
+// L2 requests do not grow with the window.
+constexpr int SG1_SHIFT = 2 * SG_SHIFT;
+
+// Byte sizes of the two sample tables of a learned array with N + 1 knots
+// (S right after the knots' copy, S1 right after S).
+__host__ __device__ __forceinline__ size_t sample_bytes(int32_t n, size_t elem)
+{
+    return ((size_t)((n >> SG_SHIFT) + 2) * elem + 15) / 16 * 16;
+}
+__host__ __device__ __forceinline__ size_t sample1_bytes(int32_t n, size_t elem)
+{
+    return ((size_t)((n >> SG1_SHIFT) + 2) * elem + 15) / 16 * 16;
+}
 
 constexpr uint32_t NO_X_IN_IMG = 0xFFFFFFFFu;  // the image does not hold the knots
 
@@ -59,7 +76,8 @@ struct __align__(16) ArrDesc {
     int32_t e_lo, e_hi;   // learned: recorded error bounds
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
-    long long sg;         // learned: byte offset of the sampled knots S_k = X_{min(32 k, N)}, k = 0..N/32+1
+    long long sg;         // learned: byte offset of the sampled knots S_k = X_{min(32 k, N)}, k = 0..N/32+1,
+                          // followed by S1_k = X_{min(1024 k, N)}, k = 0..N/1024+1
     uint32_t g_in_img;    // direct: byte offset of the knot fingerprints inside the image
     uint32_t pad_;
 };

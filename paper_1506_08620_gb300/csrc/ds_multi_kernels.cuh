@@ -183,16 +183,52 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
             }
         }
         if (nfail) atomicAdd(a.fallbacks, (unsigned long long)nfail);
-        // level 1: largest k in [lo/SG, hi/SG] with S_k = X_{SG k} <= z
-        // (S_{lo/32} <= X_lo <= z and S_{hi/32+1} >= X_{hi+1} > z)
+        // level 0: largest k in [lo/1024, hi/1024] with S1_k = X_{1024 k} <= z
+        // (S1_{lo/1024} <= X_lo <= z and S1_{hi/1024+1} >= X_{hi+1} > z); the
+        // search covers 2 top0 > ws0 >= the range's length
+        // (learned-only kernels; the general kernel, at its register limit,
+        // searches every 32nd knot directly, the same answer in more steps)
         const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
-        const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
-        const int32_t top1 = 1 << (31 - __clz(ws));
-        int32_t k1[NQ], nk[NQ];
+        int32_t k1[NQ], nk[NQ], top1 = SG_STRIDE / 2;
+        if constexpr (KIND == KIND_LEARNED_ONLY) {
+            const T *S1 = reinterpret_cast<const T *>(a.blob + d.sg + sample_bytes(d.n, sizeof(T)));
+            const int32_t ws0 = nfail ? ((d.n - 1) >> SG1_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG1_SHIFT) + 2;
+            const int32_t top0 = 1 << (31 - __clz(ws0));
+            int32_t k0[NQ], nk0[NQ], i0[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            k1[q] = lo[q] >> SG_SHIFT;
-            nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
+            for (int q = 0; q < NQ; ++q) {
+                k0[q] = lo[q] >> SG1_SHIFT;
+                nk0[q] = (hi[q] >> SG1_SHIFT) - k0[q] + 1;
+                i0[q] = 0;
+            }
+            for (int32_t k = top0; k > 0; k >>= 1) {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const int32_t rr = i0[q] | k;
+                    const int32_t w = rr < nk0[q] ? rr : nk0[q];
+                    if (!lt_exact<T>(z[q], tab_ld<false>(S1 + k0[q] + w, pol))) i0[q] = rr;
+                }
+            }
+            // level 1: the at most 32 samples S_k of that block inside the window
+            // (S_{k1} <= z: it is S1 of the block, or S_{lo/32}; S_{k1+nk} > z: it
+            // is S1 of the next block, or S_{hi/32+1})
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int32_t kb = k0[q] + (i0[q] < nk0[q] ? i0[q] : nk0[q] - 1);
+                const int32_t b1 = kb << SG_SHIFT, l1 = lo[q] >> SG_SHIFT, e1 = (hi[q] >> SG_SHIFT) + 1;
+                k1[q] = b1 > l1 ? b1 : l1;
+                nk[q] = (b1 + SG_STRIDE < e1 ? b1 + SG_STRIDE : e1) - k1[q];
+            }
+        } else {
+            // level 1 over every 32nd knot in the window (S_{lo/32} <= X_lo <= z and
+            // S_{hi/32+1} >= X_{hi+1} > z)
+            const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
+            top1 = 1 << (31 - __clz(ws));
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                k1[q] = lo[q] >> SG_SHIFT;
+                nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
+            }
         }
         int32_t i1[NQ];
 #pragma unroll
@@ -565,6 +601,7 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
         const long long start = x_off[sg.arr];
         T *Xd = reinterpret_cast<T *>(blob + d.xg);
         T *S = reinterpret_cast<T *>(blob + d.sg);
+        T *S1 = reinterpret_cast<T *>(blob + d.sg + sample_bytes(d.n, sizeof(T)));
         for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
             const T x = Xcat[i];
             const long long li = i - start;
@@ -572,6 +609,8 @@ __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *_
             if (d.mode == MODE_LEARNED) {  // S_k = X_{min(SG k, N)}, k = 0 .. N/SG + 1
                 if ((li & (SG_STRIDE - 1)) == 0) S[li >> SG_SHIFT] = x;
                 if (li == d.n) S[(d.n >> SG_SHIFT) + 1] = x;
+                if ((li & ((1 << SG1_SHIFT) - 1)) == 0) S1[li >> SG1_SHIFT] = x;
+                if (li == d.n) S1[(d.n >> SG1_SHIFT) + 1] = x;
             }
             if (d.mode == MODE_DIRECT) {  // f and fingerprint exactly as a query computes them
                 uint32_t g;
