@@ -115,9 +115,19 @@ template <typename T> struct BatchArgs {
 constexpr long long STAGE_Q_PER_BYTE = 4;  // 2: 472.5, 4: 481.4 G/s on the 4096-array workload
 constexpr long long STAGE_MAX_CHUNKS = 8;
 
+// Images smaller than this are read through L1 rather than staged: their
+// chunks are short, and a bulk copy and its barrier would cost more than the
+// first-touch misses.
+constexpr uint32_t STAGE_MIN_BYTES = 4096;
+
+__host__ __device__ __forceinline__ bool stage_image(const ArrDesc &d, uint32_t smem_limit)
+{
+    return d.img_bytes >= STAGE_MIN_BYTES && d.img_bytes <= smem_limit;
+}
+
 __host__ __device__ __forceinline__ long long chunk_len(const ArrDesc &d, long long base, uint32_t smem_limit)
 {
-    if (d.img_bytes == 0 || d.img_bytes > smem_limit) return base;
+    if (!stage_image(d, smem_limit)) return base;
     const long long want = (long long)d.img_bytes * STAGE_Q_PER_BYTE;
     const long long n = (want + base - 1) / base;
     return (n < 1 ? 1 : (n > STAGE_MAX_CHUNKS ? STAGE_MAX_CHUNKS : n)) * base;

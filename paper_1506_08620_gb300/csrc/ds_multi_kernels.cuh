@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
         const ArrDesc d = a.desc[arr];
         long long zs, ze;
         chunk_range(a, d, arr, p, c, &zs, &ze);
-        const bool use_smem = d.img_bytes > 0 && d.img_bytes <= a.smem_limit;
+        const bool use_smem = stage_image(d, a.smem_limit);
         if (use_smem && staged != arr) {
             if (!stage_again(smem, a.blob + d.img, d.img_bytes, &bar, parity, a.err)) return;
             parity ^= 1u;
