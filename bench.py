@@ -603,6 +603,10 @@ def setup_learned(args, ds, W, torch, dev, rank):
                                       "train_steps", "train_ms", "final_loss", "table_bytes")}
     if args.tune == "auto":  # the same engine autotuner as the batched form
         job.table["tune"] = ds.ds_learned_autotune(L, Zd, zo, out)
+    elif args.tune != "default":
+        blk, items, smem = (int(v) for v in args.tune.split(","))
+        ds.ds_learned_set_tune(L, blk, items, smem)
+        job.table["tune"] = ds.ds_learned_get_tune(L)
     job.kernel_key = "learned_search_%s" % job.dtype_name
     job.launches_per_step = 2
     if five:

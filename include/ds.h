@@ -364,6 +364,12 @@ DS_API ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, co
  * outputs are overwritten with valid results.  Synchronous. */
 DS_API ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
                                      int32_t *Icat_dev, void *stream, ds_tune_t *best);
+/* Set or read the launch configuration of the learned search, as
+ * ds_batch_set_tune / ds_batch_get_tune (DS_E_ARG for an smem_limit outside
+ * [-1, the device's opt-in limit - 2048] or a configuration that cannot be
+ * resident). */
+DS_API ds_status ds_learned_set_tune(ds_learned *L, const ds_tune_t *cfg);
+DS_API ds_status ds_learned_get_tune(const ds_learned *L, ds_tune_t *cfg);
 
 /* Host copy of array a's network parameters (1153 floats: W1[32] b1[32]
  * W2[32][32] b2[32] w3[32] b3) and its recorded error bounds: every knot i

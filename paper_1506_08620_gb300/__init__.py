@@ -19,7 +19,8 @@ from ._abi import (DS_CACHE_LAYOUT, DS_CHECKED, DS_F32, DS_F64, DS_FMA, DS_LEARN
 __all__ = [
     "ds_build", "ds_search", "ds_search_host", "ds_index_export", "ds_batch_build", "ds_batch_search",
     "ds_batch_autotune", "ds_batch_set_tune", "ds_batch_get_tune", "ds_batch_array", "ds_learned_build",
-    "ds_learned_search", "ds_learned_array", "ds_learned_cfg_default", "ds_mlp_forward", "ds_mlp_loss_grad",
+    "ds_learned_search", "ds_learned_autotune", "ds_learned_set_tune", "ds_learned_get_tune", "ds_learned_array",
+    "ds_learned_cfg_default", "ds_mlp_forward", "ds_mlp_loss_grad",
     "ds_adam_step", "ds_info", "ds_free", "DsError",
 ]
 
@@ -306,6 +307,17 @@ def ds_learned_autotune(L, Z, z_off=None, out=None, stream=None):
     check(lib().ds_learned_autotune(L.ptr, _dev(Z, "Z", L.dtype), zo, Z.numel(), _dev(out, "out", torch.int32),
                                     _stream(stream), ctypes.byref(best)), "ds_learned_autotune")
     return best.as_dict()
+
+
+def ds_learned_set_tune(L, block, items, smem_limit, blocks_per_sm=0):
+    t = _abi.ds_tune_t(block, items, smem_limit, blocks_per_sm, 0.0)
+    check(lib().ds_learned_set_tune(L.ptr, ctypes.byref(t)), "ds_learned_set_tune")
+
+
+def ds_learned_get_tune(L):
+    t = _abi.ds_tune_t()
+    check(lib().ds_learned_get_tune(L.ptr, ctypes.byref(t)), "ds_learned_get_tune")
+    return t.as_dict()
 
 
 def ds_learned_array(L, a):

@@ -84,6 +84,8 @@ _SIGS = {
     "ds_search_sorted": (ST, [P, I64, ST, P, I64, P, P]),
     "ds_histogram": (ST, [P, P, I64, P, P]),
     "ds_learned_autotune": (ST, [P, P, P, I64, P, P, ctypes.POINTER(ds_tune_t)]),
+    "ds_learned_set_tune": (ST, [P, ctypes.POINTER(ds_tune_t)]),
+    "ds_learned_get_tune": (ST, [P, ctypes.POINTER(ds_tune_t)]),
     "ds_lsearch_constants": (ST, [ctypes.c_int32, I64, P, ctypes.POINTER(I64)]),
     "ds_lsearch_build": (ST, [P, I64, ST, ctypes.c_int32, U32, P, ctypes.POINTER(P)]),
     "ds_lsearch_search": (ST, [P, P, I64, P, P]),

@@ -621,6 +621,23 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
     return DS_OK;
 }
 
+// A launch configuration given by the caller: values normalised as the
+// launch normalises them, and checked for residency.
+ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg)
+{
+    if (cfg.smem_limit < -1 || cfg.smem_limit > e->props.max_smem_optin - 2048) {
+        set_error("set_tune: smem_limit %d outside [-1, %d]", cfg.smem_limit, e->props.max_smem_optin - 2048);
+        return DS_E_ARG;
+    }
+    ds_tune_t t = cfg;
+    t.block = t.block == 128 || t.block == 512 || t.block == 1024 ? t.block : 256;
+    t.items = t.items == 1 || t.items == 2 ? t.items : 4;
+    int grid = 0;
+    DS_TRY(occupancy(e, t, false, true, &grid));
+    e->tune = t;
+    return DS_OK;
+}
+
 ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
                           cudaStream_t s, ds_tune_t *best_out)
 {
@@ -782,19 +799,12 @@ ds_status ds_batch_autotune(ds_batch *b, const void *Zcat_dev, const int64_t *z_
 
 ds_status ds_batch_set_tune(ds_batch *b, const ds_tune_t *cfg)
 {
-    if (!batch_ok(b) || !cfg || cfg->smem_limit < -1 || cfg->smem_limit > b->eng.props.max_smem_optin - 2048) {
+    if (!batch_ok(b) || !cfg) {
         ds::set_error("ds_batch_set_tune: bad argument");
         return DS_E_ARG;
     }
-    ds_tune_t t = *cfg;
-    t.block = t.block == 128 || t.block == 512 || t.block == 1024 ? t.block : 256;
-    t.items = t.items == 1 || t.items == 2 ? t.items : 4;
-    int grid = 0;
-    DS_TRY(ds::occupancy(&b->eng, t, false, true, &grid));
-    b->eng.tune = t;
-    return DS_OK;
+    return ds::engine_set_tune(&b->eng, *cfg);
 }
-
 ds_status ds_batch_get_tune(const ds_batch *b, ds_tune_t *cfg)
 {
     if (!batch_ok(b) || !cfg) return DS_E_ARG;

@@ -61,6 +61,7 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
                         void *y_out, int32_t *I, cudaStream_t s);
 ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
                           cudaStream_t s, ds_tune_t *best_out);
+ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg);
 void engine_free(Engine *e);
 ds_tune_t default_tune();
 

@@ -920,6 +920,22 @@ ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t
                                (cudaStream_t)stream, best);
 }
 
+ds_status ds_learned_set_tune(ds_learned *L, const ds_tune_t *cfg)
+{
+    if (!learned_ok(L) || !cfg) {
+        ds::set_error("ds_learned_set_tune: bad argument");
+        return DS_E_ARG;
+    }
+    return ds::engine_set_tune(&L->eng, *cfg);
+}
+
+ds_status ds_learned_get_tune(const ds_learned *L, ds_tune_t *cfg)
+{
+    if (!learned_ok(L) || !cfg) return DS_E_ARG;
+    *cfg = L->eng.tune;
+    return DS_OK;
+}
+
 ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, int32_t *e_lo, int32_t *e_hi,
                            int32_t *mode)
 {

@@ -251,3 +251,18 @@ def test_autotuned_learned_stays_exact(ds):
     I, _ = L5.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
     assert np.array_equal(I.cpu().numpy(), oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)[0])
     L5.free()
+
+
+def test_learned_set_tune_every_configuration_exact(ds):
+    w = _learned_small(n_knots=50_001, m=100_000)
+    X, Z = w["X"], _queries(w["X"], w["Z"], np.float64)
+    ref = oracle.upper_bound(X, Z)
+    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds))
+    for block, items, smem in ((512, 1, 0), (256, 2, -1), (128, 4, 48 * 1024), (1024, 1, 0)):
+        ds.ds_learned_set_tune(L, block, items, smem)
+        t = ds.ds_learned_get_tune(L)
+        assert (t["items"], t["smem_limit"]) == (items, smem)
+        assert np.array_equal(L.search(_cuda(Z)).cpu().numpy(), ref), (block, items, smem)
+    with pytest.raises(ds.DsError):
+        ds.ds_learned_set_tune(L, 256, 1, -2)
+    L.free()
