@@ -106,6 +106,126 @@ __host__ __device__ constexpr bool direct_kind(int k)
     return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
 }
 
+// Learned form, learned-only kernels: the window [lo, hi] (or, with `full`,
+// the whole array) searched in three fixed-depth levels, over S1_k =
+// X_{1024 k} (L1-resident), over at most 32 samples S_k = X_{32 k} (one
+// 256-byte run), then over at most 32 knots (another); r = the largest i in
+// the range with X_i <= z, if z lies in [X_lo, X_{hi+1}).
+template <typename T, int NQ, bool SM>
+__device__ __forceinline__ void learned_window3(const BatchArgs<T> &a, const ArrDesc &d, const T *X, const T *z,
+                                                const int32_t *lo_in, const int32_t *hi_in, bool full, int32_t *r,
+                                                uint64_t pol)
+{
+    const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
+    const T *S1 = reinterpret_cast<const T *>(a.blob + d.sg + sample_bytes(d.n, sizeof(T)));
+    int32_t lo[NQ], hi[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        lo[q] = full ? 0 : lo_in[q];
+        hi[q] = full ? d.n - 1 : hi_in[q];
+    }
+    // level 0: largest k in [lo/1024, hi/1024] with S1_k <= z (S1_{lo/1024} <=
+    // X_lo and S1_{hi/1024+1} >= X_{hi+1}); 2 top0 > ws0 >= the range's length
+    const int32_t ws0 = full ? ((d.n - 1) >> SG1_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG1_SHIFT) + 2;
+    const int32_t top0 = 1 << (31 - __clz(ws0));
+    int32_t k0[NQ], nk0[NQ], i0[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        k0[q] = lo[q] >> SG1_SHIFT;
+        nk0[q] = (hi[q] >> SG1_SHIFT) - k0[q] + 1;
+        i0[q] = 0;
+    }
+    for (int32_t k = top0; k > 0; k >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t rr = i0[q] | k;
+            const int32_t w = rr < nk0[q] ? rr : nk0[q];
+            if (!lt_exact<T>(z[q], tab_ld<false>(S1 + k0[q] + w, pol))) i0[q] = rr;
+        }
+    }
+    // level 1: the at most 32 samples of that block inside the range (the
+    // first is S1 of the block or S_{lo/32}, at most z; the one after the
+    // last is S1 of the next block or S_{hi/32+1}, above z)
+    int32_t k1[NQ], nk[NQ], i1[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int32_t kb = k0[q] + (i0[q] < nk0[q] ? i0[q] : nk0[q] - 1);
+        const int32_t b1 = kb << SG_SHIFT, l1 = lo[q] >> SG_SHIFT, e1 = (hi[q] >> SG_SHIFT) + 1;
+        k1[q] = b1 > l1 ? b1 : l1;
+        nk[q] = (b1 + SG_STRIDE < e1 ? b1 + SG_STRIDE : e1) - k1[q];
+        i1[q] = 0;
+    }
+    for (int32_t k = SG_STRIDE / 2; k > 0; k >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t rr = i1[q] | k;
+            const int32_t w = rr < nk[q] ? rr : nk[q];
+            if (!lt_exact<T>(z[q], tab_ld<SM>(S + k1[q] + w, pol))) i1[q] = rr;
+        }
+    }
+    // level 2: at most 32 knots
+    int32_t n2[NQ], i2[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int32_t ks = k1[q] + (i1[q] < nk[q] ? i1[q] : nk[q] - 1);
+        const int32_t b0 = ks << SG_SHIFT;
+        const int32_t l2 = b0 > lo[q] ? b0 : lo[q];
+        const int32_t e2 = (b0 + SG_STRIDE < hi[q] + 1) ? b0 + SG_STRIDE : hi[q] + 1;
+        lo[q] = l2;
+        n2[q] = e2 - l2;
+        i2[q] = 0;
+    }
+    for (int32_t k = SG_STRIDE / 2; k > 0; k >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t rr = i2[q] | k;
+            const int32_t w = rr < n2[q] ? rr : n2[q];
+            if (!lt_exact<T>(z[q], tab_ld<SM>(X + lo[q] + w, pol))) i2[q] = rr;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) r[q] = lo[q] + (i2[q] < n2[q] ? i2[q] : n2[q] - 1);
+}
+
+// Learned form, learned-only kernels.  The certificate is taken on the
+// answer instead of on the window: i is the answer exactly when
+// X_i <= z < X_{i+1} (the knots are sorted), and this fails exactly when z
+// lies outside [X_lo, X_{hi+1}).  The two knots sit in the lines the last
+// level has just read, so the check costs no gather of its own.  A thread
+// with a failed check searches all its queries again over the whole array
+// (out-of-domain queries: -1 and N).
+template <typename T, int NQ, bool SM>
+__device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrDesc &d, const T *X, const T *z,
+                                               int32_t *r, uint64_t pol)
+{
+    const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
+    int stop = 1;
+    while (stop * 2 <= d.seg_n) stop *= 2;
+    int32_t lo[NQ], hi[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const float p = pred_eval(pred_u<T>(z[q], d), sx, sa, sb, d.seg_n, stop);
+        window_of(floor_clamped(p, d.n), d, &lo[q], &hi[q]);
+    }
+    learned_window3<T, NQ, SM>(a, d, X, z, lo, hi, false, r, pol);
+    int nfail = 0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        nfail += !(!lt_exact<T>(z[q], tab_ld<SM>(X + r[q], pol)) && lt_exact<T>(z[q], tab_ld<SM>(X + r[q] + 1, pol)));
+    if (nfail) {
+        atomicAdd(a.fallbacks, (unsigned long long)nfail);
+        learned_window3<T, NQ, SM>(a, d, X, z, lo, hi, true, r, pol);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            if (lt_exact<T>(z[q], X[0])) r[q] = -1;
+            else if (!lt_exact<T>(z[q], X[d.n])) r[q] = d.n;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        if (a.checked && is_nan<T>(z[q])) r[q] = -1;
+}
+
 // img: the array's image (shared or global memory: for a direct array its
 // rank words and knot fingerprints); X: its knots (global memory for direct
 // arrays, shared or global for bisected ones).
@@ -151,9 +271,13 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         }
         return;
     }
+    if constexpr (KIND == KIND_LEARNED_ONLY) {
+        learned_answer<T, NQ, SM>(a, d, X, z, r, pol);
+        return;
+    }
     int32_t lo[NQ], n[NQ], top;
     bool done[NQ];
-    if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {
+    if (d.mode == MODE_LEARNED) {
         const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
         int stop = 1;
         while (stop * 2 <= d.seg_n) stop *= 2;
@@ -183,52 +307,16 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
             }
         }
         if (nfail) atomicAdd(a.fallbacks, (unsigned long long)nfail);
-        // level 0: largest k in [lo/1024, hi/1024] with S1_k = X_{1024 k} <= z
-        // (S1_{lo/1024} <= X_lo <= z and S1_{hi/1024+1} >= X_{hi+1} > z); the
-        // search covers 2 top0 > ws0 >= the range's length
-        // (learned-only kernels; the general kernel, at its register limit,
-        // searches every 32nd knot directly, the same answer in more steps)
+        // level 1: largest k in [lo/SG, hi/SG] with S_k = X_{SG k} <= z
+        // (S_{lo/32} <= X_lo <= z and S_{hi/32+1} >= X_{hi+1} > z)
         const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
-        int32_t k1[NQ], nk[NQ], top1 = SG_STRIDE / 2;
-        if constexpr (KIND == KIND_LEARNED_ONLY) {
-            const T *S1 = reinterpret_cast<const T *>(a.blob + d.sg + sample_bytes(d.n, sizeof(T)));
-            const int32_t ws0 = nfail ? ((d.n - 1) >> SG1_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG1_SHIFT) + 2;
-            const int32_t top0 = 1 << (31 - __clz(ws0));
-            int32_t k0[NQ], nk0[NQ], i0[NQ];
+        const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
+        const int32_t top1 = 1 << (31 - __clz(ws));
+        int32_t k1[NQ], nk[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                k0[q] = lo[q] >> SG1_SHIFT;
-                nk0[q] = (hi[q] >> SG1_SHIFT) - k0[q] + 1;
-                i0[q] = 0;
-            }
-            for (int32_t k = top0; k > 0; k >>= 1) {
-#pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const int32_t rr = i0[q] | k;
-                    const int32_t w = rr < nk0[q] ? rr : nk0[q];
-                    if (!lt_exact<T>(z[q], tab_ld<false>(S1 + k0[q] + w, pol))) i0[q] = rr;
-                }
-            }
-            // level 1: the at most 32 samples S_k of that block inside the window
-            // (S_{k1} <= z: it is S1 of the block, or S_{lo/32}; S_{k1+nk} > z: it
-            // is S1 of the next block, or S_{hi/32+1})
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int32_t kb = k0[q] + (i0[q] < nk0[q] ? i0[q] : nk0[q] - 1);
-                const int32_t b1 = kb << SG_SHIFT, l1 = lo[q] >> SG_SHIFT, e1 = (hi[q] >> SG_SHIFT) + 1;
-                k1[q] = b1 > l1 ? b1 : l1;
-                nk[q] = (b1 + SG_STRIDE < e1 ? b1 + SG_STRIDE : e1) - k1[q];
-            }
-        } else {
-            // level 1 over every 32nd knot in the window (S_{lo/32} <= X_lo <= z and
-            // S_{hi/32+1} >= X_{hi+1} > z)
-            const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
-            top1 = 1 << (31 - __clz(ws));
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                k1[q] = lo[q] >> SG_SHIFT;
-                nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
-            }
+        for (int q = 0; q < NQ; ++q) {
+            k1[q] = lo[q] >> SG_SHIFT;
+            nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
         }
         int32_t i1[NQ];
 #pragma unroll
