@@ -106,7 +106,7 @@ __host__ __device__ constexpr bool direct_kind(int k)
     return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
 }
 
-// Learned form, learned-only kernels: the window [lo, hi] (or, with `full`,
+// Learned form: the window [lo, hi] (or, with `full`,
 // the whole array) searched in three fixed-depth levels, over S1_k =
 // X_{1024 k} (L1-resident), over at most 32 samples S_k = X_{32 k} (one
 // 256-byte run), then over at most 32 knots (another); r = the largest i in
@@ -187,7 +187,7 @@ __device__ __forceinline__ void learned_window3(const BatchArgs<T> &a, const Arr
     for (int q = 0; q < NQ; ++q) r[q] = lo[q] + (i2[q] < n2[q] ? i2[q] : n2[q] - 1);
 }
 
-// Learned form, learned-only kernels.  The certificate is taken on the
+// Learned form.  The certificate is taken on the
 // answer instead of on the window: i is the answer exactly when
 // X_i <= z < X_{i+1} (the knots are sorted), and this fails exactly when z
 // lies outside [X_lo, X_{hi+1}).  The two knots sit in the lines the last
@@ -271,86 +271,22 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         }
         return;
     }
-    if constexpr (KIND == KIND_LEARNED_ONLY) {
+    if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {  // learned arrays
         learned_answer<T, NQ, SM>(a, d, X, z, r, pol);
         return;
     }
-    int32_t lo[NQ], n[NQ], top;
+    // bisected arrays: fixed-depth search over all knots (Algorithm binaryoptnopad)
+    int32_t lo[NQ], n[NQ];
     bool done[NQ];
-    if (d.mode == MODE_LEARNED) {
-        const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
-        int stop = 1;
-        while (stop * 2 <= d.seg_n) stop *= 2;
-        int32_t hi[NQ];
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float p = pred_eval(pred_u<T>(z[q], d), sx, sa, sb, d.seg_n, stop);
-            window_of(floor_clamped(p, d.n), d, &lo[q], &hi[q]);
-        }
-        T xl[NQ], xh[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            xl[q] = tab_ld<SM>(X + lo[q], pol);
-            xh[q] = tab_ld<SM>(X + hi[q] + 1, pol);
-        }
-        int nfail = 0;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            done[q] = false;
-            // certificate X_lo <= z < X_{hi+1}; otherwise the exact full search
-            if (!(!lt_exact<T>(z[q], xl[q]) && lt_exact<T>(z[q], xh[q]))) {
-                ++nfail;
-                lo[q] = 0;
-                hi[q] = d.n - 1;
-                if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
-                else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
-            }
-        }
-        if (nfail) atomicAdd(a.fallbacks, (unsigned long long)nfail);
-        // level 1: largest k in [lo/SG, hi/SG] with S_k = X_{SG k} <= z
-        // (S_{lo/32} <= X_lo <= z and S_{hi/32+1} >= X_{hi+1} > z)
-        const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
-        const int32_t ws = nfail ? ((d.n - 1) >> SG_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG_SHIFT) + 2;
-        const int32_t top1 = 1 << (31 - __clz(ws));
-        int32_t k1[NQ], nk[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            k1[q] = lo[q] >> SG_SHIFT;
-            nk[q] = (hi[q] >> SG_SHIFT) - k1[q] + 1;
-        }
-        int32_t i1[NQ];
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) i1[q] = 0;
-        for (int32_t k = top1; k > 0; k >>= 1) {
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const int32_t rr = i1[q] | k;
-                const int32_t w = rr < nk[q] ? rr : nk[q];
-                if (!lt_exact<T>(z[q], tab_ld<SM>(S + k1[q] + w, pol))) i1[q] = rr;
-            }
-        }
-        // level 2: at most SG_STRIDE knots
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int32_t ks = k1[q] + (i1[q] < nk[q] ? i1[q] : nk[q] - 1);
-            const int32_t b0 = ks << SG_SHIFT;
-            const int32_t l2 = b0 > lo[q] ? b0 : lo[q];
-            const int32_t e2 = (b0 + SG_STRIDE < hi[q] + 1) ? b0 + SG_STRIDE : hi[q] + 1;
-            lo[q] = l2;
-            n[q] = e2 - l2;
-        }
-        top = SG_STRIDE / 2;
-    } else {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            lo[q] = 0;
-            n[q] = d.n;
-            done[q] = false;
-            if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
-            else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
-        }
-        top = d.pbits;
+    for (int q = 0; q < NQ; ++q) {
+        lo[q] = 0;
+        n[q] = d.n;
+        done[q] = false;
+        if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
+        else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
     }
+    const int32_t top = d.pbits;
     // interleaved fixed-depth bisection (Algorithm binaryoptnopad)
     int32_t i[NQ];
 #pragma unroll
