@@ -762,10 +762,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             const bool zero = (cfg.flags & DS_LEARNED_ZERO_BOUND) != 0;
             d.e_lo = zero ? 0 : hlo[k];
             d.e_hi = zero ? 0 : hhi[k];
-            long long w = (long long)d.e_lo + d.e_hi + 3;
-            long long t = 1;
-            while (t * 2 <= w) t *= 2;
-            d.aux = (int32_t)t;
+            const long long w = (long long)d.e_lo + d.e_hi + 3;
             L->max_window = std::max(L->max_window, w);
         }
         ce = cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);

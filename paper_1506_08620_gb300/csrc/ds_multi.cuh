@@ -67,8 +67,7 @@ struct __align__(16) ArrDesc {
     uint32_t R;           // direct: largest cell
     int32_t form;         // direct: FForm
     int32_t pbits;        // bisection over all knots: 2^floor(log2 N)
-    int32_t aux;          // learned: 2^floor(log2(window width)); direct: 1 if the knot
-                          // fingerprints of the rank table are used
+    int32_t aux;          // direct: 1 if the knot fingerprints of the rank table are used
     double H, W, X0;      // direct: parameters in the array's precision (held exactly)
     double XN;            // last knot
     float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32)
