@@ -316,8 +316,11 @@ DS_API ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double 
  * on exact answers of sampled queries; the largest prediction error over all
  * knots is recorded at build time and each query is answered exactly by a
  * fixed-depth bisection (Algorithm binaryopt) inside the bounded window around
- * the prediction, certified by X_lo <= z < X_{hi+1}; a failed certificate
- * falls back to the array's exact full search.  Arrays on which direct search
+ * the prediction, in three levels (every 1024th knot, at most 32 of every 32nd
+ * knot, at most 32 knots); the window certificate X_lo <= z < X_{hi+1} is
+ * tested in its equivalent form X_i <= z < X_{i+1} on the answer i, and a
+ * failed certificate falls back to the array's exact full search (in the
+ * batched form a thread's queries are searched again together).  Arrays on which direct search
  * is feasible with at most max_cells_per_knot cells per knot use it instead
  * (unless DS_LEARNED_FORCE).
  * ------------------------------------------------------------------------ */
