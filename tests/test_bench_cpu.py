@@ -1,0 +1,67 @@
+"""Host-side logic of bench.py, on CPU: the DRAM traffic of a capture is
+scaled to the full workload and tied to the kernel sources it was taken on,
+and every workload names its configuration."""
+import argparse
+import json
+
+import pytest
+
+import bench
+
+
+def _args(**kw):
+    base = dict(gpus=1, steps=1, warmup=0, impl="ours", workload="direct_f64", variant="plain", no_extras=True,
+                cpu_seconds=0.1, queries=0, tune="auto", record_traffic="")
+    base.update(kw)
+    return argparse.Namespace(**base)
+
+
+def _ncu_csv(path, reads, writes):
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for i, (r, w) in enumerate(zip(reads, writes)):
+        rows.append('"%d","k","dram__bytes_read.sum","Mbyte","%s"' % (i, r))
+        rows.append('"%d","k","dram__bytes_write.sum","byte","%s"' % (i, w))
+        rows.append('"%d","k","gpu__time_duration.sum","ns","1000"' % i)
+    path.write_text("==PROF== a line ncu prints\n" + "\n".join(rows) + "\n")
+
+
+def test_traffic_is_scaled_and_tied_to_the_sources(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    csv = tmp_path / "cap.csv"
+    _ncu_csv(csv, ["100", "102", "104"], ["1,000,000", "2000000", "3000000"])
+    full = bench.workload_config(_args())["queries"]
+    bench.record_traffic(_args(record_traffic=str(csv), queries=full // 8))
+    d = json.load(open(bench.TRAFFIC_PATH))
+    e = d["search_f64_plain"]
+    assert e["launches"] == 3
+    assert e["captured_bytes_per_launch"] == pytest.approx(102e6 + 2e6)
+    assert e["bytes_per_launch"] == pytest.approx(8 * (102e6 + 2e6))
+    assert bench.traffic_for("search_f64_plain") == pytest.approx(8 * (102e6 + 2e6))
+    # a change of the kernel sources makes the capture stale
+    monkeypatch.setattr(bench, "source_hash", lambda key: "0" * 16)
+    assert bench.traffic_for("search_f64_plain") is None
+
+
+def test_capture_at_the_full_size_is_not_scaled(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    csv = tmp_path / "cap.csv"
+    _ncu_csv(csv, ["2000"], ["1000000000"])
+    full = bench.workload_config(_args(workload="batched_f32"))["queries"]
+    bench.record_traffic(_args(workload="batched_f32", record_traffic=str(csv), queries=full))
+    e = json.load(open(bench.TRAFFIC_PATH))["batch_search_f32"]
+    assert e["bytes_per_launch"] == pytest.approx(3e9) and e["scaled"] == "captured at the full workload"
+
+
+def test_capture_without_dram_rows_is_refused(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "TRAFFIC_PATH", str(tmp_path / "traffic.json"))
+    csv = tmp_path / "cap.csv"
+    csv.write_text('"ID","Metric Name","Metric Unit","Metric Value"\n"0","gpu__time_duration.sum","ns","5"\n')
+    with pytest.raises(SystemExit):
+        bench.record_traffic(_args(record_traffic=str(csv), queries=1 << 20))
+
+
+@pytest.mark.parametrize("workload", bench.WORKLOADS)
+def test_every_workload_names_its_configuration(workload):
+    cfg = bench.workload_config(_args(workload=workload))
+    assert cfg["workload"] and "queries" in cfg and "step" in cfg and "l2" in cfg
+    assert bench.kernel_key_of(_args(workload=workload))
