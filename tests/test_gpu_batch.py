@@ -229,3 +229,33 @@ def test_many_arrays_claim_order_and_long_chunks(ds):
         got = ds.ds_batch_search(b, _cuda(Zcat), _cuda(z_off)).cpu().numpy()
         assert np.array_equal(got, ref), (block, items, smem, int(np.count_nonzero(got != ref)))
     b.free()
+
+
+def test_array_near_the_32_bit_cell_limit(ds):
+    # one narrow gap among unit gaps sets R = trunc(H D_N) close to 2^32: about
+    # 1 GB of rank words, built by warps whose cell spans hold millions of
+    # groups, and searched through L1 (no shared-memory limit holds it)
+    g = np.random.default_rng(41)
+    gaps = np.ones(999)
+    gaps[500] = 2.6e-7
+    big = W.knots_from_gaps(-3.0, gaps, np.float64)
+    small = W.knots_from_gaps(5.0, g.uniform(0.5, 1.5, 300), np.float64)
+    hr = oracle.compute_hr(big)
+    assert hr["status"] == oracle.OR_OK and 3.0e9 < hr["R"] < 2 ** 32
+    x_off = W.csr([big.size, small.size])
+    Xcat = np.concatenate([big, small])
+    Zs = []
+    for a in (big, small):
+        Zs.append(np.concatenate([W.adversarial_queries(a), W.midpoints(a), W.uniform_queries(g, a[0], a[-1], 200_000, np.float64),
+                                  np.array([np.nextafter(a[0], -np.inf), a[-1], a[-1] + 1.0])]))
+    z_off = W.csr([z.size for z in Zs])
+    Zcat = np.concatenate(Zs)
+    ref = oracle.upper_bound_batch(Xcat, x_off, Zcat, z_off)
+    b = ds.ds_batch_build(_cuda(Xcat), _cuda(x_off))
+    p = ds.ds_batch_array(b, 0)
+    assert p["mode"] == 0 and p["R"] == hr["R"] and p["H"] == hr["H"]
+    for block, items, smem in ((512, 1, 96 * 1024), (256, 2, 0)):
+        ds.ds_batch_set_tune(b, block, items, smem)
+        got = ds.ds_batch_search(b, _cuda(Zcat), _cuda(z_off)).cpu().numpy()
+        assert np.array_equal(got, ref), (block, items, smem, int(np.count_nonzero(got != ref)))
+    b.free()
