@@ -267,6 +267,17 @@ def cpu_baseline(X, Z, seconds):
     dt = time.perf_counter() - t0
     res = {"value": n / dt, "unit": "lookups/s", "cores": 1, "kind": "oracle",
            "sample": "first %d of the %d queries, one pass, %.1f s" % (n, Z.size, dt)}
+    # the same oracle on every host core: a static partition of the sample, one
+    # slice per thread (the C calls run without the interpreter lock)
+    cores = os.cpu_count() or 1
+    if cores > 1:
+        import concurrent.futures as cf
+        parts = np.array_split(np.arange(n), cores)
+        with cf.ThreadPoolExecutor(cores) as ex:
+            t0 = time.perf_counter()
+            list(ex.map(lambda idx: oracle.upper_bound(X, Z[idx[0]:idx[-1] + 1]) if idx.size else None, parts))
+            dt_all = time.perf_counter() - t0
+        res["all_cores"] = {"value": n / dt_all, "cores": cores}
     # the paper's method on the host: the oracle's own Algorithm direct (scalar,
     # one thread) with its own table, on the same sample, where it is feasible
     try:
