@@ -1,0 +1,87 @@
+"""Pins, on the oracle's own tables, for the two facts the batched rank table
+rests on (Section 4, Eq. indexdef):
+
+* with pairs (i, i+1) ComputeHR makes F strictly increasing, so a cell holds at
+  most one knot and K_j = min{i : F_i >= j} is the rank #{i : F_i < j}; a
+  word per 32 cells (K at the group's first cell and a mask of the cells that
+  hold a knot) then gives K_j = K_{32 g} + popc(mask below j mod 32);
+* the knot fingerprint floor(256 (v - trunc v)) is computed exactly in float
+  arithmetic (v - trunc v is exact, and so is the product by 256), and within
+  one cell it is a non-decreasing function of v."""
+from fractions import Fraction
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1506_08620_gb300 import workloads as W
+
+
+def _arrays(dtype, count, seed):
+    g = np.random.default_rng(seed)
+    for _ in range(count):
+        n = int(g.integers(2, 400))
+        law = g.integers(0, 3)
+        gaps = (g.uniform(0.5, 1.5, n - 1) if law == 0 else
+                g.lognormal(0.0, 1.0, n - 1) if law == 1 else
+                np.where(g.random(n - 1) < 0.05, g.uniform(50, 100, n - 1), g.uniform(0.5, 1.5, n - 1)))
+        yield W.knots_from_gaps(float(g.uniform(-50, 50)), gaps, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("fma", [False, True])
+def test_k_is_the_rank_of_the_knot_cells(dtype, fma):
+    checked = 0
+    for X in _arrays(dtype, 150, 5 + fma + 2 * (dtype == np.float64)):
+        hr = oracle.compute_hr(X, fma)
+        if hr["status"] != oracle.OR_OK:
+            continue
+        st, K, F = oracle.fill_k(X, hr["H"], hr["W"], hr["R"], fma)
+        assert st == oracle.OR_OK
+        F = F.astype(np.int64)
+        assert np.all(np.diff(F) > 0)  # strictly increasing: at most one knot per cell
+        R = int(hr["R"])
+        j = np.arange(R + 1)
+        assert np.array_equal(K, np.searchsorted(F, j, side="left"))  # K_j = #{i : F_i < j}
+        assert set(np.unique(np.diff(K))) <= {0, 1}
+        # the 32-cell words: K at each group's first cell and the knot mask
+        holds = np.zeros(R + 1, dtype=bool)
+        holds[F] = True
+        G = R // 32 + 1
+        base = K[np.arange(G) * 32]
+        mask = np.zeros(G, dtype=np.uint64)
+        for c in np.nonzero(holds)[0]:
+            mask[c // 32] |= np.uint64(1) << np.uint64(c % 32)
+        for jj in j:
+            below = int(mask[jj // 32]) & ((1 << (jj % 32)) - 1)
+            assert base[jj // 32] + bin(below).count("1") == K[jj]
+            assert bool((int(mask[jj // 32]) >> (jj % 32)) & 1) == holds[jj]
+        checked += 1
+    assert checked > 100
+
+
+def _exact_fp(v):
+    fv = Fraction(float(v))
+    if fv < 0:
+        return 0
+    return math.floor(256 * (fv - math.floor(fv)))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_fingerprint_is_exact_and_monotone_within_a_cell(dtype):
+    g = np.random.default_rng(17)
+    # values across the exponent range of the cells a table can have
+    v = np.concatenate([g.uniform(0, 1, 4000), g.uniform(0, 2 ** 12, 4000), g.uniform(0, 2 ** 23, 4000),
+                        2.0 ** g.uniform(-10, 31, 4000)]).astype(dtype)
+    j = np.trunc(v)
+    frac = (v - j).astype(dtype)  # one rounding of the array's precision
+    fp = np.floor(frac * dtype(256)).astype(np.int64)
+    exact = np.array([_exact_fp(x) for x in v])
+    assert np.array_equal(fp, exact)
+    # monotone within a cell: sort, and compare neighbours in the same cell
+    order = np.argsort(v, kind="stable")
+    vs, js, fs = v[order], j[order], fp[order]
+    same = js[1:] == js[:-1]
+    assert np.all(fs[1:][same] >= fs[:-1][same])
+    assert np.all((fs >= 0) & (fs < 256))
