@@ -7,7 +7,10 @@ rests on (Section 4, Eq. indexdef):
   hold a knot) then gives K_j = K_{32 g} + popc(mask below j mod 32);
 * the knot fingerprint floor(256 (v - trunc v)) is computed exactly in float
   arithmetic (v - trunc v is exact, and so is the product by 256), and within
-  one cell it is a non-decreasing function of v."""
+  one cell it is a non-decreasing function of v;
+
+and, for the learned form, that the certificate tested on the answer is the
+window certificate."""
 from fractions import Fraction
 import math
 
@@ -85,3 +88,23 @@ def test_fingerprint_is_exact_and_monotone_within_a_cell(dtype):
     same = js[1:] == js[:-1]
     assert np.all(fs[1:][same] >= fs[:-1][same])
     assert np.all((fs >= 0) & (fs < 256))
+
+
+def test_answer_side_certificate_equals_the_window_certificate():
+    # learned form: for every window [lo, hi] and query z, some i in [lo, hi]
+    # passes X_i <= z < X_{i+1} exactly when X_lo <= z < X_{hi+1}, and then
+    # that i is the definition's answer (the knots are sorted)
+    g = np.random.default_rng(23)
+    for _ in range(40):
+        X = W.knots_from_gaps(float(g.uniform(-5, 5)), g.uniform(0.5, 1.5, int(g.integers(2, 24))), np.float64)
+        N = X.size - 1
+        Z = np.concatenate([X, np.nextafter(X, -np.inf), np.nextafter(X, np.inf), g.uniform(X[0] - 2, X[-1] + 2, 50)])
+        truth = oracle.upper_bound(X, Z)
+        for lo in range(N):
+            for hi in range(lo, N):
+                win = (X[lo] <= Z) & (Z < X[hi + 1])
+                for k, z in enumerate(Z):
+                    passing = [i for i in range(lo, hi + 1) if X[i] <= z < X[i + 1]]
+                    assert bool(passing) == bool(win[k])
+                    if passing:
+                        assert passing == [truth[k]]
