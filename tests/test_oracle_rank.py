@@ -9,8 +9,9 @@ rests on (Section 4, Eq. indexdef):
   arithmetic (v - trunc v is exact, and so is the product by 256), and within
   one cell it is a non-decreasing function of v;
 
-and, for the learned form, that the certificate tested on the answer is the
-window certificate."""
+and, for the float32 one-conversion cell form, that trunc(m(256 H y + 256 c))
+equals 256 j + g; and, for the learned form, that the certificate tested on
+the answer is the window certificate."""
 from fractions import Fraction
 import math
 
@@ -108,3 +109,37 @@ def test_answer_side_certificate_equals_the_window_certificate():
                     assert bool(passing) == bool(win[k])
                     if passing:
                         assert passing == [truth[k]]
+
+
+def test_one_conversion_cell_form_of_float32():
+    # q = trunc(m(256 H y + 256 c)) gives the cell and the fingerprint at once:
+    # scaling by 256 commutes with the single rounding of the fused multiply-add
+    # (where the result is a normal float; below 2^-126 both give cell 0 and
+    # fingerprint 0), and trunc(256 v) = 256 trunc(v) + floor(256 frac(v))
+    from tests import exact
+    g = np.random.default_rng(29)
+    f32 = np.float32
+    checked = 0
+    for _ in range(4000):
+        H = f32(2.0 ** g.uniform(-12, 16))
+        if g.random() < 0.5:  # Eq. function: y = m(z - X0), c = 0
+            X0 = f32(g.uniform(-1e4, 1e4))
+            z = f32(float(X0) + g.uniform(-10, 2 ** 24 / float(H)))
+            y = exact.add(z, -X0, f32)
+            c = f32(0.0)
+        else:  # Eq. fma: y = z, c = -W with W = m(H X0)
+            X0 = f32(g.uniform(-1e4, 1e4))
+            y = f32(float(X0) + g.uniform(-10, 2 ** 24 / float(H)))
+            c = -exact.mul(H, X0, f32)
+        v = exact.round_nearest(Fraction(float(H)) * Fraction(float(y)) + Fraction(float(c)), f32)
+        v256 = exact.round_nearest(Fraction(float(f32(256) * H)) * Fraction(float(y)) + Fraction(float(f32(256) * c)), f32)
+        if abs(float(v)) >= 2.0 ** -126:
+            assert float(v256) == 256.0 * float(v)
+        elif float(v) >= 0:
+            assert 0 <= float(v256) < 1.0
+        if 0 <= float(v) < 2 ** 24 - 1:
+            q = exact.trunc_u32(v256)
+            fv = Fraction(float(v))
+            assert q == 256 * math.floor(fv) + math.floor(256 * (fv - math.floor(fv)))
+            checked += 1
+    assert checked > 1500
