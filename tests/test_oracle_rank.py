@@ -143,3 +143,26 @@ def test_one_conversion_cell_form_of_float32():
             assert q == 256 * math.floor(fv) + math.floor(256 * (fv - math.floor(fv)))
             checked += 1
     assert checked > 1500
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 5])
+def test_packed_cell_differences_fit_six_bits(q):
+    # the float64 single-array path packs K in blocks of 12 cells as a base and
+    # 12 differences of 6 bits: a cell holds at most q knots (pairs (i, i+q)
+    # are separated), so within a block K grows by at most 11 q <= 55 < 64
+    g = np.random.default_rng(31 + q)
+    checked = 0
+    for X in _arrays(np.float64, 120, 40 + q):
+        hr = oracle.compute_hr(X, False, q=q, general=q > 1)
+        if hr["status"] != oracle.OR_OK:
+            continue
+        st, K, _ = oracle.fill_k(X, hr["H"], hr["W"], hr["R"], False, q=q, general=q > 1)
+        assert st == oracle.OR_OK
+        K = K.astype(np.int64) & 0x3FFFFFFF
+        d = np.diff(K)
+        assert d.min() >= 0 and d.max() <= q
+        nb = (K.size + 11) // 12
+        Kp = np.concatenate([K, np.full(nb * 12 - K.size, K[-1])]).reshape(nb, 12)
+        assert (Kp - Kp[:, :1]).max() <= 11 * q < 64
+        checked += 1
+    assert checked > 60
