@@ -410,11 +410,15 @@ DS_API ds_status ds_adam_step(float *theta_dev, float *m_dev, float *v_dev, cons
  * new buffer.  The call allocates nothing (no cudaMalloc, cudaFree or
  * allocating library routine) and returns after the table is written.
  *
- * The first call on a device looks up the scratch array's device address
- * (with that device current); make that first call before any stream
- * capture.  Every call uses the same scratch and re-initialises the parts
+ * Every call looks up the scratch array's device address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing), so the call stays
+ * valid after cudaDeviceReset.  The call reads H, W and R back to the host
+ * and synchronizes `stream`: it must not be made while the stream is being
+ * captured.  Every call uses the same scratch and re-initialises the parts
  * that must start from a known value; calls whose GPU work overlaps (from two
- * streams or two host threads) race on the scratch.  flags: 0 or DS_FMA.
+ * streams or two host threads) race on the scratch.  An infeasible array
+ * returns the status and message of ds_build (with the offending knot).
+ * flags: 0 or DS_FMA.
  * ------------------------------------------------------------------------ */
 #define DS_STATIC_MAX_KNOTS 262144
 DS_API ds_status ds_build_table_static(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t flags,

@@ -176,17 +176,6 @@ static ds_status refine_h(const T *X, long long n_knots, HRState *st, HRState *h
     return DS_OK;
 }
 
-static const char *hr_message(int status)
-{
-    switch (status) {
-    case DS_E_NOT_INCREASING: return "knots are not strictly increasing finite values";
-    case DS_E_INDISTINGUISHABLE: return "m(X_i - X_0) == m(X_{i-g} - X_0) (g = 1, or 2 for DirectGap2): direct search infeasible";
-    case DS_E_OVERFLOW: return "m(H (X_N - X_0)) >= 2^32: direct search infeasible (Q = 32)";
-    case DS_E_NO_CONVERGENCE: return "growth of H did not settle";
-    default: return "";
-    }
-}
-
 template <typename T, bool FMA>
 static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags, int q, cudaStream_t s, ds_index *idx,
                              bool x0zero)
@@ -209,10 +198,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     idx->H = hs.H;
     idx->W = hs.W;
     if (hs.status != DS_OK) {
-        set_error("ds_build: %s (knot %lld)", hr_message(hs.status),
-                  (long long)(hs.status == DS_E_NOT_INCREASING
-                                  ? (hs.bad_nonfinite != NONE64 ? hs.bad_nonfinite : hs.bad_order)
-                                  : hs.bad_indist));
+        set_error("ds_build: %s (knot %lld)", hr_message(hs.status), hr_bad_knot(hs));
         return (ds_status)hs.status;
     }
     const unsigned long long R = hs.R;

@@ -67,6 +67,26 @@ struct HRState {
 constexpr unsigned long long NONE64 = ~0ull;
 constexpr int MAX_HR_PASSES = 64;
 
+// Message of a ComputeHR failure status, and the knot it names: the first
+// non-finite or out-of-order knot, or the first indistinguishable one.
+inline const char *hr_message(int status)
+{
+    switch (status) {
+    case DS_E_NOT_INCREASING: return "knots are not strictly increasing finite values";
+    case DS_E_INDISTINGUISHABLE:
+        return "m(X_i - X_0) == m(X_{i-g} - X_0) (g = 1, or 2 for DirectGap2): direct search infeasible";
+    case DS_E_OVERFLOW: return "m(H (X_N - X_0)) >= 2^32: direct search infeasible (Q = 32)";
+    case DS_E_NO_CONVERGENCE: return "growth of H did not settle";
+    default: return "";
+    }
+}
+inline long long hr_bad_knot(const HRState &hs)
+{
+    if (hs.status == DS_E_NOT_INCREASING)
+        return (long long)(hs.bad_nonfinite != NONE64 ? hs.bad_nonfinite : hs.bad_order);
+    return (long long)hs.bad_indist;
+}
+
 // ------------------------------------------------------------------ arithmetic
 template <typename T> struct Arith;
 
@@ -279,8 +299,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after `limit` polls (each poll may suspend the
-// thread for a hardware-defined time), returns false on timeout.
 // Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned address and
 // size; no shared memory, registers or barrier involved).
 __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes)
@@ -288,6 +306,8 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Bounded wait: gives up after `limit` polls (each poll may suspend the
+// thread for a hardware-defined time), returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
     for (uint32_t it = 0; it < limit; ++it)

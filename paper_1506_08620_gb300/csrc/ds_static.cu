@@ -16,7 +16,6 @@
 // start from a known value; two calls whose GPU work overlaps (two streams,
 // two host threads) race on it.
 #include <cstring>
-#include <mutex>
 
 #include "ds_index.cuh"
 
@@ -29,31 +28,24 @@ static_assert(sizeof(HRState) <= STATIC_HR_BYTES, "HRState must fit its slot");
 
 static __device__ __align__(256) unsigned char g_static_scratch[STATIC_BYTES];
 
-// Device address of the scratch array, looked up once per device with that
-// device current (in host code the symbol names a host-side stand-in, never
-// the device memory itself).
-static void *static_scratch_address(int device, ds_status *rc)
+// Device address of the scratch array on the current device.  In host code
+// the symbol names a host-side stand-in, never the device memory itself, so
+// the address is looked up with cudaGetSymbolAddress (which allocates
+// nothing).  It is looked up on every call rather than cached: a context
+// destroyed by cudaDeviceReset and created again may place the array
+// elsewhere, and a cached address would then point at memory the library
+// does not own.
+static void *static_scratch_address(ds_status *rc)
 {
-    static std::mutex mu;
-    static void *addr[64] = {};
-    std::lock_guard<std::mutex> lock(mu);
-    if (device < 0 || device >= 64) {
-        set_error("ds_build_table_static: device ordinal %d out of range", device);
-        *rc = DS_E_ARG;
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("ds_build_table_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        *rc = DS_E_CUDA;
         return nullptr;
     }
-    if (!addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("ds_build_table_static: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            *rc = DS_E_CUDA;
-            return nullptr;
-        }
-        addr[device] = p;
-    }
     *rc = DS_OK;
-    return addr[device];
+    return p;
 }
 
 template <typename T, bool FMA>
@@ -91,8 +83,7 @@ static ds_status static_build(const T *X, long long n_knots, int32_t *K_out, lon
     *W_out = hs.W;
     *R_out = hs.R;
     if (hs.status != DS_OK) {
-        set_error("ds_build_table_static: direct search infeasible on this array (%s)",
-                  ds_status_str((ds_status)hs.status));
+        set_error("ds_build_table_static: %s (knot %lld)", hr_message(hs.status), hr_bad_knot(hs));
         return (ds_status)hs.status;
     }
     if ((long long)hs.R + 1 > K_capacity) {
@@ -128,10 +119,8 @@ extern "C" ds_status ds_build_table_static(const void *X_dev, int64_t n_knots, d
                       "(DS_STATIC_MAX_KNOTS); use ds_build", (long long)n_knots, ds::STATIC_MAX_KNOTS);
         return DS_E_ARG;
     }
-    int device = 0;
-    DS_TRY_CUDA(cudaGetDevice(&device));
     ds_status rc;
-    unsigned char *scratch = (unsigned char *)ds::static_scratch_address(device, &rc);
+    unsigned char *scratch = (unsigned char *)ds::static_scratch_address(&rc);
     if (!scratch) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const bool fma = (flags & DS_FMA) != 0;

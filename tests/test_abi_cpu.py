@@ -63,3 +63,14 @@ def test_argument_errors_need_no_gpu(libds):
 def test_cuda_sources_target_sm103a_only():
     from paper_1506_08620_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_static_build_source_allocates_nothing():
+    """The allocation-free build's translation unit names no allocating call:
+    its scratch is the file-scope __device__ array, looked up by address."""
+    src = open(os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", "ds_static.cu")).read()
+    code = "\n".join(l.split("//")[0] for l in src.splitlines())
+    for call in ("cudaMalloc", "cudaFree", "cudaMallocAsync", "cudaFreeAsync", "cudaMallocHost", "cudaHostAlloc",
+                 "cudaMallocManaged", "cudaMallocPitch", "malloc(", "new ", "std::vector"):
+        assert call not in code, call
+    assert "__device__ __align__(256)" in code and "cudaGetSymbolAddress" in code
