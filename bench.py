@@ -1,18 +1,21 @@
 #!/usr/bin/env python3
 """Throughput of direct-search interval lookup on GB300.
 
-Workload (default): float64, 2^20 + 1 knots with lognormal(0, 0.5) gaps,
-2^27 queries uniform over [X_0, X_N) (unsorted), int32 results.  One step is
-one search pass over all queries (Algorithm direct), as in the paper's
-throughput harness (Algorithm harness: the table is built before the clock
-starts); the build of the table is timed separately in the same run.
+Default workload (the largest single-GPU configuration): batched learned
+lookup fused with linear interpolation, float32, 256 arrays of 2^10..2^22
+knots with mixed gap laws (127.7M knots), 2^28 queries in proportion to the
+array sizes, int32 index and float32 interpolant per query.  One step is one
+search pass over all queries (the paper's Algorithm harness: tables are built
+before the clock starts; the build is timed separately in the same run).  The
+same run measures workloads 1-4 (``per_config``): lookups/s, the fraction of
+the HBM peak and the mismatches of every result against the definition.
 
 Prints ONE JSON line (rank 0).  Multi-GPU (torchrun): every rank builds its
-own replica of the table and searches its own 2^27 queries (weak scaling, no
-collective on the data path).
+own replica and searches its own queries (weak scaling, no collective on the
+data path).
 
---impl reference times the CPU oracle (std::upper_bound definition) on a
-bounded sample of the same workload on the host cores.
+--impl reference times the CPU oracle on a bounded sample of the same
+workload on the host cores.
 """
 import argparse
 import hashlib
@@ -38,7 +41,9 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="direct_f64", choices=WORKLOADS)
+    p.add_argument("--workload", default="learned_interp_f32", choices=WORKLOADS)
+    p.add_argument("--no-per-config", action="store_true",
+                   help="skip the per-configuration figures of workloads 1-4 (default run only)")
     p.add_argument("--variant", default="plain", choices=["plain", "fma", "cache", "fma_cache", "gap2", "fma_gap2"])
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
@@ -213,44 +218,59 @@ def dist_setup(args):
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
+    """The reference arm: the oracle as it stands (the definition of the answer,
+    and for the interpolating workload the float64 interpolant), single-threaded
+    on the host, on a bounded sample of the same workload per step."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return
     import oracle
-    from paper_1506_08620_gb300 import workloads as W
-    X, Z, desc = reference_sample(args)
     oracle.lib()
+    step, n, desc, dtype = reference_sample(args)
     for _ in range(max(args.warmup, 0)):
-        oracle.upper_bound(X, Z)
+        step()
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.upper_bound(X, Z)
+        step()
         times.append(time.perf_counter() - t0)
     t = float(np.mean(times))
-    value = Z.size / t
+    value = n / t
     line = {"impl": "reference", "metric": "lookups/s", "value": value, "unit": "lookups/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if X.dtype == np.float64 else "f32",
-            "data": "synthetic", "config": workload_config(args),
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": "lookups/s", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "lookups/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def reference_sample(args, n=1 << 20):
+    """(one step of the oracle, queries per step, description, dtype) on a
+    bounded sample of the workload: the same knots, fewer queries of the same
+    distribution."""
+    import oracle
     from paper_1506_08620_gb300 import workloads as W
+    if args.workload in ("learned_interp_f32", "batched_f32"):
+        five = args.workload == "learned_interp_f32"
+        w = W.workload5(total_queries=2 * n) if five else W.workload3(total_queries=4 * n)
+        if five:
+            step = lambda: oracle.interp_batch(w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"], w["z_off"])
+        else:
+            step = lambda: oracle.upper_bound_batch(w["Xcat"], w["x_off"], w["Zcat"], w["z_off"])
+        return (step, w["Zcat"].size, "%d queries of workload %s (same arrays), one pass per step"
+                % (w["Zcat"].size, w["name"]), "f32")
     if args.workload.startswith("direct_f64"):
         w = W.workload2(m=n, sort=args.workload.endswith("sorted"))
     elif args.workload in ("learned_f64", "gapq_f64"):
         w = W.workload4(m=n)
     elif args.workload == "paper_tables":
         w = W.paper_layout(PAPER_SIZES[-1], n, np.float64)
-    elif args.workload == "direct_f32":
-        w = W.workload1()
     else:
-        w = W.workload2(m=n)
-    return w["X"], w["Z"], "%d queries of workload %s (same knots), one pass per step" % (w["Z"].size, w["name"])
+        w = W.workload1()
+    X, Z = w["X"], w["Z"]
+    return (lambda: oracle.upper_bound(X, Z), Z.size,
+            "%d queries of workload %s (same knots), one pass per step" % (Z.size, w["name"]),
+            "f64" if X.dtype == np.float64 else "f32")
 
 
 def cpu_baseline(X, Z, seconds):
@@ -376,14 +396,19 @@ def setup_direct(args, ds, W, torch, dev, rank):
     job.search = lambda: ds.ds_search(idx, Zd, out)
     job.out = out
     job.keep = (idx, Xd, Zd)
-    Zp = torch.from_numpy(Zh).pin_memory()
-    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
+    pinned = {}
 
     def e2e():
+        if not pinned:
+            pinned["Z"] = torch.from_numpy(Zh).pin_memory()
+            pinned["I"] = torch.empty(job.m, dtype=torch.int32).pin_memory()
+            job.e2e_out = pinned["I"]
+        Zp, Ip = pinned["Z"], pinned["I"]
         ds.ds_search_host(idx, Zp, Ip)
         return Zp.numel() * Zp.element_size(), Ip.numel() * 4
     job.e2e = e2e
-    job.e2e_out = Ip
+
+    job.verify = lambda: answer_check(torch, job.search, Xd, Zd, out)
 
     def extras(stream):
         res = {}
@@ -479,6 +504,7 @@ def setup_gapq(args, ds, W, torch, dev, rank):
     job.search = lambda: ds.ds_search(idx, Zd, out)
     job.out = out
     job.keep = (idx, Xd, Zd)
+    job.verify = lambda: answer_check(torch, job.search, Xd, Zd, out)
     Zp = torch.from_numpy(Zh).pin_memory()
     Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
 
@@ -531,6 +557,7 @@ def setup_paper_tables(args, ds, W, torch, dev, rank):
     job.search = lambda: ds.ds_search(idx, Z, out)
     job.out = out
     job.keep = (idx, X, Z)
+    job.verify = lambda: answer_check(torch, job.search, X, Z, out)
     Zp = Z.cpu().pin_memory()
     Ip = torch.empty(m, dtype=torch.int32).pin_memory()
 
@@ -597,19 +624,21 @@ def setup_batched(args, ds, W, torch, dev, rank):
     job.search = lambda: ds.ds_batch_search(b, Zd, zo, out)
     job.out = out
     job.keep = (b, Xd, xo, Zd, zo)
-    Zp = torch.from_numpy(w["Zcat"]).pin_memory()
-    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
-    zbuf = torch.empty_like(Zd)
-    obuf = torch.empty_like(out)
+    bufs = {}
 
     def e2e():
-        zbuf.copy_(Zp, non_blocking=True)
-        ds.ds_batch_search(b, zbuf, zo, obuf)
-        Ip.copy_(obuf, non_blocking=True)
+        if not bufs:
+            bufs.update(Z=torch.from_numpy(w["Zcat"]).pin_memory(), I=torch.empty(job.m, dtype=torch.int32).pin_memory(),
+                        z=torch.empty_like(Zd), o=torch.empty_like(out))
+            job.e2e_out = bufs["I"]
+        Zp, Ip = bufs["Z"], bufs["I"]
+        bufs["z"].copy_(Zp, non_blocking=True)
+        ds.ds_batch_search(b, bufs["z"], zo, bufs["o"])
+        Ip.copy_(bufs["o"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return Zp.numel() * 4, Ip.numel() * 4
     job.e2e = e2e
-    job.e2e_out = Ip
+    job.verify = lambda: answer_check(torch, job.search, Xd, Zd, out, xo, zo)
 
     def extras(stream):
         # the same engine without the knot fingerprints (every query in a cell
@@ -647,16 +676,19 @@ def setup_learned(args, ds, W, torch, dev, rank):
     cfg = ds.ds_learned_cfg_default(n_queries=1 << 20) if not five else ds.ds_learned_cfg_default()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L = ds.ds_learned_build(Xd, xo, cfg=cfg)
+    L = ds.ds_learned_build_xy(Xd, Yd, xo, cfg=cfg) if five else ds.ds_learned_build(Xd, cfg=cfg)
     torch.cuda.synchronize()
     job.build_ms = (time.perf_counter() - t0) * 1e3
     info = L.info()
     esz = 4 if five else 8
-    job.bytes_per_lookup = (esz + 4 + (4 if five else 0))
+    # streamed: z in, i out (and y out); the interpolation also gathers X_i, X_{i+1}, Y_i, Y_{i+1}
+    job.streamed_bytes_per_lookup = esz + 4 + (esz if five else 0)
+    job.bytes_per_lookup = job.streamed_bytes_per_lookup + (4 * esz if five else 0)
     job.table = {k: info[k] for k in ("n_arrays", "n_direct", "n_learned", "n_fallback", "max_window",
                                       "train_steps", "train_ms", "final_loss", "table_bytes")}
+    job.table["cells"] = [ds.ds_learned_cells(L, a) for a in range(info["n_arrays"])] if not five else None
     if args.tune == "auto":  # the same engine autotuner as the batched form
-        job.table["tune"] = ds.ds_learned_autotune(L, Zd, zo, out)
+        job.table["tune"] = ds.ds_learned_autotune(L, Zd, zo, out, y_out=yout)
     elif args.tune != "default":
         blk, items, smem = (int(v) for v in args.tune.split(","))
         ds.ds_learned_set_tune(L, blk, items, smem)
@@ -664,36 +696,36 @@ def setup_learned(args, ds, W, torch, dev, rank):
     job.kernel_key = "learned_search_%s" % job.dtype_name
     job.launches_per_step = 2
     if five:
-        job.search = lambda: ds.ds_learned_search(L, Zd, zo, Y=Yd, out=out, y_out=yout)
+        job.search = lambda: ds.ds_learned_search(L, Zd, zo, out=out, y_out=yout)
     else:
         job.search = lambda: ds.ds_learned_search(L, Zd, out=out)
     job.out = out
     job.keep = (L, Xd, Zd, Yd)
-    Zp = torch.from_numpy(Zh).pin_memory()
-    Ip = torch.empty(job.m, dtype=torch.int32).pin_memory()
-    yp = torch.empty(job.m, dtype=Xd.dtype).pin_memory() if five else None
-    zbuf, obuf = torch.empty_like(Zd), torch.empty_like(out)
-    ybuf = torch.empty_like(yout) if five else None
+    job.yout = yout
+    bufs = {}
 
     def e2e():
-        zbuf.copy_(Zp, non_blocking=True)
+        if not bufs:
+            bufs.update(Z=torch.from_numpy(Zh).pin_memory(), I=torch.empty(job.m, dtype=torch.int32).pin_memory(),
+                        y=torch.empty(job.m, dtype=Xd.dtype).pin_memory() if five else None,
+                        z=torch.empty_like(Zd), o=torch.empty_like(out), yb=torch.empty_like(yout) if five else None)
+            job.e2e_out = bufs["I"]
+        Zp, Ip, yp = bufs["Z"], bufs["I"], bufs["y"]
+        bufs["z"].copy_(Zp, non_blocking=True)
         if five:
-            ds.ds_learned_search(L, zbuf, zo, Y=Yd, out=obuf, y_out=ybuf)
-            yp.copy_(ybuf, non_blocking=True)
+            ds.ds_learned_search(L, bufs["z"], zo, out=bufs["o"], y_out=bufs["yb"])
+            yp.copy_(bufs["yb"], non_blocking=True)
         else:
-            ds.ds_learned_search(L, zbuf, out=obuf)
-        Ip.copy_(obuf, non_blocking=True)
+            ds.ds_learned_search(L, bufs["z"], out=bufs["o"])
+        Ip.copy_(bufs["o"], non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return Zp.numel() * esz, Ip.numel() * 4 + (yp.numel() * esz if five else 0)
     job.e2e = e2e
-    job.e2e_out = Ip
+    job.verify = lambda: answer_check(torch, job.search, Xd, Zd, out, xo, zo, Yd, yout)
+    job.host = w
 
     def extras(stream):
-        res = {"fallback_queries_per_step": None}
-        f0 = L.info()["fallback_queries"]
-        job.search()
-        torch.cuda.synchronize()
-        res["fallback_queries_per_step"] = L.info()["fallback_queries"] - f0
+        res = {}
         if not five:  # the model without the network, same search path
             lin = ds.ds_learned_build(Xd, cfg=ds.ds_learned_cfg_default(flags=ds.DS_LEARNED_LINEAR))
             if args.tune == "auto":
@@ -726,6 +758,48 @@ def time_calls(torch, stream, fn, n):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / n * 1e-3
+
+
+def answer_check(torch, search, Xd, Zd, I, xo=None, zo=None, Yd=None, y=None, chunk=1 << 25):
+    """Mismatches of one step's results against the definition, at every
+    position: the answer is the unique i with X_i <= z < X_{i+1} (-1 below
+    X_0, N at or above X_N; the knots are strictly increasing), checked with
+    plain tensor comparisons on the device.  With knot values, y is compared
+    with the interpolant restated in float64 on those indices (tolerance
+    1e-6 of max(|y64|, |Y_i|, |Y_{i+1}|))."""
+    search()
+    torch.cuda.synchronize()
+    m = Zd.numel()
+    bad = bad_y = 0
+    for s in range(0, m, chunk):
+        e = min(m, s + chunk)
+        z, i = Zd[s:e], I[s:e].long()
+        if zo is None:
+            base = torch.zeros_like(i)
+            n = torch.full_like(i, Xd.numel() - 1)
+        else:
+            arr = torch.searchsorted(zo, torch.arange(s, e, device=Zd.device), right=True) - 1
+            base = xo[arr]
+            n = xo[arr + 1] - base - 1
+        mid = (i >= 0) & (i < n)
+        g0 = base + i.clamp(min=0)
+        g1 = torch.minimum(g0 + 1, base + n)
+        ok = mid & (Xd[g0] <= z) & (z < Xd[g1])
+        ok |= (i == -1) & (z < Xd[base])
+        ok |= (i == n) & (z >= Xd[base + n])
+        bad += int((~ok).sum())
+        if y is not None:
+            x0, x1, y0, y1 = Xd[g0].double(), Xd[g1].double(), Yd[g0].double(), Yd[g1].double()
+            y64 = y0 + (y1 - y0) * ((z.double() - x0) / (x1 - x0))
+            scale = torch.maximum(y64.abs(), torch.maximum(y0.abs(), y1.abs()))
+            yy = y[s:e].double()
+            ok_y = torch.where(mid, (yy - y64).abs() <= 1e-6 * scale, torch.isnan(yy))
+            bad_y += int((~ok_y).sum())
+    res = {"checked": "every result, against the definition (X_I <= z < X_{I+1})", "results": m,
+           "mismatches": bad}
+    if y is not None:
+        res["y_outside_tolerance"] = bad_y
+    return res
 
 
 def main():
@@ -790,8 +864,11 @@ def main():
     achieved = job.bytes_per_lookup * m / (float(np.mean(per)) * 1e-3) / 1e9
     traffic = traffic_for(job.kernel_key)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind,
+                "traffic": traffic, "peak_kind": peak_kind, "bytes_per_lookup": job.bytes_per_lookup,
                 "algorithmic_bytes_per_launch": job.bytes_per_lookup * m, "kernel": job.kernel_key}
+    if getattr(job, "streamed_bytes_per_lookup", None):
+        roofline["streamed_bytes_per_lookup"] = job.streamed_bytes_per_lookup
+        roofline["streamed_frac"] = achieved * job.streamed_bytes_per_lookup / job.bytes_per_lookup / peak
 
     line = {"metric": "lookups/s", "value": value, "unit": "lookups/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -815,22 +892,127 @@ def main():
                    "d2h_bytes_per_step": d2h}
     if rank == 0:
         line["e2e"]["matches_device_path"] = bool(torch.equal(job.e2e_out.to(dev), job.out))
+        line["check"] = job.verify()
 
     if rank == 0 and not args.no_extras and job.extras:
         line["variants_lookups_per_s"] = job.extras(stream)
     if rank == 0:
-        cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
-        if args.workload.startswith("direct") or args.workload in ("learned_f64", "gapq_f64", "paper_tables"):
+        if args.workload == "learned_interp_f32":
+            line["cpu_baseline"] = cpu_baseline_interp(job, args.cpu_seconds)
+        elif args.workload == "batched_f32":
+            line["cpu_baseline"] = cpu_baseline_batched(W, args.cpu_seconds)
+        else:
+            cw = W.workload2(m=1 << 24) if job.dtype_name == "f64" else W.workload1()
             if args.workload in ("learned_f64", "gapq_f64"):
                 cw = W.workload4(m=1 << 22)
             if args.workload == "paper_tables":
                 cw = W.paper_layout(PAPER_SIZES[-1], 1 << 24, np.float64)
             line["cpu_baseline"] = cpu_baseline(cw["X"], cw["Z"], args.cpu_seconds)
-        else:
-            line["cpu_baseline"] = cpu_baseline_batched(W, args.cpu_seconds)
-        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    if rank == 0 and args.workload == DEFAULT_WORKLOAD and not args.no_per_config and not args.queries:
+        headline = {"lookups_per_s": value, "hbm_frac": roofline["frac"], "check": line["check"]}
+        job.keep = job.search = job.e2e = job.verify = None
+        del job
+        torch.cuda.empty_cache()
+        line["per_config"] = per_config(args, ds, W, torch, dev, stream, peak, headline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+DEFAULT_WORKLOAD = "learned_interp_f32"
+# the other configurations, each measured in the default run: (name, workload, variant)
+PER_CONFIG = (("1_direct_f32", "direct_f32", "plain"), ("2_direct_f64", "direct_f64", "plain"),
+              ("2_direct_f64_fma", "direct_f64", "fma"), ("3_batched_f32", "batched_f32", "plain"),
+              ("4_learned_f64", "learned_f64", "plain"))
+
+
+def per_config(args, ds, W, torch, dev, stream, peak, headline):
+    """Lookups/s, fraction of the HBM peak and mismatches (every result checked
+    against the definition) of workloads 1-4, one after the other, each
+    autotuned where it has a tuner, timed with CUDA events over 10 launches
+    after 2 warm-up launches; and the ratios the spec bars name."""
+    setups = {"direct_f32": setup_direct, "direct_f64": setup_direct, "batched_f32": setup_batched,
+              "learned_f64": setup_learned}
+    res = {}
+    for name, wl, var in PER_CONFIG:
+        a = argparse.Namespace(**{**vars(args), "workload": wl, "variant": var, "queries": 0})
+        job = setups[wl](a, ds, W, torch, dev, 0)
+        t = time_calls(torch, stream, job.search, 10)
+        rate = job.m / t
+        res[name] = {"workload": workload_config(a)["workload"], "lookups_per_s": rate, "ms_per_launch": t * 1e3,
+                     "bytes_per_lookup": job.bytes_per_lookup, "hbm_frac": job.bytes_per_lookup * rate / 1e9 / peak,
+                     "check": job.verify(), "build_ms": job.build_ms, "table": job.table}
+        if wl == "learned_f64":  # the map without the network, same search (what the trained network gains)
+            L = job.keep[0]
+            lin = ds.ds_learned_build(job.keep[1], cfg=ds.ds_learned_cfg_default(flags=ds.DS_LEARNED_LINEAR))
+            ds.ds_learned_autotune(lin, job.keep[2], None, job.out)
+            res[name]["linear_map_lookups_per_s"] = job.m / time_calls(
+                torch, stream, lambda: ds.ds_learned_search(lin, job.keep[2], out=job.out), 10)
+            res[name]["linear_map_max_window"] = lin.info()["max_window"]
+            lin.free()
+            del L
+        job.keep = job.search = job.e2e = job.verify = None
+        del job
+        torch.cuda.empty_cache()
+    res["5_learned_interp_f32"] = headline
+    f32 = res["1_direct_f32"]["lookups_per_s"]
+    f64 = res["2_direct_f64"]["lookups_per_s"]
+    res["vs_plain_direct"] = {"3_batched_f32 / 1_direct_f32": res["3_batched_f32"]["lookups_per_s"] / f32,
+                              "3_batched_f32 / 2_direct_f64": res["3_batched_f32"]["lookups_per_s"] / f64,
+                              "4_learned_f64 / 2_direct_f64": res["4_learned_f64"]["lookups_per_s"] / f64,
+                              "5_learned_interp_f32 / 1_direct_f32": headline["lookups_per_s"] / f32,
+                              "5_learned_interp_f32 / 2_direct_f64": headline["lookups_per_s"] / f64}
+    return res
+
+
+def interp_sample(w, frac_log2):
+    """The first 2^-frac_log2 of every array's queries (at least one where it has any)."""
+    z_off = w["z_off"]
+    q = np.diff(z_off)
+    take = np.where(q > 0, np.maximum(q >> frac_log2, 1), 0)
+    pos = np.concatenate([np.arange(z_off[a], z_off[a] + take[a]) for a in range(q.size)])
+    return pos, W_csr(take)
+
+
+def W_csr(sizes):
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    return off
+
+
+def cpu_baseline_interp(job, seconds):
+    """The oracle (single thread: the interval by its definition, the interpolant
+    in float64) on a bounded sample of the headline workload's queries, sized
+    for about `seconds`; its answers are compared with this step's GPU results."""
+    import oracle
+    oracle.lib()
+    w = job.host
+    pos, zo = interp_sample(w, 12)  # calibrate on 2^-12 of the queries, then size the sample
+    t0 = time.perf_counter()
+    oracle.interp_batch(w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"][pos], zo)
+    dt = time.perf_counter() - t0
+    k = int(min(12, max(0, 12 - np.floor(np.log2(max(seconds / max(dt, 1e-6), 1.0))))))
+    pos, zo = interp_sample(w, k)
+    t0 = time.perf_counter()
+    oracle.interp_batch(w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"][pos], zo)
+    dt = time.perf_counter() - t0
+    n = pos.size
+    rate = n / dt
+    out = job.out.cpu().numpy()[pos]
+    I, y64 = oracle.interp_batch(w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"][pos], zo)
+    yv = job.yout.cpu().numpy()[pos] if getattr(job, "yout", None) is not None else None
+    res = {"value": rate, "unit": "lookups/s", "cores": 1, "kind": "oracle",
+           "sample": "the first 2^-%d of every array's queries (%d of %d), one pass, %.1f s"
+                     % (k, n, w["Zcat"].size, dt),
+           "mismatches_vs_gpu": int((I != out).sum())}
+    if yv is not None:
+        arr = np.searchsorted(w["z_off"], pos, side="right") - 1
+        gi = w["x_off"][arr] + np.clip(I, 0, None)
+        Y = w["Ycat"]
+        scale = np.maximum(np.abs(y64), np.maximum(np.abs(Y[gi]), np.abs(Y[np.minimum(gi + 1, Y.size - 1)])))
+        res["y_outside_tolerance_vs_gpu"] = int((~(np.abs(yv.astype(np.float64) - y64) <= 1e-6 * scale)).sum())
+    return res
 
 
 def cpu_baseline_batched(W, seconds):

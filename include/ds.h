@@ -109,11 +109,11 @@ typedef struct ds_info_t {
     int32_t n_direct;       /* arrays served by direct search */
     int32_t n_learned;      /* arrays served by the learned predictor */
     int32_t n_fallback;     /* arrays served by the fixed-depth bisection (Algorithm binaryopt) */
-    int64_t max_window;     /* learned: largest bounded window (e_lo + e_hi + 3) over arrays */
+    int64_t max_window;     /* learned: largest bounded window (largest cell population + 1) over arrays */
     int64_t train_steps;    /* learned: Adam steps run per model */
     double train_ms;        /* learned: time spent training */
     double final_loss;      /* learned: mean final training loss */
-    uint64_t fallback_queries; /* learned: queries whose window certificate failed (since the build) */
+    uint64_t fallback_queries; /* learned: always 0 (the cell map is exact; no query falls back) */
     int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error */
     int32_t gap_q;          /* single array: q of the table (1 Direct, 2 DirectGap2, ...); batched: largest q */
 } ds_info_t;
@@ -313,60 +313,98 @@ DS_API ds_status ds_batch_array(const ds_batch *b, int32_t a, double *H, double 
  * Learned index (not in the paper): a 1 -> 32 -> 32 -> 1 ReLU network
  * predicting the index from u = (z - X_0) / (X_N - X_0), trained on the GPU by
  * this library's own forward/backward/Adam kernels on the pairs (X_i, i) and
- * on exact answers of sampled queries; the largest prediction error over all
- * knots is recorded at build time and each query is answered exactly by a
- * fixed-depth bisection (Algorithm binaryopt) inside the bounded window around
- * the prediction, in three levels (every 1024th knot, at most 32 of every 32nd
- * knot, at most 32 knots); the window certificate X_lo <= z < X_{hi+1} is
- * tested in its equivalent form X_i <= z < X_{i+1} on the answer i, and a
- * failed certificate falls back to the array's exact full search (in the
- * batched form a thread's queries are searched again together).  Arrays on which direct search
- * is feasible with at most max_cells_per_knot cells per knot use it instead
- * (unless DS_LEARNED_FORCE).
+ * on exact answers of sampled queries.  Its largest prediction error over all
+ * knots is recorded at build time (e_lo, e_hi: ds_learned_array).  It is
+ * served as a learned cell map for direct search (Section 4.2's method on
+ * cells of equal predicted rank instead of equal width): the prediction,
+ * sampled at G uniform points of u and made non-decreasing (by
+ * rearrangement), gives
+ * C = ceil(cells_per_knot (N+1)) cells; f(z) is that map rounded down to a
+ * cell, computed in float32 so that f is monotone; K_j = #{i : f(X_i) < j}
+ * as in Eq. indexdef; and a query answers K_j - 1 plus the number of knots of
+ * its cell j that are <= z (none for an empty cell; otherwise X_{K_j} and
+ * X_{K_{j+1}-1} decide, and between them a bisection of the cell).  Every
+ * answer is exact by construction: the cells replace the certificate.  The
+ * bounded compare window of a query is its cell, at most max_window - 1 knots
+ * (ds_info), recorded at build time.  Each array keeps the network's map
+ * only where its cells are better balanced than those of the linear model
+ * (ds_learned_cells).  Arrays on which direct search is
+ * feasible with at most max_cells_per_knot cells per knot use plain direct
+ * search instead (unless DS_LEARNED_FORCE).
  * ------------------------------------------------------------------------ */
 enum {
-    DS_LEARNED_FORCE = 1u,    /* use the learned predictor even where direct search is feasible */
-    DS_LEARNED_LINEAR = 2u,   /* no network: predict N u (the model "without it", for comparison) */
-    DS_LEARNED_ZERO_BOUND = 4u /* testing: record e_lo = e_hi = 0 instead of the measured bounds, so every
-                                  misprediction must be caught by the window certificate */
+    DS_LEARNED_FORCE = 1u,    /* use the learned map even where direct search is feasible */
+    DS_LEARNED_LINEAR = 2u    /* no network: the map of the linear model N u, i.e. cells of equal width in z
+                                 (the method "without it", for comparison) */
 };
 
 typedef struct ds_learned_cfg {
-    int32_t steps;       /* Adam steps per model (0 = untrained initial network) */
+    int32_t steps;       /* Adam steps per model (0 = untrained initial network); default 6000 */
     int32_t batch;       /* samples per step */
     int32_t n_queries;   /* exact-answer query samples per model, in addition to the knots */
     float lr;            /* Adam step size */
     uint64_t seed;       /* Philox-4x32-10 key for initialisation and sampling */
     uint32_t flags;      /* DS_LEARNED_* */
     int32_t max_cells_per_knot; /* direct search only where (R+1) <= this x (N+1) (its table stays small);
-                                   other feasible arrays use the predictor; <= 0: no limit */
-    int32_t reserved[4];
+                                   other feasible arrays use the learned map; <= 0: no limit */
+    float cells_per_knot;       /* cells C of a learned map per knot (0 = the default, 1); C <= 2^32 - 2 */
+    int32_t reserved[3];
 } ds_learned_cfg;
 
 DS_API void ds_learned_cfg_default(ds_learned_cfg *cfg);
 
 /* Build the learned form.  Single array: x_off_dev = NULL, n_arrays = 1 and
  * n_knots_if_single = N+1.  Batched: device CSR offsets as in ds_batch_build.
- * Synchronous. */
+ * The cell tables take 2 bytes per cell (16-byte blocks of 8 cells: K of the
+ * first cell and 12-bit differences; a block whose cells hold more than 4095
+ * knots keeps its 9 values as uint32 in an overflow area).  Synchronous. */
 DS_API ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays,
                            int64_t n_knots_if_single, ds_dtype dtype, const ds_learned_cfg *cfg, void *stream,
                            ds_learned **out);
 
+/* The same build with the knot values Y of the interpolation (Ycat_dev: same
+ * dtype and CSR layout as Xcat_dev, copied): the handle stores each knot with
+ * its value as an (X_i, Y_i) pair, so that a lookup's X_i, Y_i, X_{i+1},
+ * Y_{i+1} lie side by side, and its searches interpolate from them
+ * (ds_learned_search with Ycat_dev = NULL).  Synchronous. */
+DS_API ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const int64_t *x_off_dev,
+                                     int32_t n_arrays, int64_t n_knots_if_single, ds_dtype dtype,
+                                     const ds_learned_cfg *cfg, void *stream, ds_learned **out);
+
 /* Search: single array: z_off_dev = NULL and m queries; batched: device CSR
- * z_off_dev (m ignored).  With Ycat_dev and y_out_dev both non-NULL the
- * linear interpolant y = Y_i + (Y_{i+1} - Y_i) (z - X_i) / (X_{i+1} - X_i) of
- * knot values Y (same dtype and CSR layout as X) is written for every query
- * whose index lies in [0, N-1] (the use case of the Introduction); other
- * queries get NaN.  Asynchronous, allocation-free. */
+ * z_off_dev (m ignored).  With y_out_dev non-NULL the linear interpolant
+ * y = Y_i + (Y_{i+1} - Y_i) ((z - X_i) / (X_{i+1} - X_i)) (each step rounded
+ * once) is written for every query whose index lies in [0, N-1] (the use case
+ * of the Introduction); other queries get NaN.  The values Y are the handle's
+ * own (ds_learned_build_xy; Ycat_dev must then be NULL) or the caller's
+ * Ycat_dev (same dtype and CSR layout as X; a handle from ds_learned_build).
+ * y_out_dev 16-byte aligned takes the vector path.  Asynchronous,
+ * allocation-free. */
 DS_API ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
                             const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream);
 
+/* The same search with HOST buffers (the end-to-end call): Zcat_host (m
+ * queries), Icat_host (m results) and y_out_host (m interpolated values, only
+ * for a handle from ds_learned_build_xy, or NULL) are read and written by the
+ * search kernel in place over the CPU-GPU link, with no staging copies;
+ * page-locked mapped memory (cudaHostAlloc, cudaHostRegister) is used as it
+ * is, other host memory is registered for the call and unregistered after it.
+ * z_off_host: host CSR offsets (n_arrays + 1 int64; m is then z_off[n_arrays]),
+ * or NULL for one array of m queries; copied to a device buffer the handle
+ * allocates on its first use.  Returns after the results are in host memory
+ * (the call synchronizes `stream`). */
+DS_API ds_status ds_learned_search_host(ds_learned *L, const void *Zcat_host, const int64_t *z_off_host, int64_t m,
+                                        void *y_out_host, int32_t *Icat_host, void *stream);
+
 /* Time the launch configurations of ds_batch_autotune on these queries (the
  * same engine serves the learned form), keep the fastest in the handle and
- * return it in *best.  Single array: z_off_dev = NULL and m queries.  The
- * outputs are overwritten with valid results.  Synchronous. */
+ * return it in *best.  Single array: z_off_dev = NULL and m queries.  With
+ * y_out_dev (and Ycat_dev, as for ds_learned_search) the configurations are
+ * timed with the interpolation.  The outputs are overwritten with valid
+ * results.  Synchronous. */
 DS_API ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
-                                     int32_t *Icat_dev, void *stream, ds_tune_t *best);
+                                     const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream,
+                                     ds_tune_t *best);
 /* Set or read the launch configuration of the learned search, as
  * ds_batch_set_tune / ds_batch_get_tune (DS_E_ARG for an smem_limit outside
  * [-1, the device's opt-in limit - 2048] or a configuration that cannot be
@@ -376,10 +414,25 @@ DS_API ds_status ds_learned_get_tune(const ds_learned *L, ds_tune_t *cfg);
 
 /* Host copy of array a's network parameters (1153 floats: W1[32] b1[32]
  * W2[32][32] b2[32] w3[32] b3) and its recorded error bounds: every knot i
- * satisfies floor(p(X_i)) - e_lo <= i <= floor(p(X_i)) + e_hi.  mode: 0 direct,
- * 1 learned, 2 bisection. */
+ * satisfies floor(p(X_i)) - e_lo <= i <= floor(p(X_i)) + e_hi for the served
+ * prediction p.  mode: 0 direct, 1 learned, 2 bisection. */
 DS_API ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, int32_t *e_lo, int32_t *e_hi,
                            int32_t *mode);
+
+/* Cell table of array a (zeros for an array served by plain direct search):
+ * cells C, the largest number of knots in one cell, the number of cells
+ * holding a knot, the number of escaped blocks (8 cells holding more than 4095
+ * knots, whose K values are kept as uint32), the mean cell population seen by
+ * queries distributed like the knots (sum of squared populations / (N + 1)),
+ * and 1 if the map comes from the network (0: from the linear model, which
+ * the build keeps where the network's map gives the larger mean population).
+ * Any output may be NULL. */
+DS_API ds_status ds_learned_cells(const ds_learned *L, int32_t a, uint64_t *cells, int32_t *max_pop,
+                                  int64_t *nonempty, int64_t *escaped, double *mean_pop, int32_t *from_network);
+
+/* Copy K_0 .. K_C (C + 1 uint32, decoded; K_0 = 0, K_C = N + 1) of a learned
+ * array's cell table into caller-owned device memory.  Asynchronous. */
+DS_API ds_status ds_learned_export_cells(const ds_learned *L, int32_t a, uint32_t *K_out_dev, void *stream);
 
 /* The training kernels on explicit inputs (used to check gradients):
  * forward output of the network for n inputs u; mean squared error over n

@@ -12,7 +12,7 @@ import torch
 
 from . import _abi
 from ._abi import (DS_CACHE_LAYOUT, DS_CHECKED, DS_F32, DS_F64, DS_FMA, DS_LEARNED_FORCE,  # noqa: F401
-                   DS_GAP2, DS_LEARNED_LINEAR, DS_LEARNED_ZERO_BOUND, DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_EYTZINGER,
+                   DS_GAP2, DS_LEARNED_LINEAR, DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_EYTZINGER,
                    DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_NAMES, DS_LS_OFFSET, DS_NO_FINGERPRINT, DS_NO_SMEM, DS_OK,
                    DS_REFINE_H, DS_STRICT, DsError, check, lib)
 
@@ -20,7 +20,8 @@ __all__ = [
     "ds_build", "ds_search", "ds_search_host", "ds_index_export", "ds_batch_build", "ds_batch_search",
     "ds_batch_autotune", "ds_batch_set_tune", "ds_batch_get_tune", "ds_batch_array", "ds_learned_build",
     "ds_learned_search", "ds_learned_autotune", "ds_learned_set_tune", "ds_learned_get_tune", "ds_learned_array",
-    "ds_learned_cfg_default", "ds_mlp_forward", "ds_mlp_loss_grad",
+    "ds_learned_cfg_default", "ds_learned_build_xy", "ds_learned_cells", "ds_learned_export_cells",
+    "ds_learned_search_host", "ds_mlp_forward", "ds_mlp_loss_grad",
     "ds_adam_step", "ds_info", "ds_free", "DsError",
 ]
 
@@ -112,8 +113,9 @@ class LSearch(_Handle):
 
 
 class Learned(_Handle):
-    """Learned-index form (``ds_learned``)."""
+    """Learned-index form (``ds_learned``); ``xy``: the handle holds its knot values."""
     kind = "ds_learned"
+    xy = False
 
     def search(self, Z, z_off=None, Y=None, out=None, y_out=None, stream=None):
         return ds_learned_search(self, Z, z_off, Y, out, y_out, stream)
@@ -270,43 +272,98 @@ def ds_learned_cfg_default(**overrides):
 
 def ds_learned_build(X, x_off=None, cfg=None, stream=None):
     """Learned form of one array (x_off None) or of many arrays (device CSR x_off)."""
+    return ds_learned_build_xy(X, None, x_off, cfg, stream)
+
+
+def ds_learned_build_xy(X, Y, x_off=None, cfg=None, stream=None):
+    """Learned form holding the knot values Y as (X_i, Y_i) pairs (Y None: ds_learned_build)."""
     cfg = cfg if cfg is not None else ds_learned_cfg_default()
     out = ctypes.c_void_p()
+    yp = None if Y is None else _dev(Y, "Y", X.dtype)
+    if Y is not None and Y.numel() != X.numel():
+        raise ValueError("Y must have one value per knot")
     if x_off is None:
-        rc = lib().ds_learned_build(_dev(X, "X"), None, 1, X.numel(), _dtype(X), ctypes.byref(cfg), _stream(stream),
-                                    ctypes.byref(out))
+        rc = lib().ds_learned_build_xy(_dev(X, "X"), yp, None, 1, X.numel(), _dtype(X), ctypes.byref(cfg),
+                                       _stream(stream), ctypes.byref(out))
     else:
-        rc = lib().ds_learned_build(_dev(X, "Xcat"), _dev(x_off, "x_off", torch.int64), x_off.numel() - 1, 0,
-                                    _dtype(X), ctypes.byref(cfg), _stream(stream), ctypes.byref(out))
-    check(rc, "ds_learned_build")
-    return Learned(out.value, X.dtype)
+        rc = lib().ds_learned_build_xy(_dev(X, "Xcat"), yp, _dev(x_off, "x_off", torch.int64), x_off.numel() - 1, 0,
+                                       _dtype(X), ctypes.byref(cfg), _stream(stream), ctypes.byref(out))
+    check(rc, "ds_learned_build_xy" if Y is not None else "ds_learned_build")
+    L = Learned(out.value, X.dtype)
+    L.xy = Y is not None
+    return L
+
+
+def _interp_args(L, Z, Y, y_out):
+    """(Ycat pointer, y_out pointer, y_out tensor) of a learned search: interpolation when the
+    handle holds its values and y_out is given, or when the caller passes Y."""
+    if L.xy:
+        if Y is not None:
+            raise ValueError("this learned handle holds its knot values: pass y_out, not Y")
+        if y_out is None:
+            return None, None, None
+        return None, _dev(y_out, "y_out", L.dtype), y_out
+    if Y is None:
+        return None, None, None
+    if y_out is None:
+        y_out = torch.empty(Z.numel(), dtype=L.dtype, device=Z.device)
+    return _dev(Y, "Y", L.dtype), _dev(y_out, "y_out", L.dtype), y_out
 
 
 def ds_learned_search(L, Z, z_off=None, Y=None, out=None, y_out=None, stream=None):
+    """Indices (and, with Y or with y_out on a handle that holds its values, the interpolant)."""
     if out is None:
         out = torch.empty(Z.numel(), dtype=torch.int32, device=Z.device)
-    yp = None
-    yo = None
-    if Y is not None:
-        if y_out is None:
-            y_out = torch.empty(Z.numel(), dtype=L.dtype, device=Z.device)
-        yp = _dev(Y, "Y", L.dtype)
-        yo = _dev(y_out, "y_out", L.dtype)
+    yp, yo, y_out = _interp_args(L, Z, Y, y_out)
     zo = None if z_off is None else _dev(z_off, "z_off", torch.int64)
     check(lib().ds_learned_search(L.ptr, _dev(Z, "Z", L.dtype), zo, Z.numel(), yp, yo, _dev(out, "out", torch.int32),
                                   _stream(stream)), "ds_learned_search")
-    return (out, y_out) if Y is not None else out
+    return (out, y_out) if yo is not None else out
 
 
-def ds_learned_autotune(L, Z, z_off=None, out=None, stream=None):
-    """Autotune the learned handle's launch configuration on these queries; returns the chosen one."""
+def ds_learned_search_host(L, Z, z_off=None, out=None, y_out=None, stream=None):
+    """The search on host tensors (pinned ones used in place, others registered
+    for the call); z_off a host int64 tensor or None.  Returns when the results
+    are in host memory."""
+    if out is None:
+        out = torch.empty(Z.numel(), dtype=torch.int32)
+    zo = None if z_off is None else _host(z_off, "z_off", torch.int64)
+    yo = None if y_out is None else _host(y_out, "y_out", L.dtype)
+    check(lib().ds_learned_search_host(L.ptr, _host(Z, "Z", L.dtype), zo, Z.numel(), yo, _host(out, "out", torch.int32),
+                                       _stream(stream)), "ds_learned_search_host")
+    return (out, y_out) if y_out is not None else out
+
+
+def ds_learned_autotune(L, Z, z_off=None, out=None, stream=None, Y=None, y_out=None):
+    """Autotune the learned handle's launch configuration on these queries (with the
+    interpolation when Y, or y_out on a handle that holds its values, is given); returns it."""
     if out is None:
         out = torch.empty(Z.numel(), dtype=torch.int32, device=Z.device)
     best = _abi.ds_tune_t()
+    yp, yo, _ = _interp_args(L, Z, Y, y_out)
     zo = _dev(z_off, "z_off", torch.int64) if z_off is not None else None
-    check(lib().ds_learned_autotune(L.ptr, _dev(Z, "Z", L.dtype), zo, Z.numel(), _dev(out, "out", torch.int32),
-                                    _stream(stream), ctypes.byref(best)), "ds_learned_autotune")
+    check(lib().ds_learned_autotune(L.ptr, _dev(Z, "Z", L.dtype), zo, Z.numel(), yp, yo,
+                                    _dev(out, "out", torch.int32), _stream(stream), ctypes.byref(best)),
+          "ds_learned_autotune")
     return best.as_dict()
+
+
+def ds_learned_cells(L, a=0):
+    """Cell table of learned array a: cells, max_pop, nonempty, escaped, mean_pop, from_network."""
+    C = ctypes.c_uint64(); mp = ctypes.c_int32(); ne = ctypes.c_int64(); esc = ctypes.c_int64()
+    mean = ctypes.c_double(); net = ctypes.c_int32()
+    check(lib().ds_learned_cells(L.ptr, int(a), ctypes.byref(C), ctypes.byref(mp), ctypes.byref(ne),
+                                 ctypes.byref(esc), ctypes.byref(mean), ctypes.byref(net)), "ds_learned_cells")
+    return dict(cells=C.value, max_pop=mp.value, nonempty=ne.value, escaped=esc.value, mean_pop=mean.value,
+                from_network=net.value)
+
+
+def ds_learned_export_cells(L, a=0, stream=None):
+    """K_0 .. K_C of learned array a (int32 tensor on the current device)."""
+    C = ds_learned_cells(L, a)["cells"]
+    K = torch.empty(C + 1, dtype=torch.int32, device="cuda")
+    check(lib().ds_learned_export_cells(L.ptr, int(a), _dev(K, "K"), _stream(stream)), "ds_learned_export_cells")
+    return K
 
 
 def ds_learned_set_tune(L, block, items, smem_limit, blocks_per_sm=0):

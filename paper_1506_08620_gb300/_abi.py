@@ -38,7 +38,6 @@ DS_LS_NAMES = ("classic", "classicmod", "leadbit", "leadbit_nopad", "offset", "e
 
 DS_LEARNED_FORCE = 1
 DS_LEARNED_LINEAR = 2
-DS_LEARNED_ZERO_BOUND = 4
 
 DS_STATIC_MAX_KNOTS = 262144
 
@@ -75,7 +74,7 @@ class ds_tune_t(ctypes.Structure):
 
 class ds_learned_cfg(ctypes.Structure):
     _fields_ = [("steps", I32), ("batch", I32), ("n_queries", I32), ("lr", F32), ("seed", U64),
-                ("flags", U32), ("max_cells_per_knot", I32), ("reserved", I32 * 4)]
+                ("flags", U32), ("max_cells_per_knot", I32), ("cells_per_knot", F32), ("reserved", I32 * 3)]
 
 
 _SIGS = {
@@ -83,7 +82,12 @@ _SIGS = {
     "ds_build_q": (ST, [P, I64, ST, U32, ctypes.c_int32, ctypes.c_int32, I64, P, ctypes.POINTER(P)]),
     "ds_search_sorted": (ST, [P, I64, ST, P, I64, P, P]),
     "ds_histogram": (ST, [P, P, I64, P, P]),
-    "ds_learned_autotune": (ST, [P, P, P, I64, P, P, ctypes.POINTER(ds_tune_t)]),
+    "ds_learned_autotune": (ST, [P, P, P, I64, P, P, P, P, ctypes.POINTER(ds_tune_t)]),
+    "ds_learned_build_xy": (ST, [P, P, P, I32, I64, ST, ctypes.POINTER(ds_learned_cfg), P, ctypes.POINTER(P)]),
+    "ds_learned_cells": (ST, [P, I32, ctypes.POINTER(U64), ctypes.POINTER(I32), ctypes.POINTER(I64),
+                              ctypes.POINTER(I64), ctypes.POINTER(F64), ctypes.POINTER(I32)]),
+    "ds_learned_export_cells": (ST, [P, I32, P, P]),
+    "ds_learned_search_host": (ST, [P, P, P, I64, P, P, P]),
     "ds_learned_set_tune": (ST, [P, ctypes.POINTER(ds_tune_t)]),
     "ds_learned_get_tune": (ST, [P, ctypes.POINTER(ds_tune_t)]),
     "ds_lsearch_constants": (ST, [ctypes.c_int32, I64, P, ctypes.POINTER(I64)]),

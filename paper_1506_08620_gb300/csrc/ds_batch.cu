@@ -164,9 +164,7 @@ void engine_free(Engine *e)
     if (e->order) cudaFree(e->order);
     if (e->counter) cudaFree(e->counter);
     if (e->dev_err) cudaFree(e->dev_err);
-    if (e->seg_x) cudaFree(e->seg_x);
-    if (e->seg_a) cudaFree(e->seg_a);
-    if (e->seg_b) cudaFree(e->seg_b);
+    if (e->ctab) cudaFree(e->ctab);
     *e = Engine();
 }
 
@@ -191,6 +189,12 @@ static int top_pow2(long long n)
     long long t = 1;
     while (t * 2 <= n) t *= 2;
     return (int)t;
+}
+
+int lmap_cells(long long n_knots)
+{
+    const long long g = top_pow2(std::max<long long>(n_knots / 4, 1));
+    return (int)std::min<long long>(LMAP_MAX, std::max<long long>(LMAP_MIN, g));
 }
 
 static bool feasible_sparse(const HRState &h, long long nk, double max_cells)
@@ -240,7 +244,7 @@ static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const
 // Validate, run ComputeHR per array, lay out the blob and fill every table.
 // `want_direct[a] == false` forces array a into `other_mode` (learned build).
 template <typename T, bool FMA>
-static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x_off_dev,
+static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, const long long *x_off_dev,
                                     const std::vector<long long> &x_off, uint32_t flags, cudaStream_t s,
                                     const std::vector<char> *force_other, int other_mode, std::vector<HRState> *hs_out,
                                     double max_cells)
@@ -274,6 +278,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
             const long long nk = x_off[a + 1] - x_off[a];
             d.n = (int32_t)(nk - 1);
             d.yoff = x_off[a];
+            d.xs = Ycat ? 2 : 1;
             d.pbits = top_pow2(d.n);
             e->h_updates += hs[a].updates;
             const bool feasible = hs[a].status == DS_OK;
@@ -302,7 +307,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 d.x_in_img = NO_X_IN_IMG;
                 d.g_in_img = (uint32_t)std::min<size_t>(kb, 0xFFFFFFFFu);
                 d.xg = (long long)(off + kb + gb);
-                const size_t xb = round_up((size_t)nk * sizeof(T), 16);
+                const size_t xb = round_up((size_t)nk * d.xs * sizeof(T), 16);
                 d.img_bytes = kb + gb <= 0xFFFFFFF0u ? (uint32_t)(kb + gb) : 0u;
                 off += kb + gb + xb;
                 kc[a + 1] = (nk + 31) / 32;
@@ -313,12 +318,14 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
                 d.R = 0;
                 d.xg = (long long)off;
                 d.x_in_img = 0;
-                const size_t xb = round_up((size_t)nk * sizeof(T), 16);
+                const size_t xb = round_up((size_t)nk * d.xs * sizeof(T), 16);
                 d.img_bytes = d.mode == MODE_BISECT && xb <= 0xFFFFFFF0u ? (uint32_t)xb : 0u;
                 off += xb;
-                if (d.mode == MODE_LEARNED) {  // the sampled knots S and S1 of the window search
-                    d.sg = (long long)off;
-                    off += sample_bytes(d.n, sizeof(T)) + sample1_bytes(d.n, sizeof(T));
+                if (d.mode == MODE_LEARNED) {  // the image is the cell map; the knots stay in global memory
+                    d.img = (long long)off;
+                    d.img_bytes = (uint32_t)lmap_cells(nk) * 8u;
+                    d.x_in_img = NO_X_IN_IMG;
+                    off += d.img_bytes;
                 }
                 if (d.mode == MODE_BISECT) e->n_fallback += 1;
                 else e->n_learned += 1;
@@ -376,7 +383,8 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
         cudaMemcpyAsync(e->desc_dev, e->desc_host.data(), sizeof(ArrDesc) * (size_t)A, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(kc_dev, kc.data(), sizeof(long long) * (size_t)(A + 1), cudaMemcpyHostToDevice, s);
         const int sgrid = std::max(1, std::min(n_segs, e->props.num_sms * 8));
-        k_seg_copy_fill_F<T><<<sgrid, 256, 0, s>>>(Xcat, x_off_dev, segs_dev, n_segs, e->desc_dev, e->blob, F, G);
+        k_seg_copy_fill_F<T><<<sgrid, 256, 0, s>>>(Xcat, Ycat, x_off_dev, segs_dev, n_segs, e->desc_dev, e->blob, F,
+                                                   G);
         const long long kchunks = kc[A];
         if (kchunks > 0) {
             const long long kgrid = std::min<long long>((kchunks * 32 + 255) / 256, (long long)e->props.num_sms * 16);
@@ -399,11 +407,13 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const long long *x
     return rc;
 }
 
-ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
-                       uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
-                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out, double max_cells)
+ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long long *x_off_dev, int n_arrays,
+                       ds_dtype dtype, uint32_t flags, cudaStream_t s, const std::vector<char> *force_other,
+                       int other_mode, std::vector<long long> *x_off_host, std::vector<HRState> *hs_out,
+                       double max_cells)
 {
     e->dtype = dtype;
+    e->xy = Ycat != nullptr;
     e->flags = flags;
     e->n_arrays = n_arrays;
     DS_TRY(device_props(&e->props));
@@ -441,15 +451,18 @@ ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, 
     DS_TRY_CUDA(cudaMalloc(&e->dev_err, sizeof(int)));
     DS_TRY_CUDA(cudaMemset(e->dev_err, 0, sizeof(int)));
     const bool fma = (flags & DS_FMA) != 0;
-    if (dtype == DS_F32)
-        return fma ? build_engine_typed<float, true>(e, (const float *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                     other_mode, hs_out, max_cells)
-                   : build_engine_typed<float, false>(e, (const float *)Xcat, x_off_dev, x_off, flags, s,
-                                                      force_other, other_mode, hs_out, max_cells);
-    return fma ? build_engine_typed<double, true>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                  other_mode, hs_out, max_cells)
-               : build_engine_typed<double, false>(e, (const double *)Xcat, x_off_dev, x_off, flags, s, force_other,
-                                                   other_mode, hs_out, max_cells);
+    if (dtype == DS_F32) {
+        const float *X = (const float *)Xcat, *Y = (const float *)Ycat;
+        return fma ? build_engine_typed<float, true>(e, X, Y, x_off_dev, x_off, flags, s, force_other, other_mode,
+                                                     hs_out, max_cells)
+                   : build_engine_typed<float, false>(e, X, Y, x_off_dev, x_off, flags, s, force_other, other_mode,
+                                                      hs_out, max_cells);
+    }
+    const double *X = (const double *)Xcat, *Y = (const double *)Ycat;
+    return fma ? build_engine_typed<double, true>(e, X, Y, x_off_dev, x_off, flags, s, force_other, other_mode,
+                                                  hs_out, max_cells)
+               : build_engine_typed<double, false>(e, X, Y, x_off_dev, x_off, flags, s, force_other, other_mode,
+                                                   hs_out, max_cells);
 }
 
 // ---------------------------------------------------------------- launch
@@ -533,13 +546,13 @@ static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, boo
 }
 
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
-                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s)
+                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s,
+                               bool host_io)
 {
-    const bool interp = Y && y_out;
+    const bool interp = y_out != nullptr;
     const int L = e->dtype == DS_F32 ? 4 : 2;
-    const size_t esz = e->dtype == DS_F32 ? 4 : 8;
     const bool vec = ((uintptr_t)Z % 16 == 0) && ((uintptr_t)I % (L * 4) == 0) &&
-                     (!interp || (uintptr_t)y_out % esz == 0);
+                     (!interp || (uintptr_t)y_out % 16 == 0);
     int grid = 0;
     DS_TRY(occupancy(e, t, interp, vec, &grid));
     const int block = eff_block(e, t, vec), vpt = clamp_vpt(t.items);
@@ -556,9 +569,9 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
         memset(&a, 0, sizeof(a));
         a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
         a.Z = (const float *)Z; a.I = I; a.Y = (const float *)Y; a.y_out = (float *)y_out;
-        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1;
+        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter;
         a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
-        a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
+        a.err = e->dev_err; a.ctab = e->ctab; a.l2pf = host_io ? 0 : 1;
         void *args[] = {&a};
         DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
     } else {
@@ -566,9 +579,9 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
         memset(&a, 0, sizeof(a));
         a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
         a.Z = (const double *)Z; a.I = I; a.Y = (const double *)Y; a.y_out = (double *)y_out;
-        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter; a.fallbacks = e->counter + 1;
+        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter;
         a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
-        a.err = e->dev_err; a.seg_x = e->seg_x; a.seg_a = e->seg_a; a.seg_b = e->seg_b;
+        a.err = e->dev_err; a.ctab = e->ctab; a.l2pf = host_io ? 0 : 1;
         void *args[] = {&a};
         DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
     }
@@ -638,8 +651,8 @@ ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg)
     return DS_OK;
 }
 
-ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
-                          cudaStream_t s, ds_tune_t *best_out)
+ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
+                          void *y_out, int32_t *I, cudaStream_t s, ds_tune_t *best_out)
 {
     const int blocks[] = {128, 256, 512, 1024};
     const int items[] = {1, 2, 4};
@@ -662,11 +675,11 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
                 t.items = it;
                 t.smem_limit = sm;
                 int grid = 0;
-                if (occupancy(e, t, false, true, &grid) != DS_OK) continue;
-                rc = engine_launch_direct(e, t, Z, z_off, m_single, nullptr, nullptr, I, s);
+                if (occupancy(e, t, y_out != nullptr, true, &grid) != DS_OK) continue;
+                rc = engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
                 if (rc != DS_OK) break;
                 cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; ++r) engine_launch_direct(e, t, Z, z_off, m_single, nullptr, nullptr, I, s);
+                for (int r = 0; r < 3; ++r) engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
                 cudaEventRecord(e1, s);
                 if (cudaEventSynchronize(e1) != cudaSuccess) {
                     rc = DS_E_CUDA;
@@ -762,7 +775,7 @@ ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t
     ds_batch *b = new ds_batch;
     b->hdr.kind = ds::KIND_BATCH;
     b->hdr.magic = ds::HANDLE_MAGIC;
-    ds_status rc = ds::engine_build(&b->eng, Xcat_dev, (const long long *)x_off_dev, n_arrays, dtype, flags,
+    ds_status rc = ds::engine_build(&b->eng, Xcat_dev, nullptr, (const long long *)x_off_dev, n_arrays, dtype, flags,
                                     (cudaStream_t)stream, nullptr, ds::MODE_BISECT, nullptr, nullptr);
     if (rc != DS_OK) {
         ds::free_batch(b);
@@ -793,7 +806,8 @@ ds_status ds_batch_autotune(ds_batch *b, const void *Zcat_dev, const int64_t *z_
         ds::set_error("ds_batch_autotune: bad argument");
         return DS_E_ARG;
     }
-    return ds::engine_autotune(&b->eng, Zcat_dev, (const long long *)z_off_dev, 0, Icat_dev, (cudaStream_t)stream,
+    return ds::engine_autotune(&b->eng, Zcat_dev, (const long long *)z_off_dev, 0, nullptr, nullptr, Icat_dev,
+                               (cudaStream_t)stream,
                                best);
 }
 

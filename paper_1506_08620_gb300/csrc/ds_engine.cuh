@@ -30,9 +30,11 @@ struct Engine {
     size_t table_bytes = 0;
     long long *chunk_off = nullptr;
     int *order = nullptr;  // claim order of the arrays: most knots first
-    unsigned long long *counter = nullptr;  // [0] chunk counter, [1] certificate failures
+    unsigned long long *counter = nullptr;  // [0] chunk counter
     int *dev_err = nullptr;
-    float *seg_x = nullptr, *seg_a = nullptr, *seg_b = nullptr;
+    unsigned char *ctab = nullptr;  // learned arrays' cell tables
+    size_t ctab_bytes = 0;
+    bool xy = false;                // knots stored as (X_i, Y_i) pairs
     ds_tune_t tune = {};
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -50,17 +52,27 @@ struct Engine {
 // force_other[a] set (or infeasible for direct search) get mode other_mode
 // (MODE_LEARNED) or MODE_BISECT.
 // max_cells_per_knot > 0: a feasible array with (R+1) > max_cells_per_knot (N+1)
-// also gets other_mode.
-ds_status engine_build(Engine *e, const void *Xcat, const long long *x_off_dev, int n_arrays, ds_dtype dtype,
-                       uint32_t flags, cudaStream_t s, const std::vector<char> *force_other, int other_mode,
-                       std::vector<long long> *x_off_host, std::vector<HRState> *hs_out,
+// also gets other_mode.  Ycat (same CSR as Xcat, or nullptr): the knot values,
+// stored with the knots as (X_i, Y_i) pairs.  A learned array gets room for
+// its cell map in the blob (filled later by the learned build).
+ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long long *x_off_dev, int n_arrays,
+                       ds_dtype dtype, uint32_t flags, cudaStream_t s, const std::vector<char> *force_other,
+                       int other_mode, std::vector<long long> *x_off_host, std::vector<HRState> *hs_out,
                        double max_cells_per_knot = 0.0);
+// Interpolation: y_out non-null; the knot values come from the stored pairs
+// (Y nullptr) or from the caller's Y.
+// host_io: Z, I and y_out are host memory mapped into the device (no bulk L2
+// prefetch of the query stream).
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
-                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s);
+                               long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s,
+                               bool host_io = false);
 ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
                         void *y_out, int32_t *I, cudaStream_t s);
-ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, int32_t *I,
-                          cudaStream_t s, ds_tune_t *best_out);
+ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
+                          void *y_out, int32_t *I, cudaStream_t s, ds_tune_t *best_out);
+// Macro cells G of a learned array's cell map for N + 1 knots: a power of two
+// in [LMAP_MIN, LMAP_MAX], about (N + 1) / 4.
+int lmap_cells(long long n_knots);
 ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg);
 void engine_free(Engine *e);
 ds_tune_t default_tune();

@@ -1,11 +1,15 @@
 // ds_learned.cu -- learned-index form (not in the paper): a 1 -> 32 -> 32 -> 1
 // ReLU network g predicting i / N = u + g(u) from u = (z - X_0) / (X_N - X_0)
 // (the network learns the deviation from the uniform-grid model N u, and its
-// output layer starts at zero, so the untrained model is that linear model), trained on
-// the GPU by the forward/backward/Adam kernels below; served as the network's
-// exact piecewise-linear form; error bound recorded at build time; exact
-// bounded window + certificate + fall-back in the shared ragged search kernel
-// (MODE_LEARNED in ds_multi_kernels.cuh).
+// output layer starts at zero, so the untrained model is that linear model),
+// trained on the GPU by the forward/backward/Adam kernels below.  Its exact
+// piecewise-linear form gives the recorded error bound and, sampled at G
+// uniform points and made monotone, the learned cell map: cells of equal
+// predicted rank instead of equal width in z.  Direct search runs on that map
+// (MODE_LEARNED in ds_multi_kernels.cuh) with the table K of Eq. indexdef over
+// its cells, so every answer is exact by construction; a cell may hold several
+// knots, and the largest cell population is the bounded window recorded at
+// build time.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
         y = s.y;
     } else {
         const int32_t i = (int32_t)below(r.v[1], (uint32_t)d.n + 1u);
-        u = pred_u<T>(X[i], d);
+        u = pred_u<T>(X[(size_t)i * d.xs], d);
         y = (float)i / (float)d.n;
     }
     const float res = y - u;  // the network's target: deviation from the linear model
@@ -398,11 +402,32 @@ __global__ void k_pool_queries(const ArrDesc *desc, const unsigned char *blob, c
         const P4 r = philox((uint32_t)k, (uint32_t)(k >> 32), (uint32_t)model, 0xB0B0u, seed_lo, seed_hi);
         const double f = ((double)r.v[0] * 4294967296.0 + (double)r.v[1]) * (1.0 / 18446744073709551616.0);
         T z = (T)((double)X0 + f * ((double)XN - (double)X0));
-        if (!(z < XN)) z = X[d.n - 1];
+        if (!(z < XN)) z = X[(size_t)(d.n - 1) * d.xs];
         if (z < X0) z = X0;
-        const int32_t i = bisect<T>(X, 0, d.n, d.pbits, z);
+        const int32_t i = bisect<T>(X, d.xs, 0, d.n, d.pbits, z);
         pool[p0 + k] = make_float2(pred_u<T>(z, d), (float)i / (float)d.n);
     }
+}
+
+// Piecewise-linear served form of the network: segment k covers
+// [seg_x[k], seg_x[k+1]) (seg_x[0] = -inf), value seg_a[k] * u + seg_b[k].
+__device__ __forceinline__ float pred_eval(float u, const float *sx, const float *sa, const float *sb, int n,
+                                           int top)
+{
+    int k = 0;
+    for (int s = top; s > 0; s >>= 1) {
+        const int r = k + s;
+        if (r < n && sx[r] <= u) k = r;
+    }
+    return __fmaf_rn(sa[k], u, sb[k]);
+}
+
+__device__ __forceinline__ int32_t floor_clamped(float p, int32_t n)
+{
+    // floor, with NaN and out-of-range predictions pinned inside [-2^30, 2^30]
+    if (!(p > -1073741824.0f)) p = -1073741824.0f;
+    if (p > 1073741824.0f) p = 1073741824.0f;
+    return __float2int_rd(p);
 }
 
 // Error bound of the served predictor: at every knot i (answer i) and at the
@@ -434,11 +459,11 @@ __global__ void k_error_bound(const ArrDesc *desc, const unsigned char *blob, co
     while (top * 2 <= d.seg_n) top *= 2;
     int lo = 0, hi = 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= d.n; i += (long long)gridDim.x * blockDim.x) {
-        const int32_t pf = floor_clamped(pred_eval(pred_u<T>(X[i], d), sx, sa, sb, d.seg_n, top), d.n);
+        const int32_t pf = floor_clamped(pred_eval(pred_u<T>(X[(size_t)i * d.xs], d), sx, sa, sb, d.seg_n, top), d.n);
         lo = max(lo, (int)min((long long)pf - i, (long long)1 << 30));
         hi = max(hi, (int)min(i - (long long)pf, (long long)1 << 30));
         if (i < d.n) {
-            const T z = next_down<T>(X[i + 1]);
+            const T z = next_down<T>(X[(size_t)(i + 1) * d.xs]);
             const int32_t pz = floor_clamped(pred_eval(pred_u<T>(z, d), sx, sa, sb, d.seg_n, top), d.n);
             lo = max(lo, (int)min((long long)pz - i, (long long)1 << 30));
             hi = max(hi, (int)min(i - (long long)pz, (long long)1 << 30));
@@ -452,6 +477,128 @@ __global__ void k_error_bound(const ArrDesc *desc, const unsigned char *blob, co
     if ((threadIdx.x & 31) == 0) {
         atomicMax(e_lo + model, lo);
         atomicMax(e_hi + model, hi);
+    }
+}
+
+// ------------------------------------------------------------------ learned cell tables
+// F_i = f(X_i) on the learned cell map, exactly as a query computes it, for
+// the knots of every model's array (model k's knots start at F + kbase[k]).
+template <typename T>
+__global__ void k_learned_F(const ArrDesc *desc, const unsigned char *blob, const int *model_arr,
+                            const long long *kbase, uint32_t *F)
+{
+    const int model = blockIdx.y;
+    const ArrDesc d = desc[model_arr[model]];
+    const T *X = reinterpret_cast<const T *>(blob + d.xg);
+    const uint2 *M = reinterpret_cast<const uint2 *>(blob + d.img);
+    const uint32_t G = d.img_bytes >> 3;
+    uint32_t *Fm = F + kbase[model];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= d.n;
+         i += (long long)gridDim.x * blockDim.x)
+        Fm[i] = learned_cell<T>(X[(size_t)i * d.xs], d, M, G);
+}
+
+// #{i in [lo, n1) : F_i < v} + lo for non-decreasing F, given F_i < v below lo.
+__device__ __forceinline__ uint32_t count_below(const uint32_t *F, uint32_t lo, uint32_t n1, uint32_t v)
+{
+    uint32_t hi = n1;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (F[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct LStats {
+    unsigned int max_pop;           // largest K_{j+1} - K_j
+    unsigned int escaped;           // blocks of 8 cells holding more than LBLK_MAXSPAN knots
+    unsigned long long nonempty;    // cells holding a knot
+    unsigned long long sum_pop2;    // sum over cells of (K_{j+1} - K_j)^2
+};
+
+// Blocks of 8 cells of every model's cell table: K_j = #{i : F_i < j} (Eq.
+// indexdef; cells at or past C count every knot).  fill = 0: statistics per
+// model; fill = 1: write the table (K_{8b} and the differences K_{8b+r} -
+// K_{8b}, r = 1..8, 12 bits each; an escaped block takes the next slot of its
+// model's overflow area, counted in st[model].escaped, which starts at 0).
+__global__ void k_learned_cells(const ArrDesc *desc, const int *model_arr, const long long *kbase, const uint32_t *F,
+                                LStats *st, unsigned char *ctab, int fill)
+{
+    const int model = blockIdx.y;
+    const ArrDesc d = desc[model_arr[model]];
+    const uint32_t *Fm = F + kbase[model];
+    const uint32_t n1 = (uint32_t)d.n + 1u;
+    const unsigned long long C = (unsigned long long)d.R + 1ull;
+    const unsigned long long nb = lblk_count(d.R);
+    unsigned int max_pop = 0, esc = 0;
+    unsigned long long ne = 0, p2 = 0;
+    for (unsigned long long b = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+         b += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t K[9];
+        uint32_t lo = 0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const unsigned long long j = (b << LBLK_SHIFT) + r;
+            K[r] = j >= C ? n1 : count_below(Fm, lo, n1, (uint32_t)j);
+            lo = K[r];
+        }
+        const bool escaped = K[8] - K[0] > LBLK_MAXSPAN;
+        if (!fill) {
+            esc += escaped;
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                if ((b << LBLK_SHIFT) + r < C) {
+                    const unsigned int pop = K[r + 1] - K[r];
+                    max_pop = max(max_pop, pop);
+                    ne += pop > 0;
+                    p2 += (unsigned long long)pop * pop;
+                }
+            continue;
+        }
+        uint4 *blk = reinterpret_cast<uint4 *>(ctab + d.ct);
+        if (escaped) {
+            const unsigned int slot = atomicAdd(&st[model].escaped, 1u);
+            uint32_t *O = reinterpret_cast<uint32_t *>(ctab + d.ct + nb * 16ull) + (size_t)slot * 9u;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) O[r] = K[r];
+            blk[b] = make_uint4(LBLK_ESC, slot, 0u, 0u);
+        } else {
+            uint32_t w[3] = {0u, 0u, 0u};
+#pragma unroll
+            for (int r = 1; r <= 8; ++r) {
+                const uint32_t v = K[r] - K[0], o = 12u * (r - 1);
+                w[o >> 5] |= v << (o & 31u);
+                if ((o & 31u) > 20u) w[(o >> 5) + 1] |= v >> (32u - (o & 31u));
+            }
+            blk[b] = make_uint4(K[0], w[0], w[1], w[2]);
+        }
+    }
+    if (fill) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        max_pop = max(max_pop, __shfl_xor_sync(0xffffffffu, max_pop, o));
+        esc += __shfl_xor_sync(0xffffffffu, esc, o);
+        ne += __shfl_xor_sync(0xffffffffu, ne, o);
+        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st[model].max_pop, max_pop);
+        atomicAdd(&st[model].escaped, esc);
+        atomicAdd(&st[model].nonempty, ne);
+        atomicAdd(&st[model].sum_pop2, p2);
+    }
+}
+
+// K_0 .. K_C of one learned array's cell table, decoded (for inspection).
+__global__ void k_export_cells(const unsigned char *ct, uint32_t R, uint32_t *K)
+{
+    const unsigned long long n = (unsigned long long)R + 2ull;
+    for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t t0, t1;
+        learned_bounds(ct, R, (uint32_t)(j <= R ? j : R), &t0, &t1);
+        K[j] = j <= R ? t0 : t1;
     }
 }
 
@@ -548,6 +695,41 @@ static void pwl_of(const float *thf, double scale, Segments &out)
     }
 }
 
+// The learned cell map of one array: the served prediction p sampled at
+// u = g / G, g = 0..G, made non-decreasing by rearrangement (the sampled
+// values sorted: Chernozhukov, Fernandez-Val and Galichon, "Improving point
+// and interval estimators of monotone functions by rearrangement",
+// Biometrika 2009; for a prediction that dips it keeps the rise spread over
+// the dip, where a running maximum would pile its knots into one cell), then
+// J_g = floor(p C / (N + 1)) clamped into [0, C - 1], with J_0 = 0 and
+// J_G = C - 1 (so the map covers every cell); entry g holds {J_g, J_{g+1}}.
+// Any non-decreasing J gives exact answers (the search kernel's f is
+// monotone); a good p gives cells of equal population.
+static void cell_map(const Segments &sg, long long n_knots, unsigned long long C, int G, std::vector<uint2> &out)
+{
+    std::vector<double> p(G + 1);
+    size_t k = 0;
+    for (int g = 0; g <= G; ++g) {
+        const double u = (double)g / (double)G;
+        while (k + 1 < sg.x.size() && (double)sg.x[k + 1] <= u) ++k;
+        p[g] = (double)sg.a[k] * u + (double)sg.b[k];
+        if (!(p[g] == p[g])) p[g] = 0.0;  // NaN: never from finite parameters; kept in range regardless
+    }
+    std::sort(p.begin(), p.end());
+    std::vector<unsigned long long> J(G + 1);
+    for (int g = 0; g <= G; ++g) {
+        double c = std::floor(p[g] * (double)C / (double)n_knots);
+        if (!(c >= 0.0)) c = 0.0;
+        if (c > (double)(C - 1)) c = (double)(C - 1);
+        J[g] = (unsigned long long)c;
+    }
+    J[0] = 0;
+    J[G] = C - 1;
+    for (int g = 1; g <= G; ++g) J[g] = std::max(J[g], J[g - 1]);
+    out.resize(G);
+    for (int g = 0; g < G; ++g) out[g] = make_uint2((uint32_t)J[g], (uint32_t)J[g + 1]);
+}
+
 }  // namespace ds
 
 // ------------------------------------------------------------------ handle
@@ -560,11 +742,20 @@ struct ds_learned {
     int steps = 0;
     double train_ms = 0, final_loss = 0;
     long long max_window = 0;
+    // per model: cells C, largest cell population, cells holding a knot, uint32 table
+    std::vector<unsigned long long> cells;
+    std::vector<unsigned int> max_pop;
+    std::vector<unsigned long long> nonempty;
+    std::vector<unsigned int> escaped;
+    std::vector<double> mean_pop;      // sum of squared cell populations / (N + 1)
+    std::vector<int> from_network;     // 1: the map comes from the network, 0: from the linear model
+    long long *zoff_dev = nullptr;     // device copy of the query offsets of ds_learned_search_host
 };
 
 namespace ds {
 void free_learned(ds_learned *L)
 {
+    if (L->zoff_dev) cudaFree(L->zoff_dev);
     engine_free(&L->eng);
     L->hdr.magic = 0;
     delete L;
@@ -595,9 +786,7 @@ ds_status info_learned(const ds_learned *L, ds_info_t *o)
         o->H = d.H;
         o->W = d.W;
     }
-    unsigned long long fb = 0;
-    if (e.counter && cudaMemcpy(&fb, e.counter + 1, sizeof(fb), cudaMemcpyDeviceToHost) == cudaSuccess)
-        o->fallback_queries = fb;
+    o->fallback_queries = 0;  // exact by construction: no query needs a fall-back
     int err = 0;
     if (e.dev_err && cudaMemcpy(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
         o->device_error = err;
@@ -625,6 +814,10 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
     long long *pool_off_d = nullptr;
     float2 *pool = nullptr;
     float *theta = nullptr, *mom = nullptr, *vel = nullptr, *part = nullptr, *plos = nullptr, *loss = nullptr;
+    float *seg_x = nullptr, *seg_a = nullptr, *seg_b = nullptr;
+    uint32_t *Fk = nullptr;
+    long long *kbase_d = nullptr;
+    LStats *lst = nullptr;
     ds_status rc = DS_OK;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -713,9 +906,11 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
         double ls = 0;
         for (float v : lh) ls += v;
         L->final_loss = ls / nm;
-        Segments all, one;
+        std::vector<Segments> segs(nm);
+        Segments all;
         for (int k = 0; k < nm; ++k) {
             ArrDesc &d = e.desc_host[L->model_arr[k]];
+            Segments &one = segs[k];
             if (linear) {
                 one.x.assign(1, -INFINITY);
                 one.a.assign(1, (float)d.n);
@@ -730,23 +925,22 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             all.b.insert(all.b.end(), one.b.begin(), one.b.end());
         }
         const size_t nseg = all.x.size();
-        A((void **)&e.seg_x, sizeof(float) * nseg);
-        A((void **)&e.seg_a, sizeof(float) * nseg);
-        A((void **)&e.seg_b, sizeof(float) * nseg);
+        A((void **)&seg_x, sizeof(float) * nseg);
+        A((void **)&seg_a, sizeof(float) * nseg);
+        A((void **)&seg_b, sizeof(float) * nseg);
         if (ce != cudaSuccess) {
             set_error("learned build: allocation failed");
             rc = DS_E_NOMEM;
             break;
         }
-        e.table_bytes += 3 * sizeof(float) * nseg;
-        cudaMemcpyAsync(e.seg_x, all.x.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(e.seg_a, all.a.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(e.seg_b, all.b.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(seg_x, all.x.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(seg_a, all.a.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(seg_b, all.b.data(), sizeof(float) * nseg, cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
         cudaMemsetAsync(elo, 0, sizeof(int) * nm, s);
         cudaMemsetAsync(ehi, 0, sizeof(int) * nm, s);
         k_error_bound<T><<<dim3(std::max(1, std::min(e.props.num_sms * 8 / std::max(1, nm), 2048)), nm), 256, 0, s>>>(
-            e.desc_dev, e.blob, model_arr, e.seg_x, e.seg_a, e.seg_b, elo, ehi);
+            e.desc_dev, e.blob, model_arr, seg_x, seg_a, seg_b, elo, ehi);
         std::vector<int> hlo(nm), hhi(nm);
         ce = cudaGetLastError();
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(hlo.data(), elo, sizeof(int) * nm, cudaMemcpyDeviceToHost, s);
@@ -757,18 +951,113 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             rc = DS_E_CUDA;
             break;
         }
+        // the cell maps: C cells per array, the served prediction sampled at G
+        // points (the network's, and the linear model's), each made monotone
+        const double cpk = cfg.cells_per_knot > 0.f ? (double)cfg.cells_per_knot : 1.0;
+        std::vector<std::vector<uint2>> net_maps(nm), lin_maps(nm);
+        std::vector<long long> kbase(nm + 1, 0);
+        L->cells.assign(nm, 0);
+        Segments linseg;
         for (int k = 0; k < nm; ++k) {
             ArrDesc &d = e.desc_host[L->model_arr[k]];
-            const bool zero = (cfg.flags & DS_LEARNED_ZERO_BOUND) != 0;
-            d.e_lo = zero ? 0 : hlo[k];
-            d.e_hi = zero ? 0 : hhi[k];
-            const long long w = (long long)d.e_lo + d.e_hi + 3;
-            L->max_window = std::max(L->max_window, w);
+            d.e_lo = hlo[k];
+            d.e_hi = hhi[k];
+            const double want = std::ceil(cpk * (double)(d.n + 1));
+            const unsigned long long C =
+                (unsigned long long)std::min(std::max(want, 1.0), (double)(0xFFFFFFFFull - 1));
+            L->cells[k] = C;
+            d.R = (uint32_t)(C - 1);
+            const int G = (int)(d.img_bytes >> 3);
+            linseg.x.assign(1, -INFINITY);
+            linseg.a.assign(1, (float)d.n);
+            linseg.b.assign(1, 0.f);
+            cell_map(segs[k], (long long)d.n + 1, C, G, net_maps[k]);
+            cell_map(linseg, (long long)d.n + 1, C, G, lin_maps[k]);
+            kbase[k + 1] = kbase[k] + d.n + 1;
         }
-        ce = cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
+        A((void **)&Fk, sizeof(uint32_t) * (size_t)kbase[nm]);
+        A((void **)&kbase_d, sizeof(long long) * (size_t)(nm + 1));
+        A((void **)&lst, sizeof(LStats) * nm);
+        if (ce != cudaSuccess) {
+            set_error("learned build: allocation failed");
+            rc = DS_E_NOMEM;
+            break;
+        }
+        cudaMemcpyAsync(kbase_d, kbase.data(), sizeof(long long) * (nm + 1), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
+        const dim3 lgrid(std::max(1, std::min(e.props.num_sms * 8 / std::max(1, nm), 2048)), nm);
+        // statistics of the maps in the blob: cell of every knot, then the cells' populations
+        auto map_stats = [&](const std::vector<std::vector<uint2>> &maps, std::vector<LStats> &hst) {
+            for (int k = 0; k < nm; ++k) {
+                const ArrDesc &d = e.desc_host[L->model_arr[k]];
+                cudaMemcpyAsync(e.blob + d.img, maps[k].data(), d.img_bytes, cudaMemcpyHostToDevice, s);
+            }
+            cudaMemsetAsync(lst, 0, sizeof(LStats) * nm, s);
+            k_learned_F<T><<<lgrid, 256, 0, s>>>(e.desc_dev, e.blob, model_arr, kbase_d, Fk);
+            k_learned_cells<<<lgrid, 256, 0, s>>>(e.desc_dev, model_arr, kbase_d, Fk, lst, nullptr, 0);
+            hst.resize(nm);
+            cudaError_t c2 = cudaGetLastError();
+            if (c2 == cudaSuccess) c2 = cudaMemcpyAsync(hst.data(), lst, sizeof(LStats) * nm, cudaMemcpyDeviceToHost, s);
+            if (c2 == cudaSuccess) c2 = cudaStreamSynchronize(s);
+            return c2;
+        };
+        // each array keeps the map whose cells a query shares with fewer knots
+        // (sum of squared populations: the mean population seen by queries
+        // distributed like the knots); the network's map only where it wins
+        std::vector<LStats> st_lin, st_net;
+        ce = map_stats(lin_maps, st_lin);
+        if (ce == cudaSuccess && !linear) ce = map_stats(net_maps, st_net);
+        if (ce != cudaSuccess) {
+            set_error("learned build: cell statistics failed: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+            break;
+        }
+        L->from_network.assign(nm, 0);
+        std::vector<std::vector<uint2>> chosen(nm);
+        for (int k = 0; k < nm; ++k) {
+            const bool net = !linear && st_net[k].sum_pop2 < st_lin[k].sum_pop2;
+            L->from_network[k] = net ? 1 : 0;
+            chosen[k] = net ? net_maps[k] : lin_maps[k];
+        }
+        std::vector<LStats> hst;
+        ce = map_stats(chosen, hst);
+        if (ce != cudaSuccess) {
+            set_error("learned build: cell statistics failed: %s", cudaGetErrorString(ce));
+            rc = DS_E_CUDA;
+            break;
+        }
+        size_t cbytes = 0;
+        L->max_pop.assign(nm, 0);
+        L->nonempty.assign(nm, 0);
+        L->escaped.assign(nm, 0);
+        L->mean_pop.assign(nm, 0.0);
+        for (int k = 0; k < nm; ++k) {
+            ArrDesc &d = e.desc_host[L->model_arr[k]];
+            d.aux = 0;
+            d.ct = (long long)cbytes;
+            cbytes += round_up((size_t)lblk_count(d.R) * 16 + (size_t)hst[k].escaped * 36, 16);
+            L->max_pop[k] = hst[k].max_pop;
+            L->nonempty[k] = hst[k].nonempty;
+            L->escaped[k] = hst[k].escaped;
+            L->mean_pop[k] = (double)hst[k].sum_pop2 / (double)(d.n + 1);
+            L->max_window = std::max(L->max_window, (long long)hst[k].max_pop + 1);
+        }
+        ce = cudaMalloc(&e.ctab, std::max<size_t>(cbytes, 16));
+        if (ce != cudaSuccess) {
+            e.ctab = nullptr;
+            set_error("learned build: cell tables (%zu bytes): allocation failed", cbytes);
+            rc = DS_E_NOMEM;
+            break;
+        }
+        e.ctab_bytes = cbytes;
+        e.table_bytes += cbytes;
+        cudaMemcpyAsync(e.desc_dev, e.desc_host.data(), sizeof(ArrDesc) * e.desc_host.size(), cudaMemcpyHostToDevice, s);
+        cudaMemsetAsync(lst, 0, sizeof(LStats) * nm, s);  // escaped slots are handed out from 0
+        k_learned_cells<<<lgrid, 256, 0, s>>>(e.desc_dev, model_arr, kbase_d, Fk, lst, e.ctab, 1);
+        ce = cudaGetLastError();
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
         if (ce != cudaSuccess) {
-            set_error("learned build: %s", cudaGetErrorString(ce));
+            set_error("learned build: cell table fill failed: %s", cudaGetErrorString(ce));
             rc = DS_E_CUDA;
         }
     } while (0);
@@ -776,7 +1065,8 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
     if (graph) cudaGraphDestroy(graph);
     if (cs) cudaStreamDestroy(cs);
     for (void *p : {(void *)model_arr, (void *)step, (void *)elo, (void *)ehi, (void *)pool_off_d, (void *)pool,
-                    (void *)theta, (void *)mom, (void *)vel, (void *)part, (void *)plos, (void *)loss})
+                    (void *)theta, (void *)mom, (void *)vel, (void *)part, (void *)plos, (void *)loss, (void *)seg_x,
+                    (void *)seg_a, (void *)seg_b, (void *)Fk, (void *)kbase_d, (void *)lst})
         if (p) cudaFree(p);
     L->train_ms = now_ms() - t0;
     return rc;
@@ -795,17 +1085,25 @@ void ds_learned_cfg_default(ds_learned_cfg *cfg)
 {
     if (!cfg) return;
     memset(cfg, 0, sizeof(*cfg));
-    cfg->steps = 2000;
+    cfg->steps = 6000;
     cfg->batch = 8192;
     cfg->n_queries = 1 << 18;
     cfg->lr = 3e-3f;
     cfg->seed = 1506086200ull;
     cfg->flags = 0;
     cfg->max_cells_per_knot = 16;
+    cfg->cells_per_knot = 1.0f;
 }
 
 ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, int64_t n_knots_if_single,
                            ds_dtype dtype, const ds_learned_cfg *cfg_in, void *stream, ds_learned **out)
+{
+    return ds_learned_build_xy(Xcat_dev, nullptr, x_off_dev, n_arrays, n_knots_if_single, dtype, cfg_in, stream, out);
+}
+
+ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const int64_t *x_off_dev, int32_t n_arrays,
+                              int64_t n_knots_if_single, ds_dtype dtype, const ds_learned_cfg *cfg_in, void *stream,
+                              ds_learned **out)
 {
     ds::clear_error();
     if (!out) {
@@ -818,7 +1116,8 @@ ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32
     else ds_learned_cfg_default(&cfg);
     if (!Xcat_dev || n_arrays < 1 || (dtype != DS_F32 && dtype != DS_F64) || (!x_off_dev && n_arrays != 1) ||
         (!x_off_dev && n_knots_if_single < 2) || cfg.batch < 1 || cfg.steps < 0 || !(cfg.lr > 0.f) ||
-        (cfg.flags & ~(uint32_t)(DS_LEARNED_FORCE | DS_LEARNED_LINEAR | DS_LEARNED_ZERO_BOUND))) {
+        !(cfg.cells_per_knot >= 0.f && cfg.cells_per_knot <= 64.f) ||
+        (cfg.flags & ~(uint32_t)(DS_LEARNED_FORCE | DS_LEARNED_LINEAR))) {
         ds::set_error("ds_learned_build: bad argument");
         return DS_E_ARG;
     }
@@ -845,8 +1144,8 @@ ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32
         force.assign(n_arrays, 1);
         fp = &force;
     }
-    ds_status rc = ds::engine_build(&L->eng, Xcat_dev, xo, n_arrays, dtype, 0, s, fp, ds::MODE_LEARNED, nullptr,
-                                    nullptr, (double)cfg.max_cells_per_knot);
+    ds_status rc = ds::engine_build(&L->eng, Xcat_dev, Ycat_dev, xo, n_arrays, dtype, 0, s, fp, ds::MODE_LEARNED,
+                                    nullptr, nullptr, (double)cfg.max_cells_per_knot);
     if (single_off) cudaFree(single_off);
     if (rc == DS_OK) {
         ds::Engine &e = L->eng;
@@ -897,8 +1196,9 @@ ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int
                             const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream)
 {
     if (!learned_ok(L) || !Zcat_dev || !Icat_dev || (!z_off_dev && (m < 0 || L->eng.n_arrays != 1)) ||
-        ((Ycat_dev == nullptr) != (y_out_dev == nullptr))) {
-        ds::set_error("ds_learned_search: bad argument");
+        (L->eng.xy ? Ycat_dev != nullptr : (Ycat_dev == nullptr) != (y_out_dev == nullptr))) {
+        ds::set_error("ds_learned_search: bad argument%s",
+                      L && L->eng.xy && Ycat_dev ? " (this handle holds its knot values: pass Ycat = NULL)" : "");
         return DS_E_ARG;
     }
     if (!z_off_dev && m == 0) return DS_OK;
@@ -907,14 +1207,15 @@ ds_status ds_learned_search(const ds_learned *L, const void *Zcat_dev, const int
 }
 
 ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
-                              int32_t *Icat_dev, void *stream, ds_tune_t *best)
+                              const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream, ds_tune_t *best)
 {
-    if (!learned_ok(L) || !Zcat_dev || !Icat_dev || (!z_off_dev && (m < 1 || L->eng.n_arrays != 1))) {
+    if (!learned_ok(L) || !Zcat_dev || !Icat_dev || (!z_off_dev && (m < 1 || L->eng.n_arrays != 1)) ||
+        (L->eng.xy ? Ycat_dev != nullptr : (Ycat_dev == nullptr) != (y_out_dev == nullptr))) {
         ds::set_error("ds_learned_autotune: bad argument");
         return DS_E_ARG;
     }
-    return ds::engine_autotune(&L->eng, Zcat_dev, (const long long *)z_off_dev, z_off_dev ? 0 : m, Icat_dev,
-                               (cudaStream_t)stream, best);
+    return ds::engine_autotune(&L->eng, Zcat_dev, (const long long *)z_off_dev, z_off_dev ? 0 : m, Ycat_dev,
+                               y_out_dev, Icat_dev, (cudaStream_t)stream, best);
 }
 
 ds_status ds_learned_set_tune(ds_learned *L, const ds_tune_t *cfg)
@@ -1002,6 +1303,109 @@ ds_status ds_adam_step(float *theta_dev, float *m_dev, float *v_dev, const float
         return DS_E_ARG;
     }
     ds::k_adam_explicit<<<5, 256, 0, (cudaStream_t)stream>>>(theta_dev, m_dev, v_dev, grad_dev, t, lr);
+    DS_TRY_CUDA(cudaGetLastError());
+    return DS_OK;
+}
+
+// Device address of host memory: mapped page-locked memory as it is, other
+// host memory registered (mapped) for this call; *reg is set when the caller
+// must unregister it.
+static ds_status host_mapped(void *h, size_t bytes, void **d, bool *reg)
+{
+    *reg = false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer &&
+        at.hostPointer) {
+        *d = (char *)at.devicePointer + ((char *)h - (char *)at.hostPointer);
+        return DS_OK;
+    }
+    cudaGetLastError();
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        ds::set_error("ds_learned_search_host: a buffer is device memory (use ds_learned_search)");
+        return DS_E_ARG;
+    }
+    DS_TRY_CUDA(cudaHostRegister(h, bytes, cudaHostRegisterMapped));
+    *reg = true;
+    const cudaError_t e = cudaHostGetDevicePointer(d, h, 0);
+    if (e != cudaSuccess) {
+        cudaHostUnregister(h);
+        *reg = false;
+        ds::set_error("ds_learned_search_host: %s", cudaGetErrorString(e));
+        return DS_E_CUDA;
+    }
+    return DS_OK;
+}
+
+ds_status ds_learned_search_host(ds_learned *L, const void *Zcat_host, const int64_t *z_off_host, int64_t m,
+                                 void *y_out_host, int32_t *Icat_host, void *stream)
+{
+    ds::clear_error();
+    if (!learned_ok(L) || !Zcat_host || !Icat_host || (!z_off_host && (m < 0 || L->eng.n_arrays != 1)) ||
+        (y_out_host && !L->eng.xy)) {
+        ds::set_error("ds_learned_search_host: bad argument%s",
+                      L && y_out_host && !L->eng.xy ? " (interpolation needs a handle from ds_learned_build_xy)" : "");
+        return DS_E_ARG;
+    }
+    ds::Engine &e = L->eng;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (z_off_host) {
+        if (z_off_host[0] != 0) {
+            ds::set_error("ds_learned_search_host: z_off[0] must be 0");
+            return DS_E_ARG;
+        }
+        m = z_off_host[e.n_arrays];
+        if (!L->zoff_dev) DS_TRY_CUDA(cudaMalloc(&L->zoff_dev, sizeof(long long) * (size_t)(e.n_arrays + 1)));
+        DS_TRY_CUDA(cudaMemcpyAsync(L->zoff_dev, z_off_host, sizeof(long long) * (size_t)(e.n_arrays + 1),
+                                    cudaMemcpyHostToDevice, s));
+    }
+    if (m == 0) return DS_OK;
+    const size_t esz = e.dtype == DS_F32 ? 4 : 8;
+    void *zd = nullptr, *id = nullptr, *yd = nullptr;
+    bool rz = false, ri = false, ry = false;
+    ds_status rc = host_mapped(const_cast<void *>(Zcat_host), (size_t)m * esz, &zd, &rz);
+    if (rc == DS_OK) rc = host_mapped(Icat_host, (size_t)m * 4, &id, &ri);
+    if (rc == DS_OK && y_out_host) rc = host_mapped(y_out_host, (size_t)m * esz, &yd, &ry);
+    if (rc == DS_OK)
+        rc = ds::engine_launch_direct(&e, e.tune, zd, z_off_host ? L->zoff_dev : nullptr, z_off_host ? 0 : m, nullptr,
+                                      yd, (int32_t *)id, s, true);
+    const cudaError_t ce = cudaStreamSynchronize(s);
+    if (rc == DS_OK && ce != cudaSuccess) {
+        ds::set_error("ds_learned_search_host: %s", cudaGetErrorString(ce));
+        rc = DS_E_CUDA;
+    }
+    if (rz) cudaHostUnregister(const_cast<void *>(Zcat_host));
+    if (ri) cudaHostUnregister(Icat_host);
+    if (ry) cudaHostUnregister(y_out_host);
+    return rc;
+}
+
+ds_status ds_learned_cells(const ds_learned *L, int32_t a, uint64_t *cells, int32_t *max_pop, int64_t *nonempty,
+                           int64_t *escaped, double *mean_pop, int32_t *from_network)
+{
+    if (!learned_ok(L) || a < 0 || a >= L->eng.n_arrays) {
+        ds::set_error("ds_learned_cells: bad argument");
+        return DS_E_ARG;
+    }
+    const int k = L->arr_model[a];
+    if (cells) *cells = k < 0 ? 0 : L->cells[k];
+    if (max_pop) *max_pop = k < 0 ? 0 : (int32_t)L->max_pop[k];
+    if (nonempty) *nonempty = k < 0 ? 0 : (int64_t)L->nonempty[k];
+    if (escaped) *escaped = k < 0 ? 0 : (int64_t)L->escaped[k];
+    if (mean_pop) *mean_pop = k < 0 ? 0.0 : L->mean_pop[k];
+    if (from_network) *from_network = k < 0 ? 0 : L->from_network[k];
+    return DS_OK;
+}
+
+ds_status ds_learned_export_cells(const ds_learned *L, int32_t a, uint32_t *K_out_dev, void *stream)
+{
+    if (!learned_ok(L) || a < 0 || a >= L->eng.n_arrays || !K_out_dev || L->arr_model[a] < 0) {
+        ds::set_error("ds_learned_export_cells: bad argument (array %d is not served by the learned map)", a);
+        return DS_E_ARG;
+    }
+    const ds::ArrDesc &d = L->eng.desc_host[a];
+    const unsigned long long n = (unsigned long long)d.R + 2ull;
+    const int grid = (int)std::min<unsigned long long>((n + 255) / 256, 4096ull);
+    ds::k_export_cells<<<grid, 256, 0, (cudaStream_t)stream>>>(L->eng.ctab + d.ct, d.R, K_out_dev);
     DS_TRY_CUDA(cudaGetLastError());
     return DS_OK;
 }

@@ -6,21 +6,28 @@
 // offsets on the device (so the whole search is stream-ordered and can be
 // captured in a CUDA graph); persistent blocks then claim chunks with an
 // atomic counter.  A block that claims a chunk of an array whose image (the
-// rank table of a direct array, or the knots of a bisected one) fits the
-// shared-memory budget stages that image with a bulk asynchronous copy, unless
-// it already holds it from its previous chunk; other arrays are read from
-// global memory, where the array being worked on stays L2-resident.
+// rank table of a direct array, the cell map of a learned one, or the knots
+// of a bisected one) fits the shared-memory budget stages that image with a
+// bulk asynchronous copy, unless it already holds it from its previous chunk;
+// other arrays are read from global memory, where the array being worked on
+// stays L2-resident.
 //
 // Per-array modes:
 //   MODE_DIRECT    Algorithm direct with the array's own H, W, R; K is held
 //                  as a rank table with knot fingerprints (below).
-//   MODE_LEARNED   predicted index, bounded window, certificate, exact
-//                  fall-back; the window is searched in three fixed-depth
-//                  levels: over every 1024th knot (L1-resident), over at most
-//                  32 of every 32nd knot, then over at most 32 knots.
+//   MODE_LEARNED   direct search on a learned cell map: the cell of z is
+//                  j = f(z) with f a monotone piecewise-linear map sampled
+//                  from the trained network's CDF (uniform in predicted
+//                  rank, not in z), K_j = #{i : f(X_i) < j} (Eq. indexdef
+//                  with cells that may hold several knots), and the answer is
+//                  K_j - 1 plus the number of the cell's knots <= z.
 //   MODE_BISECT    fixed-depth bisection over all knots (Algorithm
 //                  binaryoptnopad), the log-time fall-back where direct
 //                  search is infeasible.
+//
+// Knots are stored either alone or, when the handle holds the knot values Y
+// of the interpolation, as interleaved (X_i, Y_i) pairs (stride xs = 2), so
+// that one lookup's X_i, Y_i, X_{i+1}, Y_{i+1} share one span.
 #pragma once
 
 #include "ds_search.cuh"
@@ -29,56 +36,46 @@ namespace ds {
 
 enum ArrMode : int32_t { MODE_DIRECT = 0, MODE_LEARNED = 1, MODE_BISECT = 2 };
 
-// Sampling stride of the learned window search: S_k = X_{min(k * SG_STRIDE, N)}.
-// 32 measured faster than 8 on the 2^24-knot learned workload (13.5 against
-// 11.7 G lookups/s: the 4x larger sample table raised DRAM reads per lookup
-// from 146 to 181 bytes).
-constexpr int SG_SHIFT = 5;
-constexpr int SG_STRIDE = 1 << SG_SHIFT;
-// A second sample level, every SG_STRIDE-th sample: S1_k = X_{min(k * SG_STRIDE^2, N)},
-// small enough to stay in L1 (128 KB for 2^24 float64 knots).  The window is
-// searched over S1, then over at most SG_STRIDE samples, then over at most
-// SG_STRIDE knots: the last two are contiguous 256-byte runs, so a query's
-// L2 requests do not grow with the window.
-constexpr int SG1_SHIFT = 2 * SG_SHIFT;
-
-// Byte sizes of the two sample tables of a learned array with N + 1 knots
-// (S right after the knots' copy, S1 right after S).
-__host__ __device__ __forceinline__ size_t sample_bytes(int32_t n, size_t elem)
-{
-    return ((size_t)((n >> SG_SHIFT) + 2) * elem + 15) / 16 * 16;
-}
-__host__ __device__ __forceinline__ size_t sample1_bytes(int32_t n, size_t elem)
-{
-    return ((size_t)((n >> SG1_SHIFT) + 2) * elem + 15) / 16 * 16;
-}
+// Learned cell maps: G uniform macro cells over u = (z - X_0) / (X_N - X_0)
+// in [0, 1), each holding the first cells {J_g, J_{g+1}} of its span (8 bytes).
+constexpr int LMAP_MAX = 4096;  // largest G (32 KB, staged in shared memory)
+constexpr int LMAP_MIN = 64;
+// Learned cell table: a 16-byte block per 8 cells, K_{8b} then the
+// differences K_{8b+r} - K_{8b}, r = 1..8, in 12 bits each.  A block whose 8
+// cells hold more than LBLK_MAXSPAN knots is escaped: its first word is
+// LBLK_ESC and its second the position of its 9 values K_{8b} .. K_{8b+8}
+// (uint32) in the overflow area that follows the array's blocks.
+constexpr int LBLK_SHIFT = 3;
+constexpr uint32_t LBLK_MAXSPAN = 4095;
+constexpr uint32_t LBLK_ESC = 0x80000000u;  // K <= 2^31 - 1, so bit 31 of K_{8b} is free
+__host__ __device__ __forceinline__ unsigned long long lblk_count(uint32_t R) { return ((unsigned long long)R + 1ull) / 8ull + 1ull; }
 
 constexpr uint32_t NO_X_IN_IMG = 0xFFFFFFFFu;  // the image does not hold the knots
 
 // 128 bytes per array.
 struct __align__(16) ArrDesc {
-    long long img;        // byte offset of the staged image in the blob (direct: the rank table)
-    long long xg;         // byte offset of the knots in the blob
+    long long img;        // byte offset of the staged image in the blob (direct: the rank table;
+                          // learned: the cell map, G x {J_g, J_{g+1}})
+    long long xg;         // byte offset of the knots (or (X, Y) pairs) in the blob
     long long yoff;       // element offset of the array's knot values Y in the caller's Ycat
     uint32_t img_bytes;   // bytes of the image (multiple of 16), 0 if nothing to stage
     uint32_t x_in_img;    // byte offset of the knots inside the image, or NO_X_IN_IMG
     int32_t n;            // N: the array has N+1 knots
     int32_t mode;         // ArrMode
-    uint32_t R;           // direct: largest cell
+    uint32_t R;           // direct and learned: largest cell
     int32_t form;         // direct: FForm
     int32_t pbits;        // bisection over all knots: 2^floor(log2 N)
     int32_t aux;          // direct: 1 if the knot fingerprints of the rank table are used
     double H, W, X0;      // direct: parameters in the array's precision (held exactly)
     double XN;            // last knot
-    float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32)
+    float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32), 1 / (X_N - X_0)
     float x0f;            // learned: narrow(X0)
-    int32_t e_lo, e_hi;   // learned: recorded error bounds
+    int32_t e_lo, e_hi;   // learned: recorded error bounds of the network's prediction
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
-    long long sg;         // learned: byte offset of the sampled knots S_k = X_{min(32 k, N)}, k = 0..N/32+1,
-                          // followed by S1_k = X_{min(1024 k, N)}, k = 0..N/1024+1
+    long long ct;          // learned: byte offset of the cell table K (C + 1 values) in the engine's ctab
     uint32_t g_in_img;    // direct: byte offset of the knot fingerprints inside the image
-    uint32_t pad_;
+    int32_t xs;           // knot stride: 1 (knots alone) or 2 ((X_i, Y_i) pairs)
 };
 static_assert(sizeof(ArrDesc) == 128, "ArrDesc layout");
 
@@ -90,20 +87,17 @@ template <typename T> struct BatchArgs {
     int32_t n_arrays;
     const T *Z;
     int32_t *I;
-    const T *Y;                 // knot values (interpolation) or nullptr
+    const T *Y;                 // caller's knot values (interpolation), or nullptr (stored pairs, or none)
     T *y_out;
+    const unsigned char *ctab;  // learned cell tables
     const int *order;           // claim order: position p serves array order[p] (nullptr: p itself)
     long long *chunk_off;       // n_arrays+1 chunk offsets by position (written by the planner)
     unsigned long long *counter;// chunk counter (reset by the planner)
-    unsigned long long *fallbacks; // learned: certificate failures
     long long chunk;            // queries per chunk of an array that is not staged (chunk_len)
     uint32_t smem_limit;        // largest image staged in shared memory
     int checked;
+    int l2pf;                   // 1: bulk L2 prefetch of the query stream allowed (device memory)
     int *err;
-    // learned predictor tables (device): breakpoints, slopes, intercepts
-    const float *seg_x;
-    const float *seg_a;
-    const float *seg_b;
 };
 
 // Queries per chunk of an array.  A block stages the image of every chunk it
@@ -254,36 +248,57 @@ template <typename T> __device__ __forceinline__ bool lt_exact(T a, T b)
 
 // Largest i in [lo, lo + n - 1] with X_i <= z, given X_lo <= z and
 // z < X_{lo+n} (fixed depth, Algorithm binaryoptnopad on X[lo .. lo+n]);
-// `top` = 2^floor(log2 n) (or any larger power of two).
+// `top` = 2^floor(log2 n) (or any larger power of two); knot i at X[i xs].
 template <typename T>
-__device__ __forceinline__ int32_t bisect(const T *X, int32_t lo, int32_t n, int32_t top, T z)
+__device__ __forceinline__ int32_t bisect(const T *X, int xs, int32_t lo, int32_t n, int32_t top, T z)
 {
     int32_t i = 0;
     for (int32_t k = top; k > 0; k >>= 1) {
         const int32_t r = i | k;
         const int32_t w = r < n ? r : n;
-        if (!lt_exact<T>(z, X[lo + w])) i = r;
+        if (!lt_exact<T>(z, X[(size_t)(lo + w) * xs])) i = r;
     }
     return lo + (i < n ? i : n);
 }
 
-template <typename T, bool INTERP>
-__device__ __forceinline__ void interp_store(const BatchArgs<T> &a, const ArrDesc &d, const T *X, long long q,
-                                             T z, int32_t i)
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using V = float2; };
+template <> struct Pair2<double> { using V = double2; };
+
+// The linear interpolant y = Y_i + (Y_{i+1} - Y_i) ((z - X_i) / (X_{i+1} - X_i))
+// of NQ queries with answers r (NaN where r is outside [0, N-1]), each step
+// rounded once.  Xg: the array's knots in global memory; with stored pairs
+// (xs = 2) the two pairs (X_i, Y_i), (X_{i+1}, Y_{i+1}) are read as two
+// vectors, otherwise X from the knots and Y from the caller's values.  Every
+// load is issued before the first value is formed.
+template <typename T, int NQ>
+__device__ __forceinline__ void interp_values(const BatchArgs<T> &a, const ArrDesc &d, const T *Xg, const T *z,
+                                              const int32_t *r, T *y)
 {
-    if constexpr (INTERP) {
-        using A = Arith<T>;
-        T y;
-        if (i >= 0 && i < d.n) {
-            const T x0 = X[i], x1 = X[i + 1];
-            const T y0 = a.Y[d.yoff + i], y1 = a.Y[d.yoff + i + 1];
-            // y = Y_i + (Y_{i+1} - Y_i) * ((z - X_i) / (X_{i+1} - X_i)), each step rounded once
-            const T t = A::div(A::sub(z, x0), A::sub(x1, x0));
-            y = A::fma(A::sub(y1, y0), t, y0);
-        } else {
-            y = T(NAN);
+    using A = Arith<T>;
+    using V = typename Pair2<T>::V;
+    T x0[NQ], x1[NQ], y0[NQ], y1[NQ];
+    if (d.xs == 2) {
+        const V *P = reinterpret_cast<const V *>(Xg);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
+            const V p0 = __ldg(P + i), p1 = __ldg(P + i + 1);
+            x0[q] = p0.x; y0[q] = p0.y; x1[q] = p1.x; y1[q] = p1.y;
         }
-        a.y_out[q] = y;
+    } else {
+        const T *Y = a.Y + d.yoff;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
+            x0[q] = __ldg(Xg + i); x1[q] = __ldg(Xg + i + 1);
+            y0[q] = __ldg(Y + i); y1[q] = __ldg(Y + i + 1);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const T t = A::div(A::sub(z[q], x0[q]), A::sub(x1[q], x0[q]));
+        y[q] = r[q] >= 0 && r[q] < d.n ? A::fma(A::sub(y1[q], y0[q]), t, y0[q]) : T(NAN);
     }
 }
 

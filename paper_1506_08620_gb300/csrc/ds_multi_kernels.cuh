@@ -31,36 +31,51 @@ __device__ __forceinline__ float pred_u(T z, const ArrDesc &d)
     return __fmul_rn(__fsub_rn(narrow<T>(z), d.x0f), d.uscale);
 }
 
-// Piecewise-linear served form of the network: segment k covers
-// [seg_x[k], seg_x[k+1]) (seg_x[0] = -inf), value seg_a[k] * u + seg_b[k].
-__device__ __forceinline__ float pred_eval(float u, const float *sx, const float *sa, const float *sb, int n,
-                                           int top)
+// ------------------------------------------------------------------ learned cell map
+// Cell of z on a learned array: t = u(z) G (exact, G a power of two), macro
+// cell g = min(trunc t, G - 1) with its first cells {J_g, J_{g+1}}, and
+//   j = J_g + min(trunc(m(D m(t - g))), D),  D = J_{g+1} - J_g.
+// Every step is a monotone function of z (rounding is monotone, D >= 0), and
+// j lies in [J_g, J_{g+1}] while J is non-decreasing, so f is monotone over
+// the whole line: Eq. fprop holds for it, which is all the table of Eq.
+// indexdef needs.  Negative t and NaN give cell J_0 = 0, t >= G cell J_G.
+template <typename T>
+__device__ __forceinline__ uint32_t learned_cell(T z, const ArrDesc &d, const uint2 *M, uint32_t G)
 {
-    int k = 0;
-    for (int s = top; s > 0; s >>= 1) {
-        const int r = k + s;
-        if (r < n && sx[r] <= u) k = r;
+    const float t = __fmul_rn(pred_u<T>(z, d), (float)G);
+    uint32_t g = __float2uint_rz(t);
+    g = g < G - 1u ? g : G - 1u;
+    const float fr = __fsub_rn(t, __uint2float_rn(g));
+    const uint2 J = M[g];
+    const uint32_t D = J.y - J.x;
+    const uint32_t k = __float2uint_rz(__fmul_rn(__uint2float_rn(D), fr));
+    return J.x + (k < D ? k : D);
+}
+
+// K_j and K_{j+1} of a learned array's cell table (a 16-byte block per 8
+// cells: K_{8b} and 12-bit differences, or an escaped block's 9 values in the
+// overflow area after the lblk_count(R) blocks).
+__device__ __forceinline__ uint32_t lblk_field(uint4 w, uint32_t r)
+{
+    // difference r (1..8) of the block: bits 12 (r - 1) .. 12 r - 1 of (y, z, w)
+    const uint32_t o = 12u * (r - 1u);
+    const uint32_t lo = o < 32u ? w.y : (o < 64u ? w.z : w.w);
+    const uint32_t hi = o < 32u ? w.z : (o < 64u ? w.w : 0u);
+    return __funnelshift_r(lo, hi, o & 31u) & 0xFFFu;
+}
+__device__ __forceinline__ void learned_bounds(const unsigned char *ct, uint32_t R, uint32_t j, uint32_t *t0,
+                                               uint32_t *t1)
+{
+    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(ct) + (j >> LBLK_SHIFT));
+    const uint32_t r = j & 7u;
+    if (w.x & LBLK_ESC) {
+        const uint32_t *O = reinterpret_cast<const uint32_t *>(ct + lblk_count(R) * 16ull) + (size_t)w.y * 9u;
+        *t0 = __ldg(O + r);
+        *t1 = __ldg(O + r + 1u);
+    } else {
+        *t0 = w.x + (r ? lblk_field(w, r) : 0u);
+        *t1 = w.x + lblk_field(w, r + 1u);
     }
-    return __fmaf_rn(sa[k], u, sb[k]);
-}
-
-__device__ __forceinline__ int32_t floor_clamped(float p, int32_t n)
-{
-    // floor, with NaN and out-of-range predictions pinned inside [-2^30, 2^30]
-    if (!(p > -1073741824.0f)) p = -1073741824.0f;
-    if (p > 1073741824.0f) p = 1073741824.0f;
-    return __float2int_rd(p);
-}
-
-// Window [lo, hi] around the prediction (both clamped into [0, N-1]).
-__device__ __forceinline__ void window_of(int32_t pf, const ArrDesc &d, int32_t *lo, int32_t *hi)
-{
-    long long l = (long long)pf - d.e_lo - 1, h = (long long)pf + d.e_hi + 1;
-    const long long nm1 = d.n - 1;
-    l = l < 0 ? 0 : (l > nm1 ? nm1 : l);
-    h = h < 0 ? 0 : (h > nm1 ? nm1 : h);
-    *lo = (int32_t)l;
-    *hi = (int32_t)h;
 }
 
 // Table read: shared memory (staged image) or global memory through the
@@ -106,120 +121,47 @@ __host__ __device__ constexpr bool direct_kind(int k)
     return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
 }
 
-// Learned form: the window [lo, hi] (or, with `full`,
-// the whole array) searched in three fixed-depth levels, over S1_k =
-// X_{1024 k} (L1-resident), over at most 32 samples S_k = X_{32 k} (one
-// 256-byte run), then over at most 32 knots (another); r = the largest i in
-// the range with X_i <= z, if z lies in [X_lo, X_{hi+1}).
+// Learned form: j = f(z) on the learned cell map, (t0, t1) = (K_j, K_{j+1}).
+// Knots below t0 lie in cells below j and are < z; knots from t1 on lie in
+// cells above j and are > z (f is monotone), so the answer is t0 - 1 plus the
+// number of knots i in [t0, t1) with X_i <= z: none for an empty cell, else
+// decided by X_{t0} and X_{t1-1}, and between them by a bisection of the
+// cell's knots.  img: the cell map (shared or global memory).
 template <typename T, int NQ, bool SM>
-__device__ __forceinline__ void learned_window3(const BatchArgs<T> &a, const ArrDesc &d, const T *X, const T *z,
-                                                const int32_t *lo_in, const int32_t *hi_in, bool full, int32_t *r,
-                                                uint64_t pol)
+__device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrDesc &d, const unsigned char *img,
+                                               const T *X, const T *z, int32_t *r)
 {
-    const T *S = reinterpret_cast<const T *>(a.blob + d.sg);
-    const T *S1 = reinterpret_cast<const T *>(a.blob + d.sg + sample_bytes(d.n, sizeof(T)));
-    int32_t lo[NQ], hi[NQ];
+    const uint2 *M = reinterpret_cast<const uint2 *>(img);
+    const uint32_t G = d.img_bytes >> 3;
+    const unsigned char *ct = a.ctab + d.ct;
+    const int xs = d.xs;
+    uint32_t t0[NQ], t1[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) learned_bounds(ct, d.R, learned_cell<T>(z[q], d, M, G), &t0[q], &t1[q]);
+    T xa[NQ], xb[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        lo[q] = full ? 0 : lo_in[q];
-        hi[q] = full ? d.n - 1 : hi_in[q];
+        const bool any = t1[q] > t0[q];
+        xa[q] = any ? __ldg(X + (size_t)t0[q] * xs) : T(0);
+        xb[q] = any ? __ldg(X + (size_t)(t1[q] - 1u) * xs) : T(0);
     }
-    // level 0: largest k in [lo/1024, hi/1024] with S1_k <= z (S1_{lo/1024} <=
-    // X_lo and S1_{hi/1024+1} >= X_{hi+1}); 2 top0 > ws0 >= the range's length
-    const int32_t ws0 = full ? ((d.n - 1) >> SG1_SHIFT) + 1 : ((d.e_lo + d.e_hi + 3) >> SG1_SHIFT) + 2;
-    const int32_t top0 = 1 << (31 - __clz(ws0));
-    int32_t k0[NQ], nk0[NQ], i0[NQ];
+    bool inner = false;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        k0[q] = lo[q] >> SG1_SHIFT;
-        nk0[q] = (hi[q] >> SG1_SHIFT) - k0[q] + 1;
-        i0[q] = 0;
-    }
-    for (int32_t k = top0; k > 0; k >>= 1) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int32_t rr = i0[q] | k;
-            const int32_t w = rr < nk0[q] ? rr : nk0[q];
-            if (!lt_exact<T>(z[q], tab_ld<false>(S1 + k0[q] + w, pol))) i0[q] = rr;
+        if (t1[q] == t0[q] || lt_exact<T>(z[q], xa[q])) r[q] = (int32_t)t0[q] - 1;
+        else if (!lt_exact<T>(z[q], xb[q])) r[q] = (int32_t)t1[q] - 1;
+        else {
+            r[q] = -2;  // X_{t0} <= z < X_{t1-1}: inside the cell's knots
+            inner = true;
         }
     }
-    // level 1: the at most 32 samples of that block inside the range (the
-    // first is S1 of the block or S_{lo/32}, at most z; the one after the
-    // last is S1 of the next block or S_{hi/32+1}, above z)
-    int32_t k1[NQ], nk[NQ], i1[NQ];
+    if (inner) {
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int32_t kb = k0[q] + (i0[q] < nk0[q] ? i0[q] : nk0[q] - 1);
-        const int32_t b1 = kb << SG_SHIFT, l1 = lo[q] >> SG_SHIFT, e1 = (hi[q] >> SG_SHIFT) + 1;
-        k1[q] = b1 > l1 ? b1 : l1;
-        nk[q] = (b1 + SG_STRIDE < e1 ? b1 + SG_STRIDE : e1) - k1[q];
-        i1[q] = 0;
-    }
-    for (int32_t k = SG_STRIDE / 2; k > 0; k >>= 1) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int32_t rr = i1[q] | k;
-            const int32_t w = rr < nk[q] ? rr : nk[q];
-            if (!lt_exact<T>(z[q], tab_ld<SM>(S + k1[q] + w, pol))) i1[q] = rr;
-        }
-    }
-    // level 2: at most 32 knots
-    int32_t n2[NQ], i2[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const int32_t ks = k1[q] + (i1[q] < nk[q] ? i1[q] : nk[q] - 1);
-        const int32_t b0 = ks << SG_SHIFT;
-        const int32_t l2 = b0 > lo[q] ? b0 : lo[q];
-        const int32_t e2 = (b0 + SG_STRIDE < hi[q] + 1) ? b0 + SG_STRIDE : hi[q] + 1;
-        lo[q] = l2;
-        n2[q] = e2 - l2;
-        i2[q] = 0;
-    }
-    for (int32_t k = SG_STRIDE / 2; k > 0; k >>= 1) {
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const int32_t rr = i2[q] | k;
-            const int32_t w = rr < n2[q] ? rr : n2[q];
-            if (!lt_exact<T>(z[q], tab_ld<SM>(X + lo[q] + w, pol))) i2[q] = rr;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) r[q] = lo[q] + (i2[q] < n2[q] ? i2[q] : n2[q] - 1);
-}
-
-// Learned form.  The certificate is taken on the
-// answer instead of on the window: i is the answer exactly when
-// X_i <= z < X_{i+1} (the knots are sorted), and this fails exactly when z
-// lies outside [X_lo, X_{hi+1}).  The two knots sit in the lines the last
-// level has just read, so the check costs no gather of its own.  A thread
-// with a failed check searches all its queries again over the whole array
-// (out-of-domain queries: -1 and N).
-template <typename T, int NQ, bool SM>
-__device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrDesc &d, const T *X, const T *z,
-                                               int32_t *r, uint64_t pol)
-{
-    const float *sx = a.seg_x + d.seg_off, *sa = a.seg_a + d.seg_off, *sb = a.seg_b + d.seg_off;
-    int stop = 1;
-    while (stop * 2 <= d.seg_n) stop *= 2;
-    int32_t lo[NQ], hi[NQ];
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const float p = pred_eval(pred_u<T>(z[q], d), sx, sa, sb, d.seg_n, stop);
-        window_of(floor_clamped(p, d.n), d, &lo[q], &hi[q]);
-    }
-    learned_window3<T, NQ, SM>(a, d, X, z, lo, hi, false, r, pol);
-    int nfail = 0;
-#pragma unroll
-    for (int q = 0; q < NQ; ++q)
-        nfail += !(!lt_exact<T>(z[q], tab_ld<SM>(X + r[q], pol)) && lt_exact<T>(z[q], tab_ld<SM>(X + r[q] + 1, pol)));
-    if (nfail) {
-        atomicAdd(a.fallbacks, (unsigned long long)nfail);
-        learned_window3<T, NQ, SM>(a, d, X, z, lo, hi, true, r, pol);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            if (lt_exact<T>(z[q], X[0])) r[q] = -1;
-            else if (!lt_exact<T>(z[q], X[d.n])) r[q] = d.n;
-        }
+        for (int q = 0; q < NQ; ++q)
+            if (r[q] == -2) {
+                const int32_t n = (int32_t)(t1[q] - t0[q]) - 1;
+                r[q] = bisect<T>(X, xs, (int32_t)t0[q], n, 1 << (31 - __clz(n)), z[q]);
+            }
     }
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
@@ -227,8 +169,9 @@ __device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrD
 }
 
 // img: the array's image (shared or global memory: for a direct array its
-// rank words and knot fingerprints); X: its knots (global memory for direct
-// arrays, shared or global for bisected ones).
+// rank words and knot fingerprints, for a learned one its cell map); X: its
+// knots (global memory for direct and learned arrays, shared or global for
+// bisected ones), knot i at X[i xs].
 template <typename T, int NQ, int KIND, bool SM, bool FASTF>
 __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDesc &d, const CellF<T> &f,
                                              const unsigned char *img, const T *X, const T *z, int32_t *r,
@@ -260,7 +203,8 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const bool need = h[q].knot && (!fp || g[q] == kf[q]);
-            x[q] = need ? tab_ld<false>(X + h[q].t, pol) : T(0);
+            const size_t xi = direct_kind(KIND) ? (size_t)h[q].t : (size_t)h[q].t * d.xs;
+            x[q] = need ? tab_ld<false>(X + xi, pol) : T(0);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
@@ -272,7 +216,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         return;
     }
     if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {  // learned arrays
-        learned_answer<T, NQ, SM>(a, d, X, z, r, pol);
+        learned_answer<T, NQ, SM>(a, d, img, X, z, r);
         return;
     }
     // bisected arrays: fixed-depth search over all knots (Algorithm binaryoptnopad)
@@ -284,7 +228,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         n[q] = d.n;
         done[q] = false;
         if (lt_exact<T>(z[q], X[0])) { r[q] = -1; done[q] = true; }
-        else if (!lt_exact<T>(z[q], X[d.n])) { r[q] = d.n; done[q] = true; }
+        else if (!lt_exact<T>(z[q], X[(size_t)d.n * d.xs])) { r[q] = d.n; done[q] = true; }
     }
     const int32_t top = d.pbits;
     // interleaved fixed-depth bisection (Algorithm binaryoptnopad)
@@ -296,7 +240,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         for (int q = 0; q < NQ; ++q) {
             const int32_t rr = i[q] | k;
             const int32_t w = rr < n[q] ? rr : n[q];
-            if (!lt_exact<T>(z[q], tab_ld<SM>(X + lo[q] + w, pol))) i[q] = rr;
+            if (!lt_exact<T>(z[q], tab_ld<SM>(X + (size_t)(lo[q] + w) * d.xs, pol))) i[q] = rr;
         }
     }
 #pragma unroll
@@ -327,21 +271,21 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
         va = ze;
         vb = ze;
     }
+    const T *Xg = reinterpret_cast<const T *>(a.blob + d.xg);  // the knots in global memory (interpolation)
     // scalar head and tail
-    for (long long q = zs + tid; q < va; q += nthr) {
+    auto one = [&](long long q) {
         T z = a.Z[q];
         int32_t r;
         answer_block<T, 1, KIND, SM, FASTF>(a, d, f, K, X, &z, &r, pol);
         a.I[q] = r;
-        interp_store<T, INTERP>(a, d, X, q, z, r);
-    }
-    for (long long q = vb + tid; q < ze; q += nthr) {
-        T z = a.Z[q];
-        int32_t r;
-        answer_block<T, 1, KIND, SM, FASTF>(a, d, f, K, X, &z, &r, pol);
-        a.I[q] = r;
-        interp_store<T, INTERP>(a, d, X, q, z, r);
-    }
+        if constexpr (INTERP) {
+            T y;
+            interp_values<T, 1>(a, d, Xg, &z, &r, &y);
+            a.y_out[q] = y;
+        }
+    };
+    for (long long q = zs + tid; q < va; q += nthr) one(q);
+    for (long long q = vb + tid; q < ze; q += nthr) one(q);
     if constexpr (VEC) {
         using V = typename VecOf<T>::V;
         using IV = typename VecOf<T>::IV;
@@ -370,11 +314,11 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
                 bulk_prefetch_l2(Zv + first, (uint32_t)(n * (long long)sizeof(V)));
             }
         };
-        if (PREFETCH && tid == 0)
+        if (PREFETCH && a.l2pf && tid == 0)
             for (int k = 1; k <= QP_DIST; ++k) prefetch_l2((long long)k * tile);
         if (PREFETCH && tid < nv) load_tile(tid);
         for (long long base = tid; base < nv; base += (long long)VPT * nthr) {
-            if (PREFETCH && tid == 0) prefetch_l2(base + (long long)(QP_DIST + 1) * tile);
+            if (PREFETCH && a.l2pf && tid == 0) prefetch_l2(base + (long long)(QP_DIST + 1) * tile);
             V zv[VPT];
             if constexpr (PREFETCH) {
 #pragma unroll
@@ -396,11 +340,16 @@ __device__ __forceinline__ void process_chunk(const BatchArgs<T> &a, const ArrDe
                     if constexpr (L == 4) o = make_int4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
                     else o = make_int2(r[2 * v], r[2 * v + 1]);
                     __stcs(Iv + idx, o);
-                    if constexpr (INTERP) {
+                }
+            }
+            if constexpr (INTERP) {  // one vector of queries at a time (register pressure)
+                V *yv = reinterpret_cast<V *>(a.y_out) + v0;
 #pragma unroll
-                        for (int l = 0; l < L; ++l)
-                            interp_store<T, INTERP>(a, d, X, (v0 + idx) * L + l, zs4[v * L + l], r[v * L + l]);
-                    }
+                for (int v = 0; v < VPT; ++v) {
+                    const long long idx = base + (long long)v * nthr;
+                    V o;
+                    interp_values<T, L>(a, d, Xg, zs4 + v * L, r + v * L, reinterpret_cast<T *>(&o));
+                    if (idx < nv) __stcs(yv + idx, o);
                 }
             }
         }
@@ -612,29 +561,28 @@ __global__ void k_seg_hr_grow(const T *Xcat, const long long *x_off, int n_array
     if (a < n_arrays) hr_grow_one<T, FMA>(Xcat + x_off[a], x_off[a + 1] - x_off[a], st + a);
 }
 
-// Copy every array's knots into its place in the blob; cells F_i of the
-// knots of direct arrays into F and their fingerprints into G (packed like Xcat).
+// Copy every array's knots (with their values Y as (X_i, Y_i) pairs when Ycat
+// is given) into its place in the blob; cells F_i of the knots of direct
+// arrays into F and their fingerprints into G (packed like Xcat).
 template <typename T>
-__global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const long long *__restrict__ x_off,
-                                  const Segment *__restrict__ segs, int n_segs, const ArrDesc *__restrict__ desc,
-                                  unsigned char *blob, uint32_t *__restrict__ F, uint8_t *__restrict__ G)
+__global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const T *__restrict__ Ycat,
+                                  const long long *__restrict__ x_off, const Segment *__restrict__ segs, int n_segs,
+                                  const ArrDesc *__restrict__ desc, unsigned char *blob, uint32_t *__restrict__ F,
+                                  uint8_t *__restrict__ G)
 {
     for (int s = blockIdx.x; s < n_segs; s += gridDim.x) {
         const Segment sg = segs[s];
         const ArrDesc d = desc[sg.arr];
         const long long start = x_off[sg.arr];
         T *Xd = reinterpret_cast<T *>(blob + d.xg);
-        T *S = reinterpret_cast<T *>(blob + d.sg);
-        T *S1 = reinterpret_cast<T *>(blob + d.sg + sample_bytes(d.n, sizeof(T)));
         for (long long i = sg.lo + threadIdx.x; i < sg.hi; i += blockDim.x) {
             const T x = Xcat[i];
             const long long li = i - start;
-            Xd[li] = x;
-            if (d.mode == MODE_LEARNED) {  // S_k = X_{min(SG k, N)}, k = 0 .. N/SG + 1
-                if ((li & (SG_STRIDE - 1)) == 0) S[li >> SG_SHIFT] = x;
-                if (li == d.n) S[(d.n >> SG_SHIFT) + 1] = x;
-                if ((li & ((1 << SG1_SHIFT) - 1)) == 0) S1[li >> SG1_SHIFT] = x;
-                if (li == d.n) S1[(d.n >> SG1_SHIFT) + 1] = x;
+            if (Ycat) {
+                Xd[2 * li] = x;
+                Xd[2 * li + 1] = Ycat[i];
+            } else {
+                Xd[li] = x;
             }
             if (d.mode == MODE_DIRECT) {  // f and fingerprint exactly as a query computes them
                 uint32_t g;

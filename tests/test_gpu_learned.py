@@ -1,7 +1,8 @@
 """GPU tests of the learned form: training kernels against the float64
-oracle, exactness of the learned search (window + certificate + fall-back),
-the recorded error bound, the gain over the network-free model, and the
-fused interpolation against its float64 reference."""
+oracle, exactness of direct search on the learned cell map (every map, every
+table format), the recorded bounds, the gain of the trained network over the
+network-free map, and the fused interpolation (caller's values and stored
+(X, Y) pairs) against its float64 reference."""
 import numpy as np
 import pytest
 import torch
@@ -89,7 +90,24 @@ def _queries(X, Z, dtype):
     return np.concatenate([Z, W.adversarial_queries(X), W.midpoints(X), extra]).astype(dtype)
 
 
-def test_learned_single_array_is_exact_and_bound_holds(ds):
+def _check_cells(ds, L, a, n_knots):
+    """The exported table is Eq. indexdef's over some monotone map: K_0 = 0,
+    K_C = N + 1, non-decreasing; its largest step and its non-empty cells are
+    the recorded statistics, and max_window is the largest step plus one."""
+    c = ds.ds_learned_cells(L, a)
+    K = ds.ds_learned_export_cells(L, a).cpu().numpy().astype(np.int64)
+    assert K.size == c["cells"] + 1
+    assert K[0] == 0 and K[-1] == n_knots
+    d = np.diff(K)
+    assert np.all(d >= 0)
+    assert int(d.max()) == c["max_pop"] and int((d > 0).sum()) == c["nonempty"]
+    assert c["mean_pop"] == pytest.approx(float((d * d).sum()) / n_knots, rel=1e-12)
+    blocks = np.add.reduceat(d, np.arange(0, d.size, 8))  # knots per block of 8 cells
+    assert c["escaped"] == int((blocks > 4095).sum())
+    return c, K
+
+
+def test_learned_single_array_is_exact(ds):
     w = _learned_small()
     X = w["X"]
     assert oracle.compute_hr(X)["status"] == oracle.OR_E_OVERFLOW  # plain direct search infeasible
@@ -101,37 +119,92 @@ def test_learned_single_array_is_exact_and_bound_holds(ds):
     assert arr["mode"] == 1 and arr["e_lo"] >= 0 and arr["e_hi"] >= 0
     got = L.search(_cuda(Z)).cpu().numpy()
     assert np.array_equal(got, oracle.upper_bound(X, Z))
-    # the recorded bound covers every knot and the top of every interval: no
-    # certificate may fail on those queries
-    f0 = L.info()["fallback_queries"]
-    probes = np.concatenate([X[:-1], np.nextafter(X[1:], -np.inf)])
-    got = L.search(_cuda(probes)).cpu().numpy()
-    assert np.array_equal(got, oracle.upper_bound(X, probes))
-    assert L.info()["fallback_queries"] == f0
+    c, _ = _check_cells(ds, L, 0, X.size)
+    assert info["max_window"] == c["max_pop"] + 1 and info["fallback_queries"] == 0
+    assert c["cells"] == X.size  # the default: one cell per knot
     L.free()
 
 
-def test_zero_bound_forces_the_certificate_and_stays_exact(ds):
-    w = _learned_small(n_knots=20_001, m=200_000)
-    X, Z = w["X"], _queries(w["X"], w["Z"], np.float64)
-    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds, flags=ds.DS_LEARNED_ZERO_BOUND | ds.DS_LEARNED_FORCE))
-    got = L.search(_cuda(Z)).cpu().numpy()
-    assert np.array_equal(got, oracle.upper_bound(X, Z))
-    assert L.info()["fallback_queries"] > 0
+@pytest.mark.parametrize("cpk,linear,steps", [(1.0, True, 300), (0.01, False, 0), (0.0004, True, 0), (4.0, False, 300)])
+def test_every_cell_map_is_exact(ds, cpk, linear, steps):
+    # any non-decreasing map gives exact answers: the linear map, the untrained
+    # network, cells holding thousands of knots (escaped blocks: more than 4095
+    # knots in 8 cells), and four cells per knot
+    w = _learned_small(n_knots=200_001, m=300_000, seed=77)
+    X = w["X"]
+    Z = _queries(X, w["Z"], np.float64)
+    flags = ds.DS_LEARNED_FORCE | (ds.DS_LEARNED_LINEAR if linear else 0)
+    L = ds.ds_learned_build(_cuda(X), cfg=_cfg(ds, steps=steps, flags=flags, cells_per_knot=cpk))
+    c, _ = _check_cells(ds, L, 0, X.size)
+    assert (c["escaped"] > 0) == (cpk < 0.001)
+    assert np.array_equal(L.search(_cuda(Z)).cpu().numpy(), oracle.upper_bound(X, Z))
     L.free()
+
+
+def _bumps(n, seed):
+    """Knots whose density varies at scales the network can follow: eight
+    narrow bumps of different widths over a sparse background (float64)."""
+    g = np.random.default_rng(seed)
+    parts = [g.uniform(0.0, 1.0, n // 5)]
+    for k in range(8):
+        parts.append(g.normal(0.06 + 0.12 * k, 10.0 ** g.uniform(-3, -2), (n - n // 5) // 8))
+    X = np.unique(np.concatenate(parts))
+    return W.strictly_increasing(X)
+
+
+def _time(fn, reps=20):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(3):
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / reps)
+    return best
 
 
 def test_trained_network_beats_the_model_without_it(ds):
-    w = _learned_small()
-    X = w["X"]
-    Xd = _cuda(X)
-    trained = ds.ds_learned_build(Xd, cfg=_cfg(ds, steps=600))
-    linear = ds.ds_learned_build(Xd, cfg=_cfg(ds, flags=ds.DS_LEARNED_LINEAR))
-    ti, li = trained.info(), linear.info()
-    # the recorded window (max error over all knots) shrinks
-    assert ti["max_window"] < li["max_window"], (ti["max_window"], li["max_window"])
-    Z = _cuda(w["Z"])
-    assert torch.equal(trained.search(Z), linear.search(Z))
+    # on knots whose density varies at scales the network follows, cells of
+    # equal predicted rank hold fewer knots than cells of equal width, so
+    # fewer lookups compare and bisect: the same exact answers, a smaller mean
+    # cell population, less time
+    X = _bumps(1 << 20, 3)
+    g = np.random.default_rng(4)
+    mids = W.midpoints(X)
+    Z = mids[g.integers(0, mids.size, 1 << 24)]  # queries distributed like the knots (the paper's harness)
+    Xd, Zd = _cuda(X), _cuda(Z)
+    trained = ds.ds_learned_build(Xd, cfg=_cfg(ds, steps=6000, flags=ds.DS_LEARNED_FORCE))
+    linear = ds.ds_learned_build(Xd, cfg=_cfg(ds, flags=ds.DS_LEARNED_LINEAR | ds.DS_LEARNED_FORCE))
+    ct = _check_cells(ds, trained, 0, X.size)[0]
+    cl = _check_cells(ds, linear, 0, X.size)[0]
+    assert ct["from_network"] == 1 and cl["from_network"] == 0
+    assert ct["mean_pop"] * 2 < cl["mean_pop"], (ct, cl)
+    ref = oracle.upper_bound(X, Z[: 1 << 20])
+    out_t, out_l = trained.search(Zd), linear.search(Zd)
+    assert np.array_equal(out_t[: 1 << 20].cpu().numpy(), ref)
+    assert torch.equal(out_t, out_l)
+    ds.ds_learned_autotune(trained, Zd)
+    ds.ds_learned_autotune(linear, Zd)
+    t_t = _time(lambda: trained.search(Zd, out=out_t))
+    t_l = _time(lambda: linear.search(Zd, out=out_l))
+    assert t_t * 1.15 < t_l, (t_t, t_l, ct, cl)
+    trained.free()
+    linear.free()
+
+
+def test_map_choice_never_worse_than_linear(ds):
+    # the build keeps the network's map only where its cells are better balanced
+    w = _learned_small(n_knots=(1 << 20) + 1, m=1 << 16, seed=5)
+    Xd = _cuda(w["X"])
+    trained = ds.ds_learned_build(Xd, cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
+    linear = ds.ds_learned_build(Xd, cfg=_cfg(ds, flags=ds.DS_LEARNED_LINEAR | ds.DS_LEARNED_FORCE))
+    ct, cl = ds.ds_learned_cells(trained, 0), ds.ds_learned_cells(linear, 0)
+    assert ct["mean_pop"] <= cl["mean_pop"]
+    assert (ct["from_network"] == 1) == (ct["mean_pop"] < cl["mean_pop"])
     trained.free()
     linear.free()
 
@@ -170,27 +243,57 @@ def test_batched_learned_with_interpolation(ds):
     assert 0 in modes and 1 in modes
     Id, yd = Ld.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
     Ld.free()
-    # every array through the learned predictor
-    L = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
-    info = L.info()
-    assert info["n_learned"] == 24
-    I, y = L.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
-    I, y = I.cpu().numpy(), y.cpu().numpy()
     Iref, yref = oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)
-    assert np.array_equal(I, Iref)
-    assert np.array_equal(Id.cpu().numpy(), Iref)
-    assert np.array_equal(yd.cpu().numpy(), y)
     arr = np.searchsorted(z_off, np.arange(Zcat.size), side="right") - 1
-    gi = x_off[arr] + I
-    assert np.all(_interp_tol(y, yref, Ycat[gi], Ycat[gi + 1]))
-    # at a knot the interpolant is the knot value exactly
-    Zk = np.concatenate([Xcat[x_off[a]:x_off[a + 1] - 1] for a in range(24)])
-    zk_off = W.csr(np.diff(x_off) - 1)
-    Ik, yk = L.search(_cuda(Zk), _cuda(zk_off), Y=_cuda(Ycat))
-    Ik = Ik.cpu().numpy()
-    assert np.array_equal(Ik, np.concatenate([np.arange(n - 1) for n in np.diff(x_off)]))
-    ref_yk = np.concatenate([Ycat[x_off[a]:x_off[a + 1] - 1] for a in range(24)])
-    assert np.array_equal(yk.cpu().numpy(), ref_yk)
+    gi = x_off[arr] + Iref
+    for flags in (ds.DS_LEARNED_FORCE, 0):
+        # every array through the learned map, then the default selector; the
+        # handle holds its values as (X, Y) pairs
+        L = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off), cfg=_cfg(ds, steps=50, flags=flags))
+        if flags:
+            assert L.info()["n_learned"] == 24
+        y = torch.empty(Zcat.size, dtype=torch.float32, device="cuda")
+        I, _ = L.search(_cuda(Zcat), _cuda(z_off), y_out=y)
+        I, y = I.cpu().numpy(), y.cpu().numpy()
+        assert np.array_equal(I, Iref)
+        assert np.array_equal(Id.cpu().numpy(), Iref)
+        # the same rounding steps whichever way the values are read
+        assert np.array_equal(yd.cpu().numpy(), y, equal_nan=True)
+        assert np.all(_interp_tol(y, yref, Ycat[gi], Ycat[gi + 1]))
+        # at a knot the interpolant is the knot value exactly
+        Zk = np.concatenate([Xcat[x_off[a]:x_off[a + 1] - 1] for a in range(24)])
+        zk_off = W.csr(np.diff(x_off) - 1)
+        yk = torch.empty(Zk.size, dtype=torch.float32, device="cuda")
+        Ik, _ = L.search(_cuda(Zk), _cuda(zk_off), y_out=yk)
+        assert np.array_equal(Ik.cpu().numpy(), np.concatenate([np.arange(n - 1) for n in np.diff(x_off)]))
+        ref_yk = np.concatenate([Ycat[x_off[a]:x_off[a + 1] - 1] for a in range(24)])
+        assert np.array_equal(yk.cpu().numpy(), ref_yk)
+        # a handle that holds its values refuses the caller's
+        with pytest.raises((ds.DsError, ValueError)):
+            L.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
+        L.free()
+
+
+def test_interpolation_misaligned_and_out_of_domain(ds):
+    # the scalar path (buffers off 16-byte alignment) and queries outside
+    # [X_0, X_N): NaN values, indices -1 and N
+    g = np.random.default_rng(21)
+    X = W.knots_from_gaps(0.0, g.lognormal(0, 1, 5000), np.float32)
+    Y = g.standard_normal(X.size).astype(np.float32)
+    Z = np.concatenate([W.uniform_queries(g, X[0], X[-1], 10_001, np.float32),
+                        np.array([X[0] - 1, X[-1], X[-1] + 1, X[0]], dtype=np.float32)])
+    L = ds.ds_learned_build_xy(_cuda(X), _cuda(Y), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
+    zb = torch.zeros(Z.size + 1, dtype=torch.float32, device="cuda")
+    zb[1:] = _cuda(Z)
+    ob = torch.zeros(Z.size + 1, dtype=torch.int32, device="cuda")
+    yb = torch.zeros(Z.size + 1, dtype=torch.float32, device="cuda")
+    L.search(zb[1:], out=ob[1:], y_out=yb[1:])
+    Ir, yr = oracle.interp(X, Y, Z)
+    I, y = ob[1:].cpu().numpy(), yb[1:].cpu().numpy()
+    assert np.array_equal(I, Ir)
+    ok = (Ir >= 0) & (Ir < X.size - 1)
+    assert np.all(np.isnan(y[~ok])) and np.all(~np.isnan(y[ok]))
+    assert np.all(_interp_tol(y[ok], yr[ok], Y[Ir[ok]], Y[Ir[ok] + 1]))
     L.free()
 
 
@@ -207,6 +310,7 @@ def test_workload4_full_size(ds):
     gl = out.long()
     assert bool((gl >= 0).all()) and bool((gl <= X.size - 2).all())
     assert bool((Xd[gl] <= Zd).all()) and bool((Zd < Xd[gl + 1]).all())
+    _check_cells(ds, L, 0, X.size)
     L.free()
 
 
@@ -215,8 +319,9 @@ def test_workload5_full_size(ds):
     w = W.workload5()
     Xcat, Ycat, x_off, Zcat, z_off = w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"], w["z_off"]
     Xd, Yd, xo, Zd, zo = _cuda(Xcat), _cuda(Ycat), _cuda(x_off), _cuda(Zcat), _cuda(z_off)
-    L = ds.ds_learned_build(Xd, xo)
-    I, y = L.search(Zd, zo, Y=Yd)
+    L = ds.ds_learned_build_xy(Xd, Yd, xo)
+    y = torch.empty_like(Zd)
+    I, _ = L.search(Zd, zo, y_out=y)
     g = np.random.default_rng(14)
     pos = np.sort(g.integers(0, Zcat.size, 1 << 20))
     arr = np.searchsorted(z_off, pos, side="right") - 1
@@ -227,9 +332,17 @@ def test_workload5_full_size(ds):
         Ir, yr = oracle.interp(Xa, Ya, Zcat[pos[sel]])
         assert np.array_equal(Is[sel], Ir), a
         assert np.all(_interp_tol(ys[sel], yr, Ya[Ir], Ya[Ir + 1])), a
+    # every position: the index by the defining invariant X_I <= z < X_{I+1},
+    # then y against the interpolant restated in float64 on those exact indices
     arr_all = torch.searchsorted(zo, torch.arange(Zd.numel(), device="cuda"), right=True) - 1
     gi = xo[arr_all] + I.long()
+    del arr_all
     assert bool((Xd[gi] <= Zd).all()) and bool((Zd < Xd[gi + 1]).all())
+    x0, x1 = Xd[gi].double(), Xd[gi + 1].double()
+    y0, y1 = Yd[gi].double(), Yd[gi + 1].double()
+    y64 = y0 + (y1 - y0) * ((Zd.double() - x0) / (x1 - x0))
+    scale = torch.maximum(y64.abs(), torch.maximum(y0.abs(), y1.abs()))
+    assert bool(((y.double() - y64).abs() <= 1e-6 * scale).all())
     L.free()
 
 
@@ -246,10 +359,15 @@ def test_autotuned_learned_stays_exact(ds):
     L.free()
     w5 = W.workload5(n_arrays=24, size_lo=1 << 10, size_hi=1 << 16, total_queries=1 << 20)
     Xcat, Ycat, x_off, Zcat, z_off = w5["Xcat"], w5["Ycat"], w5["x_off"], w5["Zcat"], w5["z_off"]
-    L5 = ds.ds_learned_build(_cuda(Xcat), _cuda(x_off), cfg=_cfg(ds, steps=50))
-    ds.ds_learned_autotune(L5, _cuda(Zcat), _cuda(z_off))
-    I, _ = L5.search(_cuda(Zcat), _cuda(z_off), Y=_cuda(Ycat))
-    assert np.array_equal(I.cpu().numpy(), oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)[0])
+    L5 = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off), cfg=_cfg(ds, steps=50))
+    y = torch.empty(Zcat.size, dtype=torch.float32, device="cuda")
+    ds.ds_learned_autotune(L5, _cuda(Zcat), _cuda(z_off), y_out=y)
+    I, _ = L5.search(_cuda(Zcat), _cuda(z_off), y_out=y)
+    Iref, yref = oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)
+    assert np.array_equal(I.cpu().numpy(), Iref)
+    arr = np.searchsorted(z_off, np.arange(Zcat.size), side="right") - 1
+    gi = x_off[arr] + Iref
+    assert np.all(_interp_tol(y.cpu().numpy(), yref, Ycat[gi], Ycat[gi + 1]))
     L5.free()
 
 
