@@ -42,6 +42,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="learned_interp_f32", choices=WORKLOADS)
+    p.add_argument("--cells-per-knot", type=float, default=0.0,
+                   help="learned workloads: cells of the learned cell map per knot (0: the library's default)")
+    p.add_argument("--arrays", type=int, default=0,
+                   help="learned + interpolation workload: number of arrays (profiling runs; default 256)")
     p.add_argument("--no-per-config", action="store_true",
                    help="skip the per-configuration figures of workloads 1-4 (default run only)")
     p.add_argument("--variant", default="plain", choices=["plain", "fma", "cache", "fma_cache", "gap2", "fma_gap2"])
@@ -648,6 +652,38 @@ def setup_batched(args, ds, W, torch, dev, rank):
         res = {"no_fingerprint": job.m / time_calls(torch, stream, lambda: ds.ds_batch_search(nf, Zd, zo, out), 5),
                "no_fingerprint_tune": t}
         nf.free()
+        # plain Direct on the same arrays and queries: one table and one search
+        # launch per array (4096 launches replayed from one CUDA graph), the
+        # same-dtype comparison for the batched engine
+        xo_h, zo_h = w["x_off"], w["z_off"]
+        idxs = [ds.ds_build(Xd[xo_h[a]:xo_h[a + 1]]) for a in range(len(xo_h) - 1)]
+        gs = torch.cuda.Stream()
+        gs.wait_stream(torch.cuda.current_stream())
+        # each array's queries copied to a 16-byte aligned segment (the vector path of ds_search)
+        cnt = np.diff(zo_h)
+        po = np.zeros(cnt.size + 1, dtype=np.int64)
+        np.cumsum((cnt + 3) // 4 * 4, out=po[1:])
+        Zp_d = torch.zeros(int(po[-1]), dtype=Zd.dtype, device=Zd.device)
+        Op_d = torch.empty(int(po[-1]), dtype=torch.int32, device=Zd.device)
+        for a in range(cnt.size):
+            Zp_d[po[a]:po[a] + cnt[a]] = Zd[zo_h[a]:zo_h[a + 1]]
+        views = [(Zp_d[po[a]:po[a] + cnt[a]], Op_d[po[a]:po[a] + cnt[a]]) for a in range(len(idxs))]
+        with torch.cuda.stream(gs):
+            for a, (zv, ov) in enumerate(views):
+                if zv.numel():
+                    ds.ds_search(idxs[a], zv, ov, stream=gs)
+        torch.cuda.current_stream().wait_stream(gs)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gs):
+            for a, (zv, ov) in enumerate(views):
+                if zv.numel():
+                    ds.ds_search(idxs[a], zv, ov, stream=gs)
+        res["plain_direct_per_array_graph"] = job.m / time_calls(torch, stream, graph.replay, 5)
+        res["plain_direct_per_array_launches"] = sum(1 for zv, _ in views if zv.numel())
+        del graph
+        torch.cuda.synchronize()
+        for i in idxs:
+            i.free()
         return res
     job.extras = extras
     return job
@@ -659,7 +695,8 @@ def setup_learned(args, ds, W, torch, dev, rank):
     job = Job()
     five = args.workload == "learned_interp_f32"
     if five:
-        w = W.workload5(seed=rank_seed(W, 5, rank), total_queries=args.queries or (1 << 28))
+        w = W.workload5(seed=rank_seed(W, 5, rank), total_queries=args.queries or (1 << 28),
+                        n_arrays=args.arrays or 256)
         Xd, xo = torch.from_numpy(w["Xcat"]).to(dev), torch.from_numpy(w["x_off"]).to(dev)
         Yd = torch.from_numpy(w["Ycat"]).to(dev)
         Zh, zo = w["Zcat"], torch.from_numpy(w["z_off"]).to(dev)
@@ -674,6 +711,7 @@ def setup_learned(args, ds, W, torch, dev, rank):
     out = torch.empty(job.m, dtype=torch.int32, device=dev)
     yout = torch.empty(job.m, dtype=Xd.dtype, device=dev) if five else None
     cfg = ds.ds_learned_cfg_default(n_queries=1 << 20) if not five else ds.ds_learned_cfg_default()
+    cfg.cells_per_knot = args.cells_per_knot
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     L = ds.ds_learned_build_xy(Xd, Yd, xo, cfg=cfg) if five else ds.ds_learned_build(Xd, cfg=cfg)
@@ -705,21 +743,16 @@ def setup_learned(args, ds, W, torch, dev, rank):
     bufs = {}
 
     def e2e():
+        # through the C ABI's host-buffer call: the kernel reads the queries from
+        # and writes the results to pinned host memory over the CPU-GPU link
         if not bufs:
             bufs.update(Z=torch.from_numpy(Zh).pin_memory(), I=torch.empty(job.m, dtype=torch.int32).pin_memory(),
                         y=torch.empty(job.m, dtype=Xd.dtype).pin_memory() if five else None,
-                        z=torch.empty_like(Zd), o=torch.empty_like(out), yb=torch.empty_like(yout) if five else None)
+                        zo=torch.from_numpy(w["z_off"]) if five else None)
             job.e2e_out = bufs["I"]
         Zp, Ip, yp = bufs["Z"], bufs["I"], bufs["y"]
-        bufs["z"].copy_(Zp, non_blocking=True)
-        if five:
-            ds.ds_learned_search(L, bufs["z"], zo, out=bufs["o"], y_out=bufs["yb"])
-            yp.copy_(bufs["yb"], non_blocking=True)
-        else:
-            ds.ds_learned_search(L, bufs["z"], out=bufs["o"])
-        Ip.copy_(bufs["o"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        return Zp.numel() * esz, Ip.numel() * 4 + (yp.numel() * esz if five else 0)
+        ds.ds_learned_search_host(L, Zp, bufs["zo"], out=Ip, y_out=yp)
+        return Zp.numel() * esz + (bufs["zo"].numel() * 8 if five else 0), Ip.numel() * 4 + (yp.numel() * esz if five else 0)
     job.e2e = e2e
     job.verify = lambda: answer_check(torch, job.search, Xd, Zd, out, xo, zo, Yd, yout)
     job.host = w

@@ -488,6 +488,7 @@ static const void *pick3(bool vec, bool warps, bool big, int kind)
         if constexpr (sizeof(T) == 4) return pick4<T, VPT, INTERP, KIND_DIRECT_FPF>(vec, warps, big);
         else return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
     case KIND_LEARNED_ONLY: return pick4<T, VPT, INTERP, KIND_LEARNED_ONLY>(vec, warps, big);
+    case KIND_MIXED: return pick4<T, VPT, INTERP, KIND_MIXED>(vec, warps, big);
     default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps, big);
     }
 }
@@ -505,10 +506,12 @@ static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, i
     default: return pick2<T, 4>(interp, vec, warps, big, kind);
     }
 }
-static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0; }
+// every array in direct mode, searched on its rank table with the knots alone
+// (the direct kinds read knot t at X[t]; pairs take the mixed kind)
+static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0 && !e->xy; }
 static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big)
 {
-    const int kind = !direct_only(e) ? (e->n_direct == 0 && e->n_fallback == 0 ? KIND_LEARNED_ONLY : KIND_ALL)
+    const int kind = !direct_only(e) ? (e->n_fallback > 0 ? KIND_ALL : e->n_direct == 0 ? KIND_LEARNED_ONLY : KIND_MIXED)
                      : !e->fingerprints ? KIND_DIRECT
                      : e->fast_cells    ? KIND_DIRECT_FPF
                                         : KIND_DIRECT_FP;

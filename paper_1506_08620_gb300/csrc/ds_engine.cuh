@@ -34,7 +34,7 @@ struct Engine {
     int *dev_err = nullptr;
     unsigned char *ctab = nullptr;  // learned arrays' cell tables
     size_t ctab_bytes = 0;
-    bool xy = false;                // knots stored as (X_i, Y_i) pairs
+    bool xy = false;                // knots stored as intervals (X_i, Y_i, X_{i+1}, Y_{i+1})
     ds_tune_t tune = {};
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
@@ -53,14 +53,14 @@ struct Engine {
 // (MODE_LEARNED) or MODE_BISECT.
 // max_cells_per_knot > 0: a feasible array with (R+1) > max_cells_per_knot (N+1)
 // also gets other_mode.  Ycat (same CSR as Xcat, or nullptr): the knot values,
-// stored with the knots as (X_i, Y_i) pairs.  A learned array gets room for
+// stored with the knots as intervals (X_i, Y_i, X_{i+1}, Y_{i+1}).  A learned array gets room for
 // its cell map in the blob (filled later by the learned build).
 ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long long *x_off_dev, int n_arrays,
                        ds_dtype dtype, uint32_t flags, cudaStream_t s, const std::vector<char> *force_other,
                        int other_mode, std::vector<long long> *x_off_host, std::vector<HRState> *hs_out,
                        double max_cells_per_knot = 0.0);
-// Interpolation: y_out non-null; the knot values come from the stored pairs
-// (Y nullptr) or from the caller's Y.
+// Interpolation: y_out non-null; the knot values come from the stored
+// intervals (Y nullptr) or from the caller's Y.
 // host_io: Z, I and y_out are host memory mapped into the device (no bulk L2
 // prefetch of the query stream).
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,

@@ -743,6 +743,7 @@ struct ds_learned {
     double train_ms = 0, final_loss = 0;
     long long max_window = 0;
     // per model: cells C, largest cell population, cells holding a knot, uint32 table
+    std::vector<int> e_lo, e_hi;       // per model: recorded error bounds of the network's prediction
     std::vector<unsigned long long> cells;
     std::vector<unsigned int> max_pop;
     std::vector<unsigned long long> nonempty;
@@ -957,11 +958,13 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
         std::vector<std::vector<uint2>> net_maps(nm), lin_maps(nm);
         std::vector<long long> kbase(nm + 1, 0);
         L->cells.assign(nm, 0);
+        L->e_lo.assign(nm, 0);
+        L->e_hi.assign(nm, 0);
         Segments linseg;
         for (int k = 0; k < nm; ++k) {
             ArrDesc &d = e.desc_host[L->model_arr[k]];
-            d.e_lo = hlo[k];
-            d.e_hi = hhi[k];
+            L->e_lo[k] = hlo[k];
+            L->e_hi[k] = hhi[k];
             const double want = std::ceil(cpk * (double)(d.n + 1));
             const unsigned long long C =
                 (unsigned long long)std::min(std::max(want, 1.0), (double)(0xFFFFFFFFull - 1));
@@ -1243,8 +1246,9 @@ ds_status ds_learned_array(const ds_learned *L, int32_t a, float *theta_host, in
     }
     const ds::ArrDesc &d = L->eng.desc_host[a];
     if (mode) *mode = d.mode;
-    if (e_lo) *e_lo = d.e_lo;
-    if (e_hi) *e_hi = d.e_hi;
+    const int km = L->arr_model[a];
+    if (e_lo) *e_lo = km >= 0 && !L->e_lo.empty() ? L->e_lo[km] : 0;
+    if (e_hi) *e_hi = km >= 0 && !L->e_hi.empty() ? L->e_hi[km] : 0;
     if (theta_host) {
         const int k = L->arr_model[a];
         if (k >= 0 && !L->theta_host.empty()) memcpy(theta_host, &L->theta_host[(size_t)k * ds::NP], sizeof(float) * ds::NP);

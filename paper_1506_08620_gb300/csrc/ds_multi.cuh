@@ -25,9 +25,9 @@
 //                  binaryoptnopad), the log-time fall-back where direct
 //                  search is infeasible.
 //
-// Knots are stored either alone or, when the handle holds the knot values Y
-// of the interpolation, as interleaved (X_i, Y_i) pairs (stride xs = 2), so
-// that one lookup's X_i, Y_i, X_{i+1}, Y_{i+1} share one span.
+// Knots are stored either alone (stride xs = 1) or, when the handle holds
+// the knot values Y of the interpolation, as (X_i, Y_i) pairs (stride xs =
+// 2), so that one lookup's four operands lie in 16 contiguous bytes.
 #pragma once
 
 #include "ds_search.cuh"
@@ -70,7 +70,7 @@ struct __align__(16) ArrDesc {
     double XN;            // last knot
     float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32), 1 / (X_N - X_0)
     float x0f;            // learned: narrow(X0)
-    int32_t e_lo, e_hi;   // learned: recorded error bounds of the network's prediction
+    long long rsv;        // reserved (0)
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
     long long ct;          // learned: byte offset of the cell table K (C + 1 values) in the engine's ctab
@@ -261,45 +261,58 @@ __device__ __forceinline__ int32_t bisect(const T *X, int xs, int32_t lo, int32_
     return lo + (i < n ? i : n);
 }
 
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using V = float2; };
-template <> struct Pair2<double> { using V = double2; };
+// Pair (X_i, Y_i) of knot i in the pair layout (xs = 2), and an interval
+// (X_i, Y_i, X_{i+1}, Y_{i+1}) as two pairs.
+template <typename T> struct XYPair { T x, y; };
+__device__ __forceinline__ XYPair<float> pair_ld(const float *X, int32_t i)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(X) + i);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ XYPair<double> pair_ld(const double *X, int32_t i)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(X) + i);
+    return {v.x, v.y};
+}
+template <typename T> struct Ival { T x0, y0, x1, y1; };
+template <typename T> __device__ __forceinline__ Ival<T> ival_of(XYPair<T> a, XYPair<T> b) { return {a.x, a.y, b.x, b.y}; }
 
-// The linear interpolant y = Y_i + (Y_{i+1} - Y_i) ((z - X_i) / (X_{i+1} - X_i))
-// of NQ queries with answers r (NaN where r is outside [0, N-1]), each step
-// rounded once.  Xg: the array's knots in global memory; with stored pairs
-// (xs = 2) the two pairs (X_i, Y_i), (X_{i+1}, Y_{i+1}) are read as two
-// vectors, otherwise X from the knots and Y from the caller's values.  Every
-// load is issued before the first value is formed.
+// y = Y_i + (Y_{i+1} - Y_i) ((z - X_i) / (X_{i+1} - X_i)), each step rounded
+// once; NaN where i lies outside [0, N-1].
+template <typename T>
+__device__ __forceinline__ T interp_of(const Ival<T> &v, T z, int32_t i, int32_t n)
+{
+    using A = Arith<T>;
+    const T t = A::div(A::sub(z, v.x0), A::sub(v.x1, v.x0));
+    return i >= 0 && i < n ? A::fma(A::sub(v.y1, v.y0), t, v.y0) : T(NAN);
+}
+
+// The linear interpolant of NQ queries with answers r.  Xg: the array's
+// knots in global memory: the pair layout (xs = 2, two adjacent pairs per
+// query) or the knots alone (X from them, Y from the caller's values).
+// Every load is issued before the first value is formed.
 template <typename T, int NQ>
 __device__ __forceinline__ void interp_values(const BatchArgs<T> &a, const ArrDesc &d, const T *Xg, const T *z,
                                               const int32_t *r, T *y)
 {
-    using A = Arith<T>;
-    using V = typename Pair2<T>::V;
-    T x0[NQ], x1[NQ], y0[NQ], y1[NQ];
+    Ival<T> v[NQ];
     if (d.xs == 2) {
-        const V *P = reinterpret_cast<const V *>(Xg);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
-            const V p0 = __ldg(P + i), p1 = __ldg(P + i + 1);
-            x0[q] = p0.x; y0[q] = p0.y; x1[q] = p1.x; y1[q] = p1.y;
+            v[q] = ival_of<T>(pair_ld(Xg, i), pair_ld(Xg, i + 1));
         }
     } else {
         const T *Y = a.Y + d.yoff;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
-            x0[q] = __ldg(Xg + i); x1[q] = __ldg(Xg + i + 1);
-            y0[q] = __ldg(Y + i); y1[q] = __ldg(Y + i + 1);
+            v[q].x0 = __ldg(Xg + i); v[q].x1 = __ldg(Xg + i + 1);
+            v[q].y0 = __ldg(Y + i); v[q].y1 = __ldg(Y + i + 1);
         }
     }
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const T t = A::div(A::sub(z[q], x0[q]), A::sub(x1[q], x0[q]));
-        y[q] = r[q] >= 0 && r[q] < d.n ? A::fma(A::sub(y1[q], y0[q]), t, y0[q]) : T(NAN);
-    }
+    for (int q = 0; q < NQ; ++q) y[q] = interp_of<T>(v[q], z[q], r[q], d.n);
 }
 
 }  // namespace ds

@@ -115,7 +115,11 @@ template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint8_t *p, 
 // out, which keeps the register count low), or with fingerprints and the
 // one-conversion cell form (float arrays, every R < 2^24 - 1), or learned
 // arrays only.
-enum BatchKind : int { KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3, KIND_LEARNED_ONLY = 4 };
+// KIND_MIXED: direct and learned arrays, no bisected ones (the learned
+// handles), knots alone or as (X, Y) pairs.
+enum BatchKind : int {
+    KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3, KIND_LEARNED_ONLY = 4, KIND_MIXED = 5
+};
 __host__ __device__ constexpr bool direct_kind(int k)
 {
     return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
@@ -177,12 +181,12 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
                                              const unsigned char *img, const T *X, const T *z, int32_t *r,
                                              uint64_t pol)
 {
-    if (direct_kind(KIND) || (KIND == KIND_ALL && d.mode == MODE_DIRECT)) {
+    if (direct_kind(KIND) || ((KIND == KIND_ALL || KIND == KIND_MIXED) && d.mode == MODE_DIRECT)) {
         // one rank word per query; for a cell holding a knot, the knot's
         // fingerprint; the knot X_t itself only when the two fingerprints are
         // equal (otherwise they order z and X_t: within a cell the fingerprint
         // is a non-decreasing function of f, Eq. fprop)
-        const bool fp = KIND == KIND_DIRECT_FP || KIND == KIND_DIRECT_FPF || (KIND == KIND_ALL && d.aux);
+        const bool fp = KIND == KIND_DIRECT_FP || KIND == KIND_DIRECT_FPF || ((KIND == KIND_ALL || KIND == KIND_MIXED) && d.aux);
         const uint2 *Rt = reinterpret_cast<const uint2 *>(img);
         const uint8_t *Gt = img + d.g_in_img;
         uint32_t g[NQ], j[NQ];
@@ -215,7 +219,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         }
         return;
     }
-    if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {  // learned arrays
+    if (KIND == KIND_LEARNED_ONLY || KIND == KIND_MIXED || d.mode == MODE_LEARNED) {  // learned arrays
         learned_answer<T, NQ, SM>(a, d, img, X, z, r);
         return;
     }
@@ -561,9 +565,9 @@ __global__ void k_seg_hr_grow(const T *Xcat, const long long *x_off, int n_array
     if (a < n_arrays) hr_grow_one<T, FMA>(Xcat + x_off[a], x_off[a + 1] - x_off[a], st + a);
 }
 
-// Copy every array's knots (with their values Y as (X_i, Y_i) pairs when Ycat
-// is given) into its place in the blob; cells F_i of the knots of direct
-// arrays into F and their fingerprints into G (packed like Xcat).
+// Copy every array's knots (with their values Y as (X_i, Y_i) pairs when
+// Ycat is given) into its place in the blob; cells F_i of the knots of
+// direct arrays into F and their fingerprints into G (packed like Xcat).
 template <typename T>
 __global__ void k_seg_copy_fill_F(const T *__restrict__ Xcat, const T *__restrict__ Ycat,
                                   const long long *__restrict__ x_off, const Segment *__restrict__ segs, int n_segs,

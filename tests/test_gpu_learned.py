@@ -246,11 +246,13 @@ def test_batched_learned_with_interpolation(ds):
     Iref, yref = oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)
     arr = np.searchsorted(z_off, np.arange(Zcat.size), side="right") - 1
     gi = x_off[arr] + Iref
-    for flags in (ds.DS_LEARNED_FORCE, 0):
-        # every array through the learned map, then the default selector; the
-        # handle holds its values as (X, Y) pairs
-        L = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off), cfg=_cfg(ds, steps=50, flags=flags))
-        if flags:
+    for flags, cpk in ((ds.DS_LEARNED_FORCE, 1.0), (0, 1.0), (0, 0.05), (ds.DS_LEARNED_FORCE, 0.05)):
+        # every array through the learned map, then the default selector, and
+        # with about 20 knots per learned cell (queries past a cell's second
+        # knot bisect it); the handle holds its values as intervals
+        L = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off),
+                                   cfg=_cfg(ds, steps=50, flags=flags, cells_per_knot=cpk))
+        if flags & ds.DS_LEARNED_FORCE:
             assert L.info()["n_learned"] == 24
         y = torch.empty(Zcat.size, dtype=torch.float32, device="cuda")
         I, _ = L.search(_cuda(Zcat), _cuda(z_off), y_out=y)
@@ -274,7 +276,8 @@ def test_batched_learned_with_interpolation(ds):
         L.free()
 
 
-def test_interpolation_misaligned_and_out_of_domain(ds):
+@pytest.mark.parametrize("cpk", [1.0, 0.02])
+def test_interpolation_misaligned_and_out_of_domain(ds, cpk):
     # the scalar path (buffers off 16-byte alignment) and queries outside
     # [X_0, X_N): NaN values, indices -1 and N
     g = np.random.default_rng(21)
@@ -282,7 +285,7 @@ def test_interpolation_misaligned_and_out_of_domain(ds):
     Y = g.standard_normal(X.size).astype(np.float32)
     Z = np.concatenate([W.uniform_queries(g, X[0], X[-1], 10_001, np.float32),
                         np.array([X[0] - 1, X[-1], X[-1] + 1, X[0]], dtype=np.float32)])
-    L = ds.ds_learned_build_xy(_cuda(X), _cuda(Y), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
+    L = ds.ds_learned_build_xy(_cuda(X), _cuda(Y), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE, cells_per_knot=cpk))
     zb = torch.zeros(Z.size + 1, dtype=torch.float32, device="cuda")
     zb[1:] = _cuda(Z)
     ob = torch.zeros(Z.size + 1, dtype=torch.int32, device="cuda")
@@ -295,6 +298,36 @@ def test_interpolation_misaligned_and_out_of_domain(ds):
     assert np.all(np.isnan(y[~ok])) and np.all(~np.isnan(y[ok]))
     assert np.all(_interp_tol(y[ok], yr[ok], Y[Ir[ok]], Y[Ir[ok] + 1]))
     L.free()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_search_host_buffers(ds, pinned):
+    # the end-to-end call: queries, indices and interpolated values in host
+    # memory (page-locked used in place, pageable registered for the call),
+    # the same results as the device search
+    w = W.workload5(n_arrays=16, size_lo=1 << 10, size_hi=1 << 16, total_queries=1 << 20)
+    Xcat, Ycat, x_off, Zcat, z_off = w["Xcat"], w["Ycat"], w["x_off"], w["Zcat"], w["z_off"]
+    L = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off), cfg=_cfg(ds, steps=50))
+    yd = torch.empty(Zcat.size, dtype=torch.float32, device="cuda")
+    Id, _ = L.search(_cuda(Zcat), _cuda(z_off), y_out=yd)
+    Zh = torch.from_numpy(Zcat)
+    Ih = torch.full((Zcat.size,), -7, dtype=torch.int32)
+    yh = torch.full((Zcat.size,), -7.0, dtype=torch.float32)
+    if pinned:
+        Zh, Ih, yh = Zh.pin_memory(), Ih.pin_memory(), yh.pin_memory()
+    for _ in range(2):
+        ds.ds_learned_search_host(L, Zh, torch.from_numpy(z_off), out=Ih, y_out=yh)
+        assert torch.equal(Ih, Id.cpu())
+        assert torch.equal(yh, yd.cpu())
+    # index only, one array
+    w4 = _learned_small(n_knots=20_001, m=100_003)
+    L4 = ds.ds_learned_build(_cuda(w4["X"]), cfg=_cfg(ds, flags=ds.DS_LEARNED_FORCE))
+    I4 = ds.ds_learned_search_host(L4, torch.from_numpy(w4["Z"]))
+    assert np.array_equal(I4.numpy(), oracle.upper_bound(w4["X"], w4["Z"]))
+    with pytest.raises(ds.DsError):  # interpolation needs a handle that holds its values
+        ds.ds_learned_search_host(L4, torch.from_numpy(w4["Z"]), y_out=torch.empty(w4["Z"].size, dtype=torch.float64))
+    L.free()
+    L4.free()
 
 
 @pytest.mark.slow
