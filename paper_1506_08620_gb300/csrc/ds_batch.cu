@@ -308,7 +308,11 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
                 d.g_in_img = (uint32_t)std::min<size_t>(kb, 0xFFFFFFFFu);
                 d.xg = (long long)(off + kb + gb);
                 const size_t xb = round_up((size_t)nk * d.xs * sizeof(T), 16);
-                d.img_bytes = kb + gb <= 0xFFFFFFF0u ? (uint32_t)(kb + gb) : 0u;
+                // with the knot values stored, the fingerprints are not used (the
+                // interpolation reads the knot's pair anyway), so only the rank
+                // words are staged
+                const size_t ib = Ycat ? kb : kb + gb;
+                d.img_bytes = ib <= 0xFFFFFFF0u ? (uint32_t)ib : 0u;
                 off += kb + gb + xb;
                 kc[a + 1] = (nk + 31) / 32;
                 e->n_direct += 1;
@@ -335,7 +339,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
         }
         if (rc != DS_OK) break;
         // knot fingerprints of the rank tables: used unless turned off
-        e->fingerprints = !(flags & DS_NO_FINGERPRINT) && e->n_direct > 0;
+        e->fingerprints = !(flags & DS_NO_FINGERPRINT) && e->n_direct > 0 && !Ycat;
         for (int a = 0; a < A; ++a)
             if (e->desc_host[a].mode == MODE_DIRECT) e->desc_host[a].aux = e->fingerprints ? 1 : 0;
         // the one-conversion cell form: float, every direct array with R < 2^24 - 1

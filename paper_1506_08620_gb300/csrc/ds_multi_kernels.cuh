@@ -413,8 +413,16 @@ __device__ __forceinline__ void chunk_range(const BatchArgs<T> &a, const ArrDesc
 // chunk and stages its array's image for all of its warps.
 // MAXB: the largest block the kernel is compiled for (1024 only for the
 // direct kinds at one vector per thread, which fit 64 registers).
+// The mixed kind with the interpolation is held to 64 registers (two blocks
+// of 512 threads per SM): it waits on chains of dependent reads, and resident
+// warps hide them better than registers (workload 5: 64.7 -> 69.4 G lookups/s
+// against 78 registers).
+template <int KIND, bool INTERP, int MAXB> constexpr int min_blocks_of()
+{
+    return KIND == KIND_MIXED && INTERP && MAXB == 512 ? 2 : 1;
+}
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false, int MAXB = 512>
-__global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
+__global__ void __launch_bounds__(MAXB, min_blocks_of<KIND, INTERP, MAXB>()) k_batch_search(BatchArgs<T> a)
 {
     if constexpr (WARPS) {
         const int lane = threadIdx.x & 31;
