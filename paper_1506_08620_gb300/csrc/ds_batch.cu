@@ -685,17 +685,23 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
                 if (occupancy(e, t, y_out != nullptr, true, &grid) != DS_OK) continue;
                 rc = engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
                 if (rc != DS_OK) break;
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; ++r) engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = DS_E_CUDA;
-                    set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                    break;
+                // the best of three timings of two launches each (a single timing
+                // lets clock and power swings pick the configuration)
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3 && rc == DS_OK; ++rep) {
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 2; ++r) engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc = DS_E_CUDA;
+                        set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                        break;
+                    }
+                    float one = 0;
+                    cudaEventElapsedTime(&one, e0, e1);
+                    ms = std::min(ms, one / 2);
                 }
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= 3;
+                if (rc != DS_OK) break;
                 if (ms < best.ms) {
                     best = t;
                     best.ms = ms;
