@@ -540,7 +540,7 @@ static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, boo
     const int block = eff_block(e, t, vec);
     const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0, block == 1024);
     const int smem = std::max(0, t.smem_limit);
-    if (smem > 0) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (smem > 0) DS_TRY(allow_dynamic_smem(fn, smem));
     int occ = 0;
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, block, smem));
     if (occ < 1) {

@@ -366,6 +366,12 @@ struct DeviceProps {
     int l2_bytes = 0;
 };
 ds_status device_props(DeviceProps *p);
+// Raise a kernel's dynamic shared-memory limit to the most the device allows
+// it (the opt-in limit less its static shared memory).  The attribute belongs
+// to the kernel, shared by every handle and captured graph, so it is never
+// set to one launch's size: a later, smaller setting would make an earlier
+// handle's launch invalid.  Fails if need_bytes exceeds that limit.
+ds_status allow_dynamic_smem(const void *fn, int need_bytes);
 double now_ms();
 size_t table_budget_bytes();
 size_t round_up(size_t v, size_t a);

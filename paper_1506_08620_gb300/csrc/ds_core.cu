@@ -47,6 +47,22 @@ ds_status device_props(DeviceProps *p)
     return DS_OK;
 }
 
+ds_status allow_dynamic_smem(const void *fn, int need_bytes)
+{
+    int dev = 0, optin = 0;
+    DS_TRY_CUDA(cudaGetDevice(&dev));
+    DS_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    DS_TRY_CUDA(cudaFuncGetAttributes(&fa, fn));
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if (need_bytes > lim) {
+        set_error("kernel needs %d bytes of dynamic shared memory, the device allows %d", need_bytes, lim);
+        return DS_E_ARG;
+    }
+    DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    return DS_OK;
+}
+
 // ----------------------------------------------------------------- host pipeline
 constexpr int PIPE_BUFS = 3;
 
@@ -111,6 +127,8 @@ void free_index(ds_index *idx)
     if (idx->tab) cudaFree(idx->tab);
     if (idx->pairs) cudaFree(idx->pairs);
     if (idx->k16) cudaFree(idx->k16);
+    if (idx->cw_mask) cudaFree(idx->cw_mask);
+    if (idx->cw_base) cudaFree(idx->cw_base);
     if (idx->dev_err) cudaFree(idx->dev_err);
     idx->hdr.magic = 0;
     delete idx;
@@ -194,7 +212,8 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
     }
     *out = nullptr;
     if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H |
+                             DS_CLUSTER_TABLE))) {
         set_error("ds_build: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u)", X_dev, (long long)n_knots,
                   (int)dtype, flags);
         return DS_E_ARG;

@@ -386,8 +386,7 @@ static ds_status ls_build_typed(ds_lsearch *h, const T *X, cudaStream_t s)
     DS_TRY_CUDA(cudaStreamSynchronize(s));
     h->smem = !(h->flags & DS_NO_SMEM) && h->lay_bytes <= ls_smem_limit(h->props);
     const void *fn = ls_kernel<T>(h->method, true, h->smem);
-    if (h->smem)
-        DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lay_bytes));
+    if (h->smem) DS_TRY(allow_dynamic_smem(fn, (int)h->lay_bytes));
     int occ = 0;
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, LS_BLOCK, h->smem ? h->lay_bytes : 0));
     if (occ < 1) {

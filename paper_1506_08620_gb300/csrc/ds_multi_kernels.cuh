@@ -416,10 +416,13 @@ __device__ __forceinline__ void chunk_range(const BatchArgs<T> &a, const ArrDesc
 // The mixed kind with the interpolation is held to 64 registers (two blocks
 // of 512 threads per SM): it waits on chains of dependent reads, and resident
 // warps hide them better than registers (workload 5: 64.7 -> 69.4 G lookups/s
-// against 78 registers).
+// against 78 registers).  The other kinds give no minimum (0): an explicit 1
+// lets the compiler spend up to 128 registers, and the direct kind then took
+// 72 instead of 64, one 512-thread block per SM instead of two (workload 3:
+// 492 -> 430 G lookups/s).
 template <int KIND, bool INTERP, int MAXB> constexpr int min_blocks_of()
 {
-    return KIND == KIND_MIXED && INTERP && MAXB == 512 ? 2 : 1;
+    return KIND == KIND_MIXED && INTERP && MAXB == 512 ? 2 : 0;
 }
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false, int MAXB = 512>
 __global__ void __launch_bounds__(MAXB, min_blocks_of<KIND, INTERP, MAXB>()) k_batch_search(BatchArgs<T> a)

@@ -129,9 +129,7 @@ template <typename T>
 ds_status prepare_search(SearchPlan *plan, uint32_t smem_bytes, int num_sms)
 {
     const void *fn = pick_vec<T>(*plan);
-    if (plan->smem) {
-        DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes));
-    }
+    if (plan->smem) DS_TRY(allow_dynamic_smem(fn, (int)smem_bytes));
     int occ = 0;
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, plan->block, plan->smem ? smem_bytes : 0));
     if (occ < 1) {

@@ -230,7 +230,7 @@ static ds_status histogram_typed(const ds_index *idx, const void *Z, long long m
     const size_t hbytes = (size_t)nbins * sizeof(uint32_t);
     const bool smh = hbytes <= 96 * 1024;
     const void *fn = hist_pick<T>(idx->plan.form, idx->q >= 2, smh);
-    if (smh) DS_TRY_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hbytes));
+    if (smh) DS_TRY(allow_dynamic_smem(fn, (int)hbytes));
     int occ = 0;
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, smh ? hbytes : 0));
     long long blocks = std::max(1, occ) * (long long)idx->props.num_sms;
@@ -248,7 +248,7 @@ static ds_status merge_typed(const void *X, long long NX, const void *Z, long lo
     DS_TRY_CUDA(cudaGetDevice(&dev));
     DS_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t sbytes = 2 * (size_t)MP_TILE * sizeof(typename MergeKey<T>::K) + (size_t)MP_TILE * sizeof(int32_t);
-    DS_TRY_CUDA(cudaFuncSetAttribute(k_merge_search<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sbytes));
+    DS_TRY(allow_dynamic_smem((const void *)k_merge_search<T>, (int)sbytes));
     DS_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_merge_search<T>, MP_BLOCK, sbytes));
     const long long ntiles = (NX + M + MP_TILE - 1) / MP_TILE;
     const long long blocks = std::max(1ll, std::min(ntiles, (long long)std::max(occ, 1) * sms));
