@@ -48,8 +48,7 @@ def parse():
                    help="learned + interpolation workload: number of arrays (profiling runs; default 256)")
     p.add_argument("--no-per-config", action="store_true",
                    help="skip the per-configuration figures of workloads 1-4 (default run only)")
-    p.add_argument("--variant", default="plain",
-                   choices=["plain", "fma", "cache", "fma_cache", "gap2", "fma_gap2", "cluster"])
+    p.add_argument("--variant", default="plain", choices=["plain", "fma", "cache", "fma_cache", "gap2", "fma_gap2"])
     p.add_argument("--no-extras", action="store_true", help="skip the secondary measurements")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU time of the oracle baseline")
     p.add_argument("--queries", type=int, default=0, help="override the query count (profiling runs)")
@@ -367,8 +366,6 @@ def setup_direct(args, ds, W, torch, dev, rank):
     job = Job()
     variants = {"plain": 0, "fma": ds.DS_FMA, "cache": ds.DS_CACHE_LAYOUT,
                 "fma_cache": ds.DS_FMA | ds.DS_CACHE_LAYOUT, "gap2": ds.DS_GAP2, "fma_gap2": ds.DS_FMA | ds.DS_GAP2}
-    if args.workload.startswith("direct_f64"):
-        variants["cluster"] = ds.DS_CLUSTER_TABLE
     flags = variants[args.variant]
     if args.workload in ("direct_f64", "direct_f64_sorted"):
         w = W.workload2(seed=rank_seed(W, 2, rank), m=args.queries or (1 << 27),

@@ -80,15 +80,9 @@ enum {
     DS_NO_FINGERPRINT = 64u, /* batched builds: the 8-bit knot fingerprints are not used, so every
                              query in a cell holding a knot reads the knot (the paper's correcting
                              comparison, always made) */
-    DS_REFINE_H = 128u,   /* single-array builds: when ComputeHR had to grow H, bisect the interval
+    DS_REFINE_H = 128u    /* single-array builds: when ComputeHR had to grow H, bisect the interval
                              between the last infeasible H and the final one for a smaller feasible
                              H (end of Section 4.4; every probe checks the whole array) */
-    DS_CLUSTER_TABLE = 256u /* ds_build, float64 Direct (no cache layout, not DS_GAP2): also keep K as
-                             rank words (one per 64 cells: K at the first cell and a 64-bit mask of the
-                             cells holding a knot, 12 bytes), which searches with 16- and 8-byte
-                             aligned buffers hold in the shared memory of 16-CTA thread-block clusters
-                             (192 KB per CTA) and read with distributed shared-memory loads; at most
-                             2^26 cells (DS_E_TABLE_TOO_LARGE otherwise) */
 };
 
 typedef struct ds_index ds_index;     /* one knot array with its direct-search table */

@@ -14,7 +14,7 @@ from . import _abi
 from ._abi import (DS_CACHE_LAYOUT, DS_CHECKED, DS_F32, DS_F64, DS_FMA, DS_LEARNED_FORCE,  # noqa: F401
                    DS_GAP2, DS_LEARNED_LINEAR, DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_EYTZINGER,
                    DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_NAMES, DS_LS_OFFSET, DS_NO_FINGERPRINT, DS_NO_SMEM, DS_OK,
-                   DS_REFINE_H, DS_STRICT, DS_CLUSTER_TABLE, DsError, check, lib)
+                   DS_REFINE_H, DS_STRICT, DsError, check, lib)
 
 __all__ = [
     "ds_build", "ds_search", "ds_search_host", "ds_index_export", "ds_batch_build", "ds_batch_search",

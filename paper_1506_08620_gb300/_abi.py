@@ -33,7 +33,6 @@ DS_STRICT = 16
 DS_GAP2 = 32
 DS_NO_FINGERPRINT = 64
 DS_REFINE_H = 128
-DS_CLUSTER_TABLE = 256
 DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_OFFSET, DS_LS_EYTZINGER = range(6)
 DS_LS_NAMES = ("classic", "classicmod", "leadbit", "leadbit_nopad", "offset", "eytzinger")
 

@@ -266,13 +266,6 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
         }
     }
     DS_TRY(prepare_search<T>(&plan, idx->smem_bytes, props.num_sms));
-    if (flags & DS_CLUSTER_TABLE) {
-        if (sizeof(T) != 8 || cache || gen || !plan.intops) {
-            set_error("ds_build: DS_CLUSTER_TABLE serves float64 Direct tables (no cache layout, q = 1)");
-            return DS_E_ARG;
-        }
-        DS_TRY(build_cluster_words(idx, s));
-    }
     return DS_OK;
 }
 
@@ -418,7 +411,6 @@ ds_status search_index(const ds_index *idx, const void *Z, long long m, int32_t 
         set_error("ds_search: null pointer or negative size");
         return DS_E_ARG;
     }
-    if (idx->cw_mask && (uintptr_t)Z % 16 == 0 && (uintptr_t)I % 8 == 0) return search_cluster(idx, Z, m, I, s);
     return idx->dtype == DS_F32 ? search_typed<float>(idx, Z, m, I, s) : search_typed<double>(idx, Z, m, I, s);
 }
 

@@ -127,8 +127,6 @@ void free_index(ds_index *idx)
     if (idx->tab) cudaFree(idx->tab);
     if (idx->pairs) cudaFree(idx->pairs);
     if (idx->k16) cudaFree(idx->k16);
-    if (idx->cw_mask) cudaFree(idx->cw_mask);
-    if (idx->cw_base) cudaFree(idx->cw_base);
     if (idx->dev_err) cudaFree(idx->dev_err);
     idx->hdr.magic = 0;
     delete idx;
@@ -212,8 +210,7 @@ ds_status ds_build(const void *X_dev, int64_t n_knots, ds_dtype dtype, uint32_t 
     }
     *out = nullptr;
     if (!X_dev || n_knots < 2 || (dtype != DS_F32 && dtype != DS_F64) ||
-        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H |
-                             DS_CLUSTER_TABLE))) {
+        (flags & ~(uint32_t)(DS_FMA | DS_CACHE_LAYOUT | DS_CHECKED | DS_NO_SMEM | DS_GAP2 | DS_REFINE_H))) {
         set_error("ds_build: bad argument (X=%p, n_knots=%lld, dtype=%d, flags=%u)", X_dev, (long long)n_knots,
                   (int)dtype, flags);
         return DS_E_ARG;

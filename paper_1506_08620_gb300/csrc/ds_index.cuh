@@ -30,18 +30,9 @@ struct ds_index {
     int *dev_err;
     ds::DeviceProps props;
     ds::HostPipe *pipe;
-    // DS_CLUSTER_TABLE: rank words (64 cells each) held in a cluster's shared memory
-    unsigned long long *cw_mask;
-    uint32_t *cw_base;
-    uint32_t cw_words;
 };
 
 namespace ds {
-
-// DS_CLUSTER_TABLE (ds_cluster.cu): build the rank words of a float64 Direct
-// table, and search with them held in a thread-block cluster's shared memory.
-ds_status build_cluster_words(ds_index *idx, cudaStream_t s);
-ds_status search_cluster(const ds_index *idx, const void *Z, long long m, int32_t *I, cudaStream_t s);
 
 // ---------------------------------------------------------------- kernels
 // gap: pair distance of the separation property (1 Direct, 2 DirectGap2).

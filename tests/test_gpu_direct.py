@@ -307,51 +307,6 @@ def test_array_of_2p28_knots(ds):
     idx.free()
 
 
-@pytest.mark.parametrize("flags", [256, 257], ids=["cluster", "cluster_fma"])
-def test_cluster_table_matches_definition(ds, flags):
-    # the rank words held in 16-CTA clusters' shared memory (float64 Direct):
-    # every array of the suite with adversarial queries, odd and ragged counts,
-    # and a misaligned buffer (served by the ordinary kernel)
-    g = np.random.default_rng(31)
-    for name, X in _arrays(np.float64):
-        Z = _queries(X, g)
-        idx = ds.ds_build(_cuda(X), flags)
-        Zd = _cuda(Z)
-        for m in (Z.size, Z.size - 1, 1, 2, 5):
-            got = ds.ds_search(idx, Zd[:m]).cpu().numpy()
-            assert np.array_equal(got, oracle.upper_bound(X, Z[:m])), (name, m)
-        got = ds.ds_search(idx, Zd[1:]).cpu().numpy()  # 8-byte aligned only
-        assert np.array_equal(got, oracle.upper_bound(X, Z[1:])), name
-        idx.free()
-
-
-def test_cluster_table_workload2_and_limits(ds):
-    w = W.workload2(m=1 << 24)
-    X, Z = w["X"], w["Z"]
-    Xd, Zd = _cuda(X), _cuda(Z)
-    idx = ds.ds_build(Xd, 256)
-    ref_idx = ds.ds_build(Xd)
-    got = ds.ds_search(idx, Zd)
-    assert torch.equal(got, ds.ds_search(ref_idx, Zd))
-    g = np.random.default_rng(12)
-    pos = g.integers(0, Z.size, 1 << 18)
-    assert np.array_equal(got[_cuda(pos)].cpu().numpy(), oracle.upper_bound(X, Z[pos]))
-    gl = got.long()
-    assert bool((Xd[gl] <= Zd).all()) and bool((Zd < Xd[gl + 1]).all())
-    idx.free()
-    ref_idx.free()
-    # float32, the cache layout and DirectGap2 are refused; a table past 2^26 cells too
-    with pytest.raises(ds.DsError):
-        ds.ds_build(_cuda(X.astype(np.float32)), 256)
-    with pytest.raises(ds.DsError):
-        ds.ds_build(Xd, 256 | 2)
-    with pytest.raises(ds.DsError):
-        ds.ds_build(Xd, 256 | 32)
-    big = W.knots_from_gaps(0.0, np.concatenate([[1e-5], np.ones(1 << 10)]), np.float64)  # R ~ 1e8 cells
-    with pytest.raises(ds.DsError):
-        ds.ds_build(_cuda(big), 256)
-
-
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_indices_with_different_staged_tables(ds, dtype):
     # tables staged in shared memory share one kernel: a later index with a
