@@ -363,15 +363,14 @@ DS_API ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev
                            ds_learned **out);
 
 /* The same build with the knot values Y of the interpolation (Ycat_dev: same
- * dtype and CSR layout as Xcat_dev, copied): the handle stores, for every
- * knot i, the interval (X_i, Y_i, X_{i+1}, Y_{i+1}) (the last one
- * (X_N, Y_N, X_N, Y_N)), 16 bytes for float32, 32 for float64, so that a
- * lookup's four operands are one aligned vector: the paper's DirectCache idea
- * (Section 4.8, keeping what one lookup reads together) carried to the
- * interpolation.  A lookup reads the interval below its cell's first knot
- * and, when the cell holds a knot, the next one; these also make the
- * correcting comparison.  Searches interpolate from them (ds_learned_search
- * with Ycat_dev = NULL).  Synchronous. */
+ * dtype and CSR layout as Xcat_dev, copied): the handle stores every knot
+ * with its value as an (X_i, Y_i) pair, so that a lookup's four operands
+ * X_i, Y_i, X_{i+1}, Y_{i+1} lie in 16 contiguous bytes (float32; 32 for
+ * float64): the paper's DirectCache idea (Section 4.8, keeping what one
+ * lookup reads together) carried to the interpolation.  Searches interpolate
+ * from them (ds_learned_search with Ycat_dev = NULL); the direct arrays of
+ * such a handle compare with the knot itself instead of its fingerprint, as
+ * the interpolation reads the knot's pair anyway.  Synchronous. */
 DS_API ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const int64_t *x_off_dev,
                                      int32_t n_arrays, int64_t n_knots_if_single, ds_dtype dtype,
                                      const ds_learned_cfg *cfg, void *stream, ds_learned **out);

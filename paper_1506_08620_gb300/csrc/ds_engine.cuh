@@ -34,7 +34,7 @@ struct Engine {
     int *dev_err = nullptr;
     unsigned char *ctab = nullptr;  // learned arrays' cell tables
     size_t ctab_bytes = 0;
-    bool xy = false;                // knots stored as intervals (X_i, Y_i, X_{i+1}, Y_{i+1})
+    bool xy = false;                // knots stored as (X_i, Y_i) pairs
     ds_tune_t tune = {};
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
