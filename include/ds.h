@@ -347,7 +347,9 @@ typedef struct ds_learned_cfg {
     uint32_t flags;      /* DS_LEARNED_* */
     int32_t max_cells_per_knot; /* direct search only where (R+1) <= this x (N+1) (its table stays small);
                                    other feasible arrays use the learned map; <= 0: no limit */
-    float cells_per_knot;       /* cells C of a learned map per knot (0 = the default, 1); C <= 2^32 - 2 */
+    float cells_per_knot;       /* cells C of a learned map per knot; 0 (the default): 1, or 2 for a
+                                   handle that holds the knot values (ds_learned_build_xy with Y);
+                                   C <= 2^32 - 2 */
     int32_t reserved[3];
 } ds_learned_cfg;
 

@@ -49,7 +49,7 @@ constexpr int PLAN_ROUNDS = 8;
 
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
                               const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
-                              unsigned long long *counter)
+                              unsigned long long *counter, int split)
 {
     // chunks of the array at claim position p
     auto chunks_at = [&](int p) -> long long {
@@ -87,9 +87,11 @@ __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_
             carry += total;
         }
     }
+    __syncthreads();  // every chunk_off[p] written
     if (threadIdx.x == 0) {
         chunk_off[n_arrays > 0 ? n_arrays : 0] = carry;
-        *counter = 0;
+        counter[0] = 0;
+        counter[1] = split > 0 && split < n_arrays ? (unsigned long long)chunk_off[split] : 0ull;
     }
 }
 
@@ -346,6 +348,21 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
         e->fast_cells = sizeof(T) == 4 && e->n_direct > 0;
         for (int a = 0; a < A; ++a)
             if (e->desc_host[a].mode == MODE_DIRECT && e->desc_host[a].R > FASTF_MAX_R) e->fast_cells = false;
+        // direct and learned arrays (and no bisected ones): each group gets its
+        // own launch of a kernel kind that holds only its path (fewer registers
+        // than the mixed kind), the direct arrays first in the claim order
+        if (e->n_direct > 0 && e->n_learned > 0 && e->n_fallback == 0) {
+            e->order_host.resize((size_t)A);
+            for (int a = 0; a < A; ++a) e->order_host[(size_t)a] = a;
+            std::stable_sort(e->order_host.begin(), e->order_host.end(), [&](int p, int q) {
+                const bool dp = e->desc_host[(size_t)p].mode == MODE_DIRECT;
+                const bool dq = e->desc_host[(size_t)q].mode == MODE_DIRECT;
+                if (dp != dq) return dp;
+                return x_off[p + 1] - x_off[p] > x_off[q + 1] - x_off[q];
+            });
+            e->split = e->n_direct;
+            cudaMemcpyAsync(e->order, e->order_host.data(), sizeof(int) * (size_t)A, cudaMemcpyHostToDevice, s);
+        }
         // knots X_0, X_N per array (for the descriptors)
         {
             std::vector<T> ends(2 * (size_t)A);
@@ -476,7 +493,7 @@ ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long
 template <typename T, int VPT, bool INTERP, int KIND>
 static const void *pick4(bool vec, bool warps, bool big)
 {
-    if constexpr (VPT == 1 && direct_kind(KIND))
+    if constexpr (VPT == 1 && direct_kind(KIND) && KIND != KIND_DIRECT_XY)
         if (vec && !warps && big) return (const void *)k_batch_search<T, 1, INTERP, true, KIND, false, 1024>;
     if (vec && warps) return (const void *)k_batch_search<T, VPT, INTERP, true, KIND, true>;
     return vec ? (const void *)k_batch_search<T, VPT, INTERP, true, KIND>
@@ -492,7 +509,7 @@ static const void *pick3(bool vec, bool warps, bool big, int kind)
         if constexpr (sizeof(T) == 4) return pick4<T, VPT, INTERP, KIND_DIRECT_FPF>(vec, warps, big);
         else return pick4<T, VPT, INTERP, KIND_DIRECT_FP>(vec, warps, big);
     case KIND_LEARNED_ONLY: return pick4<T, VPT, INTERP, KIND_LEARNED_ONLY>(vec, warps, big);
-    case KIND_MIXED: return pick4<T, VPT, INTERP, KIND_MIXED>(vec, warps, big);
+    case KIND_DIRECT_XY: return pick4<T, VPT, INTERP, KIND_DIRECT_XY>(vec, warps, big);
     default: return pick4<T, VPT, INTERP, KIND_ALL>(vec, warps, big);
     }
 }
@@ -513,12 +530,21 @@ static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, i
 // every array in direct mode, searched on its rank table with the knots alone
 // (the direct kinds read knot t at X[t]; pairs take the mixed kind)
 static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0 && !e->xy; }
-static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big)
+// the direct kind for a handle's direct arrays
+static int direct_kind_of(const Engine *e)
 {
-    const int kind = !direct_only(e) ? (e->n_fallback > 0 ? KIND_ALL : e->n_direct == 0 ? KIND_LEARNED_ONLY : KIND_MIXED)
-                     : !e->fingerprints ? KIND_DIRECT
-                     : e->fast_cells    ? KIND_DIRECT_FPF
-                                        : KIND_DIRECT_FP;
+    return e->xy ? KIND_DIRECT_XY : !e->fingerprints ? KIND_DIRECT : e->fast_cells ? KIND_DIRECT_FPF : KIND_DIRECT_FP;
+}
+// group: 0 for the launch over every array (or, on a split handle, over its
+// direct arrays), 1 for a split handle's learned arrays
+static const void *pick_kernel(const Engine *e, int vpt, bool interp, bool vec, bool warps, bool big, int group = 0)
+{
+    // (without a split, a handle with learned arrays and no bisected ones has
+    // no direct arrays either)
+    const int kind = e->split > 0 ? (group == 0 ? direct_kind_of(e) : KIND_LEARNED_ONLY)
+                     : e->n_fallback > 0 ? KIND_ALL
+                     : e->n_learned == 0 ? direct_kind_of(e)
+                                         : KIND_LEARNED_ONLY;
     return e->dtype == DS_F32 ? pick1<float>(vpt, interp, vec, warps, big, kind)
                               : pick1<double>(vpt, interp, vec, warps, big, kind);
 }
@@ -534,11 +560,12 @@ static int eff_block(const Engine *e, const ds_tune_t &t, bool vec)
     return t.block == 128 || t.block == 512 ? t.block : 256;
 }
 
-// Resident blocks for a configuration (and the shared-memory opt-in).
-static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid)
+// Resident blocks for a configuration (and the shared-memory opt-in), for
+// the launch of one group (pick_kernel).
+static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, bool vec, int *grid, int group = 0)
 {
     const int block = eff_block(e, t, vec);
-    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0, block == 1024);
+    const void *fn = pick_kernel(e, clamp_vpt(t.items), interp, vec, t.smem_limit < 0, block == 1024, group);
     const int smem = std::max(0, t.smem_limit);
     if (smem > 0) DS_TRY(allow_dynamic_smem(fn, smem));
     int occ = 0;
@@ -552,6 +579,26 @@ static ds_status occupancy(const Engine *e, const ds_tune_t &t, bool interp, boo
     return DS_OK;
 }
 
+// One search kernel over the claim positions [0, n_pos) whose chunks are
+// counted from *counter (the planner has set it).
+template <typename T>
+static ds_status launch_search(const Engine *e, const void *fn, int grid, int block, uint32_t smem_limit,
+                               long long chunk, int n_pos, unsigned long long *counter, const void *Z,
+                               const long long *z_off, long long m_single, const void *Y, void *y_out, int32_t *I,
+                               cudaStream_t s, bool host_io)
+{
+    BatchArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = n_pos;
+    a.Z = (const T *)Z; a.I = I; a.Y = (const T *)Y; a.y_out = (T *)y_out;
+    a.order = e->order; a.chunk_off = e->chunk_off; a.counter = counter;
+    a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
+    a.err = e->dev_err; a.ctab = e->ctab; a.l2pf = host_io ? 0 : 1;
+    void *args[] = {&a};
+    DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)smem_limit, s));
+    return DS_OK;
+}
+
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
                                long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s,
                                bool host_io)
@@ -560,37 +607,27 @@ ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *
     const int L = e->dtype == DS_F32 ? 4 : 2;
     const bool vec = ((uintptr_t)Z % 16 == 0) && ((uintptr_t)I % (L * 4) == 0) &&
                      (!interp || (uintptr_t)y_out % 16 == 0);
-    int grid = 0;
-    DS_TRY(occupancy(e, t, interp, vec, &grid));
+    const int n_launch = e->split > 0 ? 2 : 1;
+    int grid[2] = {0, 0};
+    for (int g = 0; g < n_launch; ++g) DS_TRY(occupancy(e, t, interp, vec, &grid[g], g));
     const int block = eff_block(e, t, vec), vpt = clamp_vpt(t.items);
     const bool warps = vec && t.smem_limit < 0;  // nothing staged, and warps claim their own chunks
     const int tiles = warps ? CHUNK_TILES_WARP : direct_only(e) ? CHUNK_TILES_DIRECT : CHUNK_TILES;
     const long long chunk = (long long)(warps ? 32 : block) * vpt * L * tiles;
     const uint32_t smem_limit = (uint32_t)std::max(0, t.smem_limit);
     k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->desc_dev, e->order, smem_limit,
-                                     e->chunk_off, e->counter);
+                                     e->chunk_off, e->counter, e->split);
     DS_TRY_CUDA(cudaGetLastError());
-    const void *fn = pick_kernel(e, vpt, interp, vec, warps, block == 1024);
-    if (e->dtype == DS_F32) {
-        BatchArgs<float> a;
-        memset(&a, 0, sizeof(a));
-        a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
-        a.Z = (const float *)Z; a.I = I; a.Y = (const float *)Y; a.y_out = (float *)y_out;
-        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter;
-        a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
-        a.err = e->dev_err; a.ctab = e->ctab; a.l2pf = host_io ? 0 : 1;
-        void *args[] = {&a};
-        DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
-    } else {
-        BatchArgs<double> a;
-        memset(&a, 0, sizeof(a));
-        a.desc = e->desc_dev; a.blob = e->blob; a.z_off = z_off; a.m_single = m_single; a.n_arrays = e->n_arrays;
-        a.Z = (const double *)Z; a.I = I; a.Y = (const double *)Y; a.y_out = (double *)y_out;
-        a.order = e->order; a.chunk_off = e->chunk_off; a.counter = e->counter;
-        a.chunk = chunk; a.smem_limit = smem_limit; a.checked = (e->flags & DS_CHECKED) != 0;
-        a.err = e->dev_err; a.ctab = e->ctab; a.l2pf = host_io ? 0 : 1;
-        void *args[] = {&a};
-        DS_TRY_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, (size_t)a.smem_limit, s));
+    for (int g = 0; g < n_launch; ++g) {
+        // split handle: the direct arrays' positions [0, split), then the learned ones
+        const int n_pos = n_launch == 2 && g == 0 ? e->split : e->n_arrays;
+        const void *fn = pick_kernel(e, vpt, interp, vec, warps, block == 1024, g);
+        unsigned long long *counter = e->counter + g;
+        DS_TRY(e->dtype == DS_F32
+                   ? launch_search<float>(e, fn, grid[g], block, smem_limit, chunk, n_pos, counter, Z, z_off, m_single,
+                                          Y, y_out, I, s, host_io)
+                   : launch_search<double>(e, fn, grid[g], block, smem_limit, chunk, n_pos, counter, Z, z_off,
+                                           m_single, Y, y_out, I, s, host_io));
     }
     return DS_OK;
 }
@@ -653,7 +690,7 @@ ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg)
     t.block = t.block == 128 || t.block == 512 || t.block == 1024 ? t.block : 256;
     t.items = t.items == 1 || t.items == 2 ? t.items : 4;
     int grid = 0;
-    DS_TRY(occupancy(e, t, false, true, &grid));
+    for (int g = 0; g < (e->split > 0 ? 2 : 1); ++g) DS_TRY(occupancy(e, t, false, true, &grid, g));
     e->tune = t;
     return DS_OK;
 }
@@ -683,6 +720,7 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
                 t.smem_limit = sm;
                 int grid = 0;
                 if (occupancy(e, t, y_out != nullptr, true, &grid) != DS_OK) continue;
+                if (e->split > 0 && occupancy(e, t, y_out != nullptr, true, &grid, 1) != DS_OK) continue;
                 rc = engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
                 if (rc != DS_OK) break;
                 // the best of three timings of two launches each (a single timing

@@ -29,7 +29,9 @@ struct Engine {
     size_t blob_bytes = 0;
     size_t table_bytes = 0;
     long long *chunk_off = nullptr;
-    int *order = nullptr;  // claim order of the arrays: most knots first
+    int *order = nullptr;  // claim order of the arrays: most knots first (within each launch's group)
+    std::vector<int> order_host;  // its host copy (read by an asynchronous upload)
+    int split = 0;  // > 0: direct arrays at claim positions [0, split), learned ones after, one launch each
     unsigned long long *counter = nullptr;  // [0] chunk counter
     int *dev_err = nullptr;
     unsigned char *ctab = nullptr;  // learned arrays' cell tables

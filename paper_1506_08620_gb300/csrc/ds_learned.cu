@@ -954,7 +954,11 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
         }
         // the cell maps: C cells per array, the served prediction sampled at G
         // points (the network's, and the linear model's), each made monotone
-        const double cpk = cfg.cells_per_knot > 0.f ? (double)cfg.cells_per_knot : 1.0;
+        // default: one cell per knot, two where the handle holds the knot values
+        // (every lookup then goes on to its answer's pairs, and an empty cell
+        // answers without reading a knot: with two cells per knot about 61% of
+        // uniform queries land in empty cells, against 37%)
+        const double cpk = cfg.cells_per_knot > 0.f ? (double)cfg.cells_per_knot : e.xy ? 2.0 : 1.0;
         std::vector<std::vector<uint2>> net_maps(nm), lin_maps(nm);
         std::vector<long long> kbase(nm + 1, 0);
         L->cells.assign(nm, 0);
@@ -1095,7 +1099,7 @@ void ds_learned_cfg_default(ds_learned_cfg *cfg)
     cfg->seed = 1506086200ull;
     cfg->flags = 0;
     cfg->max_cells_per_knot = 16;
-    cfg->cells_per_knot = 1.0f;
+    cfg->cells_per_knot = 0.0f;
 }
 
 ds_status ds_learned_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t n_arrays, int64_t n_knots_if_single,

@@ -114,15 +114,16 @@ template <bool SM> __device__ __forceinline__ uint32_t tab_ld(const uint8_t *p, 
 // direct arrays only, without or with fingerprints (the other paths compiled
 // out, which keeps the register count low), or with fingerprints and the
 // one-conversion cell form (float arrays, every R < 2^24 - 1), or learned
-// arrays only.
-// KIND_MIXED: direct and learned arrays, no bisected ones (the learned
-// handles), knots alone or as (X, Y) pairs.
+// arrays only, or direct arrays whose knots are stored as (X, Y) pairs,
+// without fingerprints (KIND_DIRECT_XY: the direct arrays of a learned handle
+// that holds its values).  A handle with direct and learned arrays serves
+// each group with its own launch and kind.
 enum BatchKind : int {
-    KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3, KIND_LEARNED_ONLY = 4, KIND_MIXED = 5
+    KIND_ALL = 0, KIND_DIRECT = 1, KIND_DIRECT_FP = 2, KIND_DIRECT_FPF = 3, KIND_LEARNED_ONLY = 4, KIND_DIRECT_XY = 5
 };
 __host__ __device__ constexpr bool direct_kind(int k)
 {
-    return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF;
+    return k == KIND_DIRECT || k == KIND_DIRECT_FP || k == KIND_DIRECT_FPF || k == KIND_DIRECT_XY;
 }
 
 // Learned form: j = f(z) on the learned cell map, (t0, t1) = (K_j, K_{j+1}).
@@ -181,12 +182,12 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
                                              const unsigned char *img, const T *X, const T *z, int32_t *r,
                                              uint64_t pol)
 {
-    if (direct_kind(KIND) || ((KIND == KIND_ALL || KIND == KIND_MIXED) && d.mode == MODE_DIRECT)) {
+    if (direct_kind(KIND) || (KIND == KIND_ALL && d.mode == MODE_DIRECT)) {
         // one rank word per query; for a cell holding a knot, the knot's
         // fingerprint; the knot X_t itself only when the two fingerprints are
         // equal (otherwise they order z and X_t: within a cell the fingerprint
         // is a non-decreasing function of f, Eq. fprop)
-        const bool fp = KIND == KIND_DIRECT_FP || KIND == KIND_DIRECT_FPF || ((KIND == KIND_ALL || KIND == KIND_MIXED) && d.aux);
+        const bool fp = KIND == KIND_DIRECT_FP || KIND == KIND_DIRECT_FPF || (KIND == KIND_ALL && d.aux);
         const uint2 *Rt = reinterpret_cast<const uint2 *>(img);
         const uint8_t *Gt = img + d.g_in_img;
         uint32_t g[NQ], j[NQ];
@@ -207,7 +208,9 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const bool need = h[q].knot && (!fp || g[q] == kf[q]);
-            const size_t xi = direct_kind(KIND) ? (size_t)h[q].t : (size_t)h[q].t * d.xs;
+            const size_t xi = KIND == KIND_DIRECT_XY ? (size_t)h[q].t * 2u
+                              : direct_kind(KIND)        ? (size_t)h[q].t
+                                                         : (size_t)h[q].t * d.xs;
             x[q] = need ? tab_ld<false>(X + xi, pol) : T(0);
         }
 #pragma unroll
@@ -219,7 +222,7 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         }
         return;
     }
-    if (KIND == KIND_LEARNED_ONLY || KIND == KIND_MIXED || d.mode == MODE_LEARNED) {  // learned arrays
+    if (KIND == KIND_LEARNED_ONLY || d.mode == MODE_LEARNED) {  // learned arrays
         learned_answer<T, NQ, SM>(a, d, img, X, z, r);
         return;
     }
@@ -407,25 +410,22 @@ __device__ __forceinline__ void chunk_range(const BatchArgs<T> &a, const ArrDesc
     *ze = *zs + len < zend ? *zs + len : zend;
 }
 
-// KIND: BatchKind (KIND_DIRECT*: every array of the handle is in direct mode).
+// KIND: BatchKind (KIND_DIRECT*: every array the launch serves is in direct
+// mode; a handle with direct and learned arrays may serve each group with
+// its own launch).
 // WARPS: no table is staged (a.smem_limit == 0) and every warp claims its own
 // chunks, so no block-wide barrier is needed; otherwise the block claims a
 // chunk and stages its array's image for all of its warps.
 // MAXB: the largest block the kernel is compiled for (1024 only for the
-// direct kinds at one vector per thread, which fit 64 registers).
-// The mixed kind with the interpolation is held to 64 registers (two blocks
-// of 512 threads per SM): it waits on chains of dependent reads, and resident
-// warps hide them better than registers (workload 5: 64.7 -> 69.4 G lookups/s
-// against 78 registers).  The other kinds give no minimum (0): an explicit 1
-// lets the compiler spend up to 128 registers, and the direct kind then took
-// 72 instead of 64, one 512-thread block per SM instead of two (workload 3:
-// 492 -> 430 G lookups/s).
-template <int KIND, bool INTERP, int MAXB> constexpr int min_blocks_of()
-{
-    return KIND == KIND_MIXED && INTERP && MAXB == 512 ? 2 : 0;
-}
+// direct kinds at one vector per thread, which fit 64 registers).  No kind
+// gives a minimum of resident blocks: an explicit 1 lets the compiler spend
+// up to 128 registers (the direct kind then took 72 instead of 64, one
+// 512-thread block per SM instead of two; workload 3: 492 -> 430 G
+// lookups/s), and a minimum of 2 at 512 threads (64 registers, with spills)
+// measured no better for the kinds of workload 5 (79.1 without it, 77.8 with
+// it on the learned kind, 77.9 on the direct kind over pairs).
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false, int MAXB = 512>
-__global__ void __launch_bounds__(MAXB, min_blocks_of<KIND, INTERP, MAXB>()) k_batch_search(BatchArgs<T> a)
+__global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
 {
     if constexpr (WARPS) {
         const int lane = threadIdx.x & 31;

@@ -125,6 +125,30 @@ def test_learned_single_array_is_exact(ds):
     L.free()
 
 
+def test_default_cells_per_knot(ds):
+    # the default map has one cell per knot, two on a handle that holds the
+    # knot values (ds_learned_build_xy with Y); an explicit value is kept
+    g = np.random.default_rng(33)
+    X = W.knots_from_gaps(0.0, g.lognormal(0, 1, 3000), np.float32)
+    Y = g.standard_normal(X.size).astype(np.float32)
+    Z = W.uniform_queries(g, X[0], X[-1], 20_000, np.float32)
+    Ir, yr = oracle.interp(X, Y, Z)
+    for with_y, cpk, want in ((False, 0.0, X.size), (True, 0.0, 2 * X.size), (True, 1.0, X.size)):
+        cfg = _cfg(ds, steps=100, flags=ds.DS_LEARNED_FORCE, cells_per_knot=cpk)
+        L = (ds.ds_learned_build_xy(_cuda(X), _cuda(Y), cfg=cfg) if with_y
+             else ds.ds_learned_build(_cuda(X), cfg=cfg))
+        c, _ = _check_cells(ds, L, 0, X.size)
+        assert c["cells"] == want
+        if with_y:
+            I, y = L.search(_cuda(Z), y_out=torch.empty(Z.size, dtype=torch.float32, device="cuda"))
+            I, y = I.cpu().numpy(), y.cpu().numpy()
+            ok = (Ir >= 0) & (Ir < X.size - 1)
+            assert np.array_equal(I, Ir) and np.all(_interp_tol(y[ok], yr[ok], Y[Ir[ok]], Y[Ir[ok] + 1]))
+        else:
+            assert np.array_equal(L.search(_cuda(Z)).cpu().numpy(), oracle.upper_bound(X, Z))
+        L.free()
+
+
 @pytest.mark.parametrize("cpk,linear,steps", [(1.0, True, 300), (0.01, False, 0), (0.0004, True, 0), (4.0, False, 300)])
 def test_every_cell_map_is_exact(ds, cpk, linear, steps):
     # any non-decreasing map gives exact answers: the linear map, the untrained
