@@ -99,7 +99,7 @@ def traffic_for(kernel_key):
     e = d.get(kernel_key)
     if not e or e.get("source_hash") != source_hash(kernel_key):
         return None
-    return e.get("bytes_per_launch")
+    return e.get("bytes_per_search", e.get("bytes_per_launch"))
 
 
 def kernel_key_of(args):
@@ -111,12 +111,14 @@ def kernel_key_of(args):
 
 
 def record_traffic(args):
-    """Per-launch DRAM traffic of the timed kernel from an ncu CSV (--metrics
-    dram__bytes_read.sum,dram__bytes_write.sum of a run with --queries Q),
-    scaled to the full workload by the query count, into profiles/traffic.json."""
+    """DRAM traffic per search call from an ncu CSV (--metrics
+    dram__bytes_read.sum,dram__bytes_write.sum of a run with --queries Q over
+    whole search calls: the chunk planner and one or two search kernels for the
+    batched and learned forms, one kernel otherwise), scaled to the full
+    workload by the query count, into profiles/traffic.json."""
     import csv
     scale_unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
-    per_launch = {}
+    per_launch, names = {}, {}
     with open(args.record_traffic) as f:
         lines = [l for l in f if l.startswith('"')]
     for row in csv.DictReader(lines):
@@ -124,14 +126,23 @@ def record_traffic(args):
             continue
         v = float(row["Metric Value"].replace(",", "")) * scale_unit.get(row.get("Metric Unit", "byte"), 1)
         per_launch[row["ID"]] = per_launch.get(row["ID"], 0.0) + v
+        names[row["ID"]] = row.get("Kernel Name", "")
     if not per_launch or not args.queries:
         raise SystemExit("record-traffic: no dram__bytes rows in %s, or --queries not given" % args.record_traffic)
-    captured = float(np.mean(list(per_launch.values())))
+    # one planner launch per search call where there is a planner; else one launch per call
+    calls = sum(1 for n in names.values() if n.startswith("k_plan_chunks")) or len(per_launch)
+    captured = sum(per_launch.values()) / calls
+    by_kernel = {}
+    for i, n in names.items():
+        short = n.split("(")[0]
+        by_kernel[short] = by_kernel.get(short, 0.0) + per_launch[i] / calls
     full = workload_config(argparse.Namespace(**{**vars(args), "queries": 0}))["queries"]
     key = kernel_key_of(args)
     d = json.load(open(TRAFFIC_PATH)) if os.path.exists(TRAFFIC_PATH) else {}
-    d[key] = {"bytes_per_launch": captured * full / args.queries, "captured_bytes_per_launch": captured,
+    d[key] = {"bytes_per_search": captured * full / args.queries, "captured_bytes_per_search": captured,
+              "captured_bytes_per_kernel": by_kernel,
               "captured_queries": args.queries, "full_queries": full, "launches": len(per_launch),
+              "searches": calls,
               "scaled": ("captured at the full workload" if args.queries == full else
                          "traffic grows in proportion to the queries (tables L2-resident)"),
               "source_hash": source_hash(key)}
@@ -624,7 +635,7 @@ def setup_batched(args, ds, W, torch, dev, rank):
     job.table = {"arrays": info["n_arrays"], "R_total": info["R"], "table_bytes": info["table_bytes"],
                  "tune": tune}
     job.kernel_key = "batch_search_f32"
-    job.launches_per_step = 2
+    job.launches_per_step = info["search_launches"]  # the planner and the search kernel
     job.search = lambda: ds.ds_batch_search(b, Zd, zo, out)
     job.out = out
     job.keep = (b, Xd, xo, Zd, zo)
@@ -732,7 +743,7 @@ def setup_learned(args, ds, W, torch, dev, rank):
         ds.ds_learned_set_tune(L, blk, items, smem)
         job.table["tune"] = ds.ds_learned_get_tune(L)
     job.kernel_key = "learned_search_%s" % job.dtype_name
-    job.launches_per_step = 2
+    job.launches_per_step = info["search_launches"]  # the planner, then one or two search kernels
     if five:
         job.search = lambda: ds.ds_learned_search(L, Zd, zo, out=out, y_out=yout)
     else:

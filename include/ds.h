@@ -116,6 +116,10 @@ typedef struct ds_info_t {
     uint64_t fallback_queries; /* learned: always 0 (the cell map is exact; no query falls back) */
     int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error */
     int32_t gap_q;          /* single array: q of the table (1 Direct, 2 DirectGap2, ...); batched: largest q */
+    int32_t search_launches; /* kernel launches per search call: 1 for one array; batched and learned
+                                handles: the chunk planner and one search kernel, or two where a
+                                handle's direct and learned arrays are searched by separate kernels */
+    int32_t reserved_;
 } ds_info_t;
 
 /* ------------------------------------------------------------------------

@@ -59,6 +59,7 @@ class ds_info_t(ctypes.Structure):
         ("build_ms", F64), ("smem_resident", I32), ("n_direct", I32), ("n_learned", I32),
         ("n_fallback", I32), ("max_window", I64), ("train_steps", I64), ("train_ms", F64),
         ("final_loss", F64), ("fallback_queries", U64), ("device_error", I32), ("gap_q", I32),
+        ("search_launches", I32), ("reserved_", I32),
     ]
 
     def as_dict(self):

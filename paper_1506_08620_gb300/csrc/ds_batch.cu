@@ -794,6 +794,7 @@ ds_status info_batch(const ds_batch *b, ds_info_t *o)
     o->n_direct = e.n_direct;
     o->n_fallback = e.n_fallback;
     o->n_learned = e.n_learned;
+    o->search_launches = e.split > 0 ? 3 : 2;
     int err = 0;
     if (e.dev_err && cudaMemcpy(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
         o->device_error = err;

@@ -151,6 +151,7 @@ ds_status info_index(const ds_index *idx, ds_info_t *o)
     o->smem_resident = idx->plan.smem ? 1 : 0;
     o->n_direct = 1;
     o->gap_q = idx->q;
+    o->search_launches = 1;
     int err = 0;
     if (idx->dev_err && cudaMemcpy(&err, idx->dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
         o->device_error = err;

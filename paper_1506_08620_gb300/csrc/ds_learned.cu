@@ -788,6 +788,7 @@ ds_status info_learned(const ds_learned *L, ds_info_t *o)
         o->W = d.W;
     }
     o->fallback_queries = 0;  // exact by construction: no query needs a fall-back
+    o->search_launches = e.split > 0 ? 3 : 2;
     int err = 0;
     if (e.dev_err && cudaMemcpy(&err, e.dev_err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess)
         o->device_error = err;

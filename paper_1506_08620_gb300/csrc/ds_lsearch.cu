@@ -453,6 +453,7 @@ void free_lsearch(ds_lsearch *h)
 ds_status info_lsearch(const ds_lsearch *h, ds_info_t *o)
 {
     o->kind = KIND_LSEARCH;
+    o->search_launches = 1;
     o->dtype = h->dtype;
     o->flags = h->flags;
     o->n_arrays = 1;
