@@ -497,6 +497,22 @@ DS_API const char *ds_status_str(ds_status s);
 DS_API const char *ds_last_error(void);
 DS_API int32_t ds_abi_version(void);
 
+/* ------------------------------------------------------------------------
+ * Test aids (the paper has no counterpart: they let tests reach the error
+ * paths of every build on the host, with no fault on the device).
+ *
+ * ds_debug_fail_alloc(nth): the device allocation nth + 1 from now (nth = 0:
+ * the next one) made by this library fails as if the device were out of
+ * memory (cudaErrorMemoryAllocation, reported as DS_E_NOMEM) without
+ * allocating; nth < 0 turns the hook off.  One failure per call; process-wide.
+ * ds_debug_alloc_stats: the library's live device allocations (count and
+ * bytes; either pointer may be NULL).  A handle's allocations stay live until
+ * ds_free; a call that fails leaves none behind.  ds_build_table_static
+ * allocates nothing and is not counted.
+ * ------------------------------------------------------------------------ */
+DS_API ds_status ds_debug_fail_alloc(int64_t nth);
+DS_API ds_status ds_debug_alloc_stats(int64_t *live_count, int64_t *live_bytes);
+
 #ifdef __cplusplus
 }
 #endif

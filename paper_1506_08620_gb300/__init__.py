@@ -14,7 +14,7 @@ from . import _abi
 from ._abi import (DS_CACHE_LAYOUT, DS_CHECKED, DS_F32, DS_F64, DS_FMA, DS_LEARNED_FORCE,  # noqa: F401
                    DS_GAP2, DS_LEARNED_LINEAR, DS_LS_CLASSIC, DS_LS_CLASSICMOD, DS_LS_EYTZINGER,
                    DS_LS_LEADBIT, DS_LS_LEADBIT_NOPAD, DS_LS_NAMES, DS_LS_OFFSET, DS_NO_FINGERPRINT, DS_NO_SMEM, DS_OK,
-                   DS_REFINE_H, DS_STRICT, DsError, check, lib)
+                   DS_REFINE_H, DS_STRICT, DS_E_NOMEM, DsError, check, lib)
 
 __all__ = [
     "ds_build", "ds_search", "ds_search_host", "ds_index_export", "ds_batch_build", "ds_batch_search",
@@ -22,7 +22,7 @@ __all__ = [
     "ds_learned_search", "ds_learned_autotune", "ds_learned_set_tune", "ds_learned_get_tune", "ds_learned_array",
     "ds_learned_cfg_default", "ds_learned_build_xy", "ds_learned_cells", "ds_learned_export_cells",
     "ds_learned_search_host", "ds_mlp_forward", "ds_mlp_loss_grad",
-    "ds_adam_step", "ds_info", "ds_free", "DsError",
+    "ds_adam_step", "ds_info", "ds_free", "DsError", "ds_debug_fail_alloc", "ds_debug_alloc_stats",
 ]
 
 
@@ -417,3 +417,16 @@ def ds_info(h):
 
 def ds_free(h):
     h.free()
+
+
+# ---------------------------------------------------------------- test aids
+def ds_debug_fail_alloc(nth):
+    """Make the library's device allocation nth + 1 from now fail (nth < 0: off)."""
+    check(lib().ds_debug_fail_alloc(int(nth)), "ds_debug_fail_alloc")
+
+
+def ds_debug_alloc_stats():
+    """The library's live device allocations: (count, bytes)."""
+    n, b = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().ds_debug_alloc_stats(ctypes.byref(n), ctypes.byref(b)), "ds_debug_alloc_stats")
+    return n.value, b.value

@@ -119,6 +119,8 @@ _SIGS = {
     "ds_status_str": (ctypes.c_char_p, [ST]),
     "ds_last_error": (ctypes.c_char_p, []),
     "ds_abi_version": (I32, []),
+    "ds_debug_fail_alloc": (ST, [I64]),
+    "ds_debug_alloc_stats": (ST, [ctypes.POINTER(I64), ctypes.POINTER(I64)]),
 }
 
 EXPORTED = sorted(_SIGS)

@@ -160,13 +160,13 @@ void engine_free(Engine *e)
 {
     if (e->gexec) cudaGraphExecDestroy(e->gexec);
     if (e->gstream) cudaStreamDestroy(e->gstream);
-    if (e->desc_dev) cudaFree(e->desc_dev);
-    if (e->blob) cudaFree(e->blob);
-    if (e->chunk_off) cudaFree(e->chunk_off);
-    if (e->order) cudaFree(e->order);
-    if (e->counter) cudaFree(e->counter);
-    if (e->dev_err) cudaFree(e->dev_err);
-    if (e->ctab) cudaFree(e->ctab);
+    if (e->desc_dev) dev_free(e->desc_dev);
+    if (e->blob) dev_free(e->blob);
+    if (e->chunk_off) dev_free(e->chunk_off);
+    if (e->order) dev_free(e->order);
+    if (e->counter) dev_free(e->counter);
+    if (e->dev_err) dev_free(e->dev_err);
+    if (e->ctab) dev_free(e->ctab);
     *e = Engine();
 }
 
@@ -209,7 +209,7 @@ static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const
                                 int A, cudaStream_t s, const DeviceProps &props, std::vector<HRState> &hs)
 {
     HRState *st = nullptr;
-    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState) * (size_t)A));
+    DS_TRY_CUDA(dev_alloc(&st, sizeof(HRState) * (size_t)A));
     const int sgrid = std::max(1, std::min(n_segs, props.num_sms * 8));
     const int agrid = (A + 127) / 128;
     k_hr_state_init<<<agrid, 128, 0, s>>>(st, A, 1);
@@ -239,7 +239,7 @@ static ds_status compute_hr_all(const T *Xcat, const long long *x_off_dev, const
             break;
         }
     }
-    cudaFree(st);
+    dev_free(st);
     return rc;
 }
 
@@ -255,7 +255,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
     std::vector<Segment> segs = make_segments(x_off);
     const int n_segs = (int)segs.size();
     Segment *segs_dev = nullptr;
-    DS_TRY_CUDA(cudaMalloc(&segs_dev, sizeof(Segment) * segs.size()));
+    DS_TRY_CUDA(dev_alloc(&segs_dev, sizeof(Segment) * segs.size()));
     ds_status rc = DS_OK;
     std::vector<HRState> hs;
     uint32_t *F = nullptr;
@@ -391,11 +391,11 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
             rc = DS_E_TABLE_TOO_LARGE;
             break;
         }
-        if (cudaMalloc(&e->blob, std::max<size_t>(off, 16)) != cudaSuccess ||
-            cudaMalloc(&e->desc_dev, sizeof(ArrDesc) * (size_t)A) != cudaSuccess ||
-            cudaMalloc(&F, sizeof(uint32_t) * std::max<long long>(x_off[A], 1)) != cudaSuccess ||
-            cudaMalloc(&G, std::max<long long>(x_off[A], 1)) != cudaSuccess ||
-            cudaMalloc(&kc_dev, sizeof(long long) * (size_t)(A + 1)) != cudaSuccess) {
+        if (dev_alloc(&e->blob, std::max<size_t>(off, 16)) != cudaSuccess ||
+            dev_alloc(&e->desc_dev, sizeof(ArrDesc) * (size_t)A) != cudaSuccess ||
+            dev_alloc(&F, sizeof(uint32_t) * std::max<long long>(x_off[A], 1)) != cudaSuccess ||
+            dev_alloc(&G, std::max<long long>(x_off[A], 1)) != cudaSuccess ||
+            dev_alloc(&kc_dev, sizeof(long long) * (size_t)(A + 1)) != cudaSuccess) {
             set_error("batched build: device allocation failed");
             rc = DS_E_NOMEM;
             break;
@@ -420,10 +420,10 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
             break;
         }
     } while (0);
-    cudaFree(segs_dev);
-    if (F) cudaFree(F);
-    if (G) cudaFree(G);
-    if (kc_dev) cudaFree(kc_dev);
+    dev_free(segs_dev);
+    if (F) dev_free(F);
+    if (G) dev_free(G);
+    if (kc_dev) dev_free(kc_dev);
     if (hs_out) *hs_out = hs;
     return rc;
 }
@@ -457,19 +457,19 @@ ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long
     }
     e->n_knots = x_off[n_arrays];
     if (x_off_host) *x_off_host = x_off;
-    DS_TRY_CUDA(cudaMalloc(&e->chunk_off, sizeof(long long) * (size_t)(n_arrays + 1)));
+    DS_TRY_CUDA(dev_alloc(&e->chunk_off, sizeof(long long) * (size_t)(n_arrays + 1)));
     {  // claim order: the arrays with the most knots first (longest-processing-time first)
         std::vector<int> order(n_arrays);
         for (int a = 0; a < n_arrays; ++a) order[a] = a;
         std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
             return x_off[p + 1] - x_off[p] > x_off[q + 1] - x_off[q];
         });
-        DS_TRY_CUDA(cudaMalloc(&e->order, sizeof(int) * (size_t)std::max(n_arrays, 1)));
+        DS_TRY_CUDA(dev_alloc(&e->order, sizeof(int) * (size_t)std::max(n_arrays, 1)));
         DS_TRY_CUDA(cudaMemcpy(e->order, order.data(), sizeof(int) * (size_t)n_arrays, cudaMemcpyHostToDevice));
     }
-    DS_TRY_CUDA(cudaMalloc(&e->counter, 2 * sizeof(unsigned long long)));
+    DS_TRY_CUDA(dev_alloc(&e->counter, 2 * sizeof(unsigned long long)));
     DS_TRY_CUDA(cudaMemset(e->counter, 0, 2 * sizeof(unsigned long long)));
-    DS_TRY_CUDA(cudaMalloc(&e->dev_err, sizeof(int)));
+    DS_TRY_CUDA(dev_alloc(&e->dev_err, sizeof(int)));
     DS_TRY_CUDA(cudaMemset(e->dev_err, 0, sizeof(int)));
     const bool fma = (flags & DS_FMA) != 0;
     if (dtype == DS_F32) {

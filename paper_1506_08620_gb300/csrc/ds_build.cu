@@ -182,7 +182,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
 {
     const DeviceProps &props = idx->props;
     HRState *st = nullptr;
-    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
+    DS_TRY_CUDA(dev_alloc(&st, sizeof(HRState)));
     HRState hs;
     // Gap-q separates the pairs (i, i+q); with fewer than q+1 knots the pair distance is N
     const bool gen = q >= 2;
@@ -191,7 +191,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
     ds_status rc = run_compute_hr<T, FMA>(X_user, n_knots, st, &hs, s, props, gap);
     if (rc == DS_OK && hs.status == DS_OK && hs.updates > 0 && (flags & DS_REFINE_H))
         rc = refine_h<T, FMA>(X_user, n_knots, st, &hs, s, props);
-    cudaFree(st);
+    dev_free(st);
     if (rc != DS_OK) return rc;
     idx->updates = hs.updates;
     idx->passes = hs.passes;
@@ -213,14 +213,14 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
         set_error("ds_build: table needs %zu bytes, budget is %zu (R = %llu)", idx->table_bytes, budget, R);
         return DS_E_TABLE_TOO_LARGE;
     }
-    DS_TRY_CUDA(cudaMalloc(&idx->tab, idx->k_bytes + idx->x_bytes));
+    DS_TRY_CUDA(dev_alloc(&idx->tab, idx->k_bytes + idx->x_bytes));
     DS_TRY_CUDA(cudaMemsetAsync(idx->tab, 0, idx->k_bytes + idx->x_bytes, s));
     T *Xc = reinterpret_cast<T *>(idx->tab + idx->k_bytes);
     uint32_t *K = reinterpret_cast<uint32_t *>(idx->tab);
     DS_TRY_CUDA(cudaMemcpyAsync(Xc, X_user, (size_t)n_knots * sizeof(T), cudaMemcpyDeviceToDevice, s));
-    if (cache) DS_TRY_CUDA(cudaMalloc(&idx->pairs, idx->pair_bytes));
+    if (cache) DS_TRY_CUDA(dev_alloc(&idx->pairs, idx->pair_bytes));
     uint32_t *F = nullptr;
-    DS_TRY_CUDA(cudaMalloc(&F, (size_t)n_knots * sizeof(uint32_t)));
+    DS_TRY_CUDA(dev_alloc(&F, (size_t)n_knots * sizeof(uint32_t)));
     const int block = 256;
     k_fill_F<T, FMA><<<grid_for(props, n_knots, block), block, 0, s>>>(Xc, n_knots, (T)hs.H, (T)hs.W, F);
     long long warps_work = (n_knots + 31) / 32 * 32;
@@ -231,7 +231,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
             F, n_knots, K, cache ? reinterpret_cast<Pair<T> *>(idx->pairs) : nullptr, Xc);
     cudaError_t le = cudaGetLastError();
     cudaError_t se = cudaStreamSynchronize(s);
-    cudaFree(F);
+    dev_free(F);
     if (le != cudaSuccess || se != cudaSuccess) {
         set_error("ds_build: table fill failed: %s", cudaGetErrorString(le != cudaSuccess ? le : se));
         return DS_E_CUDA;
@@ -257,7 +257,7 @@ static ds_status build_typed(const T *X_user, long long n_knots, uint32_t flags,
         if (!e || atoi(e) != 0) {
             const unsigned long long nblk = (R + PACK_CELLS) / PACK_CELLS;
             idx->k16_bytes = (size_t)nblk * sizeof(uint4);
-            DS_TRY_CUDA(cudaMalloc(&idx->k16, idx->k16_bytes));
+            DS_TRY_CUDA(dev_alloc(&idx->k16, idx->k16_bytes));
             k_pack_cells<<<grid_for(props, (long long)nblk, 256), 256, 0, s>>>(K, R, idx->k16, gen);
             DS_TRY_CUDA(cudaGetLastError());
             DS_TRY_CUDA(cudaStreamSynchronize(s));
@@ -278,7 +278,7 @@ static ds_status select_q(const T *X, long long n_knots, long long budget_bytes,
 {
     *q_out = 0;
     HRState *st = nullptr;
-    DS_TRY_CUDA(cudaMalloc(&st, sizeof(HRState)));
+    DS_TRY_CUDA(dev_alloc(&st, sizeof(HRState)));
     ds_status rc = DS_OK;
     const size_t x_bytes = round_up((size_t)n_knots * sizeof(T), 16);
     for (int q = 1; q <= q_max; ++q) {
@@ -299,7 +299,7 @@ static ds_status select_q(const T *X, long long n_knots, long long budget_bytes,
             break;
         }
     }
-    cudaFree(st);
+    dev_free(st);
     return rc;
 }
 
@@ -316,11 +316,11 @@ ds_status build_single(const void *X_dev, long long n_knots, ds_dtype dtype, uin
     idx->n_knots = n_knots;
     ds_status rc = device_props(&idx->props);
     if (rc == DS_OK) {
-        cudaError_t e = cudaMalloc(&idx->dev_err, sizeof(int));
+        cudaError_t e = dev_alloc(&idx->dev_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(idx->dev_err, 0, sizeof(int));
         if (e != cudaSuccess) {
             set_error("ds_build: %s", cudaGetErrorString(e));
-            rc = DS_E_CUDA;
+            rc = e == cudaErrorMemoryAllocation ? DS_E_NOMEM : DS_E_CUDA;
         }
     }
     // first and last knot on the host (X_0 == 0 selects the subtraction-free form)

@@ -20,6 +20,25 @@ namespace ds {
 void set_error(const char *fmt, ...);
 void clear_error();
 
+// ------------------------------------------------------------------ device memory
+// Every device allocation of the library goes through these: they keep a
+// count of the live allocations and bytes (ds_debug_alloc_stats), and
+// ds_debug_fail_alloc can make a chosen allocation fail with
+// cudaErrorMemoryAllocation without allocating, so that tests reach every
+// error path of a build on the host.
+cudaError_t dev_alloc(void **p, size_t bytes);
+cudaError_t dev_alloc_async(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p);
+void dev_free_async(void *p, cudaStream_t s);
+template <typename T> inline cudaError_t dev_alloc(T **p, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+template <typename T> inline cudaError_t dev_alloc_async(T **p, size_t bytes, cudaStream_t s)
+{
+    return dev_alloc_async(reinterpret_cast<void **>(p), bytes, s);
+}
+
 #define DS_TRY_CUDA(call)                                                                       \
     do {                                                                                        \
         cudaError_t e_ = (call);                                                                \

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "ds_index.cuh"
 
@@ -21,6 +23,71 @@ void set_error(const char *fmt, ...)
 }
 
 void clear_error() { g_err[0] = 0; }
+
+// ------------------------------------------------------------------ device memory
+namespace {
+std::mutex g_alloc_mu;
+std::unordered_map<void *, size_t> g_live;  // live allocations and their sizes
+long long g_live_bytes = 0;
+long long g_fail_at = -1;  // allocations to let through before one fails (-1: none fails)
+
+// true if this allocation is to fail (the hook counts down under the lock)
+bool take_failure()
+{
+    if (g_fail_at < 0) return false;
+    if (g_fail_at == 0) {
+        g_fail_at = -1;
+        return true;
+    }
+    --g_fail_at;
+    return false;
+}
+void note_alloc(void *p, size_t bytes)
+{
+    g_live[p] = bytes;
+    g_live_bytes += (long long)bytes;
+}
+void note_free(void *p)
+{
+    auto it = g_live.find(p);
+    if (it == g_live.end()) return;
+    g_live_bytes -= (long long)it->second;
+    g_live.erase(it);
+}
+}  // namespace
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    *p = nullptr;
+    if (take_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) note_alloc(*p, bytes);
+    return e;
+}
+cudaError_t dev_alloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    *p = nullptr;
+    if (take_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e == cudaSuccess) note_alloc(*p, bytes);
+    return e;
+}
+void dev_free(void *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    note_free(p);
+    cudaFree(p);
+}
+void dev_free_async(void *p, cudaStream_t s)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    note_free(p);
+    cudaFreeAsync(p, s);
+}
 
 double now_ms()
 {
@@ -81,8 +148,8 @@ static void destroy_pipe(HostPipe *p)
     if (p->s_run) cudaStreamSynchronize(p->s_run);
     if (p->s_out) cudaStreamSynchronize(p->s_out);
     for (int b = 0; b < PIPE_BUFS; ++b) {
-        if (p->zbuf[b]) cudaFree(p->zbuf[b]);
-        if (p->ibuf[b]) cudaFree(p->ibuf[b]);
+        if (p->zbuf[b]) dev_free(p->zbuf[b]);
+        if (p->ibuf[b]) dev_free(p->ibuf[b]);
         if (p->ev_in[b]) cudaEventDestroy(p->ev_in[b]);
         if (p->ev_run[b]) cudaEventDestroy(p->ev_run[b]);
         if (p->ev_out[b]) cudaEventDestroy(p->ev_out[b]);
@@ -108,8 +175,8 @@ static ds_status make_pipe(HostPipe **out, size_t elem_bytes)
         e = cudaEventCreateWithFlags(&p->ev_in[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_run[b], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_out[b], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMalloc(&p->zbuf[b], (size_t)p->chunk * elem_bytes);
-        if (e == cudaSuccess) e = cudaMalloc(&p->ibuf[b], (size_t)p->chunk * sizeof(int32_t));
+        if (e == cudaSuccess) e = dev_alloc(&p->zbuf[b], (size_t)p->chunk * elem_bytes);
+        if (e == cudaSuccess) e = dev_alloc(&p->ibuf[b], (size_t)p->chunk * sizeof(int32_t));
     }
     if (e != cudaSuccess) {
         set_error("ds_search_host: pipeline setup failed: %s", cudaGetErrorString(e));
@@ -124,10 +191,10 @@ void free_index(ds_index *idx)
 {
     if (!idx) return;
     destroy_pipe(idx->pipe);
-    if (idx->tab) cudaFree(idx->tab);
-    if (idx->pairs) cudaFree(idx->pairs);
-    if (idx->k16) cudaFree(idx->k16);
-    if (idx->dev_err) cudaFree(idx->dev_err);
+    if (idx->tab) dev_free(idx->tab);
+    if (idx->pairs) dev_free(idx->pairs);
+    if (idx->k16) dev_free(idx->k16);
+    if (idx->dev_err) dev_free(idx->dev_err);
     idx->hdr.magic = 0;
     delete idx;
 }
@@ -182,6 +249,21 @@ extern "C" {
 int32_t ds_abi_version(void) { return 1; }
 
 const char *ds_last_error(void) { return g_err; }
+
+ds_status ds_debug_fail_alloc(int64_t nth)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_fail_at = nth < 0 ? -1 : (long long)nth;
+    return DS_OK;
+}
+
+ds_status ds_debug_alloc_stats(int64_t *live_count, int64_t *live_bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (live_count) *live_count = (int64_t)g_live.size();
+    if (live_bytes) *live_bytes = (int64_t)g_live_bytes;
+    return DS_OK;
+}
 
 const char *ds_status_str(ds_status s)
 {

@@ -756,7 +756,7 @@ struct ds_learned {
 namespace ds {
 void free_learned(ds_learned *L)
 {
-    if (L->zoff_dev) cudaFree(L->zoff_dev);
+    if (L->zoff_dev) dev_free(L->zoff_dev);
     engine_free(&L->eng);
     L->hdr.magic = 0;
     delete L;
@@ -827,7 +827,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
     do {
         cudaError_t ce = cudaSuccess;
         auto A = [&](void **p, size_t bytes) {
-            if (ce == cudaSuccess) ce = cudaMalloc(p, std::max<size_t>(bytes, 16));
+            if (ce == cudaSuccess) ce = dev_alloc(p, std::max<size_t>(bytes, 16));
         };
         A((void **)&model_arr, sizeof(int) * nm);
         A((void **)&step, sizeof(int) * nm);
@@ -1050,7 +1050,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             L->mean_pop[k] = (double)hst[k].sum_pop2 / (double)(d.n + 1);
             L->max_window = std::max(L->max_window, (long long)hst[k].max_pop + 1);
         }
-        ce = cudaMalloc(&e.ctab, std::max<size_t>(cbytes, 16));
+        ce = dev_alloc(&e.ctab, std::max<size_t>(cbytes, 16));
         if (ce != cudaSuccess) {
             e.ctab = nullptr;
             set_error("learned build: cell tables (%zu bytes): allocation failed", cbytes);
@@ -1075,7 +1075,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
     for (void *p : {(void *)model_arr, (void *)step, (void *)elo, (void *)ehi, (void *)pool_off_d, (void *)pool,
                     (void *)theta, (void *)mom, (void *)vel, (void *)part, (void *)plos, (void *)loss, (void *)seg_x,
                     (void *)seg_a, (void *)seg_b, (void *)Fk, (void *)kbase_d, (void *)lst})
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
     L->train_ms = now_ms() - t0;
     return rc;
 }
@@ -1138,7 +1138,7 @@ ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const 
     const long long *xo = (const long long *)x_off_dev;
     if (!x_off_dev) {
         long long h[2] = {0, (long long)n_knots_if_single};
-        if (cudaMalloc(&single_off, sizeof(h)) != cudaSuccess ||
+        if (ds::dev_alloc(&single_off, sizeof(h)) != cudaSuccess ||
             cudaMemcpy(single_off, h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) {
             ds::set_error("ds_learned_build: allocation failed");
             delete L;
@@ -1154,7 +1154,7 @@ ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const 
     }
     ds_status rc = ds::engine_build(&L->eng, Xcat_dev, Ycat_dev, xo, n_arrays, dtype, 0, s, fp, ds::MODE_LEARNED,
                                     nullptr, nullptr, (double)cfg.max_cells_per_knot);
-    if (single_off) cudaFree(single_off);
+    if (single_off) ds::dev_free(single_off);
     if (rc == DS_OK) {
         ds::Engine &e = L->eng;
         L->arr_model.assign(n_arrays, -1);
@@ -1285,8 +1285,8 @@ ds_status ds_mlp_loss_grad(const float *theta_dev, const float *u_dev, const flo
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (int)((n + ds::TB - 1) / ds::TB);
     float *part = nullptr, *plos = nullptr;
-    DS_TRY_CUDA(cudaMallocAsync(&part, sizeof(float) * (size_t)nb * ds::NP, s));
-    cudaError_t ce = cudaMallocAsync(&plos, sizeof(float) * (size_t)nb, s);
+    DS_TRY_CUDA(ds::dev_alloc_async(&part, sizeof(float) * (size_t)nb * ds::NP, s));
+    cudaError_t ce = ds::dev_alloc_async(&plos, sizeof(float) * (size_t)nb, s);
     const size_t smem = ds::PARAM_SMEM + sizeof(ds::GradTile);
     if (ce == cudaSuccess)
         ce = cudaFuncSetAttribute(ds::k_grad_explicit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1295,11 +1295,11 @@ ds_status ds_mlp_loss_grad(const float *theta_dev, const float *u_dev, const flo
         ds::k_reduce_grad<<<1, 256, 0, s>>>(part, plos, nb, n, grad_dev, loss_dev);
         ce = cudaGetLastError();
     }
-    cudaFreeAsync(part, s);
-    if (plos) cudaFreeAsync(plos, s);
+    ds::dev_free_async(part, s);
+    if (plos) ds::dev_free_async(plos, s);
     if (ce != cudaSuccess) {
         ds::set_error("ds_mlp_loss_grad: %s", cudaGetErrorString(ce));
-        return DS_E_CUDA;
+        return ce == cudaErrorMemoryAllocation ? DS_E_NOMEM : DS_E_CUDA;
     }
     return DS_OK;
 }
@@ -1363,7 +1363,7 @@ ds_status ds_learned_search_host(ds_learned *L, const void *Zcat_host, const int
             return DS_E_ARG;
         }
         m = z_off_host[e.n_arrays];
-        if (!L->zoff_dev) DS_TRY_CUDA(cudaMalloc(&L->zoff_dev, sizeof(long long) * (size_t)(e.n_arrays + 1)));
+        if (!L->zoff_dev) DS_TRY_CUDA(ds::dev_alloc(&L->zoff_dev, sizeof(long long) * (size_t)(e.n_arrays + 1)));
         DS_TRY_CUDA(cudaMemcpyAsync(L->zoff_dev, z_off_host, sizeof(long long) * (size_t)(e.n_arrays + 1),
                                     cudaMemcpyHostToDevice, s));
     }

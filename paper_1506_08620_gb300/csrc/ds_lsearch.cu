@@ -377,7 +377,7 @@ static ds_status ls_build_typed(ds_lsearch *h, const T *X, cudaStream_t s)
 {
     using K = typename LsKey<T>::K;
     h->lay_bytes = round_up((size_t)h->len * sizeof(K), 16);
-    DS_TRY_CUDA(cudaMalloc(&h->lay, h->lay_bytes));
+    DS_TRY_CUDA(dev_alloc(&h->lay, h->lay_bytes));
     DS_TRY_CUDA(cudaMemsetAsync(h->lay, 0, h->lay_bytes, s));
     const long long blocks = std::min<long long>((h->len + 255) / 256, (long long)h->props.num_sms * 8);
     k_ls_layout<T><<<(int)std::max<long long>(blocks, 1), 256, 0, s>>>(X, h->n_knots, h->method, h->len, h->c[0],
@@ -444,8 +444,8 @@ static ds_status ls_search_typed(const ds_lsearch *h, const void *Z, long long m
 void free_lsearch(ds_lsearch *h)
 {
     if (!h) return;
-    if (h->lay) cudaFree(h->lay);
-    if (h->dev_err) cudaFree(h->dev_err);
+    if (h->lay) dev_free(h->lay);
+    if (h->dev_err) dev_free(h->dev_err);
     h->hdr.magic = 0;
     delete h;
 }
@@ -523,7 +523,7 @@ extern "C" ds_status ds_lsearch_build(const void *X_dev, int64_t n_knots, ds_dty
         rc = DS_E_ARG;
     }
     if (rc == DS_OK) {
-        cudaError_t e = cudaMalloc(&h->dev_err, sizeof(int));
+        cudaError_t e = dev_alloc(&h->dev_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(h->dev_err, 0, sizeof(int));
         const size_t esz = dtype == DS_F32 ? 4 : 8;
         unsigned char ends[16];
@@ -532,7 +532,7 @@ extern "C" ds_status ds_lsearch_build(const void *X_dev, int64_t n_knots, ds_dty
             e = cudaMemcpy(ends + 8, (const unsigned char *)X_dev + (n_knots - 1) * esz, esz, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             set_error("ds_lsearch_build: %s", cudaGetErrorString(e));
-            rc = DS_E_CUDA;
+            rc = e == cudaErrorMemoryAllocation ? DS_E_NOMEM : DS_E_CUDA;
         } else if (dtype == DS_F32) {
             float a, b;
             memcpy(&a, ends, 4);

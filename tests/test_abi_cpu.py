@@ -74,3 +74,27 @@ def test_static_build_source_allocates_nothing():
                  "cudaMallocManaged", "cudaMallocPitch", "malloc(", "new ", "std::vector"):
         assert call not in code, call
     assert "__device__ __align__(256)" in code and "cudaGetSymbolAddress" in code
+
+
+def test_every_device_allocation_goes_through_the_tracked_wrapper():
+    # the allocation-failure hook and the live-allocation count see every
+    # device allocation only if no source calls the runtime's allocator itself
+    import re
+    csrc = os.path.join(ROOT, "paper_1506_08620_gb300", "csrc")
+    raw = re.compile(r"\bcuda(Malloc|MallocAsync|Free|FreeAsync|MallocManaged|MallocPitch)\s*\(")
+    for f in sorted(os.listdir(csrc)):
+        if not f.endswith((".cu", ".cuh")):
+            continue
+        for n, line in enumerate(open(os.path.join(csrc, f)), 1):
+            code = line.split("//")[0]
+            if raw.search(code):
+                # only the wrapper itself may call the runtime
+                assert f == "ds_core.cu", "%s:%d calls the CUDA allocator directly: %s" % (f, n, line.strip())
+
+
+def test_allocation_hook_needs_no_device(libds):
+    n, b = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    assert libds.ds_debug_fail_alloc(ctypes.c_int64(3)) == 0
+    assert libds.ds_debug_alloc_stats(ctypes.byref(n), ctypes.byref(b)) == 0
+    assert (n.value, b.value) == (0, 0)
+    assert libds.ds_debug_fail_alloc(ctypes.c_int64(-1)) == 0
