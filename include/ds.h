@@ -114,7 +114,8 @@ typedef struct ds_info_t {
     double train_ms;        /* learned: time spent training */
     double final_loss;      /* learned: mean final training loss */
     uint64_t fallback_queries; /* learned: always 0 (the cell map is exact; no query falls back) */
-    int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error */
+    int32_t device_error;   /* nonzero if a device-side bounded wait or check recorded an error:
+                               DS_DEVERR_TIMEOUT, or (range-checking build) DS_DEVERR_BOUNDS | site << 8 */
     int32_t gap_q;          /* single array: q of the table (1 Direct, 2 DirectGap2, ...); batched: largest q */
     int32_t search_launches; /* kernel launches per search call: 1 for one array; batched and learned
                                 handles: the chunk planner and one search kernel, or two where a
@@ -496,6 +497,29 @@ DS_API void ds_free(void *handle);                            /* any handle; NUL
 DS_API const char *ds_status_str(ds_status s);
 DS_API const char *ds_last_error(void);
 DS_API int32_t ds_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Device error words (ds_info_t.device_error).  DS_DEVERR_TIMEOUT: a bounded
+ * wait of a kernel gave up (the kernel returned early).  DS_DEVERR_BOUNDS |
+ * site << 8: only in the range-checking build of the library
+ * (libds_bounds.so, compiled with -DDS_DEBUG_BOUNDS; the Python package loads
+ * it when DS_LIBRARY=bounds), the first table or knot gather of a search whose
+ * index fell outside its table; the gather read entry 0 instead.  The normal
+ * build has no such checks (indices are in range by construction).
+ * ------------------------------------------------------------------------ */
+enum { DS_DEVERR_TIMEOUT = 1, DS_DEVERR_BOUNDS = 2 };
+enum {
+    DS_BS_K = 1,       /* single array: K_j (R + 1 cells), or its cache-layout pair */
+    DS_BS_K16 = 2,     /* single array: packed block of cells */
+    DS_BS_X = 3,       /* knots X_t (N + 1), or their (X, Y) pairs */
+    DS_BS_RANK = 4,    /* batched: rank word of a cell */
+    DS_BS_FPRINT = 5,  /* batched: knot fingerprint */
+    DS_BS_CMAP = 6,    /* learned: macro cell of the cell map */
+    DS_BS_CBLOCK = 7,  /* learned: cell-table block */
+    DS_BS_CESC = 8,    /* learned: escaped block's values */
+    DS_BS_Y = 9,       /* the caller's knot values Y_i (interpolation) */
+    DS_BS_LAYOUT = 10  /* logarithmic search: element of the layout */
+};
 
 /* ------------------------------------------------------------------------
  * Test aids (the paper has no counterpart: they let tests reach the error

@@ -8,6 +8,8 @@ import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libds.so")
+# the range-checking variant (build.build(bounds=True)), selected with DS_LIBRARY=bounds
+BOUNDS_LIB_PATH = os.path.join(PKG, "libds_bounds.so")
 
 DS_OK = 0
 DS_E_ARG = 1
@@ -21,6 +23,11 @@ DS_E_TIMEOUT = 8
 DS_E_UNIMPLEMENTED = 9
 DS_E_NO_CONVERGENCE = 10
 DS_E_DEVICE = 11
+
+DS_DEVERR_TIMEOUT = 1
+DS_DEVERR_BOUNDS = 2
+(DS_BS_K, DS_BS_K16, DS_BS_X, DS_BS_RANK, DS_BS_FPRINT, DS_BS_CMAP, DS_BS_CBLOCK, DS_BS_CESC, DS_BS_Y,
+ DS_BS_LAYOUT) = range(1, 11)
 
 DS_F32 = 0
 DS_F64 = 1
@@ -141,7 +148,7 @@ def lib(path=None):
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    path = path or (BOUNDS_LIB_PATH if os.environ.get("DS_LIBRARY") == "bounds" else LIB_PATH)
     if not os.path.exists(path):
         raise ImportError("libds.so is not built (%s); run `python -c 'import __graft_entry__ as g; g.build()'` "
                           "or `python -m paper_1506_08620_gb300.build`" % path)

@@ -401,6 +401,7 @@ static ds_status search_typed(const ds_index *idx, const void *Z, long long m, i
     a.I = I;
     a.m = m;
     a.err = idx->dev_err;
+    a.n_x = idx->n_knots;
     return launch_search<T>(a, idx->plan, s);
 }
 

@@ -64,8 +64,37 @@ struct HandleHeader {
     int32_t magic;
 };
 
-// Status words written by device code (bounded waits, bounds checks).
-enum DeviceErr : int32_t { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
+// Status words written by device code (bounded waits, bounds checks; the
+// values of ds.h's DS_DEVERR_*).
+enum DeviceErr : int32_t { DEVERR_NONE = 0, DEVERR_TIMEOUT = DS_DEVERR_TIMEOUT, DEVERR_BOUNDS = DS_DEVERR_BOUNDS };
+
+// Range-checking build.  Compiled with -DDS_DEBUG_BOUNDS (the library variant
+// libds_bounds.so), every table and knot gather of the search kernels checks
+// its index against the extent it reads: an index outside [0, n) is recorded
+// in the error word as DEVERR_BOUNDS | site << 8 (the first such index only)
+// and replaced by 0, so that the read stays inside its table.  The normal
+// build compiles the checks away (in_bounds returns its index).
+// The sites are ds.h's DS_BS_*.
+enum BoundsSite : int32_t {
+    BS_K = DS_BS_K, BS_K16 = DS_BS_K16, BS_X = DS_BS_X, BS_RANK = DS_BS_RANK, BS_FPRINT = DS_BS_FPRINT,
+    BS_CMAP = DS_BS_CMAP, BS_CBLOCK = DS_BS_CBLOCK, BS_CESC = DS_BS_CESC, BS_Y = DS_BS_Y, BS_LAYOUT = DS_BS_LAYOUT
+};
+#ifdef DS_DEBUG_BOUNDS
+constexpr bool BOUNDS_CHECKS = true;
+#else
+constexpr bool BOUNDS_CHECKS = false;
+#endif
+template <typename I>
+__device__ __forceinline__ I in_bounds(I i, long long n, int site, int *err)
+{
+    if constexpr (BOUNDS_CHECKS) {
+        if ((unsigned long long)(long long)i >= (unsigned long long)n) {
+            if (err) atomicCAS(err, 0, (int)DEVERR_BOUNDS | (site << 8));
+            return I(0);
+        }
+    }
+    return i;
+}
 
 // Device-resident state of ComputeHR (one per array).  H, W, P are kept in
 // the array's precision; they are stored in double slots, which hold float

@@ -404,7 +404,7 @@ __global__ void k_pool_queries(const ArrDesc *desc, const unsigned char *blob, c
         T z = (T)((double)X0 + f * ((double)XN - (double)X0));
         if (!(z < XN)) z = X[(size_t)(d.n - 1) * d.xs];
         if (z < X0) z = X0;
-        const int32_t i = bisect<T>(X, d.xs, 0, d.n, d.pbits, z);
+        const int32_t i = bisect<T>(X, d.xs, 0, d.n, d.pbits, z, (long long)d.n + 1, nullptr);
         pool[p0 + k] = make_float2(pred_u<T>(z, d), (float)i / (float)d.n);
     }
 }
@@ -495,7 +495,7 @@ __global__ void k_learned_F(const ArrDesc *desc, const unsigned char *blob, cons
     uint32_t *Fm = F + kbase[model];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= d.n;
          i += (long long)gridDim.x * blockDim.x)
-        Fm[i] = learned_cell<T>(X[(size_t)i * d.xs], d, M, G);
+        Fm[i] = learned_cell<T>(X[(size_t)i * d.xs], d, M, G, nullptr);
 }
 
 // #{i in [lo, n1) : F_i < v} + lo for non-decreasing F, given F_i < v below lo.
@@ -591,13 +591,13 @@ __global__ void k_learned_cells(const ArrDesc *desc, const int *model_arr, const
 }
 
 // K_0 .. K_C of one learned array's cell table, decoded (for inspection).
-__global__ void k_export_cells(const unsigned char *ct, uint32_t R, uint32_t *K)
+__global__ void k_export_cells(const unsigned char *ct, uint32_t R, long long n_esc, uint32_t *K)
 {
     const unsigned long long n = (unsigned long long)R + 2ull;
     for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < n;
          j += (unsigned long long)gridDim.x * blockDim.x) {
         uint32_t t0, t1;
-        learned_bounds(ct, R, (uint32_t)(j <= R ? j : R), &t0, &t1);
+        learned_bounds(ct, R, (uint32_t)(j <= R ? j : R), &t0, &t1, n_esc, nullptr);
         K[j] = j <= R ? t0 : t1;
     }
 }
@@ -1043,6 +1043,7 @@ static ds_status train_and_bound(ds_learned *L, const ds_learned_cfg &cfg, cudaS
             ArrDesc &d = e.desc_host[L->model_arr[k]];
             d.aux = 0;
             d.ct = (long long)cbytes;
+            d.n_esc = (long long)hst[k].escaped;
             cbytes += round_up((size_t)lblk_count(d.R) * 16 + (size_t)hst[k].escaped * 36, 16);
             L->max_pop[k] = hst[k].max_pop;
             L->nonempty[k] = hst[k].nonempty;
@@ -1414,7 +1415,7 @@ ds_status ds_learned_export_cells(const ds_learned *L, int32_t a, uint32_t *K_ou
     const ds::ArrDesc &d = L->eng.desc_host[a];
     const unsigned long long n = (unsigned long long)d.R + 2ull;
     const int grid = (int)std::min<unsigned long long>((n + 255) / 256, 4096ull);
-    ds::k_export_cells<<<grid, 256, 0, (cudaStream_t)stream>>>(L->eng.ctab + d.ct, d.R, K_out_dev);
+    ds::k_export_cells<<<grid, 256, 0, (cudaStream_t)stream>>>(L->eng.ctab + d.ct, d.R, d.n_esc, K_out_dev);
     DS_TRY_CUDA(cudaGetLastError());
     return DS_OK;
 }

@@ -131,10 +131,12 @@ template <typename T> struct LsArgs {
     int32_t *I;
     long long m;
     int *err;
+    long long len;  // elements of the layout (for the range-checking build)
 };
 
-template <typename K, bool SM> __device__ __forceinline__ K ls_ld(const K *p)
+template <typename K, bool SM> __device__ __forceinline__ K ls_ld(const K *Y, long long i, long long len, int *err)
 {
+    const K *p = Y + in_bounds(i, len, BS_LAYOUT, err);
     if constexpr (SM) return *p;
     else return __ldg(p);
 }
@@ -142,7 +144,7 @@ template <typename K, bool SM> __device__ __forceinline__ K ls_ld(const K *p)
 // NQ queries (keys kz, already moved into [X_0, X_N)) through one method.
 template <typename K, int METHOD, int NQ, bool SM>
 __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, long long c2, int32_t N, const K *kz,
-                                       int32_t *r)
+                                       int32_t *r, long long len, int *err)
 {
     if constexpr (METHOD == DS_LS_CLASSIC) {
         // Algorithm naivealg: low/high bisection with a data-dependent trip count
@@ -151,7 +153,7 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
             int32_t lo = 0, hi = N;
             while (hi - lo > 1) {
                 const int32_t mid = (lo + hi) >> 1;
-                if (kz[q] < ls_ld<K, SM>(Y + mid)) hi = mid;
+                if (kz[q] < ls_ld<K, SM>(Y, mid, len, err)) hi = mid;
                 else lo = mid;
             }
             r[q] = lo;
@@ -165,7 +167,7 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int32_t mid = (lo[q] + hi[q]) >> 1;
-                const bool lt = kz[q] < ls_ld<K, SM>(Y + mid);
+                const bool lt = kz[q] < ls_ld<K, SM>(Y, mid, len, err);
                 hi[q] = lt ? mid : hi[q];
                 lo[q] = lt ? lo[q] : mid;
             }
@@ -181,7 +183,7 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int32_t rr = i[q] | k;
-                if (!(kz[q] < ls_ld<K, SM>(Y + rr))) i[q] = rr;
+                if (!(kz[q] < ls_ld<K, SM>(Y, rr, len, err))) i[q] = rr;
             }
         }
 #pragma unroll
@@ -196,7 +198,7 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int32_t rr = i[q] | k;
-                if (!(kz[q] < ls_ld<K, SM>(Y + rr))) i[q] = rr;
+                if (!(kz[q] < ls_ld<K, SM>(Y, rr, len, err))) i[q] = rr;
             }
         }
         for (; k > 0; k >>= 1) {
@@ -204,7 +206,7 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
             for (int q = 0; q < NQ; ++q) {
                 const int32_t rr = i[q] | k;
                 const int32_t w = rr < N ? rr : N;
-                if (!(kz[q] < ls_ld<K, SM>(Y + w))) i[q] = rr;
+                if (!(kz[q] < ls_ld<K, SM>(Y, w, len, err))) i[q] = rr;
             }
         }
 #pragma unroll
@@ -214,14 +216,14 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
         int32_t i[NQ];
         const int32_t F0 = (int32_t)c0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) i[q] = !(kz[q] < ls_ld<K, SM>(Y + F0)) ? F0 : 0;
+        for (int q = 0; q < NQ; ++q) i[q] = !(kz[q] < ls_ld<K, SM>(Y, F0, len, err)) ? F0 : 0;
         int32_t S = (int32_t)c1;
         for (long long j = 0; j < c2; ++j) {
             const int32_t h = S >> 1;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
                 const int32_t F = i[q] + h;
-                if (!(kz[q] < ls_ld<K, SM>(Y + F))) i[q] = F;
+                if (!(kz[q] < ls_ld<K, SM>(Y, F, len, err))) i[q] = F;
             }
             S -= h;
         }
@@ -232,10 +234,10 @@ __device__ __forceinline__ void ls_run(const K *Y, long long c0, long long c1, l
         int32_t P[NQ];
         const int32_t L = (int32_t)c0;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) P[q] = !(kz[q] < ls_ld<K, SM>(Y)) ? 2 : 1;
+        for (int q = 0; q < NQ; ++q) P[q] = !(kz[q] < ls_ld<K, SM>(Y, 0, len, err)) ? 2 : 1;
         for (int32_t l = 1; l < L; ++l) {
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) P[q] = 2 * P[q] + (!(kz[q] < ls_ld<K, SM>(Y + P[q])) ? 2 : 1);
+            for (int q = 0; q < NQ; ++q) P[q] = 2 * P[q] + (!(kz[q] < ls_ld<K, SM>(Y, P[q], len, err)) ? 2 : 1);
         }
 #pragma unroll
         for (int q = 0; q < NQ; ++q) r[q] = P[q] - (1 << L);
@@ -254,7 +256,7 @@ __device__ __forceinline__ void ls_answer(const typename LsKey<T>::K *Y, const L
         over[q] = LsKey<T>::nan(z[q]) ? -1 : (k < a.k0 ? -1 : (!(k < a.kN) ? a.N : -2));
         kz[q] = over[q] == -2 ? k : a.k0;
     }
-    ls_run<K, METHOD, NQ, SM>(Y, a.c0, a.c1, a.c2, a.N, kz, r);
+    ls_run<K, METHOD, NQ, SM>(Y, a.c0, a.c1, a.c2, a.N, kz, r, a.len, a.err);
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
         if (over[q] != -2) r[q] = over[q];
@@ -423,6 +425,7 @@ static ds_status ls_search_typed(const ds_lsearch *h, const void *Z, long long m
     a.I = I;
     a.m = m;
     a.err = h->dev_err;
+    a.len = h->len;
     constexpr int L = VecOf<T>::L;
     const bool vec = ((uintptr_t)Z % 16 == 0) && ((uintptr_t)I % (L * sizeof(int32_t)) == 0);
     const void *fn = ls_kernel<T>(h->method, vec, h->smem);

@@ -70,7 +70,7 @@ struct __align__(16) ArrDesc {
     double XN;            // last knot
     float uscale;         // learned: u = (narrow(z) - x0f) * uscale (float32), 1 / (X_N - X_0)
     float x0f;            // learned: narrow(X0)
-    long long rsv;        // reserved (0)
+    long long n_esc;      // learned: escaped blocks in the overflow area of the cell table
     int32_t seg_off;      // learned: first predictor segment in the model tables
     int32_t seg_n;        // learned: number of predictor segments
     long long ct;          // learned: byte offset of the cell table K (C + 1 values) in the engine's ctab
@@ -253,13 +253,14 @@ template <typename T> __device__ __forceinline__ bool lt_exact(T a, T b)
 // z < X_{lo+n} (fixed depth, Algorithm binaryoptnopad on X[lo .. lo+n]);
 // `top` = 2^floor(log2 n) (or any larger power of two); knot i at X[i xs].
 template <typename T>
-__device__ __forceinline__ int32_t bisect(const T *X, int xs, int32_t lo, int32_t n, int32_t top, T z)
+__device__ __forceinline__ int32_t bisect(const T *X, int xs, int32_t lo, int32_t n, int32_t top, T z, long long n_x,
+                                          int *err)
 {
     int32_t i = 0;
     for (int32_t k = top; k > 0; k >>= 1) {
         const int32_t r = i | k;
         const int32_t w = r < n ? r : n;
-        if (!lt_exact<T>(z, X[(size_t)(lo + w) * xs])) i = r;
+        if (!lt_exact<T>(z, X[(size_t)in_bounds(lo + w, n_x, BS_X, err) * xs])) i = r;
     }
     return lo + (i < n ? i : n);
 }
@@ -303,15 +304,19 @@ __device__ __forceinline__ void interp_values(const BatchArgs<T> &a, const ArrDe
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
-            v[q] = ival_of<T>(pair_ld(Xg, i), pair_ld(Xg, i + 1));
+            v[q] = ival_of<T>(pair_ld(Xg, in_bounds(i, (long long)d.n + 1, BS_X, a.err)),
+                              pair_ld(Xg, in_bounds(i + 1, (long long)d.n + 1, BS_X, a.err)));
         }
     } else {
         const T *Y = a.Y + d.yoff;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const int32_t i = r[q] >= 0 && r[q] < d.n ? r[q] : 0;
-            v[q].x0 = __ldg(Xg + i); v[q].x1 = __ldg(Xg + i + 1);
-            v[q].y0 = __ldg(Y + i); v[q].y1 = __ldg(Y + i + 1);
+            const long long n1 = (long long)d.n + 1;
+            v[q].x0 = __ldg(Xg + in_bounds(i, n1, BS_X, a.err));
+            v[q].x1 = __ldg(Xg + in_bounds(i + 1, n1, BS_X, a.err));
+            v[q].y0 = __ldg(Y + in_bounds(i, n1, BS_Y, a.err));
+            v[q].y1 = __ldg(Y + in_bounds(i + 1, n1, BS_Y, a.err));
         }
     }
 #pragma unroll

@@ -40,13 +40,13 @@ __device__ __forceinline__ float pred_u(T z, const ArrDesc &d)
 // the whole line: Eq. fprop holds for it, which is all the table of Eq.
 // indexdef needs.  Negative t and NaN give cell J_0 = 0, t >= G cell J_G.
 template <typename T>
-__device__ __forceinline__ uint32_t learned_cell(T z, const ArrDesc &d, const uint2 *M, uint32_t G)
+__device__ __forceinline__ uint32_t learned_cell(T z, const ArrDesc &d, const uint2 *M, uint32_t G, int *err)
 {
     const float t = __fmul_rn(pred_u<T>(z, d), (float)G);
     uint32_t g = __float2uint_rz(t);
     g = g < G - 1u ? g : G - 1u;
     const float fr = __fsub_rn(t, __uint2float_rn(g));
-    const uint2 J = M[g];
+    const uint2 J = M[in_bounds(g, (long long)G, BS_CMAP, err)];
     const uint32_t D = J.y - J.x;
     const uint32_t k = __float2uint_rz(__fmul_rn(__uint2float_rn(D), fr));
     return J.x + (k < D ? k : D);
@@ -64,12 +64,14 @@ __device__ __forceinline__ uint32_t lblk_field(uint4 w, uint32_t r)
     return __funnelshift_r(lo, hi, o & 31u) & 0xFFFu;
 }
 __device__ __forceinline__ void learned_bounds(const unsigned char *ct, uint32_t R, uint32_t j, uint32_t *t0,
-                                               uint32_t *t1)
+                                               uint32_t *t1, long long n_esc, int *err)
 {
-    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(ct) + (j >> LBLK_SHIFT));
+    const uint4 w = __ldg(reinterpret_cast<const uint4 *>(ct) +
+                          in_bounds(j >> LBLK_SHIFT, (long long)lblk_count(R), BS_CBLOCK, err));
     const uint32_t r = j & 7u;
     if (w.x & LBLK_ESC) {
-        const uint32_t *O = reinterpret_cast<const uint32_t *>(ct + lblk_count(R) * 16ull) + (size_t)w.y * 9u;
+        const uint32_t *O = reinterpret_cast<const uint32_t *>(ct + lblk_count(R) * 16ull) +
+                            (size_t)in_bounds(w.y, n_esc, BS_CESC, err) * 9u;
         *t0 = __ldg(O + r);
         *t1 = __ldg(O + r + 1u);
     } else {
@@ -142,13 +144,15 @@ __device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrD
     const int xs = d.xs;
     uint32_t t0[NQ], t1[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) learned_bounds(ct, d.R, learned_cell<T>(z[q], d, M, G), &t0[q], &t1[q]);
+    for (int q = 0; q < NQ; ++q)
+        learned_bounds(ct, d.R, learned_cell<T>(z[q], d, M, G, a.err), &t0[q], &t1[q], d.n_esc, a.err);
+    const long long n1 = (long long)d.n + 1;
     T xa[NQ], xb[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
         const bool any = t1[q] > t0[q];
-        xa[q] = any ? __ldg(X + (size_t)t0[q] * xs) : T(0);
-        xb[q] = any ? __ldg(X + (size_t)(t1[q] - 1u) * xs) : T(0);
+        xa[q] = any ? __ldg(X + (size_t)in_bounds(t0[q], n1, BS_X, a.err) * xs) : T(0);
+        xb[q] = any ? __ldg(X + (size_t)in_bounds(t1[q] - 1u, n1, BS_X, a.err) * xs) : T(0);
     }
     bool inner = false;
 #pragma unroll
@@ -165,7 +169,7 @@ __device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrD
         for (int q = 0; q < NQ; ++q)
             if (r[q] == -2) {
                 const int32_t n = (int32_t)(t1[q] - t0[q]) - 1;
-                r[q] = bisect<T>(X, xs, (int32_t)t0[q], n, 1 << (31 - __clz(n)), z[q]);
+                r[q] = bisect<T>(X, xs, (int32_t)t0[q], n, 1 << (31 - __clz(n)), z[q], n1, a.err);
             }
     }
 #pragma unroll
@@ -195,22 +199,25 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             j[q] = cell_q<T, FASTF>(f, d.R, z[q], &g[q]);
-            w[q] = tab_ld<SM>(Rt + (j[q] >> RANK_SHIFT), pol);
+            w[q] = tab_ld<SM>(Rt + in_bounds(j[q] >> RANK_SHIFT, ((long long)d.R >> RANK_SHIFT) + 1, BS_RANK, a.err),
+                              pol);
         }
         RankHit h[NQ];
         uint32_t kf[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             h[q] = rank_decode(w[q], j[q]);
-            kf[q] = fp && h[q].knot ? tab_ld<SM>(Gt + h[q].t, pol) : 0u;
+            kf[q] = fp && h[q].knot ? tab_ld<SM>(Gt + in_bounds(h[q].t, (long long)d.n + 1, BS_FPRINT, a.err), pol)
+                                    : 0u;
         }
         T x[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const bool need = h[q].knot && (!fp || g[q] == kf[q]);
-            const size_t xi = KIND == KIND_DIRECT_XY ? (size_t)h[q].t * 2u
-                              : direct_kind(KIND)        ? (size_t)h[q].t
-                                                         : (size_t)h[q].t * d.xs;
+            const uint32_t t = in_bounds(h[q].t, (long long)d.n + 1, BS_X, a.err);
+            const size_t xi = KIND == KIND_DIRECT_XY ? (size_t)t * 2u
+                              : direct_kind(KIND)        ? (size_t)t
+                                                         : (size_t)t * d.xs;
             x[q] = need ? tab_ld<false>(X + xi, pol) : T(0);
         }
 #pragma unroll
@@ -247,7 +254,8 @@ __device__ __forceinline__ void answer_block(const BatchArgs<T> &a, const ArrDes
         for (int q = 0; q < NQ; ++q) {
             const int32_t rr = i[q] | k;
             const int32_t w = rr < n[q] ? rr : n[q];
-            if (!lt_exact<T>(z[q], tab_ld<SM>(X + (size_t)(lo[q] + w) * d.xs, pol))) i[q] = rr;
+            const size_t xi = (size_t)in_bounds(lo[q] + w, (long long)d.n + 1, BS_X, a.err) * d.xs;
+            if (!lt_exact<T>(z[q], tab_ld<SM>(X + xi, pol))) i[q] = rr;
         }
     }
 #pragma unroll

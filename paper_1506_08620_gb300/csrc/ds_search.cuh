@@ -73,6 +73,7 @@ template <typename T> struct SearchArgs {
     int32_t *I;
     long long m;
     int *err;
+    long long n_x;        // N+1 (the extent of X, for the range-checking build)
 };
 
 template <typename T> struct VecOf;
@@ -101,8 +102,10 @@ __device__ __forceinline__ uint32_t cell_of(T z, const SearchArgs<T> &a)
 
 // Table entry of cell j: flagged t = K_j, and for the cache layout X_{K_j}.
 template <typename T, bool CACHE, bool SMEM>
-__device__ __forceinline__ uint32_t gather_k(uint32_t j, const uint32_t *K, const Pair<T> *P, T *x_out)
+__device__ __forceinline__ uint32_t gather_k(uint32_t j, const uint32_t *K, const Pair<T> *P, T *x_out,
+                                             const SearchArgs<T> &a)
 {
+    j = in_bounds(j, (long long)a.R + 1, BS_K, a.err);
     if constexpr (CACHE) {
         if constexpr (SMEM) {
             const Pair<T> p = P[j];
@@ -124,8 +127,9 @@ __device__ __forceinline__ uint32_t gather_k(uint32_t j, const uint32_t *K, cons
 }
 
 template <typename T, bool SMEM>
-__device__ __forceinline__ T gather_x(int32_t t, const T *X)
+__device__ __forceinline__ T gather_x(int32_t t, const T *X, const SearchArgs<T> &a)
 {
+    t = in_bounds(t, a.n_x, BS_X, a.err);
     if constexpr (SMEM) return X[t];
     else return __ldg(X + t);
 }
@@ -165,8 +169,10 @@ __device__ __forceinline__ bool z_less(T z, T x)
 // z < X_{t-1} the answer lies in [max(t - q, -1), t - 2] and is found by
 // bisection with X_{t-q} < z.
 template <typename T, bool INTOPS, bool SMEM>
-__device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, T xp, const T *X, int32_t q, int checked)
+__device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, T xp, const T *X, const SearchArgs<T> &args)
 {
+    const int32_t q = args.q;
+    const int checked = args.checked;
     const int32_t t = (int32_t)(e & GEN_T_MASK);
     int32_t i = t;
     if ((e & KNOT_FLAG) && z_less<T, INTOPS>(z, x)) {
@@ -175,7 +181,7 @@ __device__ __forceinline__ int32_t correct_gen(T z, uint32_t e, T x, T xp, const
             int32_t a = t - q < -1 ? -1 : t - q, b = t - 1;  // X_a <= z < X_b
             while (b - a > 1) {
                 const int32_t m = (a + b) >> 1;
-                if (z_less<T, INTOPS>(z, gather_x<T, SMEM>(m, X))) b = m;
+                if (z_less<T, INTOPS>(z, gather_x<T, SMEM>(m, X, args))) b = m;
                 else a = m;
             }
             i = a;
@@ -191,16 +197,16 @@ __device__ __forceinline__ int32_t lookup(T z, const uint32_t *K, const T *X, co
 {
     const uint32_t j = cell_of<T, FM, INTOPS>(z, a);
     T x = T(0);
-    const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x);
+    const uint32_t e = gather_k<T, CACHE, SMEM>(j, K, P, &x, a);
     if constexpr (GEN) {
         const int32_t t = (int32_t)(e & GEN_T_MASK);
         T xp = T(0);
-        if (e & KNOT_FLAG) x = gather_x<T, SMEM>(t, X);
-        if (e & KNOT_FLAG2) xp = gather_x<T, SMEM>(t - 1, X);
-        return correct_gen<T, INTOPS, SMEM>(z, e, x, xp, X, a.q, a.checked);
+        if (e & KNOT_FLAG) x = gather_x<T, SMEM>(t, X, a);
+        if (e & KNOT_FLAG2) xp = gather_x<T, SMEM>(t - 1, X, a);
+        return correct_gen<T, INTOPS, SMEM>(z, e, x, xp, X, a);
     } else {
         if constexpr (!CACHE) {
-            if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X);
+            if (e & KNOT_FLAG) x = gather_x<T, SMEM>((int32_t)(e & ~KNOT_FLAG), X, a);
         }
         return correct<T, INTOPS>(z, e, x, a.checked);
     }
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
             e[q] = cell_of<T, FM, INTOPS>(zs[q], a);
         }
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q]);
+        for (int q = 0; q < NQ; ++q) e[q] = gather_k<T, CACHE, SMEM>(e[q], K, P, &x[q], a);
         int32_t r[NQ];
         if constexpr (GEN) {
             T xp[NQ];
@@ -260,17 +266,16 @@ __global__ void __launch_bounds__(256) k_search_vec(SearchArgs<T> a, long long n
             for (int q = 0; q < NQ; ++q) {
                 const int32_t t = (int32_t)(e[q] & GEN_T_MASK);
                 xp[q] = T(0);
-                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>(t, X);
-                if (e[q] & KNOT_FLAG2) xp[q] = gather_x<T, SMEM>(t - 1, X);
+                if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>(t, X, a);
+                if (e[q] & KNOT_FLAG2) xp[q] = gather_x<T, SMEM>(t - 1, X, a);
             }
 #pragma unroll
-            for (int q = 0; q < NQ; ++q)
-                r[q] = correct_gen<T, INTOPS, SMEM>(zs[q], e[q], x[q], xp[q], X, a.q, a.checked);
+            for (int q = 0; q < NQ; ++q) r[q] = correct_gen<T, INTOPS, SMEM>(zs[q], e[q], x[q], xp[q], X, a);
         } else {
             if constexpr (!CACHE) {
 #pragma unroll
                 for (int q = 0; q < NQ; ++q)
-                    if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & ~KNOT_FLAG), X);
+                    if (e[q] & KNOT_FLAG) x[q] = gather_x<T, SMEM>((int32_t)(e[q] & ~KNOT_FLAG), X, a);
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q) r[q] = correct<T, INTOPS>(zs[q], e[q], x[q], a.checked);
@@ -336,7 +341,8 @@ __device__ __forceinline__ int32_t correct_bits(long long zb, uint32_t e, long l
 // (read by the caller under bits 31 and 30).
 template <bool SMEM>
 __device__ __forceinline__ int32_t correct_bits_gen(long long zb, uint32_t e, long long xb, long long xpb,
-                                                    const long long *Xb, uint64_t keep, int32_t q, int checked)
+                                                    const long long *Xb, uint64_t keep, int32_t q, int checked,
+                                                    long long n_x, int *err)
 {
     const long long kz = okey_bits(zb);
     const int32_t t = (int32_t)(e & GEN_T_MASK);
@@ -347,7 +353,7 @@ __device__ __forceinline__ int32_t correct_bits_gen(long long zb, uint32_t e, lo
             int32_t a = t - q < -1 ? -1 : t - q, b = t - 1;  // X_a <= z < X_b
             while (b - a > 1) {
                 const int32_t m = (a + b) >> 1;
-                const long long *px = Xb + m;
+                const long long *px = Xb + in_bounds(m, n_x, BS_X, err);
                 if (kz < okey_bits(SMEM ? *px : ld_keep(px, keep))) b = m;
                 else a = m;
             }
@@ -410,34 +416,45 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             if constexpr (CACHE) {
-                const longlong2 p = SMEM ? P[e[q]] : ld_keep(P + e[q], keep);
+                const longlong2 *pp = P + in_bounds(e[q], (long long)R + 1, BS_K, a.err);
+                const longlong2 p = SMEM ? *pp : ld_keep(pp, keep);
                 e[q] = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xb[q] = p.y;
             } else if constexpr (PACKED) {
                 const uint32_t j = e[q];
-                e[q] = unpack_cell(ld_keep(a.K16 + (__umulhi(j, 0xAAAAAAABu) >> 3), keep), j);
+                const uint32_t blk = in_bounds(__umulhi(j, 0xAAAAAAABu) >> 3, ((long long)R + PACK_CELLS) / PACK_CELLS,
+                                               BS_K16, a.err);
+                e[q] = unpack_cell(ld_keep(a.K16 + blk, keep), j);
             } else {
-                e[q] = SMEM ? K[e[q]] : ld_keep(K + e[q], keep);
+                const uint32_t *pk = K + in_bounds(e[q], (long long)R + 1, BS_K, a.err);
+                e[q] = SMEM ? *pk : ld_keep(pk, keep);
             }
         }
         if constexpr (GEN) {
             long long xpb[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) {
-                const long long *px = Xb + (e[q] & GEN_T_MASK);
+                const int32_t t = (int32_t)(e[q] & GEN_T_MASK);
                 xb[q] = 0;
                 xpb[q] = 0;
-                if (e[q] & KNOT_FLAG) xb[q] = SMEM ? px[0] : ld_keep(px, keep);
-                if (e[q] & KNOT_FLAG2) xpb[q] = SMEM ? px[-1] : ld_keep(px - 1, keep);
+                if (e[q] & KNOT_FLAG) {
+                    const long long *px = Xb + in_bounds(t, a.n_x, BS_X, a.err);
+                    xb[q] = SMEM ? *px : ld_keep(px, keep);
+                }
+                if (e[q] & KNOT_FLAG2) {
+                    const long long *px = Xb + in_bounds(t - 1, a.n_x, BS_X, a.err);
+                    xpb[q] = SMEM ? *px : ld_keep(px, keep);
+                }
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
                 const long long idx = b + (long long)v * blockDim.x;
                 if (idx < nvec)
                     __stcs(Iv + idx, make_int2(correct_bits_gen<SMEM>(zb[2 * v], e[2 * v], xb[2 * v], xpb[2 * v], Xb,
-                                                                      keep, a.q, a.checked),
+                                                                      keep, a.q, a.checked, a.n_x, a.err),
                                                correct_bits_gen<SMEM>(zb[2 * v + 1], e[2 * v + 1], xb[2 * v + 1],
-                                                                      xpb[2 * v + 1], Xb, keep, a.q, a.checked)));
+                                                                      xpb[2 * v + 1], Xb, keep, a.q, a.checked,
+                                                                      a.n_x, a.err)));
             }
         } else {
             if constexpr (!CACHE) {
@@ -445,7 +462,7 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
                 for (int q = 0; q < NQ; ++q) {
                     xb[q] = 0;
                     if (e[q] & KNOT_FLAG) {
-                        const long long *px = Xb + (e[q] & ~KNOT_FLAG);
+                        const long long *px = Xb + in_bounds((int32_t)(e[q] & ~KNOT_FLAG), a.n_x, BS_X, a.err);
                         xb[q] = SMEM ? *px : ld_keep(px, keep);
                     }
                 }
@@ -467,21 +484,24 @@ __global__ void __launch_bounds__(256) k_search_f64bits(SearchArgs<double> a, lo
             uint32_t e = cell_bits<FM>(zq, H, NW, X0, R);
             long long xq = 0;
             if constexpr (CACHE) {
-                const longlong2 p = P[e];
+                const longlong2 p = P[in_bounds(e, (long long)R + 1, BS_K, a.err)];
                 e = (uint32_t)(p.x & 0xFFFFFFFFll);
                 xq = p.y;
             } else if constexpr (PACKED) {
-                e = unpack_cell(a.K16[__umulhi(e, 0xAAAAAAABu) >> 3], e);
+                e = unpack_cell(a.K16[in_bounds(__umulhi(e, 0xAAAAAAABu) >> 3, ((long long)R + PACK_CELLS) / PACK_CELLS,
+                                                BS_K16, a.err)],
+                                e);
             } else {
-                e = K[e];
+                e = K[in_bounds(e, (long long)R + 1, BS_K, a.err)];
             }
             if constexpr (GEN) {
-                const long long *px = Xb + (e & GEN_T_MASK);
-                const long long xq0 = (e & KNOT_FLAG) ? px[0] : 0, xq1 = (e & KNOT_FLAG2) ? px[-1] : 0;
-                a.I[q] = correct_bits_gen<true>(zq, e, xq0, xq1, Xb, keep, a.q, a.checked);
+                const int32_t t = (int32_t)(e & GEN_T_MASK);
+                const long long xq0 = (e & KNOT_FLAG) ? Xb[in_bounds(t, a.n_x, BS_X, a.err)] : 0;
+                const long long xq1 = (e & KNOT_FLAG2) ? Xb[in_bounds(t - 1, a.n_x, BS_X, a.err)] : 0;
+                a.I[q] = correct_bits_gen<true>(zq, e, xq0, xq1, Xb, keep, a.q, a.checked, a.n_x, a.err);
             } else {
                 if constexpr (!CACHE) {
-                    if (e & KNOT_FLAG) xq = Xb[e & ~KNOT_FLAG];
+                    if (e & KNOT_FLAG) xq = Xb[in_bounds((int32_t)(e & ~KNOT_FLAG), a.n_x, BS_X, a.err)];
                 }
                 a.I[q] = correct_bits(zq, e, xq, a.checked);
             }

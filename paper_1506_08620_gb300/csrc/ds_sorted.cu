@@ -167,13 +167,18 @@ __global__ void __launch_bounds__(256) k_histogram(SearchArgs<T> a, unsigned lon
             // doubles as bit patterns: one FP64 instruction per query (as k_search_f64bits)
             const long long zb = __ldcs(reinterpret_cast<const long long *>(a.Z) + q);
             const long long *Xb = reinterpret_cast<const long long *>(a.X);
-            const uint32_t e = __ldg(a.K + cell_bits<FM>(zb, (double)a.H, -(double)a.W, (double)a.X0, a.R));
+            const uint32_t j = cell_bits<FM>(zb, (double)a.H, -(double)a.W, (double)a.X0, a.R);
+            const uint32_t e = __ldg(a.K + in_bounds(j, (long long)a.R + 1, BS_K, a.err));
             if constexpr (GEN) {
-                const long long *px = Xb + (e & GEN_T_MASK);
-                const long long xb = (e & KNOT_FLAG) ? __ldg(px) : 0, xpb = (e & KNOT_FLAG2) ? __ldg(px - 1) : 0;
-                i = correct_bits_gen<true>(zb, e, xb, xpb, Xb, 0, a.q, 1);  // plain loads in the bisection
+                const int32_t t = (int32_t)(e & GEN_T_MASK);
+                const long long xb = (e & KNOT_FLAG) ? __ldg(Xb + in_bounds(t, a.n_x, BS_X, a.err)) : 0;
+                const long long xpb = (e & KNOT_FLAG2) ? __ldg(Xb + in_bounds(t - 1, a.n_x, BS_X, a.err)) : 0;
+                i = correct_bits_gen<true>(zb, e, xb, xpb, Xb, 0, a.q, 1, a.n_x, a.err);  // plain loads in the bisection
             } else {
-                i = correct_bits(zb, e, (e & KNOT_FLAG) ? __ldg(Xb + (e & ~KNOT_FLAG)) : 0, 1);
+                i = correct_bits(zb, e,
+                                 (e & KNOT_FLAG) ? __ldg(Xb + in_bounds((int32_t)(e & ~KNOT_FLAG), a.n_x, BS_X, a.err))
+                                                 : 0,
+                                 1);
             }
         } else {
             i = lookup<T, FM, false, false, false, GEN>(__ldcs(a.Z + q), a.K, a.X, a.P, a);
@@ -226,6 +231,7 @@ static ds_status histogram_typed(const ds_index *idx, const void *Z, long long m
     a.Z = reinterpret_cast<const T *>(Z);
     a.m = m;
     a.err = idx->dev_err;
+    a.n_x = idx->n_knots;
     const long long nbins = idx->n_knots + 1;
     const size_t hbytes = (size_t)nbins * sizeof(uint32_t);
     const bool smh = hbytes <= 96 * 1024;
