@@ -165,11 +165,15 @@ __device__ __forceinline__ void learned_answer(const BatchArgs<T> &a, const ArrD
         }
     }
     if (inner) {
+        // X_{t0} <= z < X_{t1-1}: the answer is t0 plus the number of the knots
+        // strictly between those two that are <= z (none for two knots, so no
+        // read; otherwise a bisection over them alone)
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
             if (r[q] == -2) {
-                const int32_t n = (int32_t)(t1[q] - t0[q]) - 1;
-                r[q] = bisect<T>(X, xs, (int32_t)t0[q], n, 1 << (31 - __clz(n)), z[q], n1, a.err);
+                const int32_t n = (int32_t)(t1[q] - t0[q]) - 2;
+                r[q] = n == 0 ? (int32_t)t0[q]
+                              : bisect<T>(X, xs, (int32_t)t0[q], n, 1 << (31 - __clz(n)), z[q], n1, a.err);
             }
     }
 #pragma unroll
