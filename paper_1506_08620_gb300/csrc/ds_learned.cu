@@ -24,6 +24,7 @@ constexpr int HID = 32;
 constexpr int NP = HID + HID + HID * HID + HID + HID + 1;  // 1153
 constexpr int OW1 = 0, OB1 = 32, OW2 = 64, OB2 = 64 + 1024, OW3 = OB2 + 32, OB3 = OW3 + 32;
 constexpr int TB = 128;  // samples (threads) per training block
+static_assert(TB == 128, "the tensor-core gradient tiles W2 over four warps");
 constexpr size_t TH_BYTES = ((NP * sizeof(float) + 15) / 16) * 16;  // parameters at the head of shared memory
 constexpr float ADAM_B1 = 0.9f, ADAM_B2 = 0.999f, ADAM_EPS = 1e-8f;
 
@@ -84,63 +85,138 @@ struct GradTile {
     float H1[TB][HID + 1], DA1[TB][HID + 1], DA2[TB][HID + 1], H2[TB][HID + 1];
 };
 
-// Forward and backward of one sample (the calling thread's), written straight
-// into its row of the tile; returns out.  dscale = 2 / (batch size).  Layer 2
-// is accumulated as sum_m h1_m * W2[:, m] with the 32 outputs in registers;
-// the loops over m stay rolled (unrolling them lets the scheduler hoist all
-// 256 weight loads, which spills), and h1 lives in the tile row.
-__device__ __forceinline__ float mlp_sample(const float *sm, float u, float y, float dscale, GradTile &t)
+// ------------------------------------------------------------------ tensor cores for the 32x32 layer
+// The three products of the 32x32 layer in a training step (forward
+// A2 = H1 W2^T, backward DA1 = DA2 W2, gradient dW2 = DA2^T H1 over the
+// block's samples) run on the tensor cores as warp-level mma.sync m16n8k8 with
+// TF32 operands and FP32 accumulation, each operand split into a TF32 part
+// and a TF32 remainder (x = big + small, both exact in FP32) so that
+// big*big + big*small + small*big carries FP32 accuracy (the small*small term
+// lies below it).  The tiles are 32 samples x 32 units per warp (forward,
+// backward) and 16 x 16 units over the block's 128 samples (gradient).
+__device__ __forceinline__ uint32_t tf32_of(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &big, uint32_t &small)
+{
+    big = tf32_of(x);
+    small = tf32_of(x - __uint_as_float(big));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// acc[rt][ct] += A B over k in [0, K) for the output tiles (rows 16 rt .. +16,
+// columns 8 ct .. +8); A(row, k) and B(k, col) read the operands.  Fragment
+// layout of m16n8k8: lane = 4 g + c; A holds (g, c), (g+8, c), (g, c+4),
+// (g+8, c+4); B holds (c, g), (c+4, g); the accumulator (g, 2c), (g, 2c+1),
+// (g+8, 2c), (g+8, 2c+1).
+template <int RT, int CT, typename FA, typename FB>
+__device__ __forceinline__ void warp_mma_3xtf32(float (&acc)[RT][CT][4], int K, FA A, FB B)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll 1
+    for (int k0 = 0; k0 < K; k0 += 8) {
+        uint32_t ab[RT][4], as[RT][4], bb[CT][2], bs[CT][2];
+#pragma unroll
+        for (int rt = 0; rt < RT; ++rt) {
+            split_tf32(A(16 * rt + g, k0 + c), ab[rt][0], as[rt][0]);
+            split_tf32(A(16 * rt + g + 8, k0 + c), ab[rt][1], as[rt][1]);
+            split_tf32(A(16 * rt + g, k0 + c + 4), ab[rt][2], as[rt][2]);
+            split_tf32(A(16 * rt + g + 8, k0 + c + 4), ab[rt][3], as[rt][3]);
+        }
+#pragma unroll
+        for (int ct = 0; ct < CT; ++ct) {
+            split_tf32(B(k0 + c, 8 * ct + g), bb[ct][0], bs[ct][0]);
+            split_tf32(B(k0 + c + 4, 8 * ct + g), bb[ct][1], bs[ct][1]);
+        }
+#pragma unroll
+        for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+            for (int ct = 0; ct < CT; ++ct) {
+                mma_tf32(acc[rt][ct], as[rt], bb[ct]);
+                mma_tf32(acc[rt][ct], ab[rt], bs[ct]);
+                mma_tf32(acc[rt][ct], ab[rt], bb[ct]);
+            }
+    }
+}
+// Visit the accumulator's elements: f(row, col, value).
+template <int RT, int CT, typename F>
+__device__ __forceinline__ void warp_acc_each(const float (&acc)[RT][CT][4], F f)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int rt = 0; rt < RT; ++rt)
+#pragma unroll
+        for (int ct = 0; ct < CT; ++ct) {
+            f(16 * rt + g, 8 * ct + 2 * c, acc[rt][ct][0]);
+            f(16 * rt + g, 8 * ct + 2 * c + 1, acc[rt][ct][1]);
+            f(16 * rt + g + 8, 8 * ct + 2 * c, acc[rt][ct][2]);
+            f(16 * rt + g + 8, 8 * ct + 2 * c + 1, acc[rt][ct][3]);
+        }
+}
+
+// Forward and backward of the block's samples, one per thread (all threads
+// of each warp take part; a thread without a sample passes valid = false and
+// contributes nothing), written into the tile; returns the thread's out.
+// dscale = 2 / (batch size).
+__device__ __forceinline__ float mlp_sample(const float *sm, float u, float y, float dscale, bool valid, GradTile &t)
 {
     const float *th = sm;
-    const float4 *w2t = reinterpret_cast<const float4 *>(sm + W2T_OFF / sizeof(float));
-    const int s = threadIdx.x;
-    float a2[HID];
+    const float *w2t = sm + W2T_OFF / sizeof(float);
+    const int s = threadIdx.x, w0 = s & ~31;
+    // layer 1 (CUDA cores): h1 = relu(W1 u + b1)
+#pragma unroll 4
+    for (int m = 0; m < HID; ++m) t.H1[s][m] = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
+    __syncwarp();
+    // layer 2 (tensor cores): A2 = H1 W2^T + b2 for the warp's 32 samples, into H2
+    {
+        float acc[2][4][4];
 #pragma unroll
-    for (int n = 0; n < HID; ++n) a2[n] = th[OB2 + n];
-#pragma unroll 1
-    for (int m = 0; m < HID; ++m) {
-        const float h = relu(__fmaf_rn(th[OW1 + m], u, th[OB1 + m]));
-        t.H1[s][m] = h;
+        for (int ct = 0; ct < 4; ++ct) {
+            const int col = 8 * ct + 2 * (s & 3);
 #pragma unroll
-        for (int q = 0; q < HID / 4; ++q) {
-            const float4 w = w2t[m * (HID / 4) + q];
-            a2[4 * q + 0] = __fmaf_rn(w.x, h, a2[4 * q + 0]);
-            a2[4 * q + 1] = __fmaf_rn(w.y, h, a2[4 * q + 1]);
-            a2[4 * q + 2] = __fmaf_rn(w.z, h, a2[4 * q + 2]);
-            a2[4 * q + 3] = __fmaf_rn(w.w, h, a2[4 * q + 3]);
+            for (int rt = 0; rt < 2; ++rt) {
+                acc[rt][ct][0] = acc[rt][ct][2] = th[OB2 + col];
+                acc[rt][ct][1] = acc[rt][ct][3] = th[OB2 + col + 1];
+            }
         }
+        warp_mma_3xtf32<2, 4>(acc, HID, [&](int r, int k) { return t.H1[w0 + r][k]; },
+                              [&](int k, int n) { return w2t[k * HID + n]; });
+        warp_acc_each<2, 4>(acc, [&](int r, int n, float v) { t.H2[w0 + r][n] = v; });
     }
+    __syncwarp();
+    // output, loss and the output gradient (CUDA cores); da2 into DA2
     float out = th[OB3];
-#pragma unroll
+#pragma unroll 4
+    for (int n = 0; n < HID; ++n) out = __fmaf_rn(th[OW3 + n], relu(t.H2[s][n]), out);
+    const float d = valid ? dscale * (out - y) : 0.f;
+#pragma unroll 4
     for (int n = 0; n < HID; ++n) {
-        const float h2 = relu(a2[n]);
-        t.H2[s][n] = h2;
-        out = __fmaf_rn(th[OW3 + n], h2, out);
+        const float a2 = t.H2[s][n];
+        t.DA2[s][n] = a2 > 0.f ? d * th[OW3 + n] : 0.f;
+        t.H2[s][n] = relu(a2);
     }
-    const float d = dscale * (out - y);
-    // da2 replaces a2 (a2 > 0 exactly where h2 > 0)
-#pragma unroll
-    for (int n = 0; n < HID; ++n) {
-        a2[n] = a2[n] > 0.f ? d * th[OW3 + n] : 0.f;
-        t.DA2[s][n] = a2[n];
-    }
-#pragma unroll 1
-    for (int m = 0; m < HID; ++m) {
-        float acc = 0.f;
-#pragma unroll
-        for (int q = 0; q < HID / 4; ++q) {
-            const float4 w = w2t[m * (HID / 4) + q];
-            acc = __fmaf_rn(w.x, a2[4 * q + 0], acc);
-            acc = __fmaf_rn(w.y, a2[4 * q + 1], acc);
-            acc = __fmaf_rn(w.z, a2[4 * q + 2], acc);
-            acc = __fmaf_rn(w.w, a2[4 * q + 3], acc);
-        }
-        t.DA1[s][m] = t.H1[s][m] > 0.f ? acc : 0.f;  // a1 > 0 exactly where h1 > 0
+    __syncwarp();
+    // back through layer 2 (tensor cores): DA1 = (DA2 W2) where a1 > 0
+    {
+        float acc[2][4][4] = {};
+        warp_mma_3xtf32<2, 4>(acc, HID, [&](int r, int k) { return t.DA2[w0 + r][k]; },
+                              [&](int k, int m) { return th[OW2 + k * HID + m]; });
+        warp_acc_each<2, 4>(acc, [&](int r, int m, float v) {
+            t.DA1[w0 + r][m] = t.H1[w0 + r][m] > 0.f ? v : 0.f;  // a1 > 0 exactly where h1 > 0
+        });
     }
     t.U[s] = u;
     t.DOUT[s] = d;
     const float r = out - y;
-    t.LOSS[s] = r * r;
+    t.LOSS[s] = valid ? r * r : 0.f;
     return out;
 }
 
@@ -170,32 +246,19 @@ __device__ __forceinline__ float mlp_forward1(const float *sm, float u)
 }
 
 // Sum of the per-sample gradients of the tile's `count` samples, in parameter
-// order.  The 32x32 block of W2 is a product DA2^T H1 over the samples: each
-// thread of a 128-thread block owns 4 rows x 2 columns of it; the other 129
-// parameters take one thread each.
+// order (rows past `count` hold zero gradients).  The 32x32 block of W2 is the
+// product DA2^T H1 over the block's samples, on the tensor cores: warp w of
+// the four computes rows 16 (w / 2) .. +16 and columns 16 (w % 2) .. +16; the
+// other 129 parameters take one thread each.
 __device__ __forceinline__ void tile_gradient(const GradTile &t, int count, float *gout)
 {
     const int tid = threadIdx.x;
-    for (int base = 0; base < HID * HID; base += 8 * blockDim.x) {
-        const int cell = base / 8 + tid;  // 4 x 2 block index
-        if (cell < HID * HID / 8) {
-            const int n0 = (cell / (HID / 2)) * 4, m0 = (cell % (HID / 2)) * 2;
-            float g[4][2] = {};
-            for (int s = 0; s < count; ++s) {
-                const float h0 = t.H1[s][m0], h1 = t.H1[s][m0 + 1];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float dn = t.DA2[s][n0 + k];
-                    g[k][0] = __fmaf_rn(dn, h0, g[k][0]);
-                    g[k][1] = __fmaf_rn(dn, h1, g[k][1]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                gout[OW2 + (n0 + k) * HID + m0] = g[k][0];
-                gout[OW2 + (n0 + k) * HID + m0 + 1] = g[k][1];
-            }
-        }
+    {
+        const int w = tid >> 5, n0 = 16 * (w >> 1), m0 = 16 * (w & 1);
+        float acc[1][2][4] = {};
+        warp_mma_3xtf32<1, 2>(acc, TB, [&](int r, int s) { return t.DA2[s][n0 + r]; },
+                              [&](int s, int m) { return t.H1[s][m0 + m]; });
+        warp_acc_each<1, 2>(acc, [&](int r, int m, float v) { gout[OW2 + (n0 + r) * HID + m0 + m] = v; });
     }
     // W1, b1, b2, W3, b3: 129 sums over the samples
     for (int q = tid; q < 4 * HID + 1; q += blockDim.x) {
@@ -240,7 +303,8 @@ __global__ void __launch_bounds__(TB) k_grad_explicit(const float *theta, const 
     __syncthreads();
     const long long i = (long long)blockIdx.x * TB + threadIdx.x;
     const int count = (int)min((long long)TB, n - (long long)blockIdx.x * TB);
-    if (i < n) mlp_sample(sm, u[i], y[i], 2.0f / (float)n, t);
+    const bool valid = i < n;  // every thread takes part in the warps' tensor-core products
+    mlp_sample(sm, valid ? u[i] : 0.f, valid ? y[i] : 0.f, 2.0f / (float)n, valid, t);
     __syncthreads();
     tile_gradient(t, count, partial + (size_t)blockIdx.x * NP);
     if (threadIdx.x == 0) partial_loss[blockIdx.x] = tile_loss(t, count);
@@ -331,7 +395,7 @@ __global__ void __launch_bounds__(TB) k_train_grad(TrainArgs a)
         y = (float)i / (float)d.n;
     }
     const float res = y - u;  // the network's target: deviation from the linear model
-    mlp_sample(sm, u, res, 2.0f / (float)(a.gb * TB), t);
+    mlp_sample(sm, u, res, 2.0f / (float)(a.gb * TB), true, t);
     __syncthreads();
     tile_gradient(t, TB, a.partial + ((size_t)model * a.gb + blockIdx.x) * NP);
     if (threadIdx.x == 0) a.partial_loss[(size_t)model * a.gb + blockIdx.x] = tile_loss(t, TB);
