@@ -411,7 +411,11 @@ DS_API ds_status ds_learned_search_host(ds_learned *L, const void *Zcat_host, co
  * same engine serves the learned form), keep the fastest in the handle and
  * return it in *best.  Single array: z_off_dev = NULL and m queries.  With
  * y_out_dev (and Ycat_dev, as for ds_learned_search) the configurations are
- * timed with the interpolation.  The outputs are overwritten with valid
+ * timed with the interpolation.  A handle with direct and learned arrays
+ * searches each group with its own kernel launch: after the common
+ * configuration the autotuner tunes each launch with the other held fixed,
+ * keeps both in the handle, and returns the direct launch's in *best (with
+ * the time of the whole search).  The outputs are overwritten with valid
  * results.  Synchronous. */
 DS_API ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const int64_t *z_off_dev, int64_t m,
                                      const void *Ycat_dev, void *y_out_dev, int32_t *Icat_dev, void *stream,
@@ -419,7 +423,9 @@ DS_API ds_status ds_learned_autotune(ds_learned *L, const void *Zcat_dev, const 
 /* Set or read the launch configuration of the learned search, as
  * ds_batch_set_tune / ds_batch_get_tune (DS_E_ARG for an smem_limit outside
  * [-1, the device's opt-in limit - 2048] or a configuration that cannot be
- * resident). */
+ * resident).  Set applies the configuration to every launch of the search;
+ * get reads the first launch's (the direct arrays' on a handle with direct
+ * and learned arrays). */
 DS_API ds_status ds_learned_set_tune(ds_learned *L, const ds_tune_t *cfg);
 DS_API ds_status ds_learned_get_tune(const ds_learned *L, ds_tune_t *cfg);
 

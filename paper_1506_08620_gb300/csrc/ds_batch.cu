@@ -49,14 +49,15 @@ constexpr int PLAN_ROUNDS = 8;
 
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
                               const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
-                              unsigned long long *counter, int split)
+                              unsigned long long *counter, int split, long long chunk1, uint32_t smem_limit1)
 {
     // chunks of the array at claim position p
     auto chunks_at = [&](int p) -> long long {
         const int a = order ? order[p] : p;
         long long q = z_off ? z_off[a + 1] - z_off[a] : m_single;
         q = q < 0 ? 0 : q;
-        const long long c = chunk_len(desc[a], chunk, smem_limit);
+        const bool second = split > 0 && p >= split;
+        const long long c = chunk_len(desc[a], second ? chunk1 : chunk, second ? smem_limit1 : smem_limit);
         return (q + c - 1) / c;
     };
     const int B = blockDim.x, rounds = (n_arrays + B - 1) / B;
@@ -601,33 +602,44 @@ static ds_status launch_search(const Engine *e, const void *fn, int grid, int bl
 
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
                                long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s,
-                               bool host_io)
+                               bool host_io, const ds_tune_t *t2)
 {
     const bool interp = y_out != nullptr;
     const int L = e->dtype == DS_F32 ? 4 : 2;
     const bool vec = ((uintptr_t)Z % 16 == 0) && ((uintptr_t)I % (L * 4) == 0) &&
                      (!interp || (uintptr_t)y_out % 16 == 0);
     const int n_launch = e->split > 0 ? 2 : 1;
-    int grid[2] = {0, 0};
-    for (int g = 0; g < n_launch; ++g) DS_TRY(occupancy(e, t, interp, vec, &grid[g], g));
-    const int block = eff_block(e, t, vec), vpt = clamp_vpt(t.items);
-    const bool warps = vec && t.smem_limit < 0;  // nothing staged, and warps claim their own chunks
-    const int tiles = warps ? CHUNK_TILES_WARP : direct_only(e) ? CHUNK_TILES_DIRECT : CHUNK_TILES;
-    const long long chunk = (long long)(warps ? 32 : block) * vpt * L * tiles;
-    const uint32_t smem_limit = (uint32_t)std::max(0, t.smem_limit);
-    k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, chunk, e->desc_dev, e->order, smem_limit,
-                                     e->chunk_off, e->counter, e->split);
+    // each launch's configuration: block, vectors per thread, claims, chunk base, staging limit
+    struct Cfg {
+        int grid, block, vpt;
+        bool warps;
+        long long chunk;
+        uint32_t smem_limit;
+    } c[2];
+    for (int g = 0; g < n_launch; ++g) {
+        const ds_tune_t &tg = g == 1 && t2 ? *t2 : t;
+        DS_TRY(occupancy(e, tg, interp, vec, &c[g].grid, g));
+        c[g].block = eff_block(e, tg, vec);
+        c[g].vpt = clamp_vpt(tg.items);
+        c[g].warps = vec && tg.smem_limit < 0;  // nothing staged, and warps claim their own chunks
+        const int tiles = c[g].warps ? CHUNK_TILES_WARP : direct_only(e) ? CHUNK_TILES_DIRECT : CHUNK_TILES;
+        c[g].chunk = (long long)(c[g].warps ? 32 : c[g].block) * c[g].vpt * L * tiles;
+        c[g].smem_limit = (uint32_t)std::max(0, tg.smem_limit);
+    }
+    const Cfg &c1 = c[n_launch - 1];
+    k_plan_chunks<<<1, 1024, 0, s>>>(z_off, m_single, e->n_arrays, c[0].chunk, e->desc_dev, e->order, c[0].smem_limit,
+                                     e->chunk_off, e->counter, e->split, c1.chunk, c1.smem_limit);
     DS_TRY_CUDA(cudaGetLastError());
     for (int g = 0; g < n_launch; ++g) {
         // split handle: the direct arrays' positions [0, split), then the learned ones
         const int n_pos = n_launch == 2 && g == 0 ? e->split : e->n_arrays;
-        const void *fn = pick_kernel(e, vpt, interp, vec, warps, block == 1024, g);
+        const void *fn = pick_kernel(e, c[g].vpt, interp, vec, c[g].warps, c[g].block == 1024, g);
         unsigned long long *counter = e->counter + g;
         DS_TRY(e->dtype == DS_F32
-                   ? launch_search<float>(e, fn, grid[g], block, smem_limit, chunk, n_pos, counter, Z, z_off, m_single,
-                                          Y, y_out, I, s, host_io)
-                   : launch_search<double>(e, fn, grid[g], block, smem_limit, chunk, n_pos, counter, Z, z_off,
-                                           m_single, Y, y_out, I, s, host_io));
+                   ? launch_search<float>(e, fn, c[g].grid, c[g].block, c[g].smem_limit, c[g].chunk, n_pos, counter, Z,
+                                          z_off, m_single, Y, y_out, I, s, host_io)
+                   : launch_search<double>(e, fn, c[g].grid, c[g].block, c[g].smem_limit, c[g].chunk, n_pos, counter,
+                                           Z, z_off, m_single, Y, y_out, I, s, host_io));
     }
     return DS_OK;
 }
@@ -643,9 +655,10 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
     DS_TRY_CUDA(cudaStreamIsCapturing(s, &cs));
     static const bool no_graph = getenv("DS_NO_GRAPH") != nullptr;
     if (cs != cudaStreamCaptureStatusNone || no_graph)
-        return engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, s);
+        return engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, s, false, &e->tune2);
     const void *key[6] = {Z, z_off, (const void *)(uintptr_t)m_single, Y, y_out, I};
-    const bool same = e->gexec && !memcmp(key, e->gkey, sizeof(key)) && !memcmp(&e->tune, &e->gtune, sizeof(ds_tune_t));
+    const bool same = e->gexec && !memcmp(key, e->gkey, sizeof(key)) && !memcmp(&e->tune, &e->gtune, sizeof(ds_tune_t)) &&
+                      !memcmp(&e->tune2, &e->gtune2, sizeof(ds_tune_t));
     if (!same) {
         if (e->gexec) {
             cudaGraphExecDestroy(e->gexec);
@@ -654,7 +667,7 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
         if (!e->gstream) DS_TRY_CUDA(cudaStreamCreateWithFlags(&e->gstream, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         DS_TRY_CUDA(cudaStreamBeginCapture(e->gstream, cudaStreamCaptureModeThreadLocal));
-        ds_status rc = engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, e->gstream);
+        ds_status rc = engine_launch_direct(e, e->tune, Z, z_off, m_single, Y, y_out, I, e->gstream, false, &e->tune2);
         cudaError_t ce = cudaStreamEndCapture(e->gstream, &g);
         if (rc != DS_OK) {
             if (g) cudaGraphDestroy(g);
@@ -673,6 +686,7 @@ ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long l
         }
         memcpy(e->gkey, key, sizeof(key));
         e->gtune = e->tune;
+        e->gtune2 = e->tune2;
     }
     DS_TRY_CUDA(cudaGraphLaunch(e->gexec, s));
     return DS_OK;
@@ -692,9 +706,14 @@ ds_status engine_set_tune(Engine *e, const ds_tune_t &cfg)
     int grid = 0;
     for (int g = 0; g < (e->split > 0 ? 2 : 1); ++g) DS_TRY(occupancy(e, t, false, true, &grid, g));
     e->tune = t;
+    e->tune2 = t;
     return DS_OK;
 }
 
+// Times every configuration (4 block sizes x 3 vectors per thread x 7
+// staging settings) and keeps the fastest.  On a split handle it then tunes
+// each launch with the other fixed at the best so far: the direct launch,
+// then the learned one.
 ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
                           void *y_out, int32_t *I, cudaStream_t s, ds_tune_t *best_out)
 {
@@ -704,52 +723,65 @@ ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long
     cudaEvent_t e0, e1;
     DS_TRY_CUDA(cudaEventCreate(&e0));
     DS_TRY_CUDA(cudaEventCreate(&e1));
-    ds_tune_t best;
-    memset(&best, 0, sizeof(best));
-    best.ms = 1e30f;
-    ds_status rc = DS_OK;
-    for (int b : blocks)
-        for (int it : items)
-            for (int sm : smems) {
-                if (sm > e->props.max_smem_optin - 2048) continue;
-                if (b == 1024 && (it != 1 || sm < 0 || !direct_only(e))) continue;  // runs as 512
-                ds_tune_t t;
-                memset(&t, 0, sizeof(t));
-                t.block = b;
-                t.items = it;
-                t.smem_limit = sm;
-                int grid = 0;
-                if (occupancy(e, t, y_out != nullptr, true, &grid) != DS_OK) continue;
-                if (e->split > 0 && occupancy(e, t, y_out != nullptr, true, &grid, 1) != DS_OK) continue;
-                rc = engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
-                if (rc != DS_OK) break;
-                // the best of three timings of two launches each (a single timing
-                // lets clock and power swings pick the configuration)
-                float ms = 1e30f;
-                for (int rep = 0; rep < 3 && rc == DS_OK; ++rep) {
-                    cudaEventRecord(e0, s);
-                    for (int r = 0; r < 2; ++r) engine_launch_direct(e, t, Z, z_off, m_single, Y, y_out, I, s);
-                    cudaEventRecord(e1, s);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) {
-                        rc = DS_E_CUDA;
-                        set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
-                        break;
-                    }
-                    float one = 0;
-                    cudaEventElapsedTime(&one, e0, e1);
-                    ms = std::min(ms, one / 2);
-                }
-                if (rc != DS_OK) break;
-                if (ms < best.ms) {
-                    best = t;
-                    best.ms = ms;
-                }
+    const bool interp = y_out != nullptr;
+    // the best of three timings of two launches each (a single timing lets
+    // clock and power swings pick the configuration); ms < 0 on an error
+    auto time_of = [&](const ds_tune_t &t0, const ds_tune_t &t1, ds_status *rc) -> float {
+        *rc = engine_launch_direct(e, t0, Z, z_off, m_single, Y, y_out, I, s, false, &t1);
+        if (*rc != DS_OK) return -1.f;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 2; ++r) engine_launch_direct(e, t0, Z, z_off, m_single, Y, y_out, I, s, false, &t1);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                *rc = DS_E_CUDA;
+                set_error("autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                return -1.f;
             }
+            float one = 0;
+            cudaEventElapsedTime(&one, e0, e1);
+            ms = std::min(ms, one / 2);
+        }
+        return ms;
+    };
+    // phase 0: one configuration for every launch; 1: the direct launch; 2: the learned one
+    ds_tune_t best[2];
+    memset(best, 0, sizeof(best));
+    float best_ms = 1e30f;
+    ds_status rc = DS_OK;
+    const int phases = e->split > 0 ? 3 : 1;
+    for (int phase = 0; phase < phases && rc == DS_OK; ++phase) {
+        for (int b : blocks)
+            for (int it : items)
+                for (int sm : smems) {
+                    if (rc != DS_OK) break;
+                    if (sm > e->props.max_smem_optin - 2048) continue;
+                    if (b == 1024 && (it != 1 || sm < 0 || !direct_only(e))) continue;  // runs as 512
+                    ds_tune_t t;
+                    memset(&t, 0, sizeof(t));
+                    t.block = b;
+                    t.items = it;
+                    t.smem_limit = sm;
+                    const ds_tune_t t0 = phase == 2 ? best[0] : t, t1 = phase == 1 ? best[1] : t;
+                    int grid = 0;
+                    if (occupancy(e, t0, interp, true, &grid) != DS_OK) continue;
+                    if (e->split > 0 && occupancy(e, t1, interp, true, &grid, 1) != DS_OK) continue;
+                    const float ms = time_of(t0, t1, &rc);
+                    if (rc == DS_OK && ms < best_ms) {
+                        best_ms = ms;
+                        best[0] = t0;
+                        best[1] = t1;
+                    }
+                }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != DS_OK) return rc;
-    e->tune = best;
-    if (best_out) *best_out = best;
+    best[0].ms = best[1].ms = best_ms;
+    e->tune = best[0];
+    e->tune2 = best[1];
+    if (best_out) *best_out = best[0];
     return DS_OK;
 }
 
@@ -835,6 +867,7 @@ ds_status ds_batch_build(const void *Xcat_dev, const int64_t *x_off_dev, int32_t
     }
     b->eng.tune = ds::default_tune();
     if (flags & DS_NO_SMEM) b->eng.tune.smem_limit = 0;
+    b->eng.tune2 = b->eng.tune;
     b->eng.build_ms = ds::now_ms() - t0;
     *out = b;
     return DS_OK;

@@ -42,6 +42,8 @@ struct Engine {
     cudaStream_t gstream = nullptr;
     const void *gkey[6] = {};
     ds_tune_t gtune = {};
+    ds_tune_t tune2 = {};   // a split handle's learned launch (tune: its direct launch, or the only one)
+    ds_tune_t gtune2 = {};
     long long h_updates = 0;
     unsigned long long R_total = 0;
     int n_direct = 0, n_learned = 0, n_fallback = 0;
@@ -64,10 +66,11 @@ ds_status engine_build(Engine *e, const void *Xcat, const void *Ycat, const long
 // Interpolation: y_out non-null; the knot values come from the stored
 // intervals (Y nullptr) or from the caller's Y.
 // host_io: Z, I and y_out are host memory mapped into the device (no bulk L2
-// prefetch of the query stream).
+// prefetch of the query stream).  t configures the launch (a split handle's
+// direct launch), t2 a split handle's learned launch (nullptr: t as well).
 ds_status engine_launch_direct(const Engine *e, const ds_tune_t &t, const void *Z, const long long *z_off,
                                long long m_single, const void *Y, void *y_out, int32_t *I, cudaStream_t s,
-                               bool host_io = false);
+                               bool host_io = false, const ds_tune_t *t2 = nullptr);
 ds_status engine_launch(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,
                         void *y_out, int32_t *I, cudaStream_t s);
 ds_status engine_autotune(Engine *e, const void *Z, const long long *z_off, long long m_single, const void *Y,

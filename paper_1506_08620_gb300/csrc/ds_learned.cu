@@ -1260,6 +1260,7 @@ ds_status ds_learned_build_xy(const void *Xcat_dev, const void *Ycat_dev, const 
         return rc;
     }
     L->eng.tune = ds::default_tune();
+    L->eng.tune2 = L->eng.tune;
     L->eng.build_ms = ds::now_ms() - t0;
     *out = L;
     return DS_OK;
@@ -1441,7 +1442,7 @@ ds_status ds_learned_search_host(ds_learned *L, const void *Zcat_host, const int
     if (rc == DS_OK && y_out_host) rc = host_mapped(y_out_host, (size_t)m * esz, &yd, &ry);
     if (rc == DS_OK)
         rc = ds::engine_launch_direct(&e, e.tune, zd, z_off_host ? L->zoff_dev : nullptr, z_off_host ? 0 : m, nullptr,
-                                      yd, (int32_t *)id, s, true);
+                                      yd, (int32_t *)id, s, true, &e.tune2);
     const cudaError_t ce = cudaStreamSynchronize(s);
     if (rc == DS_OK && ce != cudaSuccess) {
         ds::set_error("ds_learned_search_host: %s", cudaGetErrorString(ce));

@@ -129,11 +129,12 @@ __host__ __device__ __forceinline__ long long chunk_len(const ArrDesc &d, long l
 // Chunk offsets from the query offsets, in claim order; resets the chunk
 // counters: counter[0] = 0, and counter[1] = the first chunk of claim
 // position `split` (the second launch's first chunk when the arrays are
-// served by two launches, positions [0, split) and [split, n_arrays)).  One
-// block.
+// served by two launches, positions [0, split) and [split, n_arrays); the
+// second launch's positions have their own chunk base and staging limit,
+// chunk1 and smem_limit1).  One block.
 __global__ void k_plan_chunks(const long long *z_off, long long m_single, int n_arrays, long long chunk,
                               const ArrDesc *desc, const int *order, uint32_t smem_limit, long long *chunk_off,
-                              unsigned long long *counter, int split);
+                              unsigned long long *counter, int split, long long chunk1, uint32_t smem_limit1);
 
 __device__ __forceinline__ long long q_begin(const long long *z_off, int a) { return z_off ? z_off[a] : 0; }
 
