@@ -351,7 +351,7 @@ static ds_status build_engine_typed(Engine *e, const T *Xcat, const T *Ycat, con
             if (e->desc_host[a].mode == MODE_DIRECT && e->desc_host[a].R > FASTF_MAX_R) e->fast_cells = false;
         // direct and learned arrays (and no bisected ones): each group gets its
         // own launch of a kernel kind that holds only its path (fewer registers
-        // than the mixed kind), the direct arrays first in the claim order
+        // than one kind holding both), the direct arrays first in the claim order
         if (e->n_direct > 0 && e->n_learned > 0 && e->n_fallback == 0) {
             e->order_host.resize((size_t)A);
             for (int a = 0; a < A; ++a) e->order_host[(size_t)a] = a;
@@ -529,7 +529,7 @@ static const void *pick1(int vpt, bool interp, bool vec, bool warps, bool big, i
     }
 }
 // every array in direct mode, searched on its rank table with the knots alone
-// (the direct kinds read knot t at X[t]; pairs take the mixed kind)
+// (the direct kinds but KIND_DIRECT_XY read knot t at X[t])
 static bool direct_only(const Engine *e) { return e->n_learned == 0 && e->n_fallback == 0 && !e->xy; }
 // the direct kind for a handle's direct arrays
 static int direct_kind_of(const Engine *e)
