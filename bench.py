@@ -79,11 +79,19 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_of(text):
+    """The source without its comments and blank space (a comment edit leaves a capture valid)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def source_hash(kernel_key):
     family = kernel_key.split("_")[0]
     h = hashlib.sha256()
     for f in KERNEL_SOURCES.get(family, KERNEL_SOURCES["search"]):
-        h.update(open(os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", f), "rb").read())
+        h.update(_code_of(open(os.path.join(ROOT, "paper_1506_08620_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -82,3 +82,9 @@ def test_every_workload_names_its_configuration(workload):
     cfg = bench.workload_config(_args(workload=workload))
     assert cfg["workload"] and "queries" in cfg and "step" in cfg and "l2" in cfg
     assert bench.kernel_key_of(_args(workload=workload))
+
+
+def test_a_comment_edit_keeps_a_capture_valid():
+    code = bench._code_of("int a = 1;  // the first\n/* a block\n comment */\nint b;\n")
+    assert code == bench._code_of("int a = 1; // reworded\nint b;")
+    assert code != bench._code_of("int a = 2;\nint b;")
