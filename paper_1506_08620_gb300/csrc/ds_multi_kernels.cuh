@@ -432,10 +432,11 @@ __device__ __forceinline__ void chunk_range(const BatchArgs<T> &a, const ArrDesc
 // direct kinds at one vector per thread, which fit 64 registers).  No kind
 // gives a minimum of resident blocks: an explicit 1 lets the compiler spend
 // up to 128 registers (the direct kind then took 72 instead of 64, one
-// 512-thread block per SM instead of two; workload 3: 492 -> 430 G
-// lookups/s), and a minimum of 2 at 512 threads (64 registers, with spills)
-// measured no better for the kinds of workload 5 (79.1 without it, 77.8 with
-// it on the learned kind, 77.9 on the direct kind over pairs).
+// 512-thread block per SM instead of two; 4096 float32 arrays, 2^28 queries:
+// 492 -> 430 G lookups/s), and a minimum of 2 at 512 threads (64 registers,
+// with spills) measured no better for the kinds that serve 256 float32 arrays
+// with the interpolation (79.1 without it, 77.8 with it on the learned kind,
+// 77.9 on the direct kind over pairs).
 template <typename T, int VPT, bool INTERP, bool VEC, int KIND, bool WARPS = false, int MAXB = 512>
 __global__ void __launch_bounds__(MAXB) k_batch_search(BatchArgs<T> a)
 {
