@@ -441,3 +441,31 @@ def test_learned_set_tune_every_configuration_exact(ds):
     with pytest.raises(ds.DsError):
         ds.ds_learned_set_tune(L, 256, 1, -2)
     L.free()
+
+
+def test_split_handle_every_configuration_exact(ds):
+    # a handle with direct and learned arrays searches each group with its own
+    # launch: every configuration, set for both launches, and the autotuner's
+    # own pair of configurations, stay exact, with and without the interpolation
+    w5 = W.workload5(n_arrays=20, size_lo=1 << 10, size_hi=1 << 15, total_queries=1 << 19)
+    Xcat, Ycat, x_off, Zcat, z_off = w5["Xcat"], w5["Ycat"], w5["x_off"], w5["Zcat"], w5["z_off"]
+    L = ds.ds_learned_build_xy(_cuda(Xcat), _cuda(Ycat), _cuda(x_off), cfg=_cfg(ds, steps=50))
+    info = L.info()
+    assert info["n_direct"] > 0 and info["n_learned"] > 0 and info["search_launches"] == 3
+    Iref, yref = oracle.interp_batch(Xcat, Ycat, x_off, Zcat, z_off)
+    arr = np.searchsorted(z_off, np.arange(Zcat.size), side="right") - 1
+    gi = x_off[arr] + Iref
+    Zd, zod = _cuda(Zcat), _cuda(z_off)
+    y = torch.empty(Zcat.size, dtype=torch.float32, device="cuda")
+    for block, items, smem in ((512, 1, 0), (256, 2, -1), (128, 4, 48 * 1024), (1024, 1, 96 * 1024)):
+        ds.ds_learned_set_tune(L, block, items, smem)
+        I, _ = L.search(Zd, zod, y_out=y)
+        assert np.array_equal(I.cpu().numpy(), Iref), (block, items, smem)
+        assert np.all(_interp_tol(y.cpu().numpy(), yref, Ycat[gi], Ycat[gi + 1])), (block, items, smem)
+        assert np.array_equal(L.search(Zd, zod).cpu().numpy(), Iref), (block, items, smem)
+    tune = ds.ds_learned_autotune(L, Zd, zod, y_out=y)
+    assert tune["ms"] > 0
+    I, _ = L.search(Zd, zod, y_out=y)
+    assert np.array_equal(I.cpu().numpy(), Iref)
+    assert np.all(_interp_tol(y.cpu().numpy(), yref, Ycat[gi], Ycat[gi + 1]))
+    L.free()
